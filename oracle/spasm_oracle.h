@@ -1,0 +1,88 @@
+/*
+ * FP64 CPU oracle for the SPaSM hot path (test infrastructure only).
+ *
+ * This is a plain, slow restatement of what the paper's method computes, used by the
+ * tests, by smoke() and by the CPU-baseline leg of the benchmark to check the CUDA
+ * path.  It shares no code with the CUDA library.  It must never be called by the
+ * product path.
+ *
+ * Every quantity is double precision.  Arrays are row-major.
+ *
+ *   Stage 1 particle  x[B][4]  = (x, y, z, yaw) of the block at each stack position.
+ *   Stage 2 particle  q[C][7]  joint configurations, C = 2B(W-1)+1, q[0] = q_home.
+ */
+#ifndef SPASM_ORACLE_H
+#define SPASM_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct {
+    /* robot: 7 modified-DH rows (a, alpha, d, theta_offset), limits, spheres, tool */
+    const double *dh;          /* 7 x 4 */
+    const double *qlim;        /* 7 x 2 */
+    int n_spheres;
+    const int32_t *sphere_link;/* n_spheres, 0 = base */
+    const double *sphere;      /* n_spheres x 4 (x, y, z, r) in the link frame */
+    const double *ee;          /* 4 x 4 flange -> tool point */
+    const double *q_home;      /* 7 */
+    /* environment */
+    int n_cub;
+    const double *cub;         /* n_cub x 15: centre 3, R 9 (row-major), half 3 */
+    int n_sph;
+    const double *sph;         /* n_sph x 4 */
+    /* goal / skeleton, in stack order (bottom to top) */
+    int B;
+    const double *half;        /* B x 3 */
+    const double *init;        /* B x 4 */
+    const double *box;         /* 6: lo xyz, hi xyz */
+    double z_table, grasp_off;
+    /* parameters */
+    int N, M, P, Q, W, K_lin, K_quad, K_traj, K_al, K_ik;
+    double eta_init, alpha, eta_traj, eps, eps_start;
+    double w_stable, w_height, w_coll, w_start, w_arm, w_block, w_path, w_jl;
+    double mu0, mu_max, ik_damp;
+    uint64_t seed;
+    int max_steps;
+    int n_threads;
+} or_problem;
+
+/* constraint groups of the stage-2 augmented Lagrangian */
+enum { OR_G_START = 0, OR_G_ARM, OR_G_BLOCK, OR_G_COLL, OR_G_STABLE, OR_G_HEIGHT, OR_NG };
+
+void   or_philox4x32_10(const uint32_t ctr[4], uint64_t seed, uint32_t out[4]);
+double or_u01(uint32_t u);
+
+void   or_fk(const or_problem *pr, const double q[7], double frames[8][16], double tee[16]);
+double or_box_sd(const double c[3], double r, const double *cub, double dsd_dc[3]);
+double or_pen_box(const double c[3], double r, const double centre[3], const double R[9],
+                  const double half[3], double dpen_dc[3], double dpen_dp[3]);
+double or_pen_sph(const double c[3], double r, const double *sph, double dpen_dc[3]);
+
+/* stage 1 (Alg. 1 and the tower placement cost of the appendix) */
+double or_place_cost(const or_problem *pr, const double *x, int quad, double *grad, double terms[3]);
+int    or_place_check(const or_problem *pr, const double *x, double metrics[3]);
+void   or_place_sample(const or_problem *pr, int n, uint32_t attempt, double *x);
+void   or_argsort(int n, const double *cost, int32_t *idx);
+void   or_place_descend(const or_problem *pr, int m, double *x, int k_lin, int k_quad);
+int    or_place_solve(const or_problem *pr, double *out, int *n_found, int *attempts, int *steps);
+
+/* stage 2 (trajectory optimisation of Sec. III-B and the appendix) */
+int    or_n_configs(const or_problem *pr);
+void   or_ik(const or_problem *pr, const double target[16], const double q0[7], double q[7]);
+void   or_lift(const or_problem *pr, const double *place, int particle, uint32_t attempt, double *q);
+int    or_n_residuals(const or_problem *pr);
+double or_traj_cost(const or_problem *pr, const double *q, const double *lam, double mu,
+                    double *grad, double c_groups[OR_NG], double *path, double *jl, double *h);
+int    or_traj_check(const or_problem *pr, const double *q, double metrics[6]);
+double or_traj_rank_cost(const or_problem *pr, const double *q);
+void   or_traj_descend(const or_problem *pr, int n, double *q, double *lam, double *mu, int k_steps);
+int    or_traj_solve(const or_problem *pr, const double *place, int n_place, double *out_q,
+                     double *out_cost, int *n_found, int *attempts);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
