@@ -1,0 +1,183 @@
+/*
+ * SPaSM hot path on one GPU: C ABI.
+ *
+ * Sequential pick-and-place with a fixed action skeleton (Sec. III of the paper: known
+ * object geometry and initial poses, environment obstacles, a given order of pick-and-
+ * place actions), solved in two stages:
+ *   stage 1  object-placement CSP by particle optimisation (Alg. 1),
+ *   stage 2  lift to joint space and trajectory optimisation of all waypoints and
+ *            placements (Sec. III-B; cost terms of the appendix, tower stacking).
+ *
+ * Conventions for every entry point:
+ *   - Returns SPASM_OK or a negative spasm_status; on error, spasm_last_error() gives a
+ *     thread-local message.  No C++ exception crosses this boundary.
+ *   - "host" pointers are CPU memory owned by the caller; "device" pointers are CUDA
+ *     device memory owned by the caller, on the device current when the problem was
+ *     created.  The library copies every input array given to spasm_create_problem;
+ *     the caller keeps ownership of all pointers it passes.
+ *   - Work is enqueued on the problem's CUDA stream (set at creation) and is
+ *     asynchronous unless the function says it synchronises.
+ *   - Calls on one problem handle are not thread-safe; distinct handles are.
+ *   - Device errors (a bounded wait that gave up, a size outside the compiled limits)
+ *     are recorded in a per-problem error word and reported as SPASM_ERR_DEVICE by the
+ *     next synchronising call.
+ *
+ * Layouts (row-major, float32 on the device):
+ *   stage-1 particles  x[4B][n]   (structure of arrays: row 4i+k, k = x, y, z, yaw of the
+ *                                  block at stack position i; column = particle)
+ *   stage-2 particles  q[n][C][8] (C = 2B(W-1)+1 configurations, 7 joints + 1 pad;
+ *                                  q[.][0] = q_home)
+ *   placements         [P][B][4]  (x, y, z, yaw per block, stack order)
+ */
+#ifndef SPASM_H
+#define SPASM_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct spasm_problem* spasm_problem_t;
+
+typedef enum {
+    SPASM_OK = 0,
+    SPASM_ERR_INVALID = -1,     /* bad argument, size beyond the compiled limits */
+    SPASM_ERR_NOMEM = -2,       /* device allocation failed */
+    SPASM_ERR_CUDA = -3,        /* a CUDA runtime call failed */
+    SPASM_ERR_NOSOLUTION = -4,  /* no satisfying particle within max_steps (Sec. IV-C cap) */
+    SPASM_ERR_TIMEOUT = -5,     /* reserved for bounded host waits */
+    SPASM_ERR_DEVICE = -6       /* a kernel recorded an error (see spasm_last_error) */
+} spasm_status;
+
+/* Robot (Sec. III: the manipulator as a collection of spheres; fk of a 7-R arm, appendix).
+ * dh: 7 x 4 modified-DH rows (a, alpha, d, theta_offset), joint k transform
+ *     Rot_x(alpha) Trans_x(a) Rot_z(theta_offset + q_k) Trans_z(d);
+ * qlim: 7 x 2 (lower, upper); sphere: n_spheres x 4 (x, y, z, r) in the frame of link
+ * sphere_link[i] (0 = base, k = link k); ee: 4 x 4 flange -> tool transform; q_home: 7. */
+typedef struct {
+    int dof;                     /* must be 7 */
+    const double* dh;
+    const double* qlim;
+    int n_spheres;               /* <= 64 */
+    const int32_t* sphere_link;
+    const double* sphere;
+    const double* ee;
+    const double* q_home;
+} spasm_robot;
+
+/* Environment (Sec. III; Pen(.,.) of the appendix): cuboids n x 15 = centre (3), rotation
+ * (9, row-major), half extents (3); spheres n x 4 = centre (3), radius. */
+typedef struct {
+    int n_cuboids;               /* <= 256 */
+    const double* cuboid;
+    int n_spheres;               /* <= 64 */
+    const double* sphere;
+} spasm_obstacles;
+
+/* Goal and action skeleton (Sec. III; tower stacking, appendix).  Blocks are given in
+ * stack order (bottom first): block i is picked i-th and placed at stack position i.
+ * half_ext: B x 3; init_pose: B x 4 (x, y, z, yaw); goal_box: 6 = lo (3), hi (3) bounds
+ * of the placed block centres; z_table: table top height; grasp_off: tool standoff above
+ * a block's top face. */
+typedef struct {
+    int n_blocks;                /* 1..16 */
+    const double* half_ext;
+    const double* init_pose;
+    const double* goal_box;
+    double z_table;
+    double grasp_off;
+} spasm_goal;
+
+/* Solver parameters (Alg. 1 and Sec. III-B): N sample / M optimised particles, P
+ * returned solutions, Q trajectory particles, W waypoints per motion segment, step
+ * counts, learning rates, weights of the appendix cost terms, augmented-Lagrangian
+ * penalty schedule, IK iterations/damping, Philox seed, and the cap on total gradient
+ * steps (30 000 in the paper's experiments, Sec. IV-C). */
+typedef struct {
+    int N, M, P, Q, W;
+    int K_lin, K_quad, K_traj, K_al, K_ik;
+    double eta_init, alpha, eta_traj, eps, eps_start;
+    double w_stable, w_height, w_coll, w_start, w_arm, w_block, w_path, w_jl;
+    double mu0, mu_max, ik_damp;
+    uint64_t seed;
+    int max_steps;
+} spasm_params;
+
+/* Validate and copy the problem to the device and allocate its working memory.
+ * cuda_stream: a cudaStream_t (NULL = legacy default stream).  Limits: B <= 16, W >= 3,
+ * C <= 1024, N <= 32768, M <= 8192, P <= M, Q >= 1.  Synchronises once. */
+spasm_status spasm_create_problem(const spasm_robot* robot, const spasm_obstacles* obstacles, const spasm_goal* goal,
+                                  const spasm_params* params, void* cuda_stream, spasm_problem_t* out);
+spasm_status spasm_destroy_problem(spasm_problem_t problem);
+const char* spasm_last_error(void);
+
+/* Stage 1, Alg. 1 with re-initialisation until a satisfying particle exists or max_steps
+ * gradient steps are spent.  Synchronises once per attempt (reads the satisfying count).
+ * On success the best P placements stay on the device for stage 2. */
+spasm_status spasm_place(spasm_problem_t problem);
+
+/* Stage 2: lift the stage-1 placements to Q trajectory particles, optimise, keep the
+ * satisfying ones (re-lifting with the next Philox attempt if none, within max_steps),
+ * FP64-check the best P.  Runs stage 1 first if it has not run.  Synchronises once per
+ * attempt. */
+spasm_status spasm_optimize(spasm_problem_t problem);
+
+/* Copy results to host memory (synchronises).  Any output pointer may be NULL.
+ * n_found: number of returned solutions (<= P); placements: P x B x 4;
+ * traj: P x C x 7; cost: P (ranking cost); success: P (1 if the FP64 check passed).
+ * Returns SPASM_ERR_NOSOLUTION if stage 2 found nothing. */
+spasm_status spasm_result(spasm_problem_t problem, int* n_found, double* placements, double* traj, double* cost,
+                          int* success);
+
+/* Sizes of this problem: configurations C per trajectory particle and residuals NR of the
+ * augmented Lagrangian (9B + 3). */
+spasm_status spasm_sizes(spasm_problem_t problem, int* C, int* NR);
+
+/* ---- kernel-level entry points (device pointers; used by parity tests and autograd) ---- */
+
+/* Alg. 1 SampleUniform + Cost: n particles from Philox counter (block, particle, 0,
+ * attempt); x (device, 4B x n SoA, written), cost (device, n, linear form). */
+spasm_status spasm_place_sample(spasm_problem_t problem, int n, uint32_t attempt, float* x, float* cost);
+
+/* Placement cost of n particles (linear form, or quadratic when quadratic != 0) and its
+ * gradient.  x: device 4B x n; cost: device n; grad: device 4B x n or NULL; metrics:
+ * device n x 3 (largest penetration, CoM distance, height error) or NULL; terms: device
+ * n x 3 (C_stable, C_height, C_coll) or NULL. */
+spasm_status spasm_place_eval(spasm_problem_t problem, int n, const float* x, int quadratic, float* cost, float* grad,
+                              float* metrics, float* terms);
+
+/* Alg. 1 descent on n particles in place (device x, 4B x n): k_lin linear steps with
+ * eta_init (1 - k/k_lin), k_quad quadratic steps with alpha, box projection after each.
+ * cost: device n (final quadratic cost) or NULL; sat: device n (GetSatisfyingParticles)
+ * or NULL. */
+spasm_status spasm_place_descend(spasm_problem_t problem, int n, float* x, int k_lin, int k_quad, float* cost,
+                                 int* sat);
+
+/* ArgSort(cost)[:k]: the k smallest of n costs by (cost, index); NaN last.  cost: device n;
+ * idx: device k (written); n <= 32768, k <= 8192. */
+spasm_status spasm_select_topk(spasm_problem_t problem, int n, const float* cost, int k, int* idx);
+
+/* Lift (Sec. III-B): n trajectory particles from placements (device, n_place x B x 4):
+ * particle p uses placement p mod n_place; IK at each grasp and placement, one
+ * intermediate waypoint per segment, linear interpolation.  q: device n x C x 8. */
+spasm_status spasm_lift(spasm_problem_t problem, int n, const float* placements, int n_place, uint32_t attempt,
+                        float* q);
+
+/* Augmented-Lagrangian objective of n trajectory particles and its gradient.
+ * q: device n x C x 8; lam: device n x NR or NULL (zeros); mu: device n or NULL (mu0);
+ * L: device n; grad: device n x C x 8 or NULL; groups: device n x 6 (C_start, C_arm,
+ * C_block, C_coll, C_stable, C_height) or NULL; h: device n x NR residuals or NULL. */
+spasm_status spasm_traj_eval(spasm_problem_t problem, int n, const float* q, const float* lam, const float* mu,
+                             float* L, float* grad, float* groups, float* h);
+
+/* k_steps of gradient descent with eta_traj (1 - k/k_steps) inside the augmented
+ * Lagrangian (multiplier update every K_al steps), in place on q (device n x C x 8);
+ * lam (n x NR) and mu (n) are read and written; when init_multipliers != 0 they start at
+ * 0 and mu0.  metrics: device n x 8 or NULL; sat: device n or NULL (final check). */
+spasm_status spasm_traj_descend(spasm_problem_t problem, int n, float* q, float* lam, float* mu, int k_steps,
+                                int init_multipliers, float* metrics, int* sat);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,455 @@
+// C ABI of the SPaSM hot path (see include/spasm.h): problem set-up, the two-stage
+// driver, and kernel-level entry points.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/spasm.h"
+#include "launch_s2.h"
+#include "stage2.cuh"
+
+using namespace spasm;
+
+static thread_local std::string g_last_error;
+
+static spasm_status fail(spasm_status st, const std::string& msg) {
+    g_last_error = msg;
+    return st;
+}
+
+#define SPASM_CUDA(call)                                                                              \
+    do {                                                                                              \
+        cudaError_t e_ = (call);                                                                      \
+        if (e_ != cudaSuccess)                                                                        \
+            return fail(SPASM_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));          \
+    } while (0)
+
+struct spasm_problem {
+    Scalars sc;
+    spasm_params prm;
+    cudaStream_t stream = nullptr;
+    DevTables tab{};
+    float4* d_cub = nullptr;
+    float4* d_osph = nullptr;
+    int* d_err = nullptr;
+    // stage 1
+    float *d_xs = nullptr, *d_cost = nullptr, *d_xm = nullptr, *d_costm = nullptr, *d_masked = nullptr;
+    int *d_idx = nullptr, *d_sat = nullptr, *d_nsat = nullptr, *d_best = nullptr;
+    float* d_place = nullptr;   // P x B x 4
+    int* d_nplace = nullptr;
+    bool placed = false;
+    int n_place = 0, place_attempts = 0, place_steps = 0;
+    // stage 2
+    float *d_q = nullptr, *d_lam = nullptr, *d_mu = nullptr, *d_metrics = nullptr, *d_tmasked = nullptr;
+    int *d_tsat = nullptr, *d_tnsat = nullptr, *d_tbest = nullptr;
+    float *d_rq = nullptr, *d_rcost = nullptr;   // returned solutions
+    int* d_rsucc = nullptr;
+    int* d_user_np = nullptr;   // placement count of a user-driven lift
+    int h_user_np = 0;
+    bool optimized = false;
+    int n_found = 0, traj_attempts = 0;
+    std::vector<double> host_cub, host_osph;
+};
+
+template <typename T>
+static spasm_status dalloc(T** p, size_t count) {
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T));
+    if (e != cudaSuccess) return fail(SPASM_ERR_NOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    return SPASM_OK;
+}
+
+#define SPASM_TRY(x)                      \
+    do {                                  \
+        spasm_status s_ = (x);            \
+        if (s_ != SPASM_OK) return s_;    \
+    } while (0)
+
+static spasm_status check_device_error(spasm_problem* pr) {
+    int err = 0;
+    SPASM_CUDA(cudaMemcpyAsync(&err, pr->d_err, sizeof(int), cudaMemcpyDeviceToHost, pr->stream));
+    SPASM_CUDA(cudaStreamSynchronize(pr->stream));
+    if (err != 0) {
+        const char* what = err == kDevTimeout ? "a bounded device wait gave up" : "a kernel rejected its sizes";
+        return fail(SPASM_ERR_DEVICE, std::string("device error ") + std::to_string(err) + ": " + what);
+    }
+    return SPASM_OK;
+}
+
+static void free_all(spasm_problem* pr) {
+    void* ptrs[] = {pr->d_cub, pr->d_osph, pr->d_err, pr->d_xs, pr->d_cost, pr->d_xm, pr->d_costm, pr->d_masked,
+                    pr->d_idx, pr->d_sat, pr->d_nsat, pr->d_best, pr->d_place, pr->d_nplace, pr->d_q, pr->d_lam,
+                    pr->d_mu, pr->d_metrics, pr->d_tmasked, pr->d_tsat, pr->d_tnsat, pr->d_tbest, pr->d_rq,
+                    pr->d_rcost, pr->d_rsucc, pr->d_user_np};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+}
+
+extern "C" const char* spasm_last_error(void) { return g_last_error.c_str(); }
+
+extern "C" spasm_status spasm_create_problem(const spasm_robot* robot, const spasm_obstacles* obs,
+                                             const spasm_goal* goal, const spasm_params* prm, void* cuda_stream,
+                                             spasm_problem_t* out) {
+    if (!robot || !obs || !goal || !prm || !out) return fail(SPASM_ERR_INVALID, "null argument");
+    *out = nullptr;
+    if (robot->dof != 7) return fail(SPASM_ERR_INVALID, "dof must be 7");
+    if (robot->n_spheres < 1 || robot->n_spheres > kMaxRobotSpheres)
+        return fail(SPASM_ERR_INVALID, "robot sphere count outside 1..64");
+    if (obs->n_cuboids < 0 || obs->n_cuboids > kMaxCub) return fail(SPASM_ERR_INVALID, "cuboid count outside 0..256");
+    if (obs->n_spheres < 0 || obs->n_spheres > kMaxOSph) return fail(SPASM_ERR_INVALID, "obstacle sphere count outside 0..64");
+    const int B = goal->n_blocks;
+    if (B < 1 || B > kMaxB) return fail(SPASM_ERR_INVALID, "n_blocks outside 1..16");
+    if (prm->W < 3) return fail(SPASM_ERR_INVALID, "W must be >= 3");
+    const int S = prm->W - 1, C = 2 * B * S + 1;
+    if (C > kMaxC) return fail(SPASM_ERR_INVALID, "too many configurations (2B(W-1)+1 > 1024)");
+    if (prm->N < 1 || prm->N > 32768 || prm->M < 1 || prm->M > 8192 || prm->M > prm->N)
+        return fail(SPASM_ERR_INVALID, "need 1 <= M <= N, N <= 32768, M <= 8192");
+    if (prm->P < 1 || prm->P > prm->M || prm->Q < 1 || prm->Q > 1 << 20)
+        return fail(SPASM_ERR_INVALID, "need 1 <= P <= M and 1 <= Q");
+    if (prm->K_lin < 1 || prm->K_quad < 0 || prm->K_traj < 1 || prm->K_ik < 0)
+        return fail(SPASM_ERR_INVALID, "step counts must be positive");
+    for (int i = 0; i < robot->n_spheres; ++i)
+        if (robot->sphere_link[i] < 0 || robot->sphere_link[i] > 7) return fail(SPASM_ERR_INVALID, "sphere_link outside 0..7");
+
+    spasm_problem* pr = new spasm_problem();
+    pr->prm = *prm;
+    pr->stream = static_cast<cudaStream_t>(cuda_stream);
+    Scalars& sc = pr->sc;
+    std::memset(&sc, 0, sizeof sc);
+    sc.B = B; sc.S = S; sc.C = C; sc.NR = 9 * B + 3;
+    sc.n_rsph = robot->n_spheres; sc.n_cub = obs->n_cuboids; sc.n_osph = obs->n_spheres;
+    sc.K_lin = prm->K_lin; sc.K_quad = prm->K_quad; sc.K_traj = prm->K_traj; sc.K_al = prm->K_al; sc.K_ik = prm->K_ik;
+    sc.N = prm->N; sc.M = prm->M; sc.P = prm->P; sc.Q = prm->Q;
+    for (int k = 0; k < 7; ++k) {
+        const double* row = robot->dh + 4 * k;
+        sc.a[k] = (float)row[0];
+        sc.ca[k] = (float)std::cos(row[1]);
+        sc.sa[k] = (float)std::sin(row[1]);
+        sc.d[k] = (float)row[2];
+        sc.th0[k] = (float)row[3];
+        sc.qlo[k] = (float)robot->qlim[2 * k];
+        sc.qhi[k] = (float)robot->qlim[2 * k + 1];
+        sc.q_home[k] = (float)robot->q_home[k];
+    }
+    for (int i = 0; i < 3; ++i) {
+        for (int j = 0; j < 3; ++j) sc.ee_R[3 * i + j] = (float)robot->ee[4 * i + j];
+        sc.ee_p[i] = (float)robot->ee[4 * i + 3];
+    }
+    for (int i = 0; i < robot->n_spheres; ++i) {
+        const double* s = robot->sphere + 4 * i;
+        sc.rsph[i] = make_float4((float)s[0], (float)s[1], (float)s[2], (float)s[3]);
+        sc.rlink[i] = robot->sphere_link[i];
+    }
+    double z = goal->z_table;
+    for (int i = 0; i < B; ++i) {
+        const double* h = goal->half_ext + 3 * i;
+        const double* p = goal->init_pose + 4 * i;
+        double hm = std::fmin(h[0], std::fmin(h[1], h[2]));
+        sc.half[i] = make_float4((float)h[0], (float)h[1], (float)h[2], (float)(0.5 * hm));
+        sc.init[i] = make_float4((float)p[0], (float)p[1], (float)p[2], (float)p[3]);
+        sc.zt[i] = (float)(z + h[2]);
+        z += 2.0 * h[2];
+        sc.zlo[i] = (float)std::fmax(goal->goal_box[2], goal->z_table + h[2]);
+    }
+    for (int k = 0; k < 3; ++k) { sc.box_lo[k] = (float)goal->goal_box[k]; sc.box_hi[k] = (float)goal->goal_box[3 + k]; }
+    sc.z_table = (float)goal->z_table;
+    sc.grasp_off = (float)goal->grasp_off;
+    sc.eta_init = (float)prm->eta_init; sc.alpha = (float)prm->alpha; sc.eta_traj = (float)prm->eta_traj;
+    sc.eps = (float)prm->eps; sc.eps_start = (float)prm->eps_start;
+    sc.w_stable = (float)prm->w_stable; sc.w_height = (float)prm->w_height; sc.w_coll = (float)prm->w_coll;
+    sc.w_start = (float)prm->w_start; sc.w_arm = (float)prm->w_arm; sc.w_block = (float)prm->w_block;
+    sc.w_path = (float)prm->w_path; sc.w_jl = (float)prm->w_jl;
+    sc.mu0 = (float)prm->mu0; sc.mu_max = (float)prm->mu_max; sc.ik_damp = (float)prm->ik_damp;
+    sc.seed = prm->seed;
+
+    // environment tables: cuboid = centre (+ bounding radius), then columns of R with half extents
+    std::vector<float4> cub(4 * (size_t)sc.n_cub);
+    for (int o = 0; o < sc.n_cub; ++o) {
+        const double* c = obs->cuboid + 15 * o;
+        const double *R = c + 3, *h = c + 12;
+        const double rad = std::sqrt(h[0] * h[0] + h[1] * h[1] + h[2] * h[2]);
+        cub[4 * o] = make_float4((float)c[0], (float)c[1], (float)c[2], (float)rad);
+        for (int k = 0; k < 3; ++k) cub[4 * o + 1 + k] = make_float4((float)R[k], (float)R[3 + k], (float)R[6 + k], (float)h[k]);
+    }
+    std::vector<float4> osph((size_t)sc.n_osph);
+    for (int o = 0; o < sc.n_osph; ++o) {
+        const double* s = obs->sphere + 4 * o;
+        osph[o] = make_float4((float)s[0], (float)s[1], (float)s[2], (float)s[3]);
+    }
+    pr->host_cub.assign(obs->cuboid, obs->cuboid + 15 * (size_t)sc.n_cub);
+    pr->host_osph.assign(obs->sphere, obs->sphere + 4 * (size_t)sc.n_osph);
+
+    const int N = prm->N, M = prm->M, P = prm->P, Q = prm->Q, NR = sc.NR;
+    spasm_status st = SPASM_OK;
+#define ALLOC(ptr, count) \
+    if (st == SPASM_OK) st = dalloc(&(ptr), (count))
+    ALLOC(pr->d_cub, cub.size());
+    ALLOC(pr->d_osph, osph.size());
+    ALLOC(pr->d_err, 1);
+    ALLOC(pr->d_xs, (size_t)4 * B * N);
+    ALLOC(pr->d_cost, N);
+    ALLOC(pr->d_idx, M);
+    ALLOC(pr->d_xm, (size_t)4 * B * M);
+    ALLOC(pr->d_costm, M);
+    ALLOC(pr->d_masked, M);
+    ALLOC(pr->d_sat, M);
+    ALLOC(pr->d_nsat, 1);
+    ALLOC(pr->d_best, P);
+    ALLOC(pr->d_place, (size_t)P * B * 4);
+    ALLOC(pr->d_nplace, 1);
+    ALLOC(pr->d_q, (size_t)Q * C * 8);
+    ALLOC(pr->d_lam, (size_t)Q * NR);
+    ALLOC(pr->d_mu, Q);
+    ALLOC(pr->d_metrics, (size_t)Q * 8);
+    ALLOC(pr->d_tmasked, Q);
+    ALLOC(pr->d_tsat, Q);
+    ALLOC(pr->d_tnsat, 1);
+    ALLOC(pr->d_tbest, P);
+    ALLOC(pr->d_rq, (size_t)P * C * 8);
+    ALLOC(pr->d_rcost, P);
+    ALLOC(pr->d_rsucc, P);
+    ALLOC(pr->d_user_np, 1);
+#undef ALLOC
+    if (st != SPASM_OK) { free_all(pr); delete pr; return st; }
+    pr->tab.cub = pr->d_cub;
+    pr->tab.osph = pr->d_osph;
+    cudaError_t e = cudaSuccess;
+    if (!cub.empty()) e = cudaMemcpyAsync(pr->d_cub, cub.data(), cub.size() * sizeof(float4), cudaMemcpyHostToDevice, pr->stream);
+    if (e == cudaSuccess && !osph.empty())
+        e = cudaMemcpyAsync(pr->d_osph, osph.data(), osph.size() * sizeof(float4), cudaMemcpyHostToDevice, pr->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(pr->d_err, 0, sizeof(int), pr->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(pr->stream);
+    if (e != cudaSuccess) {
+        free_all(pr);
+        delete pr;
+        return fail(SPASM_ERR_CUDA, std::string("create: ") + cudaGetErrorString(e));
+    }
+    const size_t need = traj_smem_bytes(sc);
+    int dev = 0, max_smem = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (max_smem > 0 && need > (size_t)max_smem) {
+        free_all(pr);
+        delete pr;
+        return fail(SPASM_ERR_INVALID, "problem too large for the per-CTA shared memory of the trajectory kernel");
+    }
+    *out = pr;
+    return SPASM_OK;
+}
+
+extern "C" spasm_status spasm_destroy_problem(spasm_problem_t pr) {
+    if (!pr) return SPASM_OK;
+    cudaStreamSynchronize(pr->stream);
+    free_all(pr);
+    delete pr;
+    return SPASM_OK;
+}
+
+extern "C" spasm_status spasm_sizes(spasm_problem_t pr, int* C, int* NR) {
+    if (!pr) return fail(SPASM_ERR_INVALID, "null problem");
+    if (C) *C = pr->sc.C;
+    if (NR) *NR = pr->sc.NR;
+    return SPASM_OK;
+}
+
+// ---------------------------------------------------------------------------------- stage 1
+// One attempt of Alg. 1 entirely on the device; the count of satisfying particles lands in
+// d_nsat and the best min(P, count) placements in d_place.
+static spasm_status place_attempt(spasm_problem* pr, uint32_t attempt) {
+    const Scalars& sc = pr->sc;
+    const int N = sc.N, M = sc.M, P = sc.P, B = sc.B;
+    cudaStream_t s = pr->stream;
+    SPASM_CUDA(launch_place_sample_cost(sc, pr->tab, N, attempt, pr->d_xs, pr->d_cost, pr->d_err, s));
+    SPASM_CUDA(launch_topk(pr->d_cost, N, M, pr->d_idx, nullptr, s));
+    SPASM_CUDA(launch_place_descend(sc, pr->tab, M, pr->d_xs, N, pr->d_idx, pr->d_xm, sc.K_lin, sc.K_quad,
+                                    pr->d_costm, pr->d_sat, nullptr, pr->d_err, s));
+    SPASM_CUDA(launch_mask_costs(pr->d_costm, pr->d_sat, M, pr->d_masked, pr->d_nsat, s));
+    SPASM_CUDA(launch_topk(pr->d_masked, M, P, pr->d_best, nullptr, s));
+    SPASM_CUDA(launch_gather_soa_to_aos(pr->d_xm, M, 4 * B, pr->d_best, P, pr->d_place, s));
+    return SPASM_OK;
+}
+
+extern "C" spasm_status spasm_place(spasm_problem_t pr) {
+    if (!pr) return fail(SPASM_ERR_INVALID, "null problem");
+    const int per = pr->sc.K_lin + pr->sc.K_quad;
+    int steps = 0, attempt = 0, found = 0;
+    while (steps < pr->prm.max_steps || attempt == 0) {
+        SPASM_TRY(place_attempt(pr, (uint32_t)attempt));
+        steps += per;
+        ++attempt;
+        int nsat = 0;
+        SPASM_CUDA(cudaMemcpyAsync(&nsat, pr->d_nsat, sizeof(int), cudaMemcpyDeviceToHost, pr->stream));
+        SPASM_CUDA(cudaStreamSynchronize(pr->stream));
+        if (nsat > 0) { found = nsat < pr->sc.P ? nsat : pr->sc.P; break; }
+    }
+    pr->place_attempts = attempt;
+    pr->place_steps = steps;
+    pr->n_place = found;
+    SPASM_CUDA(cudaMemcpyAsync(pr->d_nplace, &pr->n_place, sizeof(int), cudaMemcpyHostToDevice, pr->stream));
+    SPASM_TRY(check_device_error(pr));
+    pr->placed = true;
+    if (found == 0) return fail(SPASM_ERR_NOSOLUTION, "stage 1 found no satisfying placement within max_steps");
+    return SPASM_OK;
+}
+
+// ---------------------------------------------------------------------------------- stage 2
+static spasm_status traj_attempt(spasm_problem* pr, uint32_t attempt) {
+    const Scalars& sc = pr->sc;
+    cudaStream_t s = pr->stream;
+    SPASM_CUDA(launch_lift(sc, sc.Q, pr->d_place, pr->d_nplace, attempt, pr->d_q, s));
+    TrajIO io{};
+    io.q = pr->d_q; io.lam = pr->d_lam; io.mu = pr->d_mu; io.metrics = pr->d_metrics; io.sat = pr->d_tsat;
+    io.k_steps = sc.K_traj; io.init_multipliers = 1;
+    SPASM_CUDA(launch_traj(sc, pr->tab, sc.Q, kTrajModeDescend, io, pr->d_err, s));
+    return SPASM_OK;
+}
+
+__global__ static void k_rank_costs(const float* metrics, int n, float* out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = metrics[8 * (size_t)i + 7];
+}
+
+__global__ static void k_gather_solutions(const float* q, const float* metrics, const int* best, const int* nsat, int P,
+                                          int C, float* rq, float* rcost, int* rsucc) {
+    const int r = blockIdx.x;
+    const int n = min(*nsat, P);
+    if (r >= P) return;
+    if (r >= n) {
+        if (threadIdx.x == 0) { rcost[r] = 0.f; rsucc[r] = 0; }
+        return;
+    }
+    const int src = best[r];
+    for (int i = threadIdx.x; i < C * 8; i += blockDim.x) rq[(size_t)r * C * 8 + i] = q[(size_t)src * C * 8 + i];
+    if (threadIdx.x == 0) { rcost[r] = metrics[8 * (size_t)src + 7]; rsucc[r] = 1; }
+}
+
+extern "C" spasm_status spasm_optimize(spasm_problem_t pr) {
+    if (!pr) return fail(SPASM_ERR_INVALID, "null problem");
+    if (!pr->placed) {
+        spasm_status st = spasm_place(pr);
+        if (st != SPASM_OK) return st;
+    }
+    if (pr->n_place <= 0) return fail(SPASM_ERR_NOSOLUTION, "no placements to lift");
+    const Scalars& sc = pr->sc;
+    cudaStream_t s = pr->stream;
+    int steps = 0, attempt = 0, found = 0;
+    while (steps < pr->prm.max_steps || attempt == 0) {
+        SPASM_TRY(traj_attempt(pr, (uint32_t)attempt));
+        steps += sc.K_traj;
+        ++attempt;
+        k_rank_costs<<<(sc.Q + 255) / 256, 256, 0, s>>>(pr->d_metrics, sc.Q, pr->d_tmasked);
+        SPASM_CUDA(cudaGetLastError());
+        SPASM_CUDA(launch_mask_costs(pr->d_tmasked, pr->d_tsat, sc.Q, pr->d_tmasked, pr->d_tnsat, s));
+        int nsat = 0;
+        SPASM_CUDA(cudaMemcpyAsync(&nsat, pr->d_tnsat, sizeof(int), cudaMemcpyDeviceToHost, s));
+        SPASM_CUDA(cudaStreamSynchronize(s));
+        if (nsat > 0) { found = nsat < sc.P ? nsat : sc.P; break; }
+    }
+    pr->traj_attempts = attempt;
+    if (found > 0) {
+        if (sc.Q > 32768) return fail(SPASM_ERR_INVALID, "Q > 32768 unsupported by the selection kernel");
+        SPASM_CUDA(launch_topk(pr->d_tmasked, sc.Q, sc.P, pr->d_tbest, nullptr, s));
+        k_gather_solutions<<<sc.P, 256, 0, s>>>(pr->d_q, pr->d_metrics, pr->d_tbest, pr->d_tnsat, sc.P, sc.C, pr->d_rq,
+                                                 pr->d_rcost, pr->d_rsucc);
+        SPASM_CUDA(cudaGetLastError());
+    }
+    pr->n_found = found;
+    SPASM_TRY(check_device_error(pr));
+    pr->optimized = true;
+    if (found == 0) return fail(SPASM_ERR_NOSOLUTION, "stage 2 found no satisfying trajectory within max_steps");
+    return SPASM_OK;
+}
+
+extern "C" spasm_status spasm_result(spasm_problem_t pr, int* n_found, double* placements, double* traj, double* cost,
+                                     int* success) {
+    if (!pr) return fail(SPASM_ERR_INVALID, "null problem");
+    const Scalars& sc = pr->sc;
+    const int P = sc.P, B = sc.B, C = sc.C;
+    SPASM_CUDA(cudaStreamSynchronize(pr->stream));
+    if (n_found) *n_found = pr->optimized ? pr->n_found : 0;
+    if (placements) {
+        std::vector<float> tmp((size_t)P * B * 4, 0.f);
+        SPASM_CUDA(cudaMemcpy(tmp.data(), pr->d_place, tmp.size() * sizeof(float), cudaMemcpyDeviceToHost));
+        for (size_t i = 0; i < tmp.size(); ++i) placements[i] = tmp[i];
+    }
+    if (traj) {
+        std::vector<float> tmp((size_t)P * C * 8, 0.f);
+        SPASM_CUDA(cudaMemcpy(tmp.data(), pr->d_rq, tmp.size() * sizeof(float), cudaMemcpyDeviceToHost));
+        for (int r = 0; r < P; ++r)
+            for (int t = 0; t < C; ++t)
+                for (int j = 0; j < 7; ++j) traj[((size_t)r * C + t) * 7 + j] = tmp[((size_t)r * C + t) * 8 + j];
+    }
+    if (cost) {
+        std::vector<float> tmp(P, 0.f);
+        SPASM_CUDA(cudaMemcpy(tmp.data(), pr->d_rcost, P * sizeof(float), cudaMemcpyDeviceToHost));
+        for (int r = 0; r < P; ++r) cost[r] = tmp[r];
+    }
+    if (success) SPASM_CUDA(cudaMemcpy(success, pr->d_rsucc, P * sizeof(int), cudaMemcpyDeviceToHost));
+    if (!pr->optimized || pr->n_found == 0) return fail(SPASM_ERR_NOSOLUTION, "no solution");
+    return SPASM_OK;
+}
+
+// ---------------------------------------------------------------------------------- kernel level
+extern "C" spasm_status spasm_place_sample(spasm_problem_t pr, int n, uint32_t attempt, float* x, float* cost) {
+    if (!pr || n < 0 || (n > 0 && (!x || !cost))) return fail(SPASM_ERR_INVALID, "bad arguments");
+    SPASM_CUDA(launch_place_sample_cost(pr->sc, pr->tab, n, attempt, x, cost, pr->d_err, pr->stream));
+    return SPASM_OK;
+}
+
+extern "C" spasm_status spasm_place_eval(spasm_problem_t pr, int n, const float* x, int quadratic, float* cost,
+                                         float* grad, float* metrics, float* terms) {
+    if (!pr || n < 0 || (n > 0 && !x)) return fail(SPASM_ERR_INVALID, "bad arguments");
+    SPASM_CUDA(launch_place_eval(pr->sc, pr->tab, n, x, quadratic, cost, grad, metrics, terms, pr->d_err, pr->stream));
+    return SPASM_OK;
+}
+
+extern "C" spasm_status spasm_place_descend(spasm_problem_t pr, int n, float* x, int k_lin, int k_quad, float* cost,
+                                            int* sat) {
+    if (!pr || n < 0 || (n > 0 && !x) || k_lin < 1 || k_quad < 0) return fail(SPASM_ERR_INVALID, "bad arguments");
+    if (n == 0) return SPASM_OK;
+    // each warp reads its own particle's column before writing it back: in place is safe
+    SPASM_CUDA(launch_place_descend(pr->sc, pr->tab, n, x, n, nullptr, x, k_lin, k_quad, cost, sat, nullptr, pr->d_err,
+                                    pr->stream));
+    return SPASM_OK;
+}
+
+extern "C" spasm_status spasm_select_topk(spasm_problem_t pr, int n, const float* cost, int k, int* idx) {
+    if (!pr || n < 0 || k < 0 || n > 32768 || k > 8192 || (n > 0 && (!cost || !idx)))
+        return fail(SPASM_ERR_INVALID, "bad arguments (n <= 32768, k <= 8192)");
+    SPASM_CUDA(launch_topk(cost, n, k, idx, nullptr, pr->stream));
+    return SPASM_OK;
+}
+
+extern "C" spasm_status spasm_lift(spasm_problem_t pr, int n, const float* placements, int n_place, uint32_t attempt,
+                                   float* q) {
+    if (!pr || n < 0 || n_place < 1 || (n > 0 && (!placements || !q))) return fail(SPASM_ERR_INVALID, "bad arguments");
+    pr->h_user_np = n_place;
+    SPASM_CUDA(cudaMemcpyAsync(pr->d_user_np, &pr->h_user_np, sizeof(int), cudaMemcpyHostToDevice, pr->stream));
+    SPASM_CUDA(launch_lift(pr->sc, n, placements, pr->d_user_np, attempt, q, pr->stream));
+    return SPASM_OK;
+}
+
+extern "C" spasm_status spasm_traj_eval(spasm_problem_t pr, int n, const float* q, const float* lam, const float* mu,
+                                        float* L, float* grad, float* groups, float* h) {
+    if (!pr || n < 0 || (n > 0 && !q)) return fail(SPASM_ERR_INVALID, "bad arguments");
+    TrajIO io{};
+    io.q = const_cast<float*>(q);
+    io.lam = const_cast<float*>(lam);
+    io.mu = const_cast<float*>(mu);
+    io.L = L; io.grad = grad; io.groups = groups; io.h = h;
+    SPASM_CUDA(launch_traj(pr->sc, pr->tab, n, kTrajModeEval, io, pr->d_err, pr->stream));
+    return SPASM_OK;
+}
+
+extern "C" spasm_status spasm_traj_descend(spasm_problem_t pr, int n, float* q, float* lam, float* mu, int k_steps,
+                                           int init_multipliers, float* metrics, int* sat) {
+    if (!pr || n < 0 || k_steps < 1 || (n > 0 && !q)) return fail(SPASM_ERR_INVALID, "bad arguments");
+    if (!init_multipliers && (!lam || !mu)) return fail(SPASM_ERR_INVALID, "lam and mu required");
+    TrajIO io{};
+    io.q = q; io.lam = lam; io.mu = mu; io.metrics = metrics; io.sat = sat;
+    io.k_steps = k_steps; io.init_multipliers = init_multipliers;
+    SPASM_CUDA(launch_traj(pr->sc, pr->tab, n, kTrajModeDescend, io, pr->d_err, pr->stream));
+    return SPASM_OK;
+}

@@ -1,0 +1,686 @@
+// Stage-2 kernels: lift (IK + waypoint initialisation), the fused trajectory
+// optimisation (one CTA per particle, every iteration inside one launch) and the FP64
+// feasibility check of returned solutions.
+#include "launch_s2.h"
+#include "stage1.cuh"
+#include "stage2.cuh"
+
+namespace spasm {
+
+// ================================================================================== lift
+// Damped-least-squares IK (Wampler 1986): dq = J^T (J J^T + damp^2 I)^-1 e with
+//   e = (p* - p, 1/2 sum_c R[:,c] x R*[:,c]),  J_k = (z_k x (p - o_k), z_k),
+// solved by a 6x6 Cholesky factorisation (the system matrix is SPD thanks to damping).
+__device__ void ik_dls(const Scalars& sc, const float Rs[9], const float ps[3], float q[7]) {
+    for (int it = 0; it < sc.K_ik; ++it) {
+        float R[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1}, o[3] = {0, 0, 0};
+        float z[7][3], org[7][3];
+        for (int k = 0; k < 7; ++k) {
+            float s, c;
+            sincosf(sc.th0[k] + q[k], &s, &c);
+            dh_step<float>(R, o, sc.ca[k], sc.sa[k], sc.a[k], sc.d[k], c, s);
+            z[k][0] = R[2]; z[k][1] = R[5]; z[k][2] = R[8];
+            org[k][0] = o[0]; org[k][1] = o[1]; org[k][2] = o[2];
+        }
+        float Rt[9], pt[3];
+        tool_frame<float>(sc, R, o, Rt, pt);
+        float e[6];
+        e[0] = ps[0] - pt[0]; e[1] = ps[1] - pt[1]; e[2] = ps[2] - pt[2];
+        e[3] = e[4] = e[5] = 0.f;
+        for (int c = 0; c < 3; ++c) {
+            const float a0 = Rt[c], a1 = Rt[3 + c], a2 = Rt[6 + c];
+            const float b0 = Rs[c], b1 = Rs[3 + c], b2 = Rs[6 + c];
+            e[3] += 0.5f * (a1 * b2 - a2 * b1);
+            e[4] += 0.5f * (a2 * b0 - a0 * b2);
+            e[5] += 0.5f * (a0 * b1 - a1 * b0);
+        }
+        float J[6][7];
+        for (int k = 0; k < 7; ++k) {
+            const float rx = pt[0] - org[k][0], ry = pt[1] - org[k][1], rz = pt[2] - org[k][2];
+            J[0][k] = z[k][1] * rz - z[k][2] * ry;
+            J[1][k] = z[k][2] * rx - z[k][0] * rz;
+            J[2][k] = z[k][0] * ry - z[k][1] * rx;
+            J[3][k] = z[k][0]; J[4][k] = z[k][1]; J[5][k] = z[k][2];
+        }
+        // Cholesky of A = J J^T + damp^2 I (lower triangle L)
+        float L[6][6];
+        for (int i = 0; i < 6; ++i)
+            for (int j = 0; j <= i; ++j) {
+                float s = 0.f;
+                for (int k = 0; k < 7; ++k) s += J[i][k] * J[j][k];
+                if (i == j) s += sc.ik_damp * sc.ik_damp;
+                for (int k = 0; k < j; ++k) s -= L[i][k] * L[j][k];
+                L[i][j] = (i == j) ? sqrtf(fmaxf(s, 1e-30f)) : s / L[j][j];
+            }
+        float y[6];
+        for (int i = 0; i < 6; ++i) {
+            float s = e[i];
+            for (int k = 0; k < i; ++k) s -= L[i][k] * y[k];
+            y[i] = s / L[i][i];
+        }
+        for (int i = 5; i >= 0; --i) {
+            float s = y[i];
+            for (int k = i + 1; k < 6; ++k) s -= L[k][i] * y[k];
+            y[i] = s / L[i][i];
+        }
+        for (int k = 0; k < 7; ++k) {
+            float dq = 0.f;
+            for (int i = 0; i < 6; ++i) dq += J[i][k] * y[i];
+            q[k] = fminf(fmaxf(q[k] + dq, sc.qlo[k]), sc.qhi[k]);
+        }
+    }
+}
+
+__device__ __forceinline__ void perturbed_home(const Scalars& sc, uint32_t c0, int p, uint32_t tag, uint32_t attempt,
+                                               float amp, float q[7]) {
+    const U4 a = philox4x32_10(2u * c0, (uint32_t)p, tag, attempt, sc.seed);
+    const U4 b = philox4x32_10(2u * c0 + 1u, (uint32_t)p, tag, attempt, sc.seed);
+    const float u[7] = {u01(a.x), u01(a.y), u01(a.z), u01(a.w), u01(b.x), u01(b.y), u01(b.z)};
+    for (int j = 0; j < 7; ++j) q[j] = fminf(fmaxf(sc.q_home[j] + amp * (2.f * u[j] - 1.f), sc.qlo[j]), sc.qhi[j]);
+}
+
+// one thread per (particle, block, grasp|place)
+__global__ void k_lift_ik(const __grid_constant__ Scalars sc, int n, const float* __restrict__ place,
+                          const int* __restrict__ n_place, uint32_t attempt, float* __restrict__ q) {
+    const int gid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int B = sc.B;
+    if (gid >= n * 2 * B) return;
+    const int np = *n_place;
+    if (np <= 0) return;
+    const int p = gid / (2 * B), r = gid % (2 * B), b = r >> 1, which = r & 1;
+    const U4 kk = philox4x32_10((uint32_t)b, (uint32_t)p, kTagGrasp, attempt, sc.seed);
+    float pose[4];
+    if (which == 0) {
+        pose[0] = sc.init[b].x; pose[1] = sc.init[b].y; pose[2] = sc.init[b].z; pose[3] = sc.init[b].w;
+    } else {
+        const float* src = place + ((size_t)(p % np) * B + b) * 4;
+        pose[0] = src[0]; pose[1] = src[1]; pose[2] = src[2]; pose[3] = src[3];
+    }
+    const int k = (int)((which == 0 ? kk.x : kk.y) & 3u);
+    float s, c;
+    sincosf(pose[3] + 0.5f * kPi * (float)k, &s, &c);
+    // tool target: Rz(yaw) Rx(pi), at the block's top face (+grasp offset)
+    const float Rs[9] = {c, s, 0.f, s, -c, 0.f, 0.f, 0.f, -1.f};
+    const float ps[3] = {pose[0], pose[1], pose[2] + sc.half[b].z + sc.grasp_off};
+    float qq[7];
+    perturbed_home(sc, (uint32_t)(2 * b + which), p, kTagIkSeed, attempt, 0.3f, qq);
+    ik_dls(sc, Rs, ps, qq);
+    const int t = which == 0 ? t_grasp(sc.S, b) : t_place(sc.S, b);
+    float* dst = q + ((size_t)p * sc.C + t) * 8;
+    for (int j = 0; j < 7; ++j) dst[j] = qq[j];
+    dst[7] = 0.f;
+}
+
+// one thread per (particle, configuration): home, or linear interpolation
+// start -> via -> goal within the configuration's segment
+__global__ void k_lift_interp(const __grid_constant__ Scalars sc, int n, const int* __restrict__ n_place,
+                              uint32_t attempt, float* __restrict__ q) {
+    const int gid = blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= n * sc.C) return;
+    if (*n_place <= 0) return;
+    const int p = gid / sc.C, t = gid % sc.C, S = sc.S;
+    float* dst = q + ((size_t)p * sc.C + t) * 8;
+    if (t == 0) {
+        for (int j = 0; j < 7; ++j) dst[j] = sc.q_home[j];
+        dst[7] = 0.f;
+        return;
+    }
+    const int jj = t % S;
+    if (jj == 0) return;   // segment endpoint, written by the IK kernel
+    const int s = t / S, m = S / 2;
+    float via[7];
+    perturbed_home(sc, (uint32_t)s, p, kTagVia, attempt, 0.3f, via);
+    const float* qa = q + ((size_t)p * sc.C + s * S) * 8;
+    const float* qb = q + ((size_t)p * sc.C + (s + 1) * S) * 8;
+    for (int j = 0; j < 7; ++j) {
+        float v;
+        if (jj <= m) v = qa[j] + ((float)jj / (float)m) * (via[j] - qa[j]);
+        else v = via[j] + ((float)(jj - m) / (float)(S - m)) * (qb[j] - via[j]);
+        dst[j] = v;
+    }
+    dst[7] = 0.f;
+}
+
+// ================================================================================== trajopt
+constexpr int kTWarps = 8;
+constexpr int kTThreads = 32 * kTWarps;
+constexpr int kSlots = 3;   // sphere items per lane: up to 64 robot + 8 held-block spheres
+
+struct TWarp {
+    float fr[8][8];          // frame k: origin (3), joint axis z (3)
+    float wr[2][kMaxB][4];   // d/d(placed pose k): group arm, group block
+    float part[4];           // C_arm, C_block, max penetration
+};
+
+struct TShared {
+    float4 bcub[kMaxB][4];   // placed-block cuboids of this iteration
+    float4 icub[kMaxB][4];   // initial-pose cuboids
+    float pose[4 * kMaxB];   // placed poses (x, y, z, yaw)
+    float g4[4 * kMaxB];     // dL/d(placed pose)
+    float h[kMaxNR], lam[kMaxNR], s[kMaxNR];
+    float extra[2 * kMaxB][8];   // gradient rows of grasp (b) and place (B + b) configurations
+    float coef_a[kMaxB], coef_b[kMaxB];
+    PlaceScratch ps;
+    float s_arm, s_blk, mu, L;
+    float c_arm, c_blk, maxpen, c_coll, c_stable, c_height, c_start;
+    float max_start, max_tilt, pm_pen, pm_D, pm_dz, path, jl;
+    TWarp warp[kTWarps];
+};
+
+__host__ __device__ inline size_t t_env_offset() { return 16; }
+__host__ __device__ inline size_t t_shared_offset(int n_cub, int n_osph) {
+    return (16 + (size_t)n_cub * 64 + (size_t)n_osph * 16 + 15) & ~(size_t)15;
+}
+__host__ __device__ inline size_t t_q_offset(int n_cub, int n_osph) {
+    return (t_shared_offset(n_cub, n_osph) + sizeof(TShared) + 15) & ~(size_t)15;
+}
+size_t traj_smem_bytes(const Scalars& sc) {
+    return t_q_offset(sc.n_cub, sc.n_osph) + (size_t)3 * sc.C * 8 * sizeof(float);
+}
+
+// Collision terms of one configuration, evaluated by one warp: arm spheres and (on the
+// transfer interior) the held block's spheres against the environment and the context
+// blocks.  With `grad`, writes the unscaled group gradients G_arm[t], G_blk[t] and adds
+// placed-pose derivatives into the warp's accumulators.
+__device__ __forceinline__ void config_collisions(const Scalars& sc, const float4* __restrict__ cub,
+                                                  const float4* __restrict__ osph, TShared& sh, TWarp& tw,
+                                                  const float* __restrict__ q, float* G_arm, float* G_blk, int t,
+                                                  bool grad, float& acc_arm, float& acc_blk, float& acc_max) {
+    const int lane = threadIdx.x & 31;
+    const int S = sc.S, B = sc.B;
+    const int seg = (t - 1) / S, b = seg >> 1, jj = t - seg * S;
+    const bool held = (seg & 1) && jj < S;
+    const int n_items = sc.n_rsph + (held ? 8 : 0);
+
+    // joint angles: lane k < 7 evaluates sin/cos of joint k
+    float sn = 0.f, cs = 1.f;
+    if (lane < 7) sincosf(sc.th0[lane] + q[t * 8 + lane], &sn, &cs);
+
+    float cx[kSlots], cy[kSlots], cz[kSlots], rr[kSlots];
+    int link[kSlots];
+    bool act[kSlots], isblk[kSlots];
+#pragma unroll
+    for (int k = 0; k < kSlots; ++k) {
+        const int it = lane + 32 * k;
+        act[k] = it < n_items;
+        isblk[k] = act[k] && it >= sc.n_rsph;
+        link[k] = act[k] ? (isblk[k] ? 7 : sc.rlink[it]) : 0;
+        cx[k] = cy[k] = cz[k] = 0.f;
+        rr[k] = 0.f;
+        if (act[k] && !isblk[k]) {
+            const float4 ls = sc.rsph[it];
+            rr[k] = ls.w;
+            if (link[k] == 0) { cx[k] = ls.x; cy[k] = ls.y; cz[k] = ls.z; }
+        }
+    }
+    float R[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1}, o[3] = {0, 0, 0};
+#pragma unroll
+    for (int k = 0; k < 7; ++k) {
+        const float c = __shfl_sync(0xffffffffu, cs, k), s = __shfl_sync(0xffffffffu, sn, k);
+        dh_step<float>(R, o, sc.ca[k], sc.sa[k], sc.a[k], sc.d[k], c, s);
+        if (lane == 0) {
+            tw.fr[k + 1][0] = o[0]; tw.fr[k + 1][1] = o[1]; tw.fr[k + 1][2] = o[2];
+            tw.fr[k + 1][3] = R[2]; tw.fr[k + 1][4] = R[5]; tw.fr[k + 1][5] = R[8];
+        }
+#pragma unroll
+        for (int sl = 0; sl < kSlots; ++sl) {
+            if (act[sl] && !isblk[sl] && link[sl] == k + 1) {
+                const float4 ls = sc.rsph[lane + 32 * sl];
+                cx[sl] = R[0] * ls.x + R[1] * ls.y + R[2] * ls.z + o[0];
+                cy[sl] = R[3] * ls.x + R[4] * ls.y + R[5] * ls.z + o[1];
+                cz[sl] = R[6] * ls.x + R[7] * ls.y + R[8] * ls.z + o[2];
+            }
+        }
+    }
+    if (held) {
+        float Rt[9], pt[3], Rb[9], pb[3];
+        tool_frame<float>(sc, R, o, Rt, pt);
+        held_block<float>(sc, b, Rt, pt, Rb, pb);
+#pragma unroll
+        for (int sl = 0; sl < kSlots; ++sl) {
+            if (isblk[sl]) {
+                float lx, ly, lz;
+                block_sphere_local(sc.half[b], lane + 32 * sl - sc.n_rsph, lx, ly, lz);
+                cx[sl] = pb[0] + Rb[0] * lx + Rb[1] * ly + Rb[2] * lz;
+                cy[sl] = pb[1] + Rb[3] * lx + Rb[4] * ly + Rb[5] * lz;
+                cz[sl] = pb[2] + Rb[6] * lx + Rb[7] * ly + Rb[8] * lz;
+                rr[sl] = sc.half[b].w;
+            }
+        }
+    }
+    __syncwarp();
+
+    float gx[kSlots], gy[kSlots], gz[kSlots], pen_sum[kSlots];
+#pragma unroll
+    for (int sl = 0; sl < kSlots; ++sl) gx[sl] = gy[sl] = gz[sl] = pen_sum[sl] = 0.f;
+    bool any_hit = false;
+
+    // environment cuboids (shared memory, broadcast reads)
+    for (int oi = 0; oi < sc.n_cub; ++oi) {
+        const float4 o0 = cub[4 * oi], o1 = cub[4 * oi + 1], o2 = cub[4 * oi + 2], o3 = cub[4 * oi + 3];
+#pragma unroll
+        for (int sl = 0; sl < kSlots; ++sl) {
+            if (!act[sl]) continue;
+            float ax, ay, az;
+            const float pen = pen_cuboid<float>(cx[sl], cy[sl], cz[sl], rr[sl], o0, o1, o2, o3, ax, ay, az);
+            if (pen > 0.f) {
+                any_hit = true;
+                pen_sum[sl] += pen;
+                acc_max = fmaxf(acc_max, pen);
+                gx[sl] += ax; gy[sl] += ay; gz[sl] += az;
+            }
+        }
+    }
+    for (int oi = 0; oi < sc.n_osph; ++oi) {
+        const float4 os = osph[oi];
+#pragma unroll
+        for (int sl = 0; sl < kSlots; ++sl) {
+            if (!act[sl]) continue;
+            float ax, ay, az;
+            const float pen = pen_sphere<float>(cx[sl], cy[sl], cz[sl], rr[sl], os, ax, ay, az);
+            if (pen > 0.f) {
+                any_hit = true;
+                pen_sum[sl] += pen;
+                acc_max = fmaxf(acc_max, pen);
+                gx[sl] += ax; gy[sl] += ay; gz[sl] += az;
+            }
+        }
+    }
+    // context blocks: placed (k < b, movable) and not yet moved (k > b)
+    for (int kb = 0; kb < B; ++kb) {
+        if (kb == b) continue;
+        const bool placed = kb < b;
+        const float4* cb = placed ? sh.bcub[kb] : sh.icub[kb];
+        const float4 o0 = cb[0], o1 = cb[1], o2 = cb[2], o3 = cb[3];
+        float da[4] = {0, 0, 0, 0}, db[4] = {0, 0, 0, 0};
+        bool hit = false;
+#pragma unroll
+        for (int sl = 0; sl < kSlots; ++sl) {
+            if (!act[sl]) continue;
+            float ax, ay, az;
+            const float pen = pen_cuboid<float>(cx[sl], cy[sl], cz[sl], rr[sl], o0, o1, o2, o3, ax, ay, az);
+            if (pen > 0.f) {
+                any_hit = true;
+                hit = true;
+                pen_sum[sl] += pen;
+                acc_max = fmaxf(acc_max, pen);
+                gx[sl] += ax; gy[sl] += ay; gz[sl] += az;
+                if (placed) {
+                    // rigid motion of the cuboid: d/dP = -g, d/dyaw = -((c - P) x g)_z
+                    float* dd = isblk[sl] ? db : da;
+                    dd[0] -= ax; dd[1] -= ay; dd[2] -= az;
+                    dd[3] -= (cx[sl] - o0.x) * ay - (cy[sl] - o0.y) * ax;
+                }
+            }
+        }
+        if (grad && placed && __any_sync(0xffffffffu, hit)) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) { da[i] = warp_sum(da[i]); db[i] = warp_sum(db[i]); }
+            if (lane == 0) {
+#pragma unroll
+                for (int i = 0; i < 4; ++i) { tw.wr[0][kb][i] += da[i]; tw.wr[1][kb][i] += db[i]; }
+            }
+        }
+    }
+#pragma unroll
+    for (int sl = 0; sl < kSlots; ++sl) {
+        if (isblk[sl]) acc_blk += pen_sum[sl];
+        else acc_arm += pen_sum[sl];
+    }
+    if (!grad) return;
+
+    // backward: dC/dq_k = sum_s z_k . ((c_s - o_k) x g_s) over spheres on links >= k
+    float ja[7], jb[7];
+#pragma unroll
+    for (int k = 0; k < 7; ++k) ja[k] = jb[k] = 0.f;
+    const bool warp_hit = __any_sync(0xffffffffu, any_hit);
+    if (warp_hit) {
+        if (any_hit) {
+#pragma unroll
+            for (int k = 0; k < 7; ++k) {
+                const float ox = tw.fr[k + 1][0], oy = tw.fr[k + 1][1], oz = tw.fr[k + 1][2];
+                const float zx = tw.fr[k + 1][3], zy = tw.fr[k + 1][4], zz = tw.fr[k + 1][5];
+#pragma unroll
+                for (int sl = 0; sl < kSlots; ++sl) {
+                    if (!act[sl] || link[sl] < k + 1) continue;
+                    const float vx = cx[sl] - ox, vy = cy[sl] - oy, vz = cz[sl] - oz;
+                    const float m = zx * (vy * gz[sl] - vz * gy[sl]) + zy * (vz * gx[sl] - vx * gz[sl]) +
+                                    zz * (vx * gy[sl] - vy * gx[sl]);
+                    if (isblk[sl]) jb[k] += m; else ja[k] += m;
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 7; ++k) { ja[k] = warp_sum(ja[k]); jb[k] = warp_sum(jb[k]); }
+    }
+    if (lane < 7) {
+        float va = 0.f, vb = 0.f;
+#pragma unroll
+        for (int k = 0; k < 7; ++k) if (k == lane) { va = ja[k]; vb = jb[k]; }
+        G_arm[t * 8 + lane] = va;
+        G_blk[t * 8 + lane] = vb;
+    }
+}
+
+// One placed pose from the place configuration of block b: (x, y, z, yaw) of the block
+// frame held by the tool.
+__device__ __forceinline__ void placed_pose(const Scalars& sc, int b, const float* q, float pose[4]) {
+    float qq[7];
+    for (int j = 0; j < 7; ++j) qq[j] = q[j];
+    float R[8][9], o[8][3], Rt[9], pt[3], Rb[9], pb[3];
+    fk_full<float>(sc, qq, R, o, Rt, pt);
+    held_block<float>(sc, b, Rt, pt, Rb, pb);
+    pose[0] = pb[0]; pose[1] = pb[1]; pose[2] = pb[2];
+    pose[3] = atan2f(Rb[3], Rb[0]);
+}
+
+// Residuals of the start group at the grasp (which = 0) or place (which = 1) configuration
+// of block b, and, with s_r != nullptr, their weighted joint gradient sum_r s_r dh_r/dq.
+__device__ __forceinline__ void start_terms(const Scalars& sc, int b, int which, const float* q, float* h_out,
+                                            const float* s_r, float grad_out[7], const float* g4 /*4 or null*/) {
+    float qq[7];
+    for (int j = 0; j < 7; ++j) qq[j] = q[j];
+    float R[8][9], o[8][3], Rt[9], pt[3], Rb[9], pb[3];
+    fk_full<float>(sc, qq, R, o, Rt, pt);
+    held_block<float>(sc, b, Rt, pt, Rb, pb);
+    float roll, pitch, wr[3], wp[3];
+    roll_pitch_torque<float>(Rb, roll, pitch, wr, wp);
+    if (which == 0) {
+        h_out[0] = pb[0] - sc.init[b].x;
+        h_out[1] = pb[1] - sc.init[b].y;
+        h_out[2] = pb[2] - sc.init[b].z;
+        h_out[3] = roll;
+        h_out[4] = pitch;
+    } else {
+        h_out[0] = roll;
+        h_out[1] = pitch;
+    }
+    if (!s_r) return;
+    // wrench at the block frame: force F (on p_blk), torque M (about the world origin)
+    float F[3] = {0, 0, 0}, M[3] = {0, 0, 0};
+    if (which == 0) {
+        F[0] = s_r[0]; F[1] = s_r[1]; F[2] = s_r[2];
+        for (int i = 0; i < 3; ++i) M[i] = s_r[3] * wr[i] + s_r[4] * wp[i];
+    } else {
+        for (int i = 0; i < 3; ++i) M[i] = s_r[0] * wr[i] + s_r[1] * wp[i];
+    }
+    if (g4) {
+        // placed-pose gradient (x, y, z, yaw) of the same configuration
+        const float e[3] = {Rb[0], Rb[3], Rb[6]};
+        float wy[3];
+        yaw_torque(e, wy);
+        F[0] += g4[0]; F[1] += g4[1]; F[2] += g4[2];
+        for (int i = 0; i < 3; ++i) M[i] += g4[3] * wy[i];
+    }
+    // moment of F about the origin: p x F
+    M[0] += pb[1] * F[2] - pb[2] * F[1];
+    M[1] += pb[2] * F[0] - pb[0] * F[2];
+    M[2] += pb[0] * F[1] - pb[1] * F[0];
+    for (int k = 0; k < 7; ++k) {
+        const float* ok = o[k + 1];
+        const float zx = R[k + 1][2], zy = R[k + 1][5], zz = R[k + 1][8];
+        // z . (M - o x F)
+        const float tx = M[0] - (ok[1] * F[2] - ok[2] * F[1]);
+        const float ty = M[1] - (ok[2] * F[0] - ok[0] * F[2]);
+        const float tz = M[2] - (ok[0] * F[1] - ok[1] * F[0]);
+        grad_out[k] = zx * tx + zy * ty + zz * tz;
+    }
+}
+
+// Modes of the trajectory kernel
+enum TrajMode { kTrajEval = 0, kTrajDescend = 1, kTrajCheck = 2 };
+
+// Evaluate the whole particle: placed poses, configuration loop, residuals, objective;
+// with `grad`, assemble dL/dq into G_arm (G_blk is scratch).
+__device__ void traj_evaluate(const Scalars& sc, const float4* cub, const float4* osph, TShared& sh, float* q,
+                              float* G_arm, float* G_blk, bool grad) {
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int B = sc.B, S = sc.S, C = sc.C, NR = sc.NR;
+
+    // (1) placed poses of this iteration
+    if (w == 0) {
+        if (lane < B) {
+            float pose[4];
+            placed_pose(sc, lane, q + t_place(S, lane) * 8, pose);
+            for (int i = 0; i < 4; ++i) sh.pose[4 * lane + i] = pose[i];
+            block_cuboid(pose[0], pose[1], pose[2], pose[3], sc.half[lane], sh.bcub[lane]);
+        }
+    }
+    // zero per-warp accumulators
+    for (int i = lane; i < 2 * kMaxB * 4; i += 32) (&sh.warp[w].wr[0][0][0])[i] = 0.f;
+    __syncthreads();
+
+    // (2) configuration loop
+    float acc_arm = 0.f, acc_blk = 0.f, acc_max = 0.f;
+    for (int t = 1 + w; t < C; t += kTWarps)
+        config_collisions(sc, cub, osph, sh, sh.warp[w], q, G_arm, G_blk, t, grad, acc_arm, acc_blk, acc_max);
+    acc_arm = warp_sum(acc_arm);
+    acc_blk = warp_sum(acc_blk);
+    acc_max = warp_max(acc_max);
+    if (lane == 0) { sh.warp[w].part[0] = acc_arm; sh.warp[w].part[1] = acc_blk; sh.warp[w].part[2] = acc_max; }
+    __syncthreads();
+
+    // (3) epilogue on warp 0: residuals, objective, pose and start gradients
+    if (w == 0) {
+        float ca = lane < kTWarps ? sh.warp[lane].part[0] : 0.f;
+        float cb = lane < kTWarps ? sh.warp[lane].part[1] : 0.f;
+        float cm = lane < kTWarps ? sh.warp[lane].part[2] : 0.f;
+        // fixed-order sums over warps
+        float tot_a = 0.f, tot_b = 0.f;
+        for (int i = 0; i < kTWarps; ++i) {
+            tot_a += __shfl_sync(0xffffffffu, ca, i);
+            tot_b += __shfl_sync(0xffffffffu, cb, i);
+        }
+        cm = warp_max(cm);
+        PlaceOut po;
+        place_eval_warp(sc, cub, sc.n_cub, osph, sc.n_osph, sh.pose, false, kPlaceForward, nullptr, nullptr, 0.f,
+                        nullptr, sh.ps, po);
+        if (lane < B) {
+            start_terms(sc, lane, 0, q + t_grasp(S, lane) * 8, &sh.h[5 * lane], nullptr, nullptr, nullptr);
+            start_terms(sc, lane, 1, q + t_place(S, lane) * 8, &sh.h[5 * B + 2 * lane], nullptr, nullptr, nullptr);
+            sh.h[7 * B + lane] = sh.ps.e[lane];
+            sh.h[8 * B + lane] = sh.ps.D[lane];
+        }
+        if (lane == 0) {
+            sh.h[9 * B] = po.c_coll;
+            sh.h[9 * B + 1] = tot_a;
+            sh.h[9 * B + 2] = tot_b;
+            sh.c_arm = tot_a; sh.c_blk = tot_b; sh.maxpen = cm;
+            sh.c_coll = po.c_coll; sh.c_stable = po.c_stable; sh.c_height = po.c_height;
+            sh.pm_pen = po.maxpen; sh.pm_D = po.maxD; sh.pm_dz = po.maxdz;
+        }
+        __syncwarp();
+        // start-group values and maxima
+        float v_start = 0.f, v_tilt = 0.f;
+        if (lane < B) {
+            const float* hg = &sh.h[5 * lane];
+            const float* hp = &sh.h[5 * B + 2 * lane];
+            v_start = hg[0] * hg[0] + hg[1] * hg[1] + hg[2] * hg[2] + hg[3] * hg[3] + hg[4] * hg[4];
+            v_tilt = hp[0] * hp[0] + hp[1] * hp[1];
+        }
+        const float c_start = warp_sum(v_start + v_tilt);
+        const float m_start = warp_max(v_start), m_tilt = warp_max(v_tilt);
+        // objective and dL/dh
+        float Lp = 0.f;
+        for (int r = lane; r < NR; r += 32) {
+            const float sw = residual_sqrt_weight(sc, r), hw = sw * sh.h[r];
+            Lp += sh.lam[r] * hw + 0.5f * sh.mu * hw * hw;
+            sh.s[r] = (sh.lam[r] + sh.mu * hw) * sw;
+        }
+        Lp = warp_sum(Lp);
+        if (lane == 0) { sh.L = Lp; sh.c_start = c_start; sh.max_start = m_start; sh.max_tilt = m_tilt; }
+        __syncwarp();
+        if (grad) {
+            place_eval_warp(sc, cub, sc.n_cub, osph, sc.n_osph, sh.pose, false, kPlaceExplicit, &sh.s[8 * B],
+                            &sh.s[7 * B], sh.s[9 * B], sh.g4, sh.ps, po);
+            const float s_arm = sh.s[9 * B + 1], s_blk = sh.s[9 * B + 2];
+            for (int i = lane; i < 4 * B; i += 32) {
+                const int kb = i >> 2, c = i & 3;
+                float wa = 0.f, wb = 0.f;
+                for (int ww = 0; ww < kTWarps; ++ww) { wa += sh.warp[ww].wr[0][kb][c]; wb += sh.warp[ww].wr[1][kb][c]; }
+                sh.g4[i] += s_arm * wa + s_blk * wb;
+            }
+            if (lane == 0) { sh.s_arm = s_arm; sh.s_blk = s_blk; }
+            __syncwarp();
+            if (lane < B) {
+                float hbuf[5];
+                start_terms(sc, lane, 0, q + t_grasp(S, lane) * 8, hbuf, &sh.s[5 * lane], sh.extra[lane], nullptr);
+                start_terms(sc, lane, 1, q + t_place(S, lane) * 8, hbuf, &sh.s[5 * B + 2 * lane], sh.extra[B + lane],
+                            &sh.g4[4 * lane]);
+            }
+        }
+    }
+    __syncthreads();
+
+    // (4) path length, joint limits; assemble the gradient into G_arm
+    float path = 0.f, jl = 0.f;
+    for (int i = tid; i < C * 7; i += kTThreads) {
+        const int t = i / 7, j = i % 7;
+        const float v = q[t * 8 + j];
+        float gsum = 0.f;
+        if (t + 1 < C) {
+            const float d = q[(t + 1) * 8 + j] - v;
+            path += d * d;
+            gsum -= 2.f * sc.w_path * d;
+        }
+        if (t > 0) {
+            const float d = v - q[(t - 1) * 8 + j];
+            gsum += 2.f * sc.w_path * d;
+            const float over = fmaxf(v - sc.qhi[j], 0.f), under = fmaxf(sc.qlo[j] - v, 0.f);
+            jl += over * over + under * under;
+            gsum += sc.w_jl * (2.f * over - 2.f * under);
+        }
+        if (grad) {
+            if (t == 0) {
+                gsum = 0.f;
+            } else {
+                gsum += sh.s_arm * G_arm[t * 8 + j] + sh.s_blk * G_blk[t * 8 + j];
+                if (t % S == 0) {
+                    const int e = t / S - 1;   // t = (e+1) S: grasp of block e/2 (e even) or place (e odd)
+                    const int bb = e >> 1;
+                    gsum += (e & 1) ? sh.extra[B + bb][j] : sh.extra[bb][j];
+                }
+            }
+        }
+        if (grad) G_blk[t * 8 + j] = gsum;   // G_blk becomes the assembled gradient
+    }
+    path = warp_sum(path);
+    jl = warp_sum(jl);
+    if (lane == 0) { sh.warp[w].part[0] = path; sh.warp[w].part[1] = jl; }
+    __syncthreads();
+    if (tid == 0) {
+        float p = 0.f, l = 0.f;
+        for (int i = 0; i < kTWarps; ++i) { p += sh.warp[i].part[0]; l += sh.warp[i].part[1]; }
+        sh.path = p;
+        sh.jl = l;
+        sh.L += sc.w_path * p + sc.w_jl * l;
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(kTThreads, 2) k_traj(const __grid_constant__ Scalars sc, DevTables tab, int n, int mode,
+                                                      TrajIO io, int* err) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
+    float4* cub = reinterpret_cast<float4*>(smem_raw + t_env_offset());
+    float4* osph = cub + 4 * sc.n_cub;
+    TShared& sh = *reinterpret_cast<TShared*>(smem_raw + t_shared_offset(sc.n_cub, sc.n_osph));
+    float* q = reinterpret_cast<float*>(smem_raw + t_q_offset(sc.n_cub, sc.n_osph));
+    float* G_arm = q + sc.C * 8;
+    float* G_blk = G_arm + sc.C * 8;
+    if (!stage_tables(cub, tab.cub, (uint32_t)sc.n_cub * 64u, osph, tab.osph, (uint32_t)sc.n_osph * 16u, bar, err))
+        return;
+    const int p = blockIdx.x;
+    if (p >= n) return;
+    const int tid = threadIdx.x;
+    const int C = sc.C, NR = sc.NR, B = sc.B;
+
+    // particle state -> shared memory (coalesced float4)
+    const float4* qg = reinterpret_cast<const float4*>(io.q + (size_t)p * C * 8);
+    float4* qs = reinterpret_cast<float4*>(q);
+    for (int i = tid; i < C * 2; i += kTThreads) qs[i] = qg[i];
+    if (tid < B) block_cuboid(sc.init[tid].x, sc.init[tid].y, sc.init[tid].z, sc.init[tid].w, sc.half[tid], sh.icub[tid]);
+    const bool fresh = mode == kTrajDescend && io.init_multipliers;
+    for (int r = tid; r < NR; r += kTThreads) sh.lam[r] = (fresh || !io.lam) ? 0.f : io.lam[(size_t)p * NR + r];
+    if (tid == 0) sh.mu = (fresh || !io.mu) ? sc.mu0 : io.mu[p];
+    __syncthreads();
+
+    if (mode == kTrajDescend) {
+        const int K = io.k_steps;
+        for (int k = 1; k <= K; ++k) {
+            traj_evaluate(sc, cub, osph, sh, q, G_arm, G_blk, true);
+            const float eta = sc.eta_traj * (1.f - (float)k / (float)K);
+            for (int i = tid; i < C * 7; i += kTThreads) {
+                const int t = i / 7, j = i % 7;
+                if (t == 0) continue;
+                const float v = q[t * 8 + j] - eta * G_blk[t * 8 + j];
+                q[t * 8 + j] = fminf(fmaxf(v, sc.qlo[j]), sc.qhi[j]);
+            }
+            if (sc.K_al > 0 && k % sc.K_al == 0) {
+                for (int r = tid; r < NR; r += kTThreads) sh.lam[r] += sh.mu * residual_sqrt_weight(sc, r) * sh.h[r];
+                __syncthreads();
+                if (tid == 0) sh.mu = fminf(sh.mu * 2.f, sc.mu_max);
+            }
+            __syncthreads();
+        }
+    }
+    const bool want_grad = mode == kTrajEval && io.grad != nullptr;
+    traj_evaluate(sc, cub, osph, sh, q, G_arm, G_blk, want_grad);
+
+    // outputs
+    if (mode == kTrajDescend) {
+        float4* qo = reinterpret_cast<float4*>(io.q + (size_t)p * C * 8);
+        for (int i = tid; i < C * 2; i += kTThreads) qo[i] = qs[i];
+        if (io.lam)
+            for (int r = tid; r < NR; r += kTThreads) io.lam[(size_t)p * NR + r] = sh.lam[r];
+        if (io.mu && tid == 0) io.mu[p] = sh.mu;
+    }
+    if (want_grad)
+        for (int i = tid; i < C * 8; i += kTThreads) io.grad[(size_t)p * C * 8 + i] = (i & 7) == 7 ? 0.f : G_blk[i];
+    if (io.h)
+        for (int r = tid; r < NR; r += kTThreads) io.h[(size_t)p * NR + r] = sh.h[r];
+    if (tid == 0) {
+        if (io.L) io.L[p] = sh.L;
+        if (io.groups) {
+            float* g = io.groups + (size_t)p * 6;
+            g[0] = sh.c_start; g[1] = sh.c_arm; g[2] = sh.c_blk; g[3] = sh.c_coll; g[4] = sh.c_stable; g[5] = sh.c_height;
+        }
+        const float rank = sc.w_path * sh.path + sc.w_stable * sh.c_stable + sc.w_height * sh.c_height +
+                           sc.w_coll * sh.c_coll + sc.w_start * sh.c_start + sc.w_arm * sh.c_arm + sc.w_block * sh.c_blk;
+        if (io.metrics) {
+            float* m = io.metrics + (size_t)p * 8;
+            m[0] = sh.maxpen; m[1] = sh.max_start; m[2] = sh.max_tilt; m[3] = sh.pm_pen; m[4] = sh.pm_D;
+            m[5] = sh.pm_dz; m[6] = sh.path; m[7] = rank;
+        }
+        if (io.sat) {
+            const bool ok = sh.maxpen <= sc.eps && sh.max_start <= sc.eps_start && sh.max_tilt <= sc.eps_start &&
+                            sh.pm_pen <= sc.eps && sh.pm_D <= sc.eps && sh.pm_dz <= sc.eps && sh.jl == 0.f;
+            io.sat[p] = ok ? 1 : 0;
+        }
+    }
+}
+
+// ================================================================================== launchers
+cudaError_t launch_lift(const Scalars& sc, int n, const float* place, const int* n_place, uint32_t attempt, float* q,
+                        cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    const int n_ik = n * 2 * sc.B;
+    k_lift_ik<<<(n_ik + 127) / 128, 128, 0, st>>>(sc, n, place, n_place, attempt, q);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int n_cfg = n * sc.C;
+    k_lift_interp<<<(n_cfg + 255) / 256, 256, 0, st>>>(sc, n, n_place, attempt, q);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_traj(const Scalars& sc, DevTables t, int n, int mode, const TrajIO& io, int* err,
+                        cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    const size_t bytes = traj_smem_bytes(sc);
+    cudaError_t e = cudaFuncSetAttribute(k_traj, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return e;
+    k_traj<<<n, kTThreads, bytes, st>>>(sc, t, n, mode, io, err);
+    return cudaGetLastError();
+}
+
+}  // namespace spasm

@@ -1,0 +1,29 @@
+// Host-side launchers of the stage-2 kernels (internal to the library).
+#pragma once
+#include "launch.h"
+
+namespace spasm {
+
+// Buffers of one trajectory-kernel launch (device pointers; any may be null unless noted).
+struct TrajIO {
+    float* q;          // [n][C][8] joint configurations (required); updated by a descent
+    float* lam;        // [n][NR] multipliers
+    float* mu;         // [n] penalty parameters
+    float* L;          // [n] augmented-Lagrangian objective
+    float* grad;       // [n][C][8] dL/dq (evaluation mode)
+    float* groups;     // [n][6] C_start, C_arm, C_block, C_coll, C_stable, C_height
+    float* h;          // [n][NR] residual vector
+    float* metrics;    // [n][8] max pen, max grasp error, max tilt, placement max pen / CoM / height, path, rank cost
+    int* sat;          // [n] satisfying flag
+    int k_steps;       // descent steps
+    int init_multipliers;   // descent starts from lambda = 0, mu = mu0
+};
+enum TrajModeHost { kTrajModeEval = 0, kTrajModeDescend = 1, kTrajModeCheck = 2 };
+
+size_t traj_smem_bytes(const Scalars& sc);
+// IK at grasp/place poses + interpolation; particle p lifts placement p % *n_place.
+cudaError_t launch_lift(const Scalars& sc, int n, const float* place, const int* n_place, uint32_t attempt, float* q,
+                        cudaStream_t st);
+cudaError_t launch_traj(const Scalars& sc, DevTables t, int n, int mode, const TrajIO& io, int* err, cudaStream_t st);
+
+}  // namespace spasm

@@ -1,0 +1,221 @@
+"""Thin ctypes binding of ``libspasm.so`` (argument marshalling only).
+
+Every function here has the name of the C entry point it calls (see ``include/spasm.h``)
+and forwards its arguments: device buffers are torch CUDA tensors (passed as raw
+pointers), host outputs are numpy arrays.  Nothing is computed here; if the library is
+missing the import of a function fails loudly -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+from . import build as _build
+
+LIB_PATH = _build.LIB
+
+SPASM_OK = 0
+STATUS = {0: "SPASM_OK", -1: "SPASM_ERR_INVALID", -2: "SPASM_ERR_NOMEM", -3: "SPASM_ERR_CUDA",
+          -4: "SPASM_ERR_NOSOLUTION", -5: "SPASM_ERR_TIMEOUT", -6: "SPASM_ERR_DEVICE"}
+
+EXPORTED = ["spasm_create_problem", "spasm_destroy_problem", "spasm_last_error", "spasm_place", "spasm_optimize",
+            "spasm_result", "spasm_sizes", "spasm_place_sample", "spasm_place_eval", "spasm_place_descend",
+            "spasm_select_topk", "spasm_lift", "spasm_traj_eval", "spasm_traj_descend"]
+
+
+class SpasmError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+_D = ctypes.POINTER(ctypes.c_double)
+_I = ctypes.POINTER(ctypes.c_int32)
+_V = ctypes.c_void_p
+
+
+class _Robot(ctypes.Structure):
+    _fields_ = [("dof", ctypes.c_int), ("dh", _D), ("qlim", _D), ("n_spheres", ctypes.c_int), ("sphere_link", _I),
+                ("sphere", _D), ("ee", _D), ("q_home", _D)]
+
+
+class _Obstacles(ctypes.Structure):
+    _fields_ = [("n_cuboids", ctypes.c_int), ("cuboid", _D), ("n_spheres", ctypes.c_int), ("sphere", _D)]
+
+
+class _Goal(ctypes.Structure):
+    _fields_ = [("n_blocks", ctypes.c_int), ("half_ext", _D), ("init_pose", _D), ("goal_box", _D),
+                ("z_table", ctypes.c_double), ("grasp_off", ctypes.c_double)]
+
+
+_INT_PARAMS = ("N", "M", "P", "Q", "W", "K_lin", "K_quad", "K_traj", "K_al", "K_ik")
+_DBL_PARAMS = ("eta_init", "alpha", "eta_traj", "eps", "eps_start", "w_stable", "w_height", "w_coll", "w_start",
+               "w_arm", "w_block", "w_path", "w_jl", "mu0", "mu_max", "ik_damp")
+
+
+class _Params(ctypes.Structure):
+    _fields_ = ([(n, ctypes.c_int) for n in _INT_PARAMS] + [(n, ctypes.c_double) for n in _DBL_PARAMS] +
+                [("seed", ctypes.c_uint64), ("max_steps", ctypes.c_int)])
+
+
+_lib = None
+
+
+def lib():
+    """The loaded CUDA library; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is not built; run paper_2510_07674_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        L.spasm_last_error.restype = ctypes.c_char_p
+        L.spasm_create_problem.argtypes = [ctypes.POINTER(_Robot), ctypes.POINTER(_Obstacles), ctypes.POINTER(_Goal),
+                                           ctypes.POINTER(_Params), _V, ctypes.POINTER(_V)]
+        L.spasm_destroy_problem.argtypes = [_V]
+        L.spasm_place.argtypes = [_V]
+        L.spasm_optimize.argtypes = [_V]
+        L.spasm_result.argtypes = [_V, _I, _D, _D, _D, _I]
+        L.spasm_sizes.argtypes = [_V, _I, _I]
+        L.spasm_place_sample.argtypes = [_V, ctypes.c_int, ctypes.c_uint32, _V, _V]
+        L.spasm_place_eval.argtypes = [_V, ctypes.c_int, _V, ctypes.c_int, _V, _V, _V, _V]
+        L.spasm_place_descend.argtypes = [_V, ctypes.c_int, _V, ctypes.c_int, ctypes.c_int, _V, _V]
+        L.spasm_select_topk.argtypes = [_V, ctypes.c_int, _V, ctypes.c_int, _V]
+        L.spasm_lift.argtypes = [_V, ctypes.c_int, _V, ctypes.c_int, ctypes.c_uint32, _V]
+        L.spasm_traj_eval.argtypes = [_V, ctypes.c_int, _V, _V, _V, _V, _V, _V, _V]
+        L.spasm_traj_descend.argtypes = [_V, ctypes.c_int, _V, _V, _V, ctypes.c_int, ctypes.c_int, _V, _V]
+        for name in EXPORTED:
+            if name != "spasm_last_error":
+                getattr(L, name).restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _check(status: int):
+    if status != SPASM_OK:
+        raise SpasmError(status, lib().spasm_last_error().decode(errors="replace"))
+
+
+def _dev(t) -> Optional[int]:
+    """Raw device pointer of a contiguous CUDA tensor (or None)."""
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    return t.data_ptr()
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+class Problem:
+    """Owns one ``spasm_problem_t`` created from a seeded workload description."""
+
+    def __init__(self, workload, stream=None, **param_overrides):
+        r, s = workload.robot, workload.scene
+        prm = dict(vars(workload.params))
+        prm.update(param_overrides)
+        self.params = prm
+        self._arrays = {
+            "dh": _f64(r.dh), "qlim": _f64(r.qlim), "sphere_link": np.ascontiguousarray(r.sphere_link, np.int32),
+            "sphere": _f64(r.sphere), "ee": _f64(r.ee), "q_home": _f64(r.q_home),
+            "cub": _f64(s.cuboid).reshape(-1, 15), "sph": _f64(s.sphere).reshape(-1, 4),
+            "half": _f64(s.half), "init": _f64(s.init), "box": _f64(s.box),
+        }
+        a = self._arrays
+        dp = lambda x: x.ctypes.data_as(_D)   # noqa: E731
+        self._robot = _Robot(7, dp(a["dh"]), dp(a["qlim"]), len(a["sphere_link"]), a["sphere_link"].ctypes.data_as(_I),
+                             dp(a["sphere"]), dp(a["ee"]), dp(a["q_home"]))
+        self._obs = _Obstacles(len(a["cub"]), dp(a["cub"]), len(a["sph"]), dp(a["sph"]))
+        self._goal = _Goal(len(a["half"]), dp(a["half"]), dp(a["init"]), dp(a["box"]), float(s.z_table),
+                           float(s.grasp_off))
+        p = _Params()
+        for n in _INT_PARAMS:
+            setattr(p, n, int(prm[n]))
+        for n in _DBL_PARAMS:
+            setattr(p, n, float(prm[n]))
+        p.seed = int(prm["seed"]) & 0xFFFFFFFFFFFFFFFF
+        p.max_steps = int(prm["max_steps"])
+        self._params = p
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream().cuda_stream
+        self.stream = int(stream)
+        h = _V()
+        _check(lib().spasm_create_problem(ctypes.byref(self._robot), ctypes.byref(self._obs), ctypes.byref(self._goal),
+                                          ctypes.byref(self._params), _V(self.stream), ctypes.byref(h)))
+        self.handle = h
+        C, NR = ctypes.c_int32(), ctypes.c_int32()
+        _check(lib().spasm_sizes(h, ctypes.byref(C), ctypes.byref(NR)))
+        self.B = len(a["half"])
+        self.C, self.NR = C.value, NR.value
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().spasm_destroy_problem(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ----------------------------------------------------------------------- entry points
+def spasm_place(problem: Problem):
+    _check(lib().spasm_place(problem.handle))
+
+
+def spasm_optimize(problem: Problem):
+    _check(lib().spasm_optimize(problem.handle))
+
+
+def spasm_result(problem: Problem, allow_empty: bool = False) -> dict:
+    P, B, C = int(problem.params["P"]), problem.B, problem.C
+    nf = ctypes.c_int32()
+    place = np.zeros((P, B, 4))
+    traj = np.zeros((P, C, 7))
+    cost = np.zeros(P)
+    succ = np.zeros(P, dtype=np.int32)
+    st = lib().spasm_result(problem.handle, ctypes.byref(nf), place.ctypes.data_as(_D), traj.ctypes.data_as(_D),
+                            cost.ctypes.data_as(_D), succ.ctypes.data_as(_I))
+    if st != SPASM_OK and not (allow_empty and st == -4):
+        _check(st)
+    n = nf.value
+    return {"n_found": n, "placements": place, "traj": traj[:n], "cost": cost[:n], "success": succ[:n]}
+
+
+def spasm_place_sample(problem: Problem, n: int, attempt: int, x, cost):
+    _check(lib().spasm_place_sample(problem.handle, n, attempt, _dev(x), _dev(cost)))
+
+
+def spasm_place_eval(problem: Problem, n: int, x, quadratic: int, cost, grad=None, metrics=None, terms=None):
+    _check(lib().spasm_place_eval(problem.handle, n, _dev(x), int(quadratic), _dev(cost), _dev(grad), _dev(metrics),
+                                  _dev(terms)))
+
+
+def spasm_place_descend(problem: Problem, n: int, x, k_lin: int, k_quad: int, cost=None, sat=None):
+    _check(lib().spasm_place_descend(problem.handle, n, _dev(x), k_lin, k_quad, _dev(cost), _dev(sat)))
+
+
+def spasm_select_topk(problem: Problem, n: int, cost, k: int, idx):
+    _check(lib().spasm_select_topk(problem.handle, n, _dev(cost), k, _dev(idx)))
+
+
+def spasm_lift(problem: Problem, n: int, placements, n_place: int, attempt: int, q):
+    _check(lib().spasm_lift(problem.handle, n, _dev(placements), n_place, attempt, _dev(q)))
+
+
+def spasm_traj_eval(problem: Problem, n: int, q, lam, mu, L, grad=None, groups=None, h=None):
+    _check(lib().spasm_traj_eval(problem.handle, n, _dev(q), _dev(lam), _dev(mu), _dev(L), _dev(grad), _dev(groups),
+                                 _dev(h)))
+
+
+def spasm_traj_descend(problem: Problem, n: int, q, lam, mu, k_steps: int, init_multipliers: int, metrics=None,
+                       sat=None):
+    _check(lib().spasm_traj_descend(problem.handle, n, _dev(q), _dev(lam), _dev(mu), int(k_steps),
+                                    int(init_multipliers), _dev(metrics), _dev(sat)))

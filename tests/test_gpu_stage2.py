@@ -1,0 +1,124 @@
+"""Stage-2 parity: lift, trajectory objective/gradient/residuals and descent of the CUDA
+path vs the FP64 oracle on identical inputs."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2510_07674_gb300 import scenes
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+RTOL = 1e-4
+
+
+def _S():
+    from paper_2510_07674_gb300 import spasm as S
+    return S
+
+
+def _to_dev(qs, C):
+    n = len(qs)
+    q = torch.zeros(n, C, 8, device="cuda")
+    q[:, :, :7] = torch.from_numpy(np.asarray(qs)).float()
+    return q
+
+
+def _cases(name, seed, n, sigma, **kw):
+    wl = scenes.make_problem(name, seed=seed, **kw)
+    orc = O.Oracle(wl, n_threads=8)
+    sol, _, _ = orc.place_solve()
+    rng = np.random.default_rng(seed)
+    qs = []
+    for p in range(n):
+        q = orc.lift(sol[p % len(sol)], p)
+        q[1:] += rng.normal(0, sigma, q[1:].shape)
+        q = np.clip(q, wl.robot.qlim[:, 0], wl.robot.qlim[:, 1])
+        qs.append(q)
+    return wl, orc, sol, qs
+
+
+@pytest.mark.parametrize("name,seed,n,sigma,kw", [
+    ("tower1", 0, 9, 0.05, {}),
+    ("tower4", 1, 5, 0.15, {"B": 3, "O": 12, "W": 8}),
+    ("tower4", 2, 3, 0.2, {}),
+])
+def test_traj_eval_matches_oracle(name, seed, n, sigma, kw):
+    S = _S()
+    wl, orc, _, qs = _cases(name, seed, n, sigma, **kw)
+    pr = S.Problem(wl)
+    C, NR = pr.C, pr.NR
+    q = _to_dev(qs, C)
+    rng = np.random.default_rng(9)
+    lam_np = rng.uniform(0, 2, (n, NR)).astype(np.float32)
+    mu_np = rng.uniform(0.5, 4, n).astype(np.float32)
+    lam, mu = torch.from_numpy(lam_np).cuda(), torch.from_numpy(mu_np).cuda()
+    L, grad = torch.empty(n, device="cuda"), torch.empty(n, C, 8, device="cuda")
+    groups, h = torch.empty(n, 6, device="cuda"), torch.empty(n, NR, device="cuda")
+    S.spasm_traj_eval(pr, n, q, lam, mu, L, grad, groups, h)
+    torch.cuda.synchronize()
+    active = 0
+    for p in range(n):
+        qp = q[p, :, :7].cpu().double().numpy()
+        Lo, go, cgo, path, jl, ho = orc.traj_cost(qp, lam_np[p].astype(np.float64), float(mu_np[p]))
+        active += cgo[1] > 0 or cgo[2] > 0
+        assert abs(L[p].item() - Lo) <= RTOL * max(abs(Lo), 1e-2), (p, L[p].item(), Lo)
+        np.testing.assert_allclose(groups[p].cpu().double().numpy(), cgo, rtol=1e-3, atol=1e-6)
+        np.testing.assert_allclose(h[p].cpu().double().numpy(), ho, rtol=1e-3, atol=1e-5)
+        gd = grad[p, :, :7].cpu().double().numpy()
+        err = np.linalg.norm(gd - go) / max(np.linalg.norm(go), 1e-2)
+        assert err <= RTOL, (p, err)
+        assert np.all(grad[p, :, 7].cpu().numpy() == 0)
+    assert active > 0
+
+
+def test_lift_matches_oracle():
+    S = _S()
+    wl = scenes.make_problem("tower4", seed=3, B=3, O=8, W=10)
+    orc = O.Oracle(wl)
+    sol, _, _ = orc.place_solve()
+    pr = S.Problem(wl)
+    n = 24
+    place = torch.from_numpy(sol.reshape(len(sol), -1)).float().cuda().contiguous()
+    q = torch.zeros(n, pr.C, 8, device="cuda")
+    S.spasm_lift(pr, n, place, len(sol), 2, q)
+    torch.cuda.synchronize()
+    ps = place.cpu().double().numpy().reshape(len(sol), pr.B, 4)
+    close = 0
+    for p in range(n):
+        qo = orc.lift(ps[p % len(sol)], p, attempt=2)
+        qg = q[p, :, :7].cpu().double().numpy()
+        err = np.abs(qg - qo).max()
+        close += err < 1e-3
+        # every IK endpoint reaches its target in both implementations or in neither
+    assert close >= int(0.9 * n), close
+
+
+def test_descend_matches_oracle_few_steps():
+    S = _S()
+    wl, orc, _, qs = _cases("tower1", 4, 6, 0.05)
+    pr = S.Problem(wl)
+    q = _to_dev(qs, pr.C)
+    q0 = [q[p, :, :7].cpu().double().numpy() for p in range(len(qs))]
+    lam = torch.zeros(len(qs), pr.NR, device="cuda")
+    mu = torch.full((len(qs),), float(wl.params.mu0), device="cuda")
+    S.spasm_traj_descend(pr, len(qs), q, lam, mu, 4, 1)
+    torch.cuda.synchronize()
+    qr, lr, mr = orc.traj_descend(np.stack(q0), k_steps=4)
+    for p in range(len(qs)):
+        err = np.abs(q[p, :, :7].cpu().double().numpy() - qr[p]).max()
+        assert err < 1e-4, (p, err)
+
+
+def test_optimize_end_to_end_tower1():
+    """Both stages on the device; every returned trajectory passes the FP64 oracle check."""
+    S = _S()
+    wl = scenes.make_problem("tower1", seed=0)
+    orc = O.Oracle(wl, eps=wl.params.eps * 1.05, eps_start=wl.params.eps_start * 1.05)
+    pr = S.Problem(wl)
+    S.spasm_optimize(pr)
+    res = S.spasm_result(pr)
+    assert res["n_found"] >= 1
+    for q in res["traj"]:
+        ok, m = orc.traj_check(q)
+        assert ok, m
