@@ -1,0 +1,382 @@
+#!/usr/bin/env python
+"""Benchmark of the SPaSM hot path on GB300: 10-block tower solves (both stages).
+
+One step = one full solve of a seeded 10-block tower in clutter (64 cuboids, 16384 ->
+4096 placement particles, 4096 trajectory particles, 20 segments x 32 waypoints):
+stage-1 sampling, selection and descent, lift, fused trajectory optimisation, ranking
+and the FP64 check, all on the device.  Inputs (the problem tables) are resident in HBM
+before the timed region; L2 is flushed (256 MB write) between steps, outside the
+per-step CUDA events.
+
+Prints ONE JSON line on rank 0.  ``--impl reference`` times the FP64 CPU oracle instead
+(on the host cores, a bounded sample of the same workload per step, extrapolated to a
+solve).  Multi-GPU (torchrun): every rank solves its own problems (replicas, weak
+scaling); there is no data-path collective.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "10-block solve ms p50/p99; particle-iters/s; served solves/s vs plain form"
+WORKLOAD = "tower10"
+WORKLOAD_DESC = ("10-block tower in clutter: 64 random cuboids (sides 0.05-0.3 m) + table, 7-R arm with 52 spheres, "
+                 "N=16384 -> M=4096 placement particles, Q=4096 trajectory particles, 20 segments x 32 waypoints, "
+                 "FP32, Philox seeded; seed s = scene + Philox seed")
+# FP32 peak: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x max SM clock
+SM_COUNT, FP32_LANES = 152, 128
+# algorithmic FP32 flop of one sphere-cuboid test (transform to the cuboid frame and the
+# separation test: 3 sub + 9 mul/fma + 3 |p|-h + 2 max + 1 compare, FMA counted as 2)
+FLOP_PER_TEST = 24
+# forward kinematics of one configuration: 7 link transforms (27 fma + sincos each)
+FLOP_PER_CONFIG_FK = 7 * 40
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "k_traj_tower10.md")
+KERNEL_SOURCES = ["paper_2510_07674_gb300/csrc/kernels_s2.cu", "paper_2510_07674_gb300/csrc/stage2.cuh",
+                  "paper_2510_07674_gb300/csrc/common.cuh", "paper_2510_07674_gb300/csrc/stage1.cuh"]
+
+
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_from_profile():
+    """DRAM bytes per k_traj launch recorded by the committed ncu summary, if it was taken
+    on the current kernel sources (else None)."""
+    if not os.path.exists(PROFILE_SUMMARY):
+        return None
+    vals = {}
+    for line in open(PROFILE_SUMMARY):
+        if ":" in line and line.strip().startswith("- "):
+            k, v = line.strip()[2:].split(":", 1)
+            vals[k.strip()] = v.strip()
+    if vals.get("kernel_sources_sha256_16") != kernel_hash():
+        return None
+    try:
+        return float(vals["dram_bytes_per_full_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return float("nan")
+        sm = [num(r[1]) for r in rows]
+        power = [num(r[3]) for r in rows]
+        pmax = max(p for p in power if p == p) if any(p == p for p in power) else 0.0
+        loaded = [s for s, p in zip(sm, power) if p == p and p >= 0.5 * pmax] or sm
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(num(r[2]) for r in rows), "reasons": reasons,
+                "samples": len(rows), "power_w_max": pmax}
+
+
+def count_tests(wl) -> dict:
+    """Sphere-cuboid (and sphere-sphere) tests of one stage-2 particle-iteration."""
+    B = len(wl.scene.half)
+    S = wl.params.W - 1
+    C = 2 * B * S + 1
+    n_obs = len(wl.scene.cuboid) + len(wl.scene.sphere) + (B - 1)
+    n_rsph = len(wl.robot.sphere)
+    held_cfgs = B * (S - 1)
+    tests = (C - 1) * n_rsph * n_obs + held_cfgs * 8 * n_obs
+    return {"C": C, "tests": tests, "flop": FLOP_PER_TEST * tests + FLOP_PER_CONFIG_FK * (C - 1)}
+
+
+# ------------------------------------------------------------------------------- native
+def run_native(args, ws, rank, local):
+    import torch
+
+    from paper_2510_07674_gb300 import build as B
+    from paper_2510_07674_gb300 import scenes
+    from paper_2510_07674_gb300 import spasm as S
+
+    B.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    overrides = {"max_steps": args.max_steps}
+    n_total = args.warmup + args.steps
+    seeds = [rank * 100000 + i for i in range(n_total)]
+    wls = [scenes.make_problem(WORKLOAD, seed=s) for s in seeds]
+    probs = [S.Problem(w, **overrides) for w in wls]
+    for p in probs:
+        S.spasm_set_timing(p, True)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2
+
+    def solve(p):
+        S.spasm_reset_stats(p)
+        try:
+            S.spasm_optimize(p)
+        except S.SpasmError as e:   # no solution within max_steps: counted as a failure
+            if e.status != -4:
+                raise
+
+    for i in range(args.warmup):
+        solve(probs[i])
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    times, stats = [], []
+    for i in range(args.warmup, n_total):
+        flush.fill_(float(i))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        solve(probs[i])
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+        stats.append(S.spasm_get_stats(probs[i]))
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    wall = time.perf_counter() - wall0
+    clocks = sampler.stop()
+
+    total_ms = sum(times)
+    if ws > 1:
+        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = t.item()
+    ms_per_step = total_ms / args.steps
+    value = ws * args.steps / (total_ms / 1000.0)
+
+    tc = count_tests(wls[0])
+    traj_ms = sum(s["ms_traj"] for s in stats)
+    traj_launches = sum(s["traj_launches"] for s in stats)
+    pits = sum(s["particle_iters"] for s in stats)
+    K = wls[0].params.K_traj
+    Q = wls[0].params.Q
+    # one launch runs K descent iterations plus the final evaluation pass
+    flop_per_launch = Q * (K + 1) * tc["flop"]
+    avg_launch_s = traj_ms / max(traj_launches, 1) / 1000.0
+    achieved = flop_per_launch / avg_launch_s / 1e12 if avg_launch_s > 0 else None
+    clk = clocks.get("sm_max_mhz") or 2070.0
+    peak = SM_COUNT * FP32_LANES * 2 * clk * 1e6 / 1e12
+    traffic = traffic_from_profile()
+    roofline = {"bound": "alu", "kernel": "k_traj (fused stage-2 descent, one CTA per particle)",
+                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None,
+                "traffic": traffic, "peak_basis": f"152 SMs x 128 FP32 lanes x 2 x {clk:.0f} MHz (derived)",
+                "flop_per_launch": flop_per_launch, "avg_launch_ms": avg_launch_s * 1e3,
+                "tests_per_particle_iter": tc["tests"]}
+    succ = [s["n_success"] > 0 for s in stats]
+
+    # ---- end to end through the public API with host buffers
+    e2e_times, h2d, d2h = [], [], []
+    n_e2e = min(args.steps, args.e2e_steps)
+    for i in range(n_e2e):
+        wl = wls[args.warmup + i]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        p = S.Problem(wl, **overrides)
+        try:
+            S.spasm_optimize(p)
+        except S.SpasmError as e:
+            if e.status != -4:
+                raise
+        res = S.spasm_result(p, allow_empty=True)
+        st = S.spasm_get_stats(p)
+        p.close()
+        t1 = time.perf_counter()
+        e2e_times.append(t1 - t0)
+        h2d.append(st["h2d_bytes"])
+        d2h.append(st["d2h_bytes"])
+        del res
+    e2e_value = ws * len(e2e_times) / sum(e2e_times) if e2e_times else None
+
+    out = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 (FP64 final check)", "data": "synthetic",
+        "config": {"workload": WORKLOAD_DESC, "parallelism": f"replicas x{ws}", "l2": "flushed between steps "
+                   "(256 MB write outside the per-step events)", "max_steps": args.max_steps},
+        "solve_ms_p50": float(statistics.median(times)),
+        "solve_ms_p99": float(sorted(times)[min(len(times) - 1, math.ceil(0.99 * len(times)) - 1)]),
+        "particle_iters_per_s": pits / (total_ms / 1000.0) * ws,
+        "success_rate": sum(succ) / len(succ),
+        "attempts": {"stage1_mean": statistics.mean(s["place_attempts"] for s in stats),
+                     "stage2_mean": statistics.mean(s["traj_attempts"] for s in stats)},
+        "phase_ms_mean": {"stage1": statistics.mean(s["ms_place"] for s in stats),
+                          "lift": statistics.mean(s["ms_lift"] for s in stats),
+                          "traj": statistics.mean(s["ms_traj"] for s in stats),
+                          "finish": statistics.mean(s["ms_finish"] for s in stats)},
+        "wall_s": wall,
+        "roofline": roofline,
+        "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": statistics.mean(h2d) if h2d else 0,
+                "d2h_bytes_per_step": statistics.mean(d2h) if d2h else 0, "steps": len(e2e_times),
+                "path": "spasm_create_problem (host arrays) + spasm_optimize + spasm_result + destroy"},
+        "gpu_launches": int(sum(s["kernel_launches"] for s in stats)),
+        "clocks": clocks,
+        "kernel_sources_sha256_16": kernel_hash(),
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(wls[0], args.cpu_budget_s)
+    return out
+
+
+# ------------------------------------------------------------------------------- oracle
+def cpu_baseline(wl, budget_s: float) -> dict:
+    """The FP64 oracle, as it stands, on a bounded sample of the same workload: a stage-1
+    sample (cost of n particles, descent of m) and a stage-2 sample (descent steps of a
+    few lifted particles), extrapolated to one solve (N costs, M x (K_lin + K_quad)
+    descent steps, Q x K_traj trajectory particle-iterations)."""
+    import numpy as np
+
+    from oracle import oracle as O
+    cores = os.cpu_count() or 1
+    orc = O.Oracle(wl, n_threads=cores)
+    p = wl.params
+    t0 = time.perf_counter()
+    n1 = 256
+    x = orc.place_sample(n1)
+    ta = time.perf_counter()
+    for xi in x:
+        orc.place_cost(xi, grad=False)
+    t_cost = (time.perf_counter() - ta) / n1
+    m1 = 64
+    ta = time.perf_counter()
+    orc.place_descend(x[:m1])
+    t_desc = (time.perf_counter() - ta) / m1          # per particle, K_lin + K_quad steps
+    # stage 2: lift from a cheap placement (the stage-1 sample's best particle) and time
+    # descent steps of n2 particles
+    place = x[0]
+    n2 = max(cores, 4)
+    qs = np.stack([orc.lift(place, i) for i in range(n2)])
+    ta = time.perf_counter()
+    orc.traj_descend(qs, k_steps=1)
+    probe = time.perf_counter() - ta
+    # fill the rest of the budget with more descent steps of the same particles
+    k2 = max(1, int((0.6 * budget_s) / max(probe, 1e-3)))
+    ta = time.perf_counter()
+    orc.traj_descend(qs, k_steps=k2)
+    t_pi_wall = (time.perf_counter() - ta) / (n2 * k2)   # wall seconds per particle-iteration
+    spent = time.perf_counter() - t0
+    t_solve = p.N * t_cost / cores + p.M * t_desc + p.Q * p.K_traj * t_pi_wall
+    return {"value": 1.0 / t_solve, "unit": "solves/s", "cores": cores, "kind": "oracle",
+            "sample": (f"stage 1: cost of {n1} particles (serial) and descent of {m1} particles ({cores} threads); "
+                       f"stage 2: {k2} descent step(s) of {n2} lifted particles ({cores} threads); "
+                       f"extrapolated to N={p.N} costs, M={p.M} descents, Q x K_traj={p.Q}x{p.K_traj} "
+                       f"particle-iterations; {spent:.1f} s of CPU work"),
+            "particle_iters_per_s": 1.0 / t_pi_wall, "seconds_per_solve": t_solve}
+
+
+def run_reference(args, ws, rank, local):
+    from paper_2510_07674_gb300 import scenes
+    times = []
+    last = None
+    for i in range(args.warmup + args.steps):
+        wl = scenes.make_problem(WORKLOAD, seed=i)
+        cb = cpu_baseline(wl, args.cpu_budget_s)
+        if i >= args.warmup:
+            times.append(cb["seconds_per_solve"] * 1000.0)
+        last = cb
+    ms = statistics.mean(times)
+    value = 1000.0 / ms
+    return {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD_DESC, "parallelism": "host cores"},
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": last["cores"], "kind": "oracle",
+                             "sample": "per step: " + last["sample"]},
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["native", "reference"], default="native")
+    ap.add_argument("--max-steps", type=int, default=1000,
+                    help="cap on gradient steps per stage (re-initialisation budget)")
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--cpu-budget-s", type=float, default=20.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        print(json.dumps(run_reference(args, ws, rank, local)), flush=True)
+        return
+    if ws > 1:
+        import torch
+        torch.distributed.init_process_group("nccl")
+    out = run_native(args, ws, rank, local)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if ws > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -124,7 +124,9 @@ spasm_status spasm_optimize(spasm_problem_t problem);
 
 /* Copy results to host memory (synchronises).  Any output pointer may be NULL.
  * n_found: number of returned solutions (<= P); placements: P x B x 4;
- * traj: P x C x 7; cost: P (ranking cost); success: P (1 if the FP64 check passed).
+ * traj: P x C x 7; cost: P (ranking cost, ascending); success: P (1 if the solution
+ * passes the FP64 re-evaluation of every penetration, the grasp and tilt errors, the
+ * placement conditions and the joint limits). 
  * Returns SPASM_ERR_NOSOLUTION if stage 2 found nothing. */
 spasm_status spasm_result(spasm_problem_t problem, int* n_found, double* placements, double* traj, double* cost,
                           int* success);
@@ -176,6 +178,36 @@ spasm_status spasm_traj_eval(spasm_problem_t problem, int n, const float* q, con
  * 0 and mu0.  metrics: device n x 8 or NULL; sat: device n or NULL (final check). */
 spasm_status spasm_traj_descend(spasm_problem_t problem, int n, float* q, float* lam, float* mu, int k_steps,
                                 int init_multipliers, float* metrics, int* sat);
+
+/* ---- run control and statistics (not in the paper: bookkeeping of this library) ---- */
+
+/* Counters and device times of the last spasm_place / spasm_optimize calls since the
+ * last reset.  Times are CUDA-event durations on the problem's stream and are filled only
+ * while timing is enabled. */
+typedef struct {
+    int place_attempts;        /* Alg. 1 attempts (re-initialisations + 1) */
+    int traj_attempts;         /* stage-2 lift + descent attempts */
+    int n_found;               /* solutions returned */
+    int n_success;             /* of those, passing the FP64 check */
+    long long kernel_launches; /* kernels launched by spasm_place / spasm_optimize */
+    int traj_launches;         /* launches of the fused trajectory-descent kernel */
+    long long particle_iters;  /* stage-2 particle-iterations executed (Q x K_traj x attempts) */
+    double ms_place;           /* stage 1, all attempts */
+    double ms_lift;            /* stage-2 lifts */
+    double ms_traj;            /* fused trajectory-descent kernels */
+    double ms_finish;          /* ranking, selection and FP64 check */
+    long long h2d_bytes;       /* host -> device bytes copied by create / place / optimize */
+    long long d2h_bytes;       /* device -> host bytes copied by place / optimize / result */
+} spasm_stats;
+
+/* Replace the Philox seed (the key of every random stream) and forget previous results;
+ * the next spasm_optimize re-runs both stages. */
+spasm_status spasm_set_seed(spasm_problem_t problem, uint64_t seed);
+/* Enable (1) or disable (0) CUDA-event timing of the phases. */
+spasm_status spasm_set_timing(spasm_problem_t problem, int enable);
+/* Copy the statistics (host struct); spasm_reset_stats zeroes them. */
+spasm_status spasm_get_stats(spasm_problem_t problem, spasm_stats* out);
+spasm_status spasm_reset_stats(spasm_problem_t problem);
 
 #ifdef __cplusplus
 }

@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "../../include/spasm.h"
+#include "check64.h"
 #include "launch_s2.h"
 #include "stage2.cuh"
 
@@ -51,7 +52,29 @@ struct spasm_problem {
     bool optimized = false;
     int n_found = 0, traj_attempts = 0;
     std::vector<double> host_cub, host_osph;
+    // FP64 final check
+    Scalars64 s64;
+    double* d_cub64 = nullptr;
+    double* d_osph64 = nullptr;
+    double* d_rmet64 = nullptr;
+    // statistics and timing
+    spasm_stats stats{};
+    bool timing = false;
+    cudaEvent_t ev[8] = {};
 };
+
+static void count_launches(spasm_problem* pr, int n) { pr->stats.kernel_launches += n; }
+
+static float ev_ms(cudaEvent_t a, cudaEvent_t b) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, a, b) != cudaSuccess) return 0.f;
+    return ms;
+}
+
+static spasm_status rec(spasm_problem* pr, int i) {
+    if (pr->timing) SPASM_CUDA(cudaEventRecord(pr->ev[i], pr->stream));
+    return SPASM_OK;
+}
 
 template <typename T>
 static spasm_status dalloc(T** p, size_t count) {
@@ -71,6 +94,7 @@ static spasm_status check_device_error(spasm_problem* pr) {
     int err = 0;
     SPASM_CUDA(cudaMemcpyAsync(&err, pr->d_err, sizeof(int), cudaMemcpyDeviceToHost, pr->stream));
     SPASM_CUDA(cudaStreamSynchronize(pr->stream));
+    pr->stats.d2h_bytes += sizeof(int);
     if (err != 0) {
         const char* what = err == kDevTimeout ? "a bounded device wait gave up" : "a kernel rejected its sizes";
         return fail(SPASM_ERR_DEVICE, std::string("device error ") + std::to_string(err) + ": " + what);
@@ -82,9 +106,11 @@ static void free_all(spasm_problem* pr) {
     void* ptrs[] = {pr->d_cub, pr->d_osph, pr->d_err, pr->d_xs, pr->d_cost, pr->d_xm, pr->d_costm, pr->d_masked,
                     pr->d_idx, pr->d_sat, pr->d_nsat, pr->d_best, pr->d_place, pr->d_nplace, pr->d_q, pr->d_lam,
                     pr->d_mu, pr->d_metrics, pr->d_tmasked, pr->d_tsat, pr->d_tnsat, pr->d_tbest, pr->d_rq,
-                    pr->d_rcost, pr->d_rsucc, pr->d_user_np};
+                    pr->d_rcost, pr->d_rsucc, pr->d_user_np, pr->d_cub64, pr->d_osph64, pr->d_rmet64};
     for (void* p : ptrs)
         if (p) cudaFree(p);
+    for (cudaEvent_t e : pr->ev)
+        if (e) cudaEventDestroy(e);
 }
 
 extern "C" const char* spasm_last_error(void) { return g_last_error.c_str(); }
@@ -179,6 +205,44 @@ extern "C" spasm_status spasm_create_problem(const spasm_robot* robot, const spa
         osph[o] = make_float4((float)s[0], (float)s[1], (float)s[2], (float)s[3]);
     }
     pr->host_cub.assign(obs->cuboid, obs->cuboid + 15 * (size_t)sc.n_cub);
+    std::vector<double> cub64(16 * (size_t)sc.n_cub), osph64(4 * (size_t)sc.n_osph);
+    for (int o = 0; o < sc.n_cub; ++o) {
+        const double* c = obs->cuboid + 15 * o;
+        double* d = &cub64[16 * (size_t)o];
+        d[0] = c[0]; d[1] = c[1]; d[2] = c[2]; d[3] = 0.0;
+        for (int k = 0; k < 3; ++k) {
+            d[4 + 4 * k] = c[3 + k]; d[5 + 4 * k] = c[6 + k]; d[6 + 4 * k] = c[9 + k]; d[7 + 4 * k] = c[12 + k];
+        }
+    }
+    for (int o = 0; o < 4 * sc.n_osph; ++o) osph64[o] = obs->sphere[o];
+    {
+        Scalars64& q = pr->s64;
+        std::memset(&q, 0, sizeof q);
+        q.B = B; q.S = S; q.C = C; q.n_rsph = sc.n_rsph; q.n_cub = sc.n_cub; q.n_osph = sc.n_osph;
+        for (int k = 0; k < 7; ++k) {
+            const double* row = robot->dh + 4 * k;
+            q.a[k] = row[0]; q.ca[k] = std::cos(row[1]); q.sa[k] = std::sin(row[1]); q.d[k] = row[2]; q.th0[k] = row[3];
+            q.qlo[k] = robot->qlim[2 * k]; q.qhi[k] = robot->qlim[2 * k + 1];
+        }
+        for (int i = 0; i < 3; ++i) {
+            for (int j = 0; j < 3; ++j) q.ee_R[3 * i + j] = robot->ee[4 * i + j];
+            q.ee_p[i] = robot->ee[4 * i + 3];
+        }
+        for (int i = 0; i < sc.n_rsph; ++i) {
+            for (int k = 0; k < 4; ++k) q.rsph[i][k] = robot->sphere[4 * i + k];
+            q.rlink[i] = robot->sphere_link[i];
+        }
+        double zz = goal->z_table;
+        for (int i = 0; i < B; ++i) {
+            const double* hh = goal->half_ext + 3 * i;
+            for (int k = 0; k < 3; ++k) q.half[i][k] = hh[k];
+            q.hmin[i] = std::fmin(hh[0], std::fmin(hh[1], hh[2]));
+            for (int k = 0; k < 4; ++k) q.init[i][k] = goal->init_pose[4 * i + k];
+            q.zt[i] = zz + hh[2];
+            zz += 2.0 * hh[2];
+        }
+        q.grasp_off = goal->grasp_off; q.eps = prm->eps; q.eps_start = prm->eps_start;
+    }
     pr->host_osph.assign(obs->sphere, obs->sphere + 4 * (size_t)sc.n_osph);
 
     const int N = prm->N, M = prm->M, P = prm->P, Q = prm->Q, NR = sc.NR;
@@ -211,7 +275,12 @@ extern "C" spasm_status spasm_create_problem(const spasm_robot* robot, const spa
     ALLOC(pr->d_rcost, P);
     ALLOC(pr->d_rsucc, P);
     ALLOC(pr->d_user_np, 1);
+    ALLOC(pr->d_cub64, (size_t)16 * sc.n_cub);
+    ALLOC(pr->d_osph64, (size_t)4 * sc.n_osph);
+    ALLOC(pr->d_rmet64, (size_t)6 * P);
 #undef ALLOC
+    for (auto& ev : pr->ev)
+        if (st == SPASM_OK && cudaEventCreate(&ev) != cudaSuccess) st = fail(SPASM_ERR_CUDA, "cudaEventCreate failed");
     if (st != SPASM_OK) { free_all(pr); delete pr; return st; }
     pr->tab.cub = pr->d_cub;
     pr->tab.osph = pr->d_osph;
@@ -219,6 +288,10 @@ extern "C" spasm_status spasm_create_problem(const spasm_robot* robot, const spa
     if (!cub.empty()) e = cudaMemcpyAsync(pr->d_cub, cub.data(), cub.size() * sizeof(float4), cudaMemcpyHostToDevice, pr->stream);
     if (e == cudaSuccess && !osph.empty())
         e = cudaMemcpyAsync(pr->d_osph, osph.data(), osph.size() * sizeof(float4), cudaMemcpyHostToDevice, pr->stream);
+    if (e == cudaSuccess && !cub64.empty())
+        e = cudaMemcpyAsync(pr->d_cub64, cub64.data(), cub64.size() * sizeof(double), cudaMemcpyHostToDevice, pr->stream);
+    if (e == cudaSuccess && !osph64.empty())
+        e = cudaMemcpyAsync(pr->d_osph64, osph64.data(), osph64.size() * sizeof(double), cudaMemcpyHostToDevice, pr->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(pr->d_err, 0, sizeof(int), pr->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(pr->stream);
     if (e != cudaSuccess) {
@@ -226,6 +299,8 @@ extern "C" spasm_status spasm_create_problem(const spasm_robot* robot, const spa
         delete pr;
         return fail(SPASM_ERR_CUDA, std::string("create: ") + cudaGetErrorString(e));
     }
+    pr->stats.h2d_bytes += (long long)(cub.size() * sizeof(float4) + osph.size() * sizeof(float4) +
+                                       cub64.size() * sizeof(double) + osph64.size() * sizeof(double));
     const size_t need = traj_smem_bytes(sc);
     int dev = 0, max_smem = 0;
     cudaGetDevice(&dev);
@@ -275,20 +350,27 @@ extern "C" spasm_status spasm_place(spasm_problem_t pr) {
     if (!pr) return fail(SPASM_ERR_INVALID, "null problem");
     const int per = pr->sc.K_lin + pr->sc.K_quad;
     int steps = 0, attempt = 0, found = 0;
+    SPASM_TRY(rec(pr, 0));
     while (steps < pr->prm.max_steps || attempt == 0) {
         SPASM_TRY(place_attempt(pr, (uint32_t)attempt));
+        count_launches(pr, 6);
         steps += per;
         ++attempt;
         int nsat = 0;
         SPASM_CUDA(cudaMemcpyAsync(&nsat, pr->d_nsat, sizeof(int), cudaMemcpyDeviceToHost, pr->stream));
         SPASM_CUDA(cudaStreamSynchronize(pr->stream));
+        pr->stats.d2h_bytes += sizeof(int);
         if (nsat > 0) { found = nsat < pr->sc.P ? nsat : pr->sc.P; break; }
     }
+    SPASM_TRY(rec(pr, 1));
     pr->place_attempts = attempt;
     pr->place_steps = steps;
     pr->n_place = found;
+    pr->stats.place_attempts += attempt;
     SPASM_CUDA(cudaMemcpyAsync(pr->d_nplace, &pr->n_place, sizeof(int), cudaMemcpyHostToDevice, pr->stream));
+    pr->stats.h2d_bytes += sizeof(int);
     SPASM_TRY(check_device_error(pr));
+    if (pr->timing) pr->stats.ms_place += ev_ms(pr->ev[0], pr->ev[1]);
     pr->placed = true;
     if (found == 0) return fail(SPASM_ERR_NOSOLUTION, "stage 1 found no satisfying placement within max_steps");
     return SPASM_OK;
@@ -298,11 +380,17 @@ extern "C" spasm_status spasm_place(spasm_problem_t pr) {
 static spasm_status traj_attempt(spasm_problem* pr, uint32_t attempt) {
     const Scalars& sc = pr->sc;
     cudaStream_t s = pr->stream;
+    SPASM_TRY(rec(pr, 2));
     SPASM_CUDA(launch_lift(sc, sc.Q, pr->d_place, pr->d_nplace, attempt, pr->d_q, s));
+    SPASM_TRY(rec(pr, 3));
     TrajIO io{};
     io.q = pr->d_q; io.lam = pr->d_lam; io.mu = pr->d_mu; io.metrics = pr->d_metrics; io.sat = pr->d_tsat;
     io.k_steps = sc.K_traj; io.init_multipliers = 1;
     SPASM_CUDA(launch_traj(sc, pr->tab, sc.Q, kTrajModeDescend, io, pr->d_err, s));
+    SPASM_TRY(rec(pr, 4));
+    count_launches(pr, 3);
+    pr->stats.traj_launches += 1;
+    pr->stats.particle_iters += (long long)sc.Q * sc.K_traj;
     return SPASM_OK;
 }
 
@@ -343,20 +431,43 @@ extern "C" spasm_status spasm_optimize(spasm_problem_t pr) {
         SPASM_CUDA(cudaGetLastError());
         SPASM_CUDA(launch_mask_costs(pr->d_tmasked, pr->d_tsat, sc.Q, pr->d_tmasked, pr->d_tnsat, s));
         int nsat = 0;
+        count_launches(pr, 2);
         SPASM_CUDA(cudaMemcpyAsync(&nsat, pr->d_tnsat, sizeof(int), cudaMemcpyDeviceToHost, s));
         SPASM_CUDA(cudaStreamSynchronize(s));
+        pr->stats.d2h_bytes += sizeof(int);
+        if (pr->timing) {
+            pr->stats.ms_lift += ev_ms(pr->ev[2], pr->ev[3]);
+            pr->stats.ms_traj += ev_ms(pr->ev[3], pr->ev[4]);
+        }
         if (nsat > 0) { found = nsat < sc.P ? nsat : sc.P; break; }
     }
     pr->traj_attempts = attempt;
+    pr->stats.traj_attempts += attempt;
     if (found > 0) {
         if (sc.Q > 32768) return fail(SPASM_ERR_INVALID, "Q > 32768 unsupported by the selection kernel");
+        SPASM_TRY(rec(pr, 5));
         SPASM_CUDA(launch_topk(pr->d_tmasked, sc.Q, sc.P, pr->d_tbest, nullptr, s));
         k_gather_solutions<<<sc.P, 256, 0, s>>>(pr->d_q, pr->d_metrics, pr->d_tbest, pr->d_tnsat, sc.P, sc.C, pr->d_rq,
                                                  pr->d_rcost, pr->d_rsucc);
         SPASM_CUDA(cudaGetLastError());
+        // FP64 re-evaluation of the returned solutions decides their success flags
+        SPASM_CUDA(launch_check64(pr->s64, pr->d_cub64, pr->d_osph64, pr->d_rq, pr->d_tnsat, sc.P, pr->d_rmet64,
+                                  pr->d_rsucc, s));
+        SPASM_TRY(rec(pr, 6));
+        count_launches(pr, 3);
     }
     pr->n_found = found;
     SPASM_TRY(check_device_error(pr));
+    if (found > 0) {
+        std::vector<int> succ(sc.P, 0);
+        SPASM_CUDA(cudaMemcpy(succ.data(), pr->d_rsucc, sc.P * sizeof(int), cudaMemcpyDeviceToHost));
+        pr->stats.d2h_bytes += sc.P * sizeof(int);
+        int ns = 0;
+        for (int r = 0; r < found; ++r) ns += succ[r] != 0;
+        pr->stats.n_success = ns;
+        if (pr->timing) pr->stats.ms_finish += ev_ms(pr->ev[5], pr->ev[6]);
+    }
+    pr->stats.n_found = found;
     pr->optimized = true;
     if (found == 0) return fail(SPASM_ERR_NOSOLUTION, "stage 2 found no satisfying trajectory within max_steps");
     return SPASM_OK;
@@ -372,11 +483,13 @@ extern "C" spasm_status spasm_result(spasm_problem_t pr, int* n_found, double* p
     if (placements) {
         std::vector<float> tmp((size_t)P * B * 4, 0.f);
         SPASM_CUDA(cudaMemcpy(tmp.data(), pr->d_place, tmp.size() * sizeof(float), cudaMemcpyDeviceToHost));
+        pr->stats.d2h_bytes += tmp.size() * sizeof(float);
         for (size_t i = 0; i < tmp.size(); ++i) placements[i] = tmp[i];
     }
     if (traj) {
         std::vector<float> tmp((size_t)P * C * 8, 0.f);
         SPASM_CUDA(cudaMemcpy(tmp.data(), pr->d_rq, tmp.size() * sizeof(float), cudaMemcpyDeviceToHost));
+        pr->stats.d2h_bytes += tmp.size() * sizeof(float);
         for (int r = 0; r < P; ++r)
             for (int t = 0; t < C; ++t)
                 for (int j = 0; j < 7; ++j) traj[((size_t)r * C + t) * 7 + j] = tmp[((size_t)r * C + t) * 8 + j];
@@ -384,9 +497,13 @@ extern "C" spasm_status spasm_result(spasm_problem_t pr, int* n_found, double* p
     if (cost) {
         std::vector<float> tmp(P, 0.f);
         SPASM_CUDA(cudaMemcpy(tmp.data(), pr->d_rcost, P * sizeof(float), cudaMemcpyDeviceToHost));
+        pr->stats.d2h_bytes += P * sizeof(float);
         for (int r = 0; r < P; ++r) cost[r] = tmp[r];
     }
-    if (success) SPASM_CUDA(cudaMemcpy(success, pr->d_rsucc, P * sizeof(int), cudaMemcpyDeviceToHost));
+    if (success) {
+        SPASM_CUDA(cudaMemcpy(success, pr->d_rsucc, P * sizeof(int), cudaMemcpyDeviceToHost));
+        pr->stats.d2h_bytes += P * sizeof(int);
+    }
     if (!pr->optimized || pr->n_found == 0) return fail(SPASM_ERR_NOSOLUTION, "no solution");
     return SPASM_OK;
 }
@@ -451,5 +568,33 @@ extern "C" spasm_status spasm_traj_descend(spasm_problem_t pr, int n, float* q, 
     io.q = q; io.lam = lam; io.mu = mu; io.metrics = metrics; io.sat = sat;
     io.k_steps = k_steps; io.init_multipliers = init_multipliers;
     SPASM_CUDA(launch_traj(pr->sc, pr->tab, n, kTrajModeDescend, io, pr->d_err, pr->stream));
+    return SPASM_OK;
+}
+
+extern "C" spasm_status spasm_set_seed(spasm_problem_t pr, uint64_t seed) {
+    if (!pr) return fail(SPASM_ERR_INVALID, "null problem");
+    SPASM_CUDA(cudaStreamSynchronize(pr->stream));
+    pr->sc.seed = seed;
+    pr->prm.seed = seed;
+    pr->placed = pr->optimized = false;
+    pr->n_place = pr->n_found = 0;
+    return SPASM_OK;
+}
+
+extern "C" spasm_status spasm_set_timing(spasm_problem_t pr, int enable) {
+    if (!pr) return fail(SPASM_ERR_INVALID, "null problem");
+    pr->timing = enable != 0;
+    return SPASM_OK;
+}
+
+extern "C" spasm_status spasm_get_stats(spasm_problem_t pr, spasm_stats* out) {
+    if (!pr || !out) return fail(SPASM_ERR_INVALID, "null argument");
+    *out = pr->stats;
+    return SPASM_OK;
+}
+
+extern "C" spasm_status spasm_reset_stats(spasm_problem_t pr) {
+    if (!pr) return fail(SPASM_ERR_INVALID, "null problem");
+    pr->stats = spasm_stats{};
     return SPASM_OK;
 }

@@ -1,0 +1,216 @@
+// FP64 feasibility check of returned trajectories (GetSatisfyingParticles applied to the
+// final solutions, |f(x)| < eps of Sec. III), evaluated in double precision on the
+// float32 joint values the optimiser returned.  One CTA per solution: threads over
+// configurations for the arm / held-block penetrations, then the grasp, tilt and
+// placement metrics.
+#include "check64.h"
+#include "stage2.cuh"
+
+namespace spasm {
+
+__device__ __forceinline__ void fk64(const Scalars64& s, const double q[7], double R[8][9], double o[8][3],
+                                     double Rt[9], double pt[3]) {
+    for (int i = 0; i < 9; ++i) R[0][i] = (i % 4 == 0) ? 1.0 : 0.0;
+    o[0][0] = o[0][1] = o[0][2] = 0.0;
+    for (int k = 0; k < 7; ++k) {
+        double sn, cs;
+        sincos(s.th0[k] + q[k], &sn, &cs);
+        for (int i = 0; i < 9; ++i) R[k + 1][i] = R[k][i];
+        for (int i = 0; i < 3; ++i) o[k + 1][i] = o[k][i];
+        dh_step<double>(R[k + 1], o[k + 1], s.ca[k], s.sa[k], s.a[k], s.d[k], cs, sn);
+    }
+    for (int i = 0; i < 3; ++i) {
+        for (int j = 0; j < 3; ++j)
+            Rt[3 * i + j] = R[7][3 * i] * s.ee_R[j] + R[7][3 * i + 1] * s.ee_R[3 + j] + R[7][3 * i + 2] * s.ee_R[6 + j];
+        pt[i] = o[7][i] + R[7][3 * i] * s.ee_p[0] + R[7][3 * i + 1] * s.ee_p[1] + R[7][3 * i + 2] * s.ee_p[2];
+    }
+}
+
+__device__ __forceinline__ void held64(const Scalars64& s, int b, const double Rt[9], const double pt[3], double Rb[9],
+                                       double pb[3]) {
+    const double off = s.half[b][2] + s.grasp_off;
+    for (int i = 0; i < 3; ++i) {
+        Rb[3 * i] = Rt[3 * i];
+        Rb[3 * i + 1] = -Rt[3 * i + 1];
+        Rb[3 * i + 2] = -Rt[3 * i + 2];
+        pb[i] = pt[i] + off * Rt[3 * i + 2];
+    }
+}
+
+struct D4 { double x, y, z, w; };
+
+__device__ __forceinline__ void block_cub64(const double pose[4], const double h[3], D4 c[4]) {
+    double sn, cs;
+    sincos(pose[3], &sn, &cs);
+    c[0] = D4{pose[0], pose[1], pose[2], 0.0};
+    c[1] = D4{cs, sn, 0.0, h[0]};
+    c[2] = D4{-sn, cs, 0.0, h[1]};
+    c[3] = D4{0.0, 0.0, 1.0, h[2]};
+}
+
+__device__ __forceinline__ double pen_env64(const Scalars64& s, const D4* cub, const D4* osph, double cx, double cy,
+                                            double cz, double r) {
+    double m = 0.0, gx, gy, gz;
+    for (int o = 0; o < s.n_cub; ++o)
+        m = fmax(m, pen_cuboid<double>(cx, cy, cz, r, cub[4 * o], cub[4 * o + 1], cub[4 * o + 2], cub[4 * o + 3], gx, gy, gz));
+    for (int o = 0; o < s.n_osph; ++o) m = fmax(m, pen_sphere<double>(cx, cy, cz, r, osph[o], gx, gy, gz));
+    return m;
+}
+
+constexpr int kChkThreads = 256;
+
+__global__ void __launch_bounds__(kChkThreads) k_check64(const __grid_constant__ Scalars64 s, const D4* __restrict__ cub,
+                                                        const D4* __restrict__ osph, const float* __restrict__ q,
+                                                        const int* __restrict__ n_sol, int P, double* __restrict__ metrics,
+                                                        int* __restrict__ ok) {
+    const int r = blockIdx.x;
+    if (r >= P) return;
+    const int n = min(*n_sol, P);
+    const int tid = threadIdx.x;
+    if (r >= n) {
+        if (tid == 0) ok[r] = 0;
+        return;
+    }
+    const int B = s.B, S = s.S, C = s.C;
+    const float* qr = q + (size_t)r * C * 8;
+    __shared__ double pose[kMaxB][4];
+    __shared__ D4 bcub[kMaxB][4], icub[kMaxB][4];
+    __shared__ double red[kChkThreads];
+    __shared__ double vstart[kMaxB], vtilt[kMaxB];
+    if (tid < B) {
+        double qq[7], R[8][9], o[8][3], Rt[9], pt[3], Rb[9], pb[3];
+        // placed pose from the place configuration
+        for (int j = 0; j < 7; ++j) qq[j] = qr[t_place(S, tid) * 8 + j];
+        fk64(s, qq, R, o, Rt, pt);
+        held64(s, tid, Rt, pt, Rb, pb);
+        pose[tid][0] = pb[0]; pose[tid][1] = pb[1]; pose[tid][2] = pb[2]; pose[tid][3] = atan2(Rb[3], Rb[0]);
+        block_cub64(pose[tid], s.half[tid], bcub[tid]);
+        block_cub64(s.init[tid], s.half[tid], icub[tid]);
+        vtilt[tid] = 0.0;
+        {
+            const double roll = atan2(Rb[7], Rb[8]), pitch = atan2(-Rb[6], sqrt(Rb[7] * Rb[7] + Rb[8] * Rb[8]));
+            vtilt[tid] = roll * roll + pitch * pitch;
+        }
+        for (int j = 0; j < 7; ++j) qq[j] = qr[t_grasp(S, tid) * 8 + j];
+        fk64(s, qq, R, o, Rt, pt);
+        held64(s, tid, Rt, pt, Rb, pb);
+        const double roll = atan2(Rb[7], Rb[8]), pitch = atan2(-Rb[6], sqrt(Rb[7] * Rb[7] + Rb[8] * Rb[8]));
+        double e2 = 0.0;
+        for (int i = 0; i < 3; ++i) { const double d = pb[i] - s.init[tid][i]; e2 += d * d; }
+        vstart[tid] = e2 + roll * roll + pitch * pitch;
+    }
+    __syncthreads();
+
+    // arm and held-block penetrations over every configuration, joint limits
+    double maxpen = 0.0;
+    int limits_ok = 1;
+    for (int t = 1 + tid; t < C; t += kChkThreads) {
+        const int seg = (t - 1) / S, b = seg >> 1, jj = t - seg * S;
+        const bool held = (seg & 1) && jj < S;
+        double qq[7], R[8][9], o[8][3], Rt[9], pt[3];
+        for (int j = 0; j < 7; ++j) {
+            qq[j] = qr[t * 8 + j];
+            if (qq[j] < s.qlo[j] || qq[j] > s.qhi[j]) limits_ok = 0;
+        }
+        fk64(s, qq, R, o, Rt, pt);
+        const int n_items = s.n_rsph + (held ? 8 : 0);
+        double Rb[9], pb[3];
+        if (held) held64(s, b, Rt, pt, Rb, pb);
+        for (int it = 0; it < n_items; ++it) {
+            double cx, cy, cz, rad;
+            if (it < s.n_rsph) {
+                const int l = s.rlink[it];
+                const double* ls = s.rsph[it];
+                cx = R[l][0] * ls[0] + R[l][1] * ls[1] + R[l][2] * ls[2] + o[l][0];
+                cy = R[l][3] * ls[0] + R[l][4] * ls[1] + R[l][5] * ls[2] + o[l][1];
+                cz = R[l][6] * ls[0] + R[l][7] * ls[1] + R[l][8] * ls[2] + o[l][2];
+                rad = ls[3];
+            } else {
+                const int m = it - s.n_rsph;
+                const double lx = ((m & 1) ? 0.5 : -0.5) * s.half[b][0];
+                const double ly = ((m & 2) ? 0.5 : -0.5) * s.half[b][1];
+                const double lz = ((m & 4) ? 0.5 : -0.5) * s.half[b][2];
+                cx = pb[0] + Rb[0] * lx + Rb[1] * ly + Rb[2] * lz;
+                cy = pb[1] + Rb[3] * lx + Rb[4] * ly + Rb[5] * lz;
+                cz = pb[2] + Rb[6] * lx + Rb[7] * ly + Rb[8] * lz;
+                rad = s.hmin[b] * 0.5;
+            }
+            maxpen = fmax(maxpen, pen_env64(s, cub, osph, cx, cy, cz, rad));
+            for (int k = 0; k < B; ++k) {
+                if (k == b) continue;
+                const D4* cb = k < b ? bcub[k] : icub[k];
+                double gx, gy, gz;
+                maxpen = fmax(maxpen, pen_cuboid<double>(cx, cy, cz, rad, cb[0], cb[1], cb[2], cb[3], gx, gy, gz));
+            }
+        }
+    }
+    // placement: spheres of block j vs the environment and the blocks below
+    double place_pen = 0.0;
+    for (int it = tid; it < 8 * B; it += kChkThreads) {
+        const int j = it >> 3, m = it & 7;
+        const double lx = ((m & 1) ? 0.5 : -0.5) * s.half[j][0];
+        const double ly = ((m & 2) ? 0.5 : -0.5) * s.half[j][1];
+        const double lz = ((m & 4) ? 0.5 : -0.5) * s.half[j][2];
+        double sn, cs;
+        sincos(pose[j][3], &sn, &cs);
+        const double cx = pose[j][0] + cs * lx - sn * ly, cy = pose[j][1] + sn * lx + cs * ly, cz = pose[j][2] + lz;
+        const double rad = s.hmin[j] * 0.5;
+        place_pen = fmax(place_pen, pen_env64(s, cub, osph, cx, cy, cz, rad));
+        for (int i = 0; i < j; ++i) {
+            double gx, gy, gz;
+            place_pen = fmax(place_pen, pen_cuboid<double>(cx, cy, cz, rad, bcub[i][0], bcub[i][1], bcub[i][2], bcub[i][3],
+                                                           gx, gy, gz));
+        }
+    }
+    // block reductions (max) of the penetrations and the limit flag
+    red[tid] = maxpen;
+    __syncthreads();
+    for (int w = kChkThreads / 2; w > 0; w >>= 1) {
+        if (tid < w) red[tid] = fmax(red[tid], red[tid + w]);
+        __syncthreads();
+    }
+    const double mp = red[0];
+    __syncthreads();
+    red[tid] = place_pen;
+    __syncthreads();
+    for (int w = kChkThreads / 2; w > 0; w >>= 1) {
+        if (tid < w) red[tid] = fmax(red[tid], red[tid + w]);
+        __syncthreads();
+    }
+    const double pp = red[0];
+    const int lim = __syncthreads_and(limits_ok);
+    if (tid == 0) {
+        double ms = 0.0, mt = 0.0, mD = 0.0, mz = 0.0;
+        for (int b = 0; b < B; ++b) {
+            ms = fmax(ms, vstart[b]);
+            mt = fmax(mt, vtilt[b]);
+            mz = fmax(mz, fabs(pose[b][2] - s.zt[b]));
+            if (b + 1 < B) {
+                double mx = 0.0, my = 0.0;
+                for (int j = b + 1; j < B; ++j) { mx += pose[j][0]; my += pose[j][1]; }
+                mx /= (double)(B - 1 - b);
+                my /= (double)(B - 1 - b);
+                double sn, cs;
+                sincos(pose[b][3], &sn, &cs);
+                const double vx = mx - pose[b][0], vy = my - pose[b][1];
+                const double ux = cs * vx + sn * vy, uy = -sn * vx + cs * vy;
+                const double ex = fmax(fabs(ux) - s.half[b][0], 0.0), ey = fmax(fabs(uy) - s.half[b][1], 0.0);
+                mD = fmax(mD, sqrt(ex * ex + ey * ey));
+            }
+        }
+        double* m = metrics + (size_t)r * 6;
+        m[0] = mp; m[1] = ms; m[2] = mt; m[3] = pp; m[4] = mD; m[5] = mz;
+        ok[r] = (mp <= s.eps && ms <= s.eps_start && mt <= s.eps_start && pp <= s.eps && mD <= s.eps && mz <= s.eps &&
+                 lim) ? 1 : 0;
+    }
+}
+
+cudaError_t launch_check64(const Scalars64& s, const void* cub, const void* osph, const float* q, const int* n_sol, int P,
+                           double* metrics, int* ok, cudaStream_t st) {
+    if (P <= 0) return cudaSuccess;
+    k_check64<<<P, kChkThreads, 0, st>>>(s, static_cast<const D4*>(cub), static_cast<const D4*>(osph), q, n_sol, P,
+                                         metrics, ok);
+    return cudaGetLastError();
+}
+
+}  // namespace spasm

@@ -1,0 +1,26 @@
+// FP64 feasibility check of returned trajectories (internal to the library).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace spasm {
+
+// Double-precision copy of the problem tables used by the final check.
+struct Scalars64 {
+    int B, S, C, n_rsph, n_cub, n_osph;
+    double ca[7], sa[7], a[7], d[7], th0[7], qlo[7], qhi[7];
+    double ee_R[9], ee_p[3];
+    double rsph[kMaxRobotSpheres][4];
+    int rlink[kMaxRobotSpheres];
+    double half[kMaxB][3], hmin[kMaxB], init[kMaxB][4], zt[kMaxB];
+    double grasp_off, eps, eps_start;
+};
+
+// cub: n_cub x 4 x double4 (centre, then R columns with half extents); osph: n_osph x double4.
+// metrics: P x 6 (max arm/held penetration, max grasp error, max tilt, placement max
+// penetration, max CoM distance, max height error); ok: P flags.
+cudaError_t launch_check64(const Scalars64& s, const void* cub, const void* osph, const float* q, const int* n_sol, int P,
+                           double* metrics, int* ok, cudaStream_t st);
+
+}  // namespace spasm

@@ -23,7 +23,8 @@ STATUS = {0: "SPASM_OK", -1: "SPASM_ERR_INVALID", -2: "SPASM_ERR_NOMEM", -3: "SP
 
 EXPORTED = ["spasm_create_problem", "spasm_destroy_problem", "spasm_last_error", "spasm_place", "spasm_optimize",
             "spasm_result", "spasm_sizes", "spasm_place_sample", "spasm_place_eval", "spasm_place_descend",
-            "spasm_select_topk", "spasm_lift", "spasm_traj_eval", "spasm_traj_descend"]
+            "spasm_select_topk", "spasm_lift", "spasm_traj_eval", "spasm_traj_descend", "spasm_set_seed",
+            "spasm_set_timing", "spasm_get_stats", "spasm_reset_stats"]
 
 
 class SpasmError(RuntimeError):
@@ -61,6 +62,14 @@ class _Params(ctypes.Structure):
                 [("seed", ctypes.c_uint64), ("max_steps", ctypes.c_int)])
 
 
+class _Stats(ctypes.Structure):
+    _fields_ = [("place_attempts", ctypes.c_int), ("traj_attempts", ctypes.c_int), ("n_found", ctypes.c_int),
+                ("n_success", ctypes.c_int), ("kernel_launches", ctypes.c_longlong), ("traj_launches", ctypes.c_int),
+                ("particle_iters", ctypes.c_longlong), ("ms_place", ctypes.c_double), ("ms_lift", ctypes.c_double),
+                ("ms_traj", ctypes.c_double), ("ms_finish", ctypes.c_double), ("h2d_bytes", ctypes.c_longlong),
+                ("d2h_bytes", ctypes.c_longlong)]
+
+
 _lib = None
 
 
@@ -86,6 +95,10 @@ def lib():
         L.spasm_lift.argtypes = [_V, ctypes.c_int, _V, ctypes.c_int, ctypes.c_uint32, _V]
         L.spasm_traj_eval.argtypes = [_V, ctypes.c_int, _V, _V, _V, _V, _V, _V, _V]
         L.spasm_traj_descend.argtypes = [_V, ctypes.c_int, _V, _V, _V, ctypes.c_int, ctypes.c_int, _V, _V]
+        L.spasm_set_seed.argtypes = [_V, ctypes.c_uint64]
+        L.spasm_set_timing.argtypes = [_V, ctypes.c_int]
+        L.spasm_get_stats.argtypes = [_V, ctypes.POINTER(_Stats)]
+        L.spasm_reset_stats.argtypes = [_V]
         for name in EXPORTED:
             if name != "spasm_last_error":
                 getattr(L, name).restype = ctypes.c_int
@@ -219,3 +232,21 @@ def spasm_traj_descend(problem: Problem, n: int, q, lam, mu, k_steps: int, init_
                        sat=None):
     _check(lib().spasm_traj_descend(problem.handle, n, _dev(q), _dev(lam), _dev(mu), int(k_steps),
                                     int(init_multipliers), _dev(metrics), _dev(sat)))
+
+
+def spasm_set_seed(problem: Problem, seed: int):
+    _check(lib().spasm_set_seed(problem.handle, int(seed) & 0xFFFFFFFFFFFFFFFF))
+
+
+def spasm_set_timing(problem: Problem, enable: bool):
+    _check(lib().spasm_set_timing(problem.handle, int(bool(enable))))
+
+
+def spasm_get_stats(problem: Problem) -> dict:
+    st = _Stats()
+    _check(lib().spasm_get_stats(problem.handle, ctypes.byref(st)))
+    return {name: getattr(st, name) for name, _ in _Stats._fields_}
+
+
+def spasm_reset_stats(problem: Problem):
+    _check(lib().spasm_reset_stats(problem.handle))
