@@ -41,6 +41,8 @@ SM_COUNT, FP32_LANES = 152, 128
 FLOP_PER_TEST = 24
 # forward kinematics of one configuration: 7 link transforms (27 fma + sincos each)
 FLOP_PER_CONFIG_FK = 7 * 40
+# exact box cull of one (configuration, obstacle) pair: 6 comparisons
+FLOP_PER_CULL = 6
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "k_traj_tower10.md")
 KERNEL_SOURCES = ["paper_2510_07674_gb300/csrc/kernels_s2.cu", "paper_2510_07674_gb300/csrc/stage2.cuh",
                   "paper_2510_07674_gb300/csrc/common.cuh", "paper_2510_07674_gb300/csrc/stage1.cuh"]
@@ -144,7 +146,8 @@ def count_tests(wl) -> dict:
     n_rsph = len(wl.robot.sphere)
     held_cfgs = B * (S - 1)
     tests = (C - 1) * n_rsph * n_obs + held_cfgs * 8 * n_obs
-    return {"C": C, "tests": tests, "flop": FLOP_PER_TEST * tests + FLOP_PER_CONFIG_FK * (C - 1)}
+    return {"C": C, "tests": tests, "n_obs": n_obs,
+            "flop": FLOP_PER_TEST * tests + FLOP_PER_CONFIG_FK * (C - 1)}
 
 
 # ------------------------------------------------------------------------------- native
@@ -159,9 +162,13 @@ def run_native(args, ws, rank, local):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     overrides = {"max_steps": args.max_steps}
+    for kv in args.override:
+        k, v = kv.split("=", 1)
+        overrides[k] = float(v) if any(ch in v for ch in ".e") else int(v)
     n_total = args.warmup + args.steps
     seeds = [rank * 100000 + i for i in range(n_total)]
-    wls = [scenes.make_problem(WORKLOAD, seed=s) for s in seeds]
+    wls = [scenes.make_problem(WORKLOAD, seed=s, **{k: v for k, v in overrides.items() if k != "max_steps"})
+           for s in seeds]
     probs = [S.Problem(w, **overrides) for w in wls]
     for p in probs:
         S.spasm_set_timing(p, True)
@@ -215,8 +222,14 @@ def run_native(args, ws, rank, local):
     pits = sum(s["particle_iters"] for s in stats)
     K = wls[0].params.K_traj
     Q = wls[0].params.Q
-    # one launch runs K descent iterations plus the final evaluation pass
-    flop_per_launch = Q * (K + 1) * tc["flop"]
+    # one launch runs K descent iterations plus the final evaluation pass.  Work actually
+    # required: the tests that survive the exact box cull (counted by the kernel), the cull
+    # itself and the forward kinematics; the all-pairs count is reported as effective tests/s.
+    evals = Q * (K + 1) * max(traj_launches, 1)
+    tests_exec = sum(s["tests_executed"] for s in stats)
+    flop_total = (FLOP_PER_TEST * tests_exec + FLOP_PER_CULL * evals * (tc["C"] - 1) * tc["n_obs"]
+                  + FLOP_PER_CONFIG_FK * evals * (tc["C"] - 1))
+    flop_per_launch = flop_total / max(traj_launches, 1)
     avg_launch_s = traj_ms / max(traj_launches, 1) / 1000.0
     achieved = flop_per_launch / avg_launch_s / 1e12 if avg_launch_s > 0 else None
     clk = clocks.get("sm_max_mhz") or 2070.0
@@ -226,7 +239,9 @@ def run_native(args, ws, rank, local):
                 "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None,
                 "traffic": traffic, "peak_basis": f"152 SMs x 128 FP32 lanes x 2 x {clk:.0f} MHz (derived)",
                 "flop_per_launch": flop_per_launch, "avg_launch_ms": avg_launch_s * 1e3,
-                "tests_per_particle_iter": tc["tests"]}
+                "tests_per_particle_iter_all_pairs": tc["tests"],
+                "tests_per_particle_iter_executed": tests_exec / max(evals, 1),
+                "effective_pair_tests_per_s": tc["tests"] * evals / max(traj_ms / 1000.0, 1e-9)}
     succ = [s["n_success"] > 0 for s in stats]
 
     # ---- end to end through the public API with host buffers
@@ -257,7 +272,8 @@ def run_native(args, ws, rank, local):
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32 (FP64 final check)", "data": "synthetic",
         "config": {"workload": WORKLOAD_DESC, "parallelism": f"replicas x{ws}", "l2": "flushed between steps "
-                   "(256 MB write outside the per-step events)", "max_steps": args.max_steps},
+                   "(256 MB write outside the per-step events)", "max_steps": args.max_steps,
+                   "overrides": {k: v for k, v in overrides.items() if k != "max_steps"}},
         "solve_ms_p50": float(statistics.median(times)),
         "solve_ms_p99": float(sorted(times)[min(len(times) - 1, math.ceil(0.99 * len(times)) - 1)]),
         "particle_iters_per_s": pits / (total_ms / 1000.0) * ws,
@@ -360,6 +376,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--cpu-budget-s", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--override", action="append", default=[], metavar="PARAM=VALUE",
+                    help="change a solver parameter (profiling of a reduced case only; recorded in config)")
     args = ap.parse_args()
     ws, rank, local = dist_env()
     if args.impl == "reference":

@@ -58,7 +58,7 @@ typedef struct {
     int dof;                     /* must be 7 */
     const double* dh;
     const double* qlim;
-    int n_spheres;               /* <= 64 */
+    int n_spheres;               /* <= 56 */
     const int32_t* sphere_link;
     const double* sphere;
     const double* ee;
@@ -198,6 +198,8 @@ typedef struct {
     double ms_finish;          /* ranking, selection and FP64 check */
     long long h2d_bytes;       /* host -> device bytes copied by create / place / optimize */
     long long d2h_bytes;       /* device -> host bytes copied by place / optimize / result */
+    long long tests_executed;  /* sphere-obstacle tests run by the trajectory kernels after the
+                                  exact box cull (pairs whose boxes are disjoint are skipped) */
 } spasm_stats;
 
 /* Replace the Philox seed (the key of every random stream) and forget previous results;

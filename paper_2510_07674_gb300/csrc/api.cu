@@ -48,6 +48,7 @@ struct spasm_problem {
     float *d_rq = nullptr, *d_rcost = nullptr;   // returned solutions
     int* d_rsucc = nullptr;
     int* d_user_np = nullptr;   // placement count of a user-driven lift
+    unsigned long long* d_tests = nullptr;   // sphere-obstacle tests run by the trajectory kernel
     int h_user_np = 0;
     bool optimized = false;
     int n_found = 0, traj_attempts = 0;
@@ -106,7 +107,7 @@ static void free_all(spasm_problem* pr) {
     void* ptrs[] = {pr->d_cub, pr->d_osph, pr->d_err, pr->d_xs, pr->d_cost, pr->d_xm, pr->d_costm, pr->d_masked,
                     pr->d_idx, pr->d_sat, pr->d_nsat, pr->d_best, pr->d_place, pr->d_nplace, pr->d_q, pr->d_lam,
                     pr->d_mu, pr->d_metrics, pr->d_tmasked, pr->d_tsat, pr->d_tnsat, pr->d_tbest, pr->d_rq,
-                    pr->d_rcost, pr->d_rsucc, pr->d_user_np, pr->d_cub64, pr->d_osph64, pr->d_rmet64};
+                    pr->d_rcost, pr->d_rsucc, pr->d_user_np, pr->d_cub64, pr->d_osph64, pr->d_rmet64, pr->d_tests};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (cudaEvent_t e : pr->ev)
@@ -122,7 +123,7 @@ extern "C" spasm_status spasm_create_problem(const spasm_robot* robot, const spa
     *out = nullptr;
     if (robot->dof != 7) return fail(SPASM_ERR_INVALID, "dof must be 7");
     if (robot->n_spheres < 1 || robot->n_spheres > kMaxRobotSpheres)
-        return fail(SPASM_ERR_INVALID, "robot sphere count outside 1..64");
+        return fail(SPASM_ERR_INVALID, "robot sphere count outside 1..56");
     if (obs->n_cuboids < 0 || obs->n_cuboids > kMaxCub) return fail(SPASM_ERR_INVALID, "cuboid count outside 0..256");
     if (obs->n_spheres < 0 || obs->n_spheres > kMaxOSph) return fail(SPASM_ERR_INVALID, "obstacle sphere count outside 0..64");
     const int B = goal->n_blocks;
@@ -278,6 +279,7 @@ extern "C" spasm_status spasm_create_problem(const spasm_robot* robot, const spa
     ALLOC(pr->d_cub64, (size_t)16 * sc.n_cub);
     ALLOC(pr->d_osph64, (size_t)4 * sc.n_osph);
     ALLOC(pr->d_rmet64, (size_t)6 * P);
+    ALLOC(pr->d_tests, 1);
 #undef ALLOC
     for (auto& ev : pr->ev)
         if (st == SPASM_OK && cudaEventCreate(&ev) != cudaSuccess) st = fail(SPASM_ERR_CUDA, "cudaEventCreate failed");
@@ -386,6 +388,7 @@ static spasm_status traj_attempt(spasm_problem* pr, uint32_t attempt) {
     TrajIO io{};
     io.q = pr->d_q; io.lam = pr->d_lam; io.mu = pr->d_mu; io.metrics = pr->d_metrics; io.sat = pr->d_tsat;
     io.k_steps = sc.K_traj; io.init_multipliers = 1;
+    io.tests = pr->d_tests;
     SPASM_CUDA(launch_traj(sc, pr->tab, sc.Q, kTrajModeDescend, io, pr->d_err, s));
     SPASM_TRY(rec(pr, 4));
     count_launches(pr, 3);
@@ -423,6 +426,7 @@ extern "C" spasm_status spasm_optimize(spasm_problem_t pr) {
     const Scalars& sc = pr->sc;
     cudaStream_t s = pr->stream;
     int steps = 0, attempt = 0, found = 0;
+    SPASM_CUDA(cudaMemsetAsync(pr->d_tests, 0, sizeof(unsigned long long), s));
     while (steps < pr->prm.max_steps || attempt == 0) {
         SPASM_TRY(traj_attempt(pr, (uint32_t)attempt));
         steps += sc.K_traj;
@@ -458,6 +462,12 @@ extern "C" spasm_status spasm_optimize(spasm_problem_t pr) {
     }
     pr->n_found = found;
     SPASM_TRY(check_device_error(pr));
+    {
+        unsigned long long nt = 0;
+        SPASM_CUDA(cudaMemcpy(&nt, pr->d_tests, sizeof nt, cudaMemcpyDeviceToHost));
+        pr->stats.d2h_bytes += sizeof nt;
+        pr->stats.tests_executed += (long long)nt;
+    }
     if (found > 0) {
         std::vector<int> succ(sc.P, 0);
         SPASM_CUDA(cudaMemcpy(succ.data(), pr->d_rsucc, sc.P * sizeof(int), cudaMemcpyDeviceToHost));

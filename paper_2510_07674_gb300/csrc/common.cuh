@@ -16,7 +16,7 @@
 namespace spasm {
 
 constexpr int kMaxB = 16;          // blocks per problem
-constexpr int kMaxRobotSpheres = 64;
+constexpr int kMaxRobotSpheres = 56;   // + 8 held-block spheres = 2 per lane
 constexpr int kMaxCub = 256;       // environment cuboids (incl. table)
 constexpr int kMaxOSph = 64;       // environment spheres
 constexpr int kMaxC = 1024;        // configurations per trajectory particle
@@ -103,28 +103,34 @@ __device__ __forceinline__ float warp_max(float v) {
 // ------------------------------------------------------------------------------ geometry
 // Penetration of sphere (c, r) into a cuboid, pen = max(0, -sd) with
 //   p = R^T (c - centre), q = |p| - h,  sd = ||max(q,0)|| + min(max_k q_k, 0) - r.
-// Returns pen and dpen/dc in g (zero when pen == 0).  The test max_k q_k >= r rejects
-// separated pairs exactly (then sd >= 0) before any square root is taken.
+// Split in two: cub_local gives p, q and max_k q_k; pen_finish turns them into pen and
+// dpen/dc (zero when pen == 0).  The test max_k q_k >= r rejects separated pairs exactly
+// (then sd >= 0) before any square root is taken.
 template <typename T, typename V4>
-__device__ __forceinline__ T pen_cuboid(T cx, T cy, T cz, T r, const V4& o, const V4& c0, const V4& c1,
+__device__ __forceinline__ T cub_local(T cx, T cy, T cz, const V4& o, const V4& c0, const V4& c1, const V4& c2,
+                                       T& p0, T& p1, T& p2, T& q0, T& q1, T& q2) {
+    const T dx = cx - (T)o.x, dy = cy - (T)o.y, dz = cz - (T)o.z;
+    p0 = (T)c0.x * dx + (T)c0.y * dy + (T)c0.z * dz;
+    p1 = (T)c1.x * dx + (T)c1.y * dy + (T)c1.z * dz;
+    p2 = (T)c2.x * dx + (T)c2.y * dy + (T)c2.z * dz;
+    q0 = fabs(p0) - (T)c0.w; q1 = fabs(p1) - (T)c1.w; q2 = fabs(p2) - (T)c2.w;
+    return q0 > q1 ? (q0 > q2 ? q0 : q2) : (q1 > q2 ? q1 : q2);
+}
+
+template <typename T, typename V4>
+__device__ __forceinline__ T pen_finish(T p0, T p1, T p2, T q0, T q1, T q2, T qm, T r, const V4& c0, const V4& c1,
                                         const V4& c2, T& gx, T& gy, T& gz) {
-    T dx = cx - (T)o.x, dy = cy - (T)o.y, dz = cz - (T)o.z;
-    T p0 = (T)c0.x * dx + (T)c0.y * dy + (T)c0.z * dz;
-    T p1 = (T)c1.x * dx + (T)c1.y * dy + (T)c1.z * dz;
-    T p2 = (T)c2.x * dx + (T)c2.y * dy + (T)c2.z * dz;
-    T q0 = fabs(p0) - (T)c0.w, q1 = fabs(p1) - (T)c1.w, q2 = fabs(p2) - (T)c2.w;
-    T qm = q0 > q1 ? (q0 > q2 ? q0 : q2) : (q1 > q2 ? q1 : q2);
     gx = gy = gz = (T)0;
     if (!(qm < r)) return (T)0;
-    T s0 = p0 >= (T)0 ? (T)1 : (T)-1, s1 = p1 >= (T)0 ? (T)1 : (T)-1, s2 = p2 >= (T)0 ? (T)1 : (T)-1;
+    const T s0 = p0 >= (T)0 ? (T)1 : (T)-1, s1 = p1 >= (T)0 ? (T)1 : (T)-1, s2 = p2 >= (T)0 ? (T)1 : (T)-1;
     T pen, d0, d1, d2;   // dsd/dp
     if (qm > (T)0) {
-        T m0 = q0 > (T)0 ? q0 : (T)0, m1 = q1 > (T)0 ? q1 : (T)0, m2 = q2 > (T)0 ? q2 : (T)0;
-        T n2 = m0 * m0 + m1 * m1 + m2 * m2;
+        const T m0 = q0 > (T)0 ? q0 : (T)0, m1 = q1 > (T)0 ? q1 : (T)0, m2 = q2 > (T)0 ? q2 : (T)0;
+        const T n2 = m0 * m0 + m1 * m1 + m2 * m2;
         if (!(n2 < r * r)) return (T)0;
-        T n = sqrt(n2);
+        const T n = sqrt(n2);
         pen = r - n;
-        T inv = (T)1 / n;
+        const T inv = (T)1 / n;
         d0 = s0 * m0 * inv; d1 = s1 * m1 * inv; d2 = s2 * m2 * inv;
     } else {
         pen = r - qm;
@@ -141,6 +147,14 @@ __device__ __forceinline__ T pen_cuboid(T cx, T cy, T cz, T r, const V4& o, cons
     gy = -((T)c0.y * d0 + (T)c1.y * d1 + (T)c2.y * d2);
     gz = -((T)c0.z * d0 + (T)c1.z * d1 + (T)c2.z * d2);
     return pen;
+}
+
+template <typename T, typename V4>
+__device__ __forceinline__ T pen_cuboid(T cx, T cy, T cz, T r, const V4& o, const V4& c0, const V4& c1,
+                                        const V4& c2, T& gx, T& gy, T& gz) {
+    T p0, p1, p2, q0, q1, q2;
+    const T qm = cub_local<T, V4>(cx, cy, cz, o, c0, c1, c2, p0, p1, p2, q0, q1, q2);
+    return pen_finish<T, V4>(p0, p1, p2, q0, q1, q2, qm, r, c0, c1, c2, gx, gy, gz);
 }
 
 template <typename T, typename V4>

@@ -144,7 +144,7 @@ __global__ void k_lift_interp(const __grid_constant__ Scalars sc, int n, const i
 // ================================================================================== trajopt
 constexpr int kTWarps = 8;
 constexpr int kTThreads = 32 * kTWarps;
-constexpr int kSlots = 3;   // sphere items per lane: up to 64 robot + 8 held-block spheres
+constexpr int kSlots = 2;   // sphere items per lane: up to 56 robot + 8 held-block spheres
 
 struct TWarp {
     float fr[8][8];          // frame k: origin (3), joint axis z (3)
@@ -155,6 +155,8 @@ struct TWarp {
 struct TShared {
     float4 bcub[kMaxB][4];   // placed-block cuboids of this iteration
     float4 icub[kMaxB][4];   // initial-pose cuboids
+    float4 baabb[kMaxB][2];  // their axis-aligned boxes (lo, hi)
+    float4 iaabb[kMaxB][2];
     float pose[4 * kMaxB];   // placed poses (x, y, z, yaw)
     float g4[4 * kMaxB];     // dL/d(placed pose)
     float h[kMaxNR], lam[kMaxNR], s[kMaxNR];
@@ -168,8 +170,11 @@ struct TShared {
 };
 
 __host__ __device__ inline size_t t_env_offset() { return 16; }
-__host__ __device__ inline size_t t_shared_offset(int n_cub, int n_osph) {
+__host__ __device__ inline size_t t_aabb_offset(int n_cub, int n_osph) {
     return (16 + (size_t)n_cub * 64 + (size_t)n_osph * 16 + 15) & ~(size_t)15;
+}
+__host__ __device__ inline size_t t_shared_offset(int n_cub, int n_osph) {
+    return t_aabb_offset(n_cub, n_osph) + (size_t)(n_cub + n_osph) * 32;
 }
 __host__ __device__ inline size_t t_q_offset(int n_cub, int n_osph) {
     return (t_shared_offset(n_cub, n_osph) + sizeof(TShared) + 15) & ~(size_t)15;
@@ -183,9 +188,10 @@ size_t traj_smem_bytes(const Scalars& sc) {
 // blocks.  With `grad`, writes the unscaled group gradients G_arm[t], G_blk[t] and adds
 // placed-pose derivatives into the warp's accumulators.
 __device__ __forceinline__ void config_collisions(const Scalars& sc, const float4* __restrict__ cub,
-                                                  const float4* __restrict__ osph, TShared& sh, TWarp& tw,
-                                                  const float* __restrict__ q, float* G_arm, float* G_blk, int t,
-                                                  bool grad, float& acc_arm, float& acc_blk, float& acc_max) {
+                                                  const float4* __restrict__ osph, const float4* __restrict__ aabb,
+                                                  TShared& sh, TWarp& tw, const float* __restrict__ q, float* G_arm,
+                                                  float* G_blk, int t, bool grad, float& acc_arm, float& acc_blk,
+                                                  float& acc_max, unsigned long long& n_tests) {
     const int lane = threadIdx.x & 31;
     const int S = sc.S, B = sc.B;
     const int seg = (t - 1) / S, b = seg >> 1, jj = t - seg * S;
@@ -255,34 +261,94 @@ __device__ __forceinline__ void config_collisions(const Scalars& sc, const float
     for (int sl = 0; sl < kSlots; ++sl) gx[sl] = gy[sl] = gz[sl] = pen_sum[sl] = 0.f;
     bool any_hit = false;
 
-    // environment cuboids (shared memory, broadcast reads)
-    for (int oi = 0; oi < sc.n_cub; ++oi) {
-        const float4 o0 = cub[4 * oi], o1 = cub[4 * oi + 1], o2 = cub[4 * oi + 2], o3 = cub[4 * oi + 3];
+    // exact cull: axis-aligned box of every sphere of this configuration against each
+    // obstacle's box; a pair whose boxes are disjoint cannot penetrate
+    float lo_x = 3.4e38f, lo_y = 3.4e38f, lo_z = 3.4e38f, hi_x = -3.4e38f, hi_y = -3.4e38f, hi_z = -3.4e38f;
+#pragma unroll
+    for (int sl = 0; sl < kSlots; ++sl) {
+        if (!act[sl]) continue;
+        lo_x = fminf(lo_x, cx[sl] - rr[sl]); hi_x = fmaxf(hi_x, cx[sl] + rr[sl]);
+        lo_y = fminf(lo_y, cy[sl] - rr[sl]); hi_y = fmaxf(hi_y, cy[sl] + rr[sl]);
+        lo_z = fminf(lo_z, cz[sl] - rr[sl]); hi_z = fmaxf(hi_z, cz[sl] + rr[sl]);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        lo_x = fminf(lo_x, __shfl_xor_sync(0xffffffffu, lo_x, off));
+        lo_y = fminf(lo_y, __shfl_xor_sync(0xffffffffu, lo_y, off));
+        lo_z = fminf(lo_z, __shfl_xor_sync(0xffffffffu, lo_z, off));
+        hi_x = fmaxf(hi_x, __shfl_xor_sync(0xffffffffu, hi_x, off));
+        hi_y = fmaxf(hi_y, __shfl_xor_sync(0xffffffffu, hi_y, off));
+        hi_z = fmaxf(hi_z, __shfl_xor_sync(0xffffffffu, hi_z, off));
+    }
+    auto overlaps = [&](const float4& blo, const float4& bhi) {
+        return blo.x <= hi_x && bhi.x >= lo_x && blo.y <= hi_y && bhi.y >= lo_y && blo.z <= hi_z && bhi.z >= lo_z;
+    };
+    int visits = 0;
+
+    // one cuboid against the lane's sphere slots: branch-free separation screening of
+    // both slots first, the penetration only for the (rare) overlapping ones
+    auto cuboid_pass = [&](const float4& o0, const float4& o1, const float4& o2, const float4& o3, float* dd_arm,
+                           float* dd_blk, bool& hit) {
+        float p0[kSlots], p1[kSlots], p2[kSlots], q0[kSlots], q1[kSlots], q2[kSlots], qm[kSlots];
+#pragma unroll
+        for (int sl = 0; sl < kSlots; ++sl)
+            qm[sl] = cub_local<float>(cx[sl], cy[sl], cz[sl], o0, o1, o2, o3, p0[sl], p1[sl], p2[sl], q0[sl], q1[sl],
+                                      q2[sl]);
 #pragma unroll
         for (int sl = 0; sl < kSlots; ++sl) {
-            if (!act[sl]) continue;
+            if (!act[sl] || !(qm[sl] < rr[sl])) continue;
             float ax, ay, az;
-            const float pen = pen_cuboid<float>(cx[sl], cy[sl], cz[sl], rr[sl], o0, o1, o2, o3, ax, ay, az);
+            const float pen = pen_finish<float>(p0[sl], p1[sl], p2[sl], q0[sl], q1[sl], q2[sl], qm[sl], rr[sl], o1, o2,
+                                                o3, ax, ay, az);
             if (pen > 0.f) {
                 any_hit = true;
+                hit = true;
                 pen_sum[sl] += pen;
                 acc_max = fmaxf(acc_max, pen);
                 gx[sl] += ax; gy[sl] += ay; gz[sl] += az;
+                if (dd_arm) {
+                    // rigid motion of the cuboid: d/dP = -g, d/dyaw = -((c - P) x g)_z
+                    float* dd = isblk[sl] ? dd_blk : dd_arm;
+                    dd[0] -= ax; dd[1] -= ay; dd[2] -= az;
+                    dd[3] -= (cx[sl] - o0.x) * ay - (cy[sl] - o0.y) * ax;
+                }
             }
         }
+    };
+
+    // environment cuboids (shared memory, broadcast reads), culled by a warp ballot
+    for (int base = 0; base < sc.n_cub; base += 32) {
+        const int oi = base + lane;
+        const bool ov = oi < sc.n_cub && overlaps(aabb[2 * oi], aabb[2 * oi + 1]);
+        unsigned m = __ballot_sync(0xffffffffu, ov);
+        visits += __popc(m);
+        while (m) {
+            const int o = base + __ffs(m) - 1;
+            m &= m - 1;
+            bool hit = false;
+            cuboid_pass(cub[4 * o], cub[4 * o + 1], cub[4 * o + 2], cub[4 * o + 3], nullptr, nullptr, hit);
+        }
     }
-    for (int oi = 0; oi < sc.n_osph; ++oi) {
-        const float4 os = osph[oi];
+    for (int base = 0; base < sc.n_osph; base += 32) {
+        const int oi = base + lane;
+        const bool ov = oi < sc.n_osph && overlaps(aabb[2 * (sc.n_cub + oi)], aabb[2 * (sc.n_cub + oi) + 1]);
+        unsigned m = __ballot_sync(0xffffffffu, ov);
+        visits += __popc(m);
+        while (m) {
+            const int o = base + __ffs(m) - 1;
+            m &= m - 1;
+            const float4 os = osph[o];
 #pragma unroll
-        for (int sl = 0; sl < kSlots; ++sl) {
-            if (!act[sl]) continue;
-            float ax, ay, az;
-            const float pen = pen_sphere<float>(cx[sl], cy[sl], cz[sl], rr[sl], os, ax, ay, az);
-            if (pen > 0.f) {
-                any_hit = true;
-                pen_sum[sl] += pen;
-                acc_max = fmaxf(acc_max, pen);
-                gx[sl] += ax; gy[sl] += ay; gz[sl] += az;
+            for (int sl = 0; sl < kSlots; ++sl) {
+                if (!act[sl]) continue;
+                float ax, ay, az;
+                const float pen = pen_sphere<float>(cx[sl], cy[sl], cz[sl], rr[sl], os, ax, ay, az);
+                if (pen > 0.f) {
+                    any_hit = true;
+                    pen_sum[sl] += pen;
+                    acc_max = fmaxf(acc_max, pen);
+                    gx[sl] += ax; gy[sl] += ay; gz[sl] += az;
+                }
             }
         }
     }
@@ -290,29 +356,13 @@ __device__ __forceinline__ void config_collisions(const Scalars& sc, const float
     for (int kb = 0; kb < B; ++kb) {
         if (kb == b) continue;
         const bool placed = kb < b;
+        const float4* bx = placed ? sh.baabb[kb] : sh.iaabb[kb];
+        if (!overlaps(bx[0], bx[1])) continue;
+        ++visits;
         const float4* cb = placed ? sh.bcub[kb] : sh.icub[kb];
-        const float4 o0 = cb[0], o1 = cb[1], o2 = cb[2], o3 = cb[3];
         float da[4] = {0, 0, 0, 0}, db[4] = {0, 0, 0, 0};
         bool hit = false;
-#pragma unroll
-        for (int sl = 0; sl < kSlots; ++sl) {
-            if (!act[sl]) continue;
-            float ax, ay, az;
-            const float pen = pen_cuboid<float>(cx[sl], cy[sl], cz[sl], rr[sl], o0, o1, o2, o3, ax, ay, az);
-            if (pen > 0.f) {
-                any_hit = true;
-                hit = true;
-                pen_sum[sl] += pen;
-                acc_max = fmaxf(acc_max, pen);
-                gx[sl] += ax; gy[sl] += ay; gz[sl] += az;
-                if (placed) {
-                    // rigid motion of the cuboid: d/dP = -g, d/dyaw = -((c - P) x g)_z
-                    float* dd = isblk[sl] ? db : da;
-                    dd[0] -= ax; dd[1] -= ay; dd[2] -= az;
-                    dd[3] -= (cx[sl] - o0.x) * ay - (cy[sl] - o0.y) * ax;
-                }
-            }
-        }
+        cuboid_pass(cb[0], cb[1], cb[2], cb[3], placed ? da : nullptr, db, hit);
         if (grad && placed && __any_sync(0xffffffffu, hit)) {
 #pragma unroll
             for (int i = 0; i < 4; ++i) { da[i] = warp_sum(da[i]); db[i] = warp_sum(db[i]); }
@@ -322,6 +372,7 @@ __device__ __forceinline__ void config_collisions(const Scalars& sc, const float
             }
         }
     }
+    n_tests += (unsigned long long)visits * (unsigned)n_items;
 #pragma unroll
     for (int sl = 0; sl < kSlots; ++sl) {
         if (isblk[sl]) acc_blk += pen_sum[sl];
@@ -430,10 +481,19 @@ __device__ __forceinline__ void start_terms(const Scalars& sc, int b, int which,
 // Modes of the trajectory kernel
 enum TrajMode { kTrajEval = 0, kTrajDescend = 1, kTrajCheck = 2 };
 
+// Axis-aligned box of a cuboid record (centre, then R columns with half extents).
+__device__ __forceinline__ void cuboid_aabb(const float4* c, float4* box) {
+    const float ex = fabsf(c[1].x) * c[1].w + fabsf(c[2].x) * c[2].w + fabsf(c[3].x) * c[3].w;
+    const float ey = fabsf(c[1].y) * c[1].w + fabsf(c[2].y) * c[2].w + fabsf(c[3].y) * c[3].w;
+    const float ez = fabsf(c[1].z) * c[1].w + fabsf(c[2].z) * c[2].w + fabsf(c[3].z) * c[3].w;
+    box[0] = make_float4(c[0].x - ex, c[0].y - ey, c[0].z - ez, 0.f);
+    box[1] = make_float4(c[0].x + ex, c[0].y + ey, c[0].z + ez, 0.f);
+}
+
 // Evaluate the whole particle: placed poses, configuration loop, residuals, objective;
 // with `grad`, assemble dL/dq into G_arm (G_blk is scratch).
-__device__ void traj_evaluate(const Scalars& sc, const float4* cub, const float4* osph, TShared& sh, float* q,
-                              float* G_arm, float* G_blk, bool grad) {
+__device__ void traj_evaluate(const Scalars& sc, const float4* cub, const float4* osph, const float4* aabb, TShared& sh,
+                              float* q, float* G_arm, float* G_blk, bool grad, unsigned long long& n_tests) {
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const int B = sc.B, S = sc.S, C = sc.C, NR = sc.NR;
 
@@ -444,6 +504,7 @@ __device__ void traj_evaluate(const Scalars& sc, const float4* cub, const float4
             placed_pose(sc, lane, q + t_place(S, lane) * 8, pose);
             for (int i = 0; i < 4; ++i) sh.pose[4 * lane + i] = pose[i];
             block_cuboid(pose[0], pose[1], pose[2], pose[3], sc.half[lane], sh.bcub[lane]);
+            cuboid_aabb(sh.bcub[lane], sh.baabb[lane]);
         }
     }
     // zero per-warp accumulators
@@ -453,7 +514,8 @@ __device__ void traj_evaluate(const Scalars& sc, const float4* cub, const float4
     // (2) configuration loop
     float acc_arm = 0.f, acc_blk = 0.f, acc_max = 0.f;
     for (int t = 1 + w; t < C; t += kTWarps)
-        config_collisions(sc, cub, osph, sh, sh.warp[w], q, G_arm, G_blk, t, grad, acc_arm, acc_blk, acc_max);
+        config_collisions(sc, cub, osph, aabb, sh, sh.warp[w], q, G_arm, G_blk, t, grad, acc_arm, acc_blk, acc_max,
+                          n_tests);
     acc_arm = warp_sum(acc_arm);
     acc_blk = warp_sum(acc_blk);
     acc_max = warp_max(acc_max);
@@ -584,6 +646,7 @@ __global__ void __launch_bounds__(kTThreads, 2) k_traj(const __grid_constant__ S
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
     float4* cub = reinterpret_cast<float4*>(smem_raw + t_env_offset());
     float4* osph = cub + 4 * sc.n_cub;
+    float4* aabb = reinterpret_cast<float4*>(smem_raw + t_aabb_offset(sc.n_cub, sc.n_osph));
     TShared& sh = *reinterpret_cast<TShared*>(smem_raw + t_shared_offset(sc.n_cub, sc.n_osph));
     float* q = reinterpret_cast<float*>(smem_raw + t_q_offset(sc.n_cub, sc.n_osph));
     float* G_arm = q + sc.C * 8;
@@ -599,7 +662,17 @@ __global__ void __launch_bounds__(kTThreads, 2) k_traj(const __grid_constant__ S
     const float4* qg = reinterpret_cast<const float4*>(io.q + (size_t)p * C * 8);
     float4* qs = reinterpret_cast<float4*>(q);
     for (int i = tid; i < C * 2; i += kTThreads) qs[i] = qg[i];
-    if (tid < B) block_cuboid(sc.init[tid].x, sc.init[tid].y, sc.init[tid].z, sc.init[tid].w, sc.half[tid], sh.icub[tid]);
+    if (tid < B) {
+        block_cuboid(sc.init[tid].x, sc.init[tid].y, sc.init[tid].z, sc.init[tid].w, sc.half[tid], sh.icub[tid]);
+        cuboid_aabb(sh.icub[tid], sh.iaabb[tid]);
+    }
+    for (int o = tid; o < sc.n_cub; o += kTThreads) cuboid_aabb(&cub[4 * o], &aabb[2 * o]);
+    for (int o = tid; o < sc.n_osph; o += kTThreads) {
+        const float4 sp = osph[o];
+        aabb[2 * (sc.n_cub + o)] = make_float4(sp.x - sp.w, sp.y - sp.w, sp.z - sp.w, 0.f);
+        aabb[2 * (sc.n_cub + o) + 1] = make_float4(sp.x + sp.w, sp.y + sp.w, sp.z + sp.w, 0.f);
+    }
+    unsigned long long n_tests = 0;
     const bool fresh = mode == kTrajDescend && io.init_multipliers;
     for (int r = tid; r < NR; r += kTThreads) sh.lam[r] = (fresh || !io.lam) ? 0.f : io.lam[(size_t)p * NR + r];
     if (tid == 0) sh.mu = (fresh || !io.mu) ? sc.mu0 : io.mu[p];
@@ -608,7 +681,7 @@ __global__ void __launch_bounds__(kTThreads, 2) k_traj(const __grid_constant__ S
     if (mode == kTrajDescend) {
         const int K = io.k_steps;
         for (int k = 1; k <= K; ++k) {
-            traj_evaluate(sc, cub, osph, sh, q, G_arm, G_blk, true);
+            traj_evaluate(sc, cub, osph, aabb, sh, q, G_arm, G_blk, true, n_tests);
             const float eta = sc.eta_traj * (1.f - (float)k / (float)K);
             for (int i = tid; i < C * 7; i += kTThreads) {
                 const int t = i / 7, j = i % 7;
@@ -625,7 +698,8 @@ __global__ void __launch_bounds__(kTThreads, 2) k_traj(const __grid_constant__ S
         }
     }
     const bool want_grad = mode == kTrajEval && io.grad != nullptr;
-    traj_evaluate(sc, cub, osph, sh, q, G_arm, G_blk, want_grad);
+    traj_evaluate(sc, cub, osph, aabb, sh, q, G_arm, G_blk, want_grad, n_tests);
+    if (io.tests && (threadIdx.x & 31) == 0) atomicAdd(io.tests, n_tests);
 
     // outputs
     if (mode == kTrajDescend) {
