@@ -6,7 +6,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/spasm.h"
+#include "spasm.h"
 #include "check64.h"
 #include "launch_s2.h"
 #include "stage2.cuh"

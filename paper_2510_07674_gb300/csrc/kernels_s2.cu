@@ -183,15 +183,41 @@ size_t traj_smem_bytes(const Scalars& sc) {
     return t_q_offset(sc.n_cub, sc.n_osph) + (size_t)3 * sc.C * 8 * sizeof(float);
 }
 
+// The robot spheres a lane owns (item lane + 32 k), loaded once per kernel launch: link-
+// frame centre, radius, link index.  Items beyond the robot spheres are the held block's.
+struct LaneSpheres {
+    float lx[kSlots], ly[kSlots], lz[kSlots], r[kSlots];
+    int link[kSlots];
+};
+
+__device__ __forceinline__ LaneSpheres lane_spheres(const Scalars& sc) {
+    const int lane = threadIdx.x & 31;
+    LaneSpheres ls;
+#pragma unroll
+    for (int k = 0; k < kSlots; ++k) {
+        const int it = lane + 32 * k;
+        if (it < sc.n_rsph) {
+            const float4 v = sc.rsph[it];
+            ls.lx[k] = v.x; ls.ly[k] = v.y; ls.lz[k] = v.z; ls.r[k] = v.w;
+            ls.link[k] = sc.rlink[it];
+        } else {
+            ls.lx[k] = ls.ly[k] = ls.lz[k] = ls.r[k] = 0.f;
+            ls.link[k] = 7;
+        }
+    }
+    return ls;
+}
+
 // Collision terms of one configuration, evaluated by one warp: arm spheres and (on the
 // transfer interior) the held block's spheres against the environment and the context
 // blocks.  With `grad`, writes the unscaled group gradients G_arm[t], G_blk[t] and adds
 // placed-pose derivatives into the warp's accumulators.
-__device__ __forceinline__ void config_collisions(const Scalars& sc, const float4* __restrict__ cub,
-                                                  const float4* __restrict__ osph, const float4* __restrict__ aabb,
-                                                  TShared& sh, TWarp& tw, const float* __restrict__ q, float* G_arm,
-                                                  float* G_blk, int t, bool grad, float& acc_arm, float& acc_blk,
-                                                  float& acc_max, unsigned long long& n_tests) {
+__device__ __forceinline__ void config_collisions(const Scalars& sc, const LaneSpheres& ls,
+                                                  const float4* __restrict__ cub, const float4* __restrict__ osph,
+                                                  const float4* __restrict__ aabb, TShared& sh, TWarp& tw,
+                                                  const float* __restrict__ q, float* G_arm, float* G_blk, int t,
+                                                  bool grad, float& acc_arm, float& acc_blk, float& acc_max,
+                                                  unsigned long long& n_tests) {
     const int lane = threadIdx.x & 31;
     const int S = sc.S, B = sc.B;
     const int seg = (t - 1) / S, b = seg >> 1, jj = t - seg * S;
@@ -203,21 +229,14 @@ __device__ __forceinline__ void config_collisions(const Scalars& sc, const float
     if (lane < 7) sincosf(sc.th0[lane] + q[t * 8 + lane], &sn, &cs);
 
     float cx[kSlots], cy[kSlots], cz[kSlots], rr[kSlots];
-    int link[kSlots];
     bool act[kSlots], isblk[kSlots];
 #pragma unroll
     for (int k = 0; k < kSlots; ++k) {
         const int it = lane + 32 * k;
         act[k] = it < n_items;
         isblk[k] = act[k] && it >= sc.n_rsph;
-        link[k] = act[k] ? (isblk[k] ? 7 : sc.rlink[it]) : 0;
-        cx[k] = cy[k] = cz[k] = 0.f;
-        rr[k] = 0.f;
-        if (act[k] && !isblk[k]) {
-            const float4 ls = sc.rsph[it];
-            rr[k] = ls.w;
-            if (link[k] == 0) { cx[k] = ls.x; cy[k] = ls.y; cz[k] = ls.z; }
-        }
+        rr[k] = act[k] && !isblk[k] ? ls.r[k] : 0.f;
+        cx[k] = ls.lx[k]; cy[k] = ls.ly[k]; cz[k] = ls.lz[k];   // link 0: base frame = world
     }
     float R[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1}, o[3] = {0, 0, 0};
 #pragma unroll
@@ -230,11 +249,11 @@ __device__ __forceinline__ void config_collisions(const Scalars& sc, const float
         }
 #pragma unroll
         for (int sl = 0; sl < kSlots; ++sl) {
-            if (act[sl] && !isblk[sl] && link[sl] == k + 1) {
-                const float4 ls = sc.rsph[lane + 32 * sl];
-                cx[sl] = R[0] * ls.x + R[1] * ls.y + R[2] * ls.z + o[0];
-                cy[sl] = R[3] * ls.x + R[4] * ls.y + R[5] * ls.z + o[1];
-                cz[sl] = R[6] * ls.x + R[7] * ls.y + R[8] * ls.z + o[2];
+            if (ls.link[sl] == k + 1) {
+                const float x = ls.lx[sl], y = ls.ly[sl], z = ls.lz[sl];
+                cx[sl] = R[0] * x + R[1] * y + R[2] * z + o[0];
+                cy[sl] = R[3] * x + R[4] * y + R[5] * z + o[1];
+                cz[sl] = R[6] * x + R[7] * y + R[8] * z + o[2];
             }
         }
     }
@@ -285,48 +304,35 @@ __device__ __forceinline__ void config_collisions(const Scalars& sc, const float
     };
     int visits = 0;
 
-    // one cuboid against the lane's sphere slots: branch-free separation screening of
-    // both slots first, the penetration only for the (rare) overlapping ones
-    auto cuboid_pass = [&](const float4& o0, const float4& o1, const float4& o2, const float4& o3, float* dd_arm,
-                           float* dd_blk, bool& hit) {
-        float p0[kSlots], p1[kSlots], p2[kSlots], q0[kSlots], q1[kSlots], q2[kSlots], qm[kSlots];
-#pragma unroll
-        for (int sl = 0; sl < kSlots; ++sl)
-            qm[sl] = cub_local<float>(cx[sl], cy[sl], cz[sl], o0, o1, o2, o3, p0[sl], p1[sl], p2[sl], q0[sl], q1[sl],
-                                      q2[sl]);
-#pragma unroll
-        for (int sl = 0; sl < kSlots; ++sl) {
-            if (!act[sl] || !(qm[sl] < rr[sl])) continue;
-            float ax, ay, az;
-            const float pen = pen_finish<float>(p0[sl], p1[sl], p2[sl], q0[sl], q1[sl], q2[sl], qm[sl], rr[sl], o1, o2,
-                                                o3, ax, ay, az);
-            if (pen > 0.f) {
-                any_hit = true;
-                hit = true;
-                pen_sum[sl] += pen;
-                acc_max = fmaxf(acc_max, pen);
-                gx[sl] += ax; gy[sl] += ay; gz[sl] += az;
-                if (dd_arm) {
-                    // rigid motion of the cuboid: d/dP = -g, d/dyaw = -((c - P) x g)_z
-                    float* dd = isblk[sl] ? dd_blk : dd_arm;
-                    dd[0] -= ax; dd[1] -= ay; dd[2] -= az;
-                    dd[3] -= (cx[sl] - o0.x) * ay - (cy[sl] - o0.y) * ax;
-                }
-            }
-        }
-    };
-
-    // environment cuboids (shared memory, broadcast reads), culled by a warp ballot
+    // environment cuboids (shared memory, broadcast reads), culled by a warp ballot; both
+    // slots are screened branch-free, the penetration only for overlapping ones
     for (int base = 0; base < sc.n_cub; base += 32) {
         const int oi = base + lane;
         const bool ov = oi < sc.n_cub && overlaps(aabb[2 * oi], aabb[2 * oi + 1]);
         unsigned m = __ballot_sync(0xffffffffu, ov);
         visits += __popc(m);
         while (m) {
-            const int o = base + __ffs(m) - 1;
+            const int ob = base + __ffs(m) - 1;
             m &= m - 1;
-            bool hit = false;
-            cuboid_pass(cub[4 * o], cub[4 * o + 1], cub[4 * o + 2], cub[4 * o + 3], nullptr, nullptr, hit);
+            const float4 o0 = cub[4 * ob], o1 = cub[4 * ob + 1], o2 = cub[4 * ob + 2], o3 = cub[4 * ob + 3];
+            float p0[kSlots], p1[kSlots], p2[kSlots], q0[kSlots], q1[kSlots], q2[kSlots], qm[kSlots];
+#pragma unroll
+            for (int sl = 0; sl < kSlots; ++sl)
+                qm[sl] = cub_local<float>(cx[sl], cy[sl], cz[sl], o0, o1, o2, o3, p0[sl], p1[sl], p2[sl], q0[sl],
+                                          q1[sl], q2[sl]);
+#pragma unroll
+            for (int sl = 0; sl < kSlots; ++sl) {
+                if (!act[sl] || !(qm[sl] < rr[sl])) continue;
+                float ax, ay, az;
+                const float pen = pen_finish<float>(p0[sl], p1[sl], p2[sl], q0[sl], q1[sl], q2[sl], qm[sl], rr[sl], o1,
+                                                    o2, o3, ax, ay, az);
+                if (pen > 0.f) {
+                    any_hit = true;
+                    pen_sum[sl] += pen;
+                    acc_max = fmaxf(acc_max, pen);
+                    gx[sl] += ax; gy[sl] += ay; gz[sl] += az;
+                }
+            }
         }
     }
     for (int base = 0; base < sc.n_osph; base += 32) {
@@ -335,9 +341,9 @@ __device__ __forceinline__ void config_collisions(const Scalars& sc, const float
         unsigned m = __ballot_sync(0xffffffffu, ov);
         visits += __popc(m);
         while (m) {
-            const int o = base + __ffs(m) - 1;
+            const int ob = base + __ffs(m) - 1;
             m &= m - 1;
-            const float4 os = osph[o];
+            const float4 os = osph[ob];
 #pragma unroll
             for (int sl = 0; sl < kSlots; ++sl) {
                 if (!act[sl]) continue;
@@ -352,23 +358,53 @@ __device__ __forceinline__ void config_collisions(const Scalars& sc, const float
             }
         }
     }
-    // context blocks: placed (k < b, movable) and not yet moved (k > b)
-    for (int kb = 0; kb < B; ++kb) {
-        if (kb == b) continue;
-        const bool placed = kb < b;
-        const float4* bx = placed ? sh.baabb[kb] : sh.iaabb[kb];
-        if (!overlaps(bx[0], bx[1])) continue;
-        ++visits;
-        const float4* cb = placed ? sh.bcub[kb] : sh.icub[kb];
-        float da[4] = {0, 0, 0, 0}, db[4] = {0, 0, 0, 0};
-        bool hit = false;
-        cuboid_pass(cb[0], cb[1], cb[2], cb[3], placed ? da : nullptr, db, hit);
-        if (grad && placed && __any_sync(0xffffffffu, hit)) {
+    // context blocks: placed (k < b, movable) and not yet moved (k > b); lane kb culls block kb
+    {
+        bool ov = false;
+        if (lane < B && lane != b) {
+            const float4* bx = lane < b ? sh.baabb[lane] : sh.iaabb[lane];
+            ov = overlaps(bx[0], bx[1]);
+        }
+        unsigned m = __ballot_sync(0xffffffffu, ov);
+        visits += __popc(m);
+        while (m) {
+            const int kb = __ffs(m) - 1;
+            m &= m - 1;
+            const bool placed = kb < b;
+            const float4* cb = placed ? sh.bcub[kb] : sh.icub[kb];
+            const float4 o0 = cb[0], o1 = cb[1], o2 = cb[2], o3 = cb[3];
+            float dax = 0.f, day = 0.f, daz = 0.f, dayaw = 0.f, dbx = 0.f, dby = 0.f, dbz = 0.f, dbyaw = 0.f;
+            bool hit = false;
+            float p0[kSlots], p1[kSlots], p2[kSlots], q0[kSlots], q1[kSlots], q2[kSlots], qm[kSlots];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) { da[i] = warp_sum(da[i]); db[i] = warp_sum(db[i]); }
-            if (lane == 0) {
+            for (int sl = 0; sl < kSlots; ++sl)
+                qm[sl] = cub_local<float>(cx[sl], cy[sl], cz[sl], o0, o1, o2, o3, p0[sl], p1[sl], p2[sl], q0[sl],
+                                          q1[sl], q2[sl]);
 #pragma unroll
-                for (int i = 0; i < 4; ++i) { tw.wr[0][kb][i] += da[i]; tw.wr[1][kb][i] += db[i]; }
+            for (int sl = 0; sl < kSlots; ++sl) {
+                if (!act[sl] || !(qm[sl] < rr[sl])) continue;
+                float ax, ay, az;
+                const float pen = pen_finish<float>(p0[sl], p1[sl], p2[sl], q0[sl], q1[sl], q2[sl], qm[sl], rr[sl], o1,
+                                                    o2, o3, ax, ay, az);
+                if (pen > 0.f) {
+                    any_hit = true;
+                    hit = true;
+                    pen_sum[sl] += pen;
+                    acc_max = fmaxf(acc_max, pen);
+                    gx[sl] += ax; gy[sl] += ay; gz[sl] += az;
+                    // rigid motion of the cuboid: d/dP = -g, d/dyaw = -((c - P) x g)_z
+                    const float dyaw = -((cx[sl] - o0.x) * ay - (cy[sl] - o0.y) * ax);
+                    if (isblk[sl]) { dbx -= ax; dby -= ay; dbz -= az; dbyaw += dyaw; }
+                    else { dax -= ax; day -= ay; daz -= az; dayaw += dyaw; }
+                }
+            }
+            if (grad && placed && __any_sync(0xffffffffu, hit)) {
+                dax = warp_sum(dax); day = warp_sum(day); daz = warp_sum(daz); dayaw = warp_sum(dayaw);
+                dbx = warp_sum(dbx); dby = warp_sum(dby); dbz = warp_sum(dbz); dbyaw = warp_sum(dbyaw);
+                if (lane == 0) {
+                    tw.wr[0][kb][0] += dax; tw.wr[0][kb][1] += day; tw.wr[0][kb][2] += daz; tw.wr[0][kb][3] += dayaw;
+                    tw.wr[1][kb][0] += dbx; tw.wr[1][kb][1] += dby; tw.wr[1][kb][2] += dbz; tw.wr[1][kb][3] += dbyaw;
+                }
             }
         }
     }
@@ -393,11 +429,12 @@ __device__ __forceinline__ void config_collisions(const Scalars& sc, const float
                 const float zx = tw.fr[k + 1][3], zy = tw.fr[k + 1][4], zz = tw.fr[k + 1][5];
 #pragma unroll
                 for (int sl = 0; sl < kSlots; ++sl) {
-                    if (!act[sl] || link[sl] < k + 1) continue;
+                    const int lk = isblk[sl] ? 7 : ls.link[sl];
+                    if (!act[sl] || lk < k + 1) continue;
                     const float vx = cx[sl] - ox, vy = cy[sl] - oy, vz = cz[sl] - oz;
-                    const float m = zx * (vy * gz[sl] - vz * gy[sl]) + zy * (vz * gx[sl] - vx * gz[sl]) +
-                                    zz * (vx * gy[sl] - vy * gx[sl]);
-                    if (isblk[sl]) jb[k] += m; else ja[k] += m;
+                    const float mm = zx * (vy * gz[sl] - vz * gy[sl]) + zy * (vz * gx[sl] - vx * gz[sl]) +
+                                     zz * (vx * gy[sl] - vy * gx[sl]);
+                    if (isblk[sl]) jb[k] += mm; else ja[k] += mm;
                 }
             }
         }
@@ -492,8 +529,9 @@ __device__ __forceinline__ void cuboid_aabb(const float4* c, float4* box) {
 
 // Evaluate the whole particle: placed poses, configuration loop, residuals, objective;
 // with `grad`, assemble dL/dq into G_arm (G_blk is scratch).
-__device__ void traj_evaluate(const Scalars& sc, const float4* cub, const float4* osph, const float4* aabb, TShared& sh,
-                              float* q, float* G_arm, float* G_blk, bool grad, unsigned long long& n_tests) {
+__device__ void traj_evaluate(const Scalars& sc, const LaneSpheres& ls, const float4* cub, const float4* osph,
+                              const float4* aabb, TShared& sh, float* q, float* G_arm, float* G_blk, bool grad,
+                              unsigned long long& n_tests) {
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const int B = sc.B, S = sc.S, C = sc.C, NR = sc.NR;
 
@@ -514,7 +552,7 @@ __device__ void traj_evaluate(const Scalars& sc, const float4* cub, const float4
     // (2) configuration loop
     float acc_arm = 0.f, acc_blk = 0.f, acc_max = 0.f;
     for (int t = 1 + w; t < C; t += kTWarps)
-        config_collisions(sc, cub, osph, aabb, sh, sh.warp[w], q, G_arm, G_blk, t, grad, acc_arm, acc_blk, acc_max,
+        config_collisions(sc, ls, cub, osph, aabb, sh, sh.warp[w], q, G_arm, G_blk, t, grad, acc_arm, acc_blk, acc_max,
                           n_tests);
     acc_arm = warp_sum(acc_arm);
     acc_blk = warp_sum(acc_blk);
@@ -673,6 +711,7 @@ __global__ void __launch_bounds__(kTThreads, 2) k_traj(const __grid_constant__ S
         aabb[2 * (sc.n_cub + o) + 1] = make_float4(sp.x + sp.w, sp.y + sp.w, sp.z + sp.w, 0.f);
     }
     unsigned long long n_tests = 0;
+    const LaneSpheres ls = lane_spheres(sc);
     const bool fresh = mode == kTrajDescend && io.init_multipliers;
     for (int r = tid; r < NR; r += kTThreads) sh.lam[r] = (fresh || !io.lam) ? 0.f : io.lam[(size_t)p * NR + r];
     if (tid == 0) sh.mu = (fresh || !io.mu) ? sc.mu0 : io.mu[p];
@@ -681,7 +720,7 @@ __global__ void __launch_bounds__(kTThreads, 2) k_traj(const __grid_constant__ S
     if (mode == kTrajDescend) {
         const int K = io.k_steps;
         for (int k = 1; k <= K; ++k) {
-            traj_evaluate(sc, cub, osph, aabb, sh, q, G_arm, G_blk, true, n_tests);
+            traj_evaluate(sc, ls, cub, osph, aabb, sh, q, G_arm, G_blk, true, n_tests);
             const float eta = sc.eta_traj * (1.f - (float)k / (float)K);
             for (int i = tid; i < C * 7; i += kTThreads) {
                 const int t = i / 7, j = i % 7;
@@ -698,7 +737,7 @@ __global__ void __launch_bounds__(kTThreads, 2) k_traj(const __grid_constant__ S
         }
     }
     const bool want_grad = mode == kTrajEval && io.grad != nullptr;
-    traj_evaluate(sc, cub, osph, aabb, sh, q, G_arm, G_blk, want_grad, n_tests);
+    traj_evaluate(sc, ls, cub, osph, aabb, sh, q, G_arm, G_blk, want_grad, n_tests);
     if (io.tests && (threadIdx.x & 31) == 0) atomicAdd(io.tests, n_tests);
 
     // outputs
