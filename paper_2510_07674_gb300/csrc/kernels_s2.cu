@@ -146,8 +146,11 @@ constexpr int kTWarps = 8;
 constexpr int kTThreads = 32 * kTWarps;
 constexpr int kSlots = 2;   // sphere items per lane: up to 56 robot + 8 held-block spheres
 
+constexpr int kChunk = 4;   // configurations whose kinematics one warp evaluates together
+
 struct TWarp {
-    float fr[8][8];          // frame k: origin (3), joint axis z (3)
+    float4 F[kChunk][8][3];  // frames 0..7 of each configuration of the chunk: rows (R_i0, R_i1, R_i2, o_i)
+    float4 H[kChunk][3];     // held-block frame of each configuration (same row layout)
     float wr[2][kMaxB][4];   // d/d(placed pose k): group arm, group block
     float part[4];           // C_arm, C_block, max penetration
 };
@@ -208,6 +211,60 @@ __device__ __forceinline__ LaneSpheres lane_spheres(const Scalars& sc) {
     return ls;
 }
 
+// Forward kinematics of kChunk consecutive configurations by one warp: lane 8c + k holds
+// link transform k of configuration c (k = 0: identity), and a 3-level inclusive scan of
+// affine products inside each group of 8 lanes gives frame_k = T_1 ... T_k.  Frames and
+// the held-block frame land in the warp's shared scratch.
+__device__ __forceinline__ void chunk_fk(const Scalars& sc, const float* __restrict__ q, int t0, TWarp& tw) {
+    const int lane = threadIdx.x & 31;
+    const int c = lane >> 3, k = lane & 7;
+    const int t = min(t0 + c, sc.C - 1);
+    float A[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1}, bv[3] = {0, 0, 0};
+    if (k > 0) {
+        const int j = k - 1;
+        float st, ct;
+        sincosf(sc.th0[j] + q[t * 8 + j], &st, &ct);
+        const float ca = sc.ca[j], sa = sc.sa[j];
+        A[0] = ct;      A[1] = -st;     A[2] = 0.f;
+        A[3] = ca * st; A[4] = ca * ct; A[5] = -sa;
+        A[6] = sa * st; A[7] = sa * ct; A[8] = ca;
+        bv[0] = sc.a[j]; bv[1] = -sa * sc.d[j]; bv[2] = ca * sc.d[j];
+    }
+#pragma unroll
+    for (int off = 1; off < 8; off <<= 1) {
+        float L[9], lb[3];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) L[i] = __shfl_up_sync(0xffffffffu, A[i], off, 8);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) lb[i] = __shfl_up_sync(0xffffffffu, bv[i], off, 8);
+        if (k >= off) {
+            float nA[9], nb[3];
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+#pragma unroll
+                for (int cc = 0; cc < 3; ++cc)
+                    nA[3 * r + cc] = L[3 * r] * A[cc] + L[3 * r + 1] * A[3 + cc] + L[3 * r + 2] * A[6 + cc];
+                nb[r] = L[3 * r] * bv[0] + L[3 * r + 1] * bv[1] + L[3 * r + 2] * bv[2] + lb[r];
+            }
+#pragma unroll
+            for (int i = 0; i < 9; ++i) A[i] = nA[i];
+#pragma unroll
+            for (int i = 0; i < 3; ++i) bv[i] = nb[i];
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < 3; ++r) tw.F[c][k][r] = make_float4(A[3 * r], A[3 * r + 1], A[3 * r + 2], bv[r]);
+    if (k == 7) {
+        // tool frame and the block frame it would hold in this configuration's segment
+        const int seg = (t - 1) / sc.S, b = seg >> 1;
+        float Rt[9], pt[3], Rb[9], pb[3];
+        tool_frame<float>(sc, A, bv, Rt, pt);
+        held_block<float>(sc, b, Rt, pt, Rb, pb);
+#pragma unroll
+        for (int r = 0; r < 3; ++r) tw.H[c][r] = make_float4(Rb[3 * r], Rb[3 * r + 1], Rb[3 * r + 2], pb[r]);
+    }
+}
+
 // Collision terms of one configuration, evaluated by one warp: arm spheres and (on the
 // transfer interior) the held block's spheres against the environment and the context
 // blocks.  With `grad`, writes the unscaled group gradients G_arm[t], G_blk[t] and adds
@@ -216,7 +273,7 @@ __device__ __forceinline__ void config_collisions(const Scalars& sc, const LaneS
                                                   const float4* __restrict__ cub, const float4* __restrict__ osph,
                                                   const float4* __restrict__ aabb, TShared& sh, TWarp& tw,
                                                   const float* __restrict__ q, float* G_arm, float* G_blk, int t,
-                                                  bool grad, float& acc_arm, float& acc_blk, float& acc_max,
+                                                  int ci, bool grad, float& acc_arm, float& acc_blk, float& acc_max,
                                                   unsigned long long& n_tests) {
     const int lane = threadIdx.x & 31;
     const int S = sc.S, B = sc.B;
@@ -224,10 +281,8 @@ __device__ __forceinline__ void config_collisions(const Scalars& sc, const LaneS
     const bool held = (seg & 1) && jj < S;
     const int n_items = sc.n_rsph + (held ? 8 : 0);
 
-    // joint angles: lane k < 7 evaluates sin/cos of joint k
-    float sn = 0.f, cs = 1.f;
-    if (lane < 7) sincosf(sc.th0[lane] + q[t * 8 + lane], &sn, &cs);
-
+    // sphere centres from the chunk's frames (rows of frame link, 48-byte stride: no bank conflicts)
+    const float4(*F)[3] = tw.F[ci];
     float cx[kSlots], cy[kSlots], cz[kSlots], rr[kSlots];
     bool act[kSlots], isblk[kSlots];
 #pragma unroll
@@ -235,45 +290,21 @@ __device__ __forceinline__ void config_collisions(const Scalars& sc, const LaneS
         const int it = lane + 32 * k;
         act[k] = it < n_items;
         isblk[k] = act[k] && it >= sc.n_rsph;
-        rr[k] = act[k] && !isblk[k] ? ls.r[k] : 0.f;
-        cx[k] = ls.lx[k]; cy[k] = ls.ly[k]; cz[k] = ls.lz[k];   // link 0: base frame = world
-    }
-    float R[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1}, o[3] = {0, 0, 0};
-#pragma unroll
-    for (int k = 0; k < 7; ++k) {
-        const float c = __shfl_sync(0xffffffffu, cs, k), s = __shfl_sync(0xffffffffu, sn, k);
-        dh_step<float>(R, o, sc.ca[k], sc.sa[k], sc.a[k], sc.d[k], c, s);
-        if (lane == 0) {
-            tw.fr[k + 1][0] = o[0]; tw.fr[k + 1][1] = o[1]; tw.fr[k + 1][2] = o[2];
-            tw.fr[k + 1][3] = R[2]; tw.fr[k + 1][4] = R[5]; tw.fr[k + 1][5] = R[8];
+        float x = ls.lx[k], y = ls.ly[k], z = ls.lz[k];
+        float4 r0, r1, r2;
+        if (isblk[k]) {
+            block_sphere_local(sc.half[b], it - sc.n_rsph, x, y, z);
+            r0 = tw.H[ci][0]; r1 = tw.H[ci][1]; r2 = tw.H[ci][2];
+            rr[k] = sc.half[b].w;
+        } else {
+            const int l = ls.link[k];
+            r0 = F[l][0]; r1 = F[l][1]; r2 = F[l][2];
+            rr[k] = act[k] ? ls.r[k] : 0.f;
         }
-#pragma unroll
-        for (int sl = 0; sl < kSlots; ++sl) {
-            if (ls.link[sl] == k + 1) {
-                const float x = ls.lx[sl], y = ls.ly[sl], z = ls.lz[sl];
-                cx[sl] = R[0] * x + R[1] * y + R[2] * z + o[0];
-                cy[sl] = R[3] * x + R[4] * y + R[5] * z + o[1];
-                cz[sl] = R[6] * x + R[7] * y + R[8] * z + o[2];
-            }
-        }
+        cx[k] = r0.x * x + r0.y * y + r0.z * z + r0.w;
+        cy[k] = r1.x * x + r1.y * y + r1.z * z + r1.w;
+        cz[k] = r2.x * x + r2.y * y + r2.z * z + r2.w;
     }
-    if (held) {
-        float Rt[9], pt[3], Rb[9], pb[3];
-        tool_frame<float>(sc, R, o, Rt, pt);
-        held_block<float>(sc, b, Rt, pt, Rb, pb);
-#pragma unroll
-        for (int sl = 0; sl < kSlots; ++sl) {
-            if (isblk[sl]) {
-                float lx, ly, lz;
-                block_sphere_local(sc.half[b], lane + 32 * sl - sc.n_rsph, lx, ly, lz);
-                cx[sl] = pb[0] + Rb[0] * lx + Rb[1] * ly + Rb[2] * lz;
-                cy[sl] = pb[1] + Rb[3] * lx + Rb[4] * ly + Rb[5] * lz;
-                cz[sl] = pb[2] + Rb[6] * lx + Rb[7] * ly + Rb[8] * lz;
-                rr[sl] = sc.half[b].w;
-            }
-        }
-    }
-    __syncwarp();
 
     float gx[kSlots], gy[kSlots], gz[kSlots], pen_sum[kSlots];
 #pragma unroll
@@ -425,8 +456,9 @@ __device__ __forceinline__ void config_collisions(const Scalars& sc, const LaneS
         if (any_hit) {
 #pragma unroll
             for (int k = 0; k < 7; ++k) {
-                const float ox = tw.fr[k + 1][0], oy = tw.fr[k + 1][1], oz = tw.fr[k + 1][2];
-                const float zx = tw.fr[k + 1][3], zy = tw.fr[k + 1][4], zz = tw.fr[k + 1][5];
+                const float4 f0 = F[k + 1][0], f1 = F[k + 1][1], f2 = F[k + 1][2];
+                const float ox = f0.w, oy = f1.w, oz = f2.w;
+                const float zx = f0.z, zy = f1.z, zz = f2.z;
 #pragma unroll
                 for (int sl = 0; sl < kSlots; ++sl) {
                     const int lk = isblk[sl] ? 7 : ls.link[sl];
@@ -551,9 +583,16 @@ __device__ void traj_evaluate(const Scalars& sc, const LaneSpheres& ls, const fl
 
     // (2) configuration loop
     float acc_arm = 0.f, acc_blk = 0.f, acc_max = 0.f;
-    for (int t = 1 + w; t < C; t += kTWarps)
-        config_collisions(sc, ls, cub, osph, aabb, sh, sh.warp[w], q, G_arm, G_blk, t, grad, acc_arm, acc_blk, acc_max,
-                          n_tests);
+    const int n_chunks = (C - 1 + kChunk - 1) / kChunk;
+    for (int chk = w; chk < n_chunks; chk += kTWarps) {
+        const int t0 = 1 + kChunk * chk;
+        chunk_fk(sc, q, t0, sh.warp[w]);
+        __syncwarp();
+        for (int ci = 0; ci < kChunk && t0 + ci < C; ++ci)
+            config_collisions(sc, ls, cub, osph, aabb, sh, sh.warp[w], q, G_arm, G_blk, t0 + ci, ci, grad, acc_arm,
+                              acc_blk, acc_max, n_tests);
+        __syncwarp();
+    }
     acc_arm = warp_sum(acc_arm);
     acc_blk = warp_sum(acc_blk);
     acc_max = warp_max(acc_max);
