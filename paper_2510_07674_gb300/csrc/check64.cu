@@ -116,8 +116,7 @@ __global__ void __launch_bounds__(kChkThreads) k_check64(const __grid_constant__
         const int n_items = s.n_rsph + (held ? 8 : 0);
         double Rb[9], pb[3];
         if (held) held64(s, b, Rt, pt, Rb, pb);
-        for (int it = 0; it < n_items; ++it) {
-            double cx, cy, cz, rad;
+        auto centre = [&](int it, double& cx, double& cy, double& cz, double& rad) {
             if (it < s.n_rsph) {
                 const int l = s.rlink[it];
                 const double* ls = s.rsph[it];
@@ -135,13 +134,44 @@ __global__ void __launch_bounds__(kChkThreads) k_check64(const __grid_constant__
                 cz = pb[2] + Rb[6] * lx + Rb[7] * ly + Rb[8] * lz;
                 rad = s.hmin[b] * 0.5;
             }
-            maxpen = fmax(maxpen, pen_env64(s, cub, osph, cx, cy, cz, rad));
-            for (int k = 0; k < B; ++k) {
-                if (k == b) continue;
-                const D4* cb = k < b ? bcub[k] : icub[k];
-                double gx, gy, gz;
-                maxpen = fmax(maxpen, pen_cuboid<double>(cx, cy, cz, rad, cb[0], cb[1], cb[2], cb[3], gx, gy, gz));
+        };
+        // exact cull: box of all spheres of this configuration against each obstacle's box
+        double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+        for (int it = 0; it < n_items; ++it) {
+            double cx, cy, cz, rad;
+            centre(it, cx, cy, cz, rad);
+            lo[0] = fmin(lo[0], cx - rad); lo[1] = fmin(lo[1], cy - rad); lo[2] = fmin(lo[2], cz - rad);
+            hi[0] = fmax(hi[0], cx + rad); hi[1] = fmax(hi[1], cy + rad); hi[2] = fmax(hi[2], cz + rad);
+        }
+        auto visit = [&](const D4* c) {
+            // box of a cuboid record: centre +- |R| h
+            double e[3];
+            for (int a = 0; a < 3; ++a)
+                e[a] = fabs((&c[1].x)[a]) * c[1].w + fabs((&c[2].x)[a]) * c[2].w + fabs((&c[3].x)[a]) * c[3].w;
+            if (c[0].x - e[0] > hi[0] || c[0].x + e[0] < lo[0] || c[0].y - e[1] > hi[1] || c[0].y + e[1] < lo[1] ||
+                c[0].z - e[2] > hi[2] || c[0].z + e[2] < lo[2])
+                return;
+            for (int it = 0; it < n_items; ++it) {
+                double cx, cy, cz, rad, gx, gy, gz;
+                centre(it, cx, cy, cz, rad);
+                maxpen = fmax(maxpen, pen_cuboid<double>(cx, cy, cz, rad, c[0], c[1], c[2], c[3], gx, gy, gz));
             }
+        };
+        for (int ob = 0; ob < s.n_cub; ++ob) visit(&cub[4 * ob]);
+        for (int ob = 0; ob < s.n_osph; ++ob) {
+            const D4 sp = osph[ob];
+            if (sp.x - sp.w > hi[0] || sp.x + sp.w < lo[0] || sp.y - sp.w > hi[1] || sp.y + sp.w < lo[1] ||
+                sp.z - sp.w > hi[2] || sp.z + sp.w < lo[2])
+                continue;
+            for (int it = 0; it < n_items; ++it) {
+                double cx, cy, cz, rad, gx, gy, gz;
+                centre(it, cx, cy, cz, rad);
+                maxpen = fmax(maxpen, pen_sphere<double>(cx, cy, cz, rad, sp, gx, gy, gz));
+            }
+        }
+        for (int k = 0; k < B; ++k) {
+            if (k == b) continue;
+            visit(k < b ? bcub[k] : icub[k]);
         }
     }
     // placement: spheres of block j vs the environment and the blocks below
