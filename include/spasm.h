@@ -179,6 +179,19 @@ spasm_status spasm_traj_eval(spasm_problem_t problem, int n, const float* q, con
 spasm_status spasm_traj_descend(spasm_problem_t problem, int n, float* q, float* lam, float* mu, int k_steps,
                                 int init_multipliers, float* metrics, int* sat);
 
+/* Stage-1 sampling and elite selection that allocates no device memory (the paper has no
+ * counterpart: this serves callers that cannot allocate while they plan, such as a planner
+ * in a real-time control loop that must not stall on cudaMalloc, or a plug-in in a
+ * framework that owns all device memory).  Same result as spasm_place_sample(n, attempt)
+ * followed by spasm_select_topk(m) and a gather: x_elite (device, 4B x m SoA) receives the
+ * m lowest-cost particles in ascending (cost, index) order and cost_elite (device, m) their
+ * linear-form costs.  Intermediates live in one fixed 4 MiB device array of the library:
+ * 4B*n + n + m floats must fit (else SPASM_ERR_INVALID), n <= 32768, m <= 8192.  The first
+ * call on a device looks the array up (make it before any stream capture); calls share the
+ * array, so calls that overlap on the GPU race and must be serialised by the caller. */
+spasm_status spasm_place_select_static(spasm_problem_t problem, int n, uint32_t attempt, int m, float* x_elite,
+                                       float* cost_elite);
+
 /* ---- run control and statistics (not in the paper: bookkeeping of this library) ---- */
 
 /* Counters and device times of the last spasm_place / spasm_optimize calls since the

@@ -608,3 +608,12 @@ extern "C" spasm_status spasm_reset_stats(spasm_problem_t pr) {
     pr->stats = spasm_stats{};
     return SPASM_OK;
 }
+
+// accessors used by the static-scratch entry point (noalloc.cu)
+namespace spasm {
+const Scalars& problem_scalars(const spasm_problem* pr) { return pr->sc; }
+DevTables problem_tables(const spasm_problem* pr) { return pr->tab; }
+cudaStream_t problem_stream(const spasm_problem* pr) { return pr->stream; }
+int* problem_error_word(spasm_problem* pr) { return pr->d_err; }
+spasm_status set_last_error(spasm_status st, const std::string& msg) { return fail(st, msg); }
+}  // namespace spasm

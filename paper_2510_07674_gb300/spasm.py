@@ -24,7 +24,7 @@ STATUS = {0: "SPASM_OK", -1: "SPASM_ERR_INVALID", -2: "SPASM_ERR_NOMEM", -3: "SP
 EXPORTED = ["spasm_create_problem", "spasm_destroy_problem", "spasm_last_error", "spasm_place", "spasm_optimize",
             "spasm_result", "spasm_sizes", "spasm_place_sample", "spasm_place_eval", "spasm_place_descend",
             "spasm_select_topk", "spasm_lift", "spasm_traj_eval", "spasm_traj_descend", "spasm_set_seed",
-            "spasm_set_timing", "spasm_get_stats", "spasm_reset_stats"]
+            "spasm_set_timing", "spasm_get_stats", "spasm_reset_stats", "spasm_place_select_static"]
 
 
 class SpasmError(RuntimeError):
@@ -99,6 +99,7 @@ def lib():
         L.spasm_set_timing.argtypes = [_V, ctypes.c_int]
         L.spasm_get_stats.argtypes = [_V, ctypes.POINTER(_Stats)]
         L.spasm_reset_stats.argtypes = [_V]
+        L.spasm_place_select_static.argtypes = [_V, ctypes.c_int, ctypes.c_uint32, ctypes.c_int, _V, _V]
         for name in EXPORTED:
             if name != "spasm_last_error":
                 getattr(L, name).restype = ctypes.c_int
@@ -250,3 +251,8 @@ def spasm_get_stats(problem: Problem) -> dict:
 
 def spasm_reset_stats(problem: Problem):
     _check(lib().spasm_reset_stats(problem.handle))
+
+
+def spasm_place_select_static(problem: Problem, n: int, attempt: int, m: int, x_elite, cost_elite):
+    """Sampling + elite selection with the library's fixed device scratch (no allocation)."""
+    _check(lib().spasm_place_select_static(problem.handle, n, attempt, m, _dev(x_elite), _dev(cost_elite)))
