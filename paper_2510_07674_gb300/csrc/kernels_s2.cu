@@ -153,6 +153,14 @@ struct TWarp {
     float4 H[kChunk][3];     // held-block frame of each configuration (same row layout)
     float wr[2][kMaxB][4];   // d/d(placed pose k): group arm, group block
     float part[4];           // C_arm, C_block, max penetration
+    uint32_t cmask[kMaxCub / 32];    // environment cuboids that may touch the current chunk
+    uint32_t smask[kMaxOSph / 32];   // environment spheres that may touch the current chunk
+};
+
+// Frames of one configuration kept for the epilogue (grasp and place configurations).
+struct SpecialFrames {
+    float4 F[8][3];
+    float4 H[3];
 };
 
 struct TShared {
@@ -182,8 +190,11 @@ __host__ __device__ inline size_t t_shared_offset(int n_cub, int n_osph) {
 __host__ __device__ inline size_t t_q_offset(int n_cub, int n_osph) {
     return (t_shared_offset(n_cub, n_osph) + sizeof(TShared) + 15) & ~(size_t)15;
 }
+__host__ __device__ inline size_t t_sp_offset(int n_cub, int n_osph, int C) {
+    return t_q_offset(n_cub, n_osph) + (size_t)3 * C * 8 * sizeof(float);
+}
 size_t traj_smem_bytes(const Scalars& sc) {
-    return t_q_offset(sc.n_cub, sc.n_osph) + (size_t)3 * sc.C * 8 * sizeof(float);
+    return t_sp_offset(sc.n_cub, sc.n_osph, sc.C) + (size_t)2 * sc.B * sizeof(SpecialFrames);
 }
 
 // The robot spheres a lane owns (item lane + 32 k), loaded once per kernel launch: link-
@@ -211,14 +222,16 @@ __device__ __forceinline__ LaneSpheres lane_spheres(const Scalars& sc) {
     return ls;
 }
 
-// Forward kinematics of kChunk consecutive configurations by one warp: lane 8c + k holds
-// link transform k of configuration c (k = 0: identity), and a 3-level inclusive scan of
-// affine products inside each group of 8 lanes gives frame_k = T_1 ... T_k.  Frames and
-// the held-block frame land in the warp's shared scratch.
-__device__ __forceinline__ void chunk_fk(const Scalars& sc, const float* __restrict__ q, int t0, TWarp& tw) {
+// Forward kinematics of four configurations by one warp: lane 8c + k holds link transform
+// k of configuration t_c (k = 0: identity), and a 3-level inclusive scan of affine products
+// inside each group of 8 lanes gives frame_k = T_1 ... T_k.  Group c writes its frames (rows
+// (R_i0, R_i1, R_i2, o_i)) to F_c and the frame of the block the tool would hold in t_c's
+// segment to H_c, unless `write` is false for that group.
+__device__ __forceinline__ void chunk_fk(const Scalars& sc, const float* __restrict__ q, int t_c, bool write,
+                                         float4 (*F_c)[3], float4* H_c) {
     const int lane = threadIdx.x & 31;
-    const int c = lane >> 3, k = lane & 7;
-    const int t = min(t0 + c, sc.C - 1);
+    const int k = lane & 7;
+    const int t = min(max(t_c, 1), sc.C - 1);
     float A[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1}, bv[3] = {0, 0, 0};
     if (k > 0) {
         const int j = k - 1;
@@ -252,39 +265,25 @@ __device__ __forceinline__ void chunk_fk(const Scalars& sc, const float* __restr
             for (int i = 0; i < 3; ++i) bv[i] = nb[i];
         }
     }
+    if (!write) return;
 #pragma unroll
-    for (int r = 0; r < 3; ++r) tw.F[c][k][r] = make_float4(A[3 * r], A[3 * r + 1], A[3 * r + 2], bv[r]);
+    for (int r = 0; r < 3; ++r) F_c[k][r] = make_float4(A[3 * r], A[3 * r + 1], A[3 * r + 2], bv[r]);
     if (k == 7) {
-        // tool frame and the block frame it would hold in this configuration's segment
         const int seg = (t - 1) / sc.S, b = seg >> 1;
         float Rt[9], pt[3], Rb[9], pb[3];
         tool_frame<float>(sc, A, bv, Rt, pt);
         held_block<float>(sc, b, Rt, pt, Rb, pb);
 #pragma unroll
-        for (int r = 0; r < 3; ++r) tw.H[c][r] = make_float4(Rb[3 * r], Rb[3 * r + 1], Rb[3 * r + 2], pb[r]);
+        for (int r = 0; r < 3; ++r) H_c[r] = make_float4(Rb[3 * r], Rb[3 * r + 1], Rb[3 * r + 2], pb[r]);
     }
 }
 
-// Collision terms of one configuration, evaluated by one warp: arm spheres and (on the
-// transfer interior) the held block's spheres against the environment and the context
-// blocks.  With `grad`, writes the unscaled group gradients G_arm[t], G_blk[t] and adds
-// placed-pose derivatives into the warp's accumulators.
-__device__ __forceinline__ void config_collisions(const Scalars& sc, const LaneSpheres& ls,
-                                                  const float4* __restrict__ cub, const float4* __restrict__ osph,
-                                                  const float4* __restrict__ aabb, TShared& sh, TWarp& tw,
-                                                  const float* __restrict__ q, float* G_arm, float* G_blk, int t,
-                                                  int ci, bool grad, float& acc_arm, float& acc_blk, float& acc_max,
-                                                  unsigned long long& n_tests) {
+// World centres of the lane's sphere items for one configuration (frames F, held-block
+// frame H); items beyond the robot spheres are the held block's (transfer interior only).
+__device__ __forceinline__ void sphere_centres(const Scalars& sc, const LaneSpheres& ls, const float4 (*F)[3],
+                                               const float4* H, int n_items, int b, float* cx, float* cy, float* cz,
+                                               float* rr, bool* act, bool* isblk) {
     const int lane = threadIdx.x & 31;
-    const int S = sc.S, B = sc.B;
-    const int seg = (t - 1) / S, b = seg >> 1, jj = t - seg * S;
-    const bool held = (seg & 1) && jj < S;
-    const int n_items = sc.n_rsph + (held ? 8 : 0);
-
-    // sphere centres from the chunk's frames (rows of frame link, 48-byte stride: no bank conflicts)
-    const float4(*F)[3] = tw.F[ci];
-    float cx[kSlots], cy[kSlots], cz[kSlots], rr[kSlots];
-    bool act[kSlots], isblk[kSlots];
 #pragma unroll
     for (int k = 0; k < kSlots; ++k) {
         const int it = lane + 32 * k;
@@ -294,7 +293,7 @@ __device__ __forceinline__ void config_collisions(const Scalars& sc, const LaneS
         float4 r0, r1, r2;
         if (isblk[k]) {
             block_sphere_local(sc.half[b], it - sc.n_rsph, x, y, z);
-            r0 = tw.H[ci][0]; r1 = tw.H[ci][1]; r2 = tw.H[ci][2];
+            r0 = H[0]; r1 = H[1]; r2 = H[2];
             rr[k] = sc.half[b].w;
         } else {
             const int l = ls.link[k];
@@ -305,21 +304,38 @@ __device__ __forceinline__ void config_collisions(const Scalars& sc, const LaneS
         cy[k] = r1.x * x + r1.y * y + r1.z * z + r1.w;
         cz[k] = r2.x * x + r2.y * y + r2.z * z + r2.w;
     }
+}
 
-    float gx[kSlots], gy[kSlots], gz[kSlots], pen_sum[kSlots];
-#pragma unroll
-    for (int sl = 0; sl < kSlots; ++sl) gx[sl] = gy[sl] = gz[sl] = pen_sum[sl] = 0.f;
-    bool any_hit = false;
+// Collision terms of the configurations t0 .. t0+nc-1 (kinematics in the warp's frames),
+// evaluated by one warp: arm spheres and, on the transfer interior, the held block's spheres
+// against the environment and the context blocks.  An exact cull first keeps the obstacles
+// whose boxes overlap the box of all spheres of the chunk (consecutive waypoints are close);
+// per configuration lanes own sphere items, screen both slots branch-free and evaluate the
+// penetration only where the separation test fails.  With `grad`, writes the unscaled group
+// gradients G_arm[t], G_blk[t] and accumulates placed-pose derivatives in the warp scratch.
+__device__ __forceinline__ void chunk_collisions(const Scalars& sc, const LaneSpheres& ls,
+                                                 const float4* __restrict__ cub, const float4* __restrict__ osph,
+                                                 const float4* __restrict__ aabb, TShared& sh, TWarp& tw, float* G_arm,
+                                                 float* G_blk, int t0, int nc, bool grad, float& acc_arm, float& acc_blk,
+                                                 float& acc_max, unsigned long long& n_tests) {
+    const int lane = threadIdx.x & 31;
+    const int S = sc.S, B = sc.B;
+    float cx[kSlots], cy[kSlots], cz[kSlots], rr[kSlots];
+    bool act[kSlots], isblk[kSlots];
 
-    // exact cull: axis-aligned box of every sphere of this configuration against each
-    // obstacle's box; a pair whose boxes are disjoint cannot penetrate
+    // pass 1: box of every sphere of the chunk, candidate obstacles by warp ballots
     float lo_x = 3.4e38f, lo_y = 3.4e38f, lo_z = 3.4e38f, hi_x = -3.4e38f, hi_y = -3.4e38f, hi_z = -3.4e38f;
+    for (int ci = 0; ci < nc; ++ci) {
+        const int t = t0 + ci, seg = (t - 1) / S, b = seg >> 1, jj = t - seg * S;
+        const int n_items = sc.n_rsph + (((seg & 1) && jj < S) ? 8 : 0);
+        sphere_centres(sc, ls, tw.F[ci], tw.H[ci], n_items, b, cx, cy, cz, rr, act, isblk);
 #pragma unroll
-    for (int sl = 0; sl < kSlots; ++sl) {
-        if (!act[sl]) continue;
-        lo_x = fminf(lo_x, cx[sl] - rr[sl]); hi_x = fmaxf(hi_x, cx[sl] + rr[sl]);
-        lo_y = fminf(lo_y, cy[sl] - rr[sl]); hi_y = fmaxf(hi_y, cy[sl] + rr[sl]);
-        lo_z = fminf(lo_z, cz[sl] - rr[sl]); hi_z = fmaxf(hi_z, cz[sl] + rr[sl]);
+        for (int sl = 0; sl < kSlots; ++sl) {
+            if (!act[sl]) continue;
+            lo_x = fminf(lo_x, cx[sl] - rr[sl]); hi_x = fmaxf(hi_x, cx[sl] + rr[sl]);
+            lo_y = fminf(lo_y, cy[sl] - rr[sl]); hi_y = fmaxf(hi_y, cy[sl] + rr[sl]);
+            lo_z = fminf(lo_z, cz[sl] - rr[sl]); hi_z = fmaxf(hi_z, cz[sl] + rr[sl]);
+        }
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
@@ -333,176 +349,185 @@ __device__ __forceinline__ void config_collisions(const Scalars& sc, const LaneS
     auto overlaps = [&](const float4& blo, const float4& bhi) {
         return blo.x <= hi_x && bhi.x >= lo_x && blo.y <= hi_y && bhi.y >= lo_y && blo.z <= hi_z && bhi.z >= lo_z;
     };
-    int visits = 0;
+    const int n_cw = (sc.n_cub + 31) >> 5, n_sw = (sc.n_osph + 31) >> 5;
+    for (int wd = 0; wd < n_cw; ++wd) {
+        const int oi = 32 * wd + lane;
+        const unsigned m = __ballot_sync(0xffffffffu, oi < sc.n_cub && overlaps(aabb[2 * oi], aabb[2 * oi + 1]));
+        if (lane == 0) tw.cmask[wd] = m;
+    }
+    for (int wd = 0; wd < n_sw; ++wd) {
+        const int oi = 32 * wd + lane;
+        const int ai = sc.n_cub + oi;
+        const unsigned m = __ballot_sync(0xffffffffu, oi < sc.n_osph && overlaps(aabb[2 * ai], aabb[2 * ai + 1]));
+        if (lane == 0) tw.smask[wd] = m;
+    }
+    const unsigned bm_placed = __ballot_sync(0xffffffffu, lane < B && overlaps(sh.baabb[lane][0], sh.baabb[lane][1]));
+    const unsigned bm_init = __ballot_sync(0xffffffffu, lane < B && overlaps(sh.iaabb[lane][0], sh.iaabb[lane][1]));
+    __syncwarp();
 
-    // environment cuboids (shared memory, broadcast reads), culled by a warp ballot; both
-    // slots are screened branch-free, the penetration only for overlapping ones
-    for (int base = 0; base < sc.n_cub; base += 32) {
-        const int oi = base + lane;
-        const bool ov = oi < sc.n_cub && overlaps(aabb[2 * oi], aabb[2 * oi + 1]);
-        unsigned m = __ballot_sync(0xffffffffu, ov);
-        visits += __popc(m);
-        while (m) {
-            const int ob = base + __ffs(m) - 1;
-            m &= m - 1;
-            const float4 o0 = cub[4 * ob], o1 = cub[4 * ob + 1], o2 = cub[4 * ob + 2], o3 = cub[4 * ob + 3];
-            float p0[kSlots], p1[kSlots], p2[kSlots], q0[kSlots], q1[kSlots], q2[kSlots], qm[kSlots];
+    // pass 2: every configuration against the candidates
+    for (int ci = 0; ci < nc; ++ci) {
+        const int t = t0 + ci, seg = (t - 1) / S, b = seg >> 1, jj = t - seg * S;
+        const bool held = (seg & 1) && jj < S;
+        const int n_items = sc.n_rsph + (held ? 8 : 0);
+        sphere_centres(sc, ls, tw.F[ci], tw.H[ci], n_items, b, cx, cy, cz, rr, act, isblk);
+        float gx[kSlots], gy[kSlots], gz[kSlots], pen_sum[kSlots];
 #pragma unroll
-            for (int sl = 0; sl < kSlots; ++sl)
-                qm[sl] = cub_local<float>(cx[sl], cy[sl], cz[sl], o0, o1, o2, o3, p0[sl], p1[sl], p2[sl], q0[sl],
-                                          q1[sl], q2[sl]);
-#pragma unroll
-            for (int sl = 0; sl < kSlots; ++sl) {
-                if (!act[sl] || !(qm[sl] < rr[sl])) continue;
-                float ax, ay, az;
-                const float pen = pen_finish<float>(p0[sl], p1[sl], p2[sl], q0[sl], q1[sl], q2[sl], qm[sl], rr[sl], o1,
-                                                    o2, o3, ax, ay, az);
-                if (pen > 0.f) {
-                    any_hit = true;
-                    pen_sum[sl] += pen;
-                    acc_max = fmaxf(acc_max, pen);
-                    gx[sl] += ax; gy[sl] += ay; gz[sl] += az;
-                }
-            }
-        }
-    }
-    for (int base = 0; base < sc.n_osph; base += 32) {
-        const int oi = base + lane;
-        const bool ov = oi < sc.n_osph && overlaps(aabb[2 * (sc.n_cub + oi)], aabb[2 * (sc.n_cub + oi) + 1]);
-        unsigned m = __ballot_sync(0xffffffffu, ov);
-        visits += __popc(m);
-        while (m) {
-            const int ob = base + __ffs(m) - 1;
-            m &= m - 1;
-            const float4 os = osph[ob];
-#pragma unroll
-            for (int sl = 0; sl < kSlots; ++sl) {
-                if (!act[sl]) continue;
-                float ax, ay, az;
-                const float pen = pen_sphere<float>(cx[sl], cy[sl], cz[sl], rr[sl], os, ax, ay, az);
-                if (pen > 0.f) {
-                    any_hit = true;
-                    pen_sum[sl] += pen;
-                    acc_max = fmaxf(acc_max, pen);
-                    gx[sl] += ax; gy[sl] += ay; gz[sl] += az;
-                }
-            }
-        }
-    }
-    // context blocks: placed (k < b, movable) and not yet moved (k > b); lane kb culls block kb
-    {
-        bool ov = false;
-        if (lane < B && lane != b) {
-            const float4* bx = lane < b ? sh.baabb[lane] : sh.iaabb[lane];
-            ov = overlaps(bx[0], bx[1]);
-        }
-        unsigned m = __ballot_sync(0xffffffffu, ov);
-        visits += __popc(m);
-        while (m) {
-            const int kb = __ffs(m) - 1;
-            m &= m - 1;
-            const bool placed = kb < b;
-            const float4* cb = placed ? sh.bcub[kb] : sh.icub[kb];
-            const float4 o0 = cb[0], o1 = cb[1], o2 = cb[2], o3 = cb[3];
-            float dax = 0.f, day = 0.f, daz = 0.f, dayaw = 0.f, dbx = 0.f, dby = 0.f, dbz = 0.f, dbyaw = 0.f;
-            bool hit = false;
-            float p0[kSlots], p1[kSlots], p2[kSlots], q0[kSlots], q1[kSlots], q2[kSlots], qm[kSlots];
-#pragma unroll
-            for (int sl = 0; sl < kSlots; ++sl)
-                qm[sl] = cub_local<float>(cx[sl], cy[sl], cz[sl], o0, o1, o2, o3, p0[sl], p1[sl], p2[sl], q0[sl],
-                                          q1[sl], q2[sl]);
-#pragma unroll
-            for (int sl = 0; sl < kSlots; ++sl) {
-                if (!act[sl] || !(qm[sl] < rr[sl])) continue;
-                float ax, ay, az;
-                const float pen = pen_finish<float>(p0[sl], p1[sl], p2[sl], q0[sl], q1[sl], q2[sl], qm[sl], rr[sl], o1,
-                                                    o2, o3, ax, ay, az);
-                if (pen > 0.f) {
-                    any_hit = true;
-                    hit = true;
-                    pen_sum[sl] += pen;
-                    acc_max = fmaxf(acc_max, pen);
-                    gx[sl] += ax; gy[sl] += ay; gz[sl] += az;
-                    // rigid motion of the cuboid: d/dP = -g, d/dyaw = -((c - P) x g)_z
-                    const float dyaw = -((cx[sl] - o0.x) * ay - (cy[sl] - o0.y) * ax);
-                    if (isblk[sl]) { dbx -= ax; dby -= ay; dbz -= az; dbyaw += dyaw; }
-                    else { dax -= ax; day -= ay; daz -= az; dayaw += dyaw; }
-                }
-            }
-            if (grad && placed && __any_sync(0xffffffffu, hit)) {
-                dax = warp_sum(dax); day = warp_sum(day); daz = warp_sum(daz); dayaw = warp_sum(dayaw);
-                dbx = warp_sum(dbx); dby = warp_sum(dby); dbz = warp_sum(dbz); dbyaw = warp_sum(dbyaw);
-                if (lane == 0) {
-                    tw.wr[0][kb][0] += dax; tw.wr[0][kb][1] += day; tw.wr[0][kb][2] += daz; tw.wr[0][kb][3] += dayaw;
-                    tw.wr[1][kb][0] += dbx; tw.wr[1][kb][1] += dby; tw.wr[1][kb][2] += dbz; tw.wr[1][kb][3] += dbyaw;
-                }
-            }
-        }
-    }
-    n_tests += (unsigned long long)visits * (unsigned)n_items;
-#pragma unroll
-    for (int sl = 0; sl < kSlots; ++sl) {
-        if (isblk[sl]) acc_blk += pen_sum[sl];
-        else acc_arm += pen_sum[sl];
-    }
-    if (!grad) return;
+        for (int sl = 0; sl < kSlots; ++sl) gx[sl] = gy[sl] = gz[sl] = pen_sum[sl] = 0.f;
+        bool any_hit = false;
+        int visits = 0;
 
-    // backward: dC/dq_k = sum_s z_k . ((c_s - o_k) x g_s) over spheres on links >= k
-    float ja[7], jb[7];
+        for (int wd = 0; wd < n_cw; ++wd) {
+            unsigned m = tw.cmask[wd];
+            visits += __popc(m);
+            while (m) {
+                const int ob = 32 * wd + __ffs(m) - 1;
+                m &= m - 1;
+                const float4 o0 = cub[4 * ob], o1 = cub[4 * ob + 1], o2 = cub[4 * ob + 2], o3 = cub[4 * ob + 3];
+                float p0[kSlots], p1[kSlots], p2[kSlots], q0[kSlots], q1[kSlots], q2[kSlots], qm[kSlots];
 #pragma unroll
-    for (int k = 0; k < 7; ++k) ja[k] = jb[k] = 0.f;
-    const bool warp_hit = __any_sync(0xffffffffu, any_hit);
-    if (warp_hit) {
-        if (any_hit) {
-#pragma unroll
-            for (int k = 0; k < 7; ++k) {
-                const float4 f0 = F[k + 1][0], f1 = F[k + 1][1], f2 = F[k + 1][2];
-                const float ox = f0.w, oy = f1.w, oz = f2.w;
-                const float zx = f0.z, zy = f1.z, zz = f2.z;
+                for (int sl = 0; sl < kSlots; ++sl)
+                    qm[sl] = cub_local<float>(cx[sl], cy[sl], cz[sl], o0, o1, o2, o3, p0[sl], p1[sl], p2[sl], q0[sl],
+                                              q1[sl], q2[sl]);
 #pragma unroll
                 for (int sl = 0; sl < kSlots; ++sl) {
-                    const int lk = isblk[sl] ? 7 : ls.link[sl];
-                    if (!act[sl] || lk < k + 1) continue;
-                    const float vx = cx[sl] - ox, vy = cy[sl] - oy, vz = cz[sl] - oz;
-                    const float mm = zx * (vy * gz[sl] - vz * gy[sl]) + zy * (vz * gx[sl] - vx * gz[sl]) +
-                                     zz * (vx * gy[sl] - vy * gx[sl]);
-                    if (isblk[sl]) jb[k] += mm; else ja[k] += mm;
+                    if (!act[sl] || !(qm[sl] < rr[sl])) continue;
+                    float ax, ay, az;
+                    const float pen = pen_finish<float>(p0[sl], p1[sl], p2[sl], q0[sl], q1[sl], q2[sl], qm[sl], rr[sl],
+                                                        o1, o2, o3, ax, ay, az);
+                    if (pen > 0.f) {
+                        any_hit = true;
+                        pen_sum[sl] += pen;
+                        acc_max = fmaxf(acc_max, pen);
+                        gx[sl] += ax; gy[sl] += ay; gz[sl] += az;
+                    }
                 }
             }
         }
+        for (int wd = 0; wd < n_sw; ++wd) {
+            unsigned m = tw.smask[wd];
+            visits += __popc(m);
+            while (m) {
+                const int ob = 32 * wd + __ffs(m) - 1;
+                m &= m - 1;
+                const float4 os = osph[ob];
 #pragma unroll
-        for (int k = 0; k < 7; ++k) { ja[k] = warp_sum(ja[k]); jb[k] = warp_sum(jb[k]); }
-    }
-    if (lane < 7) {
-        float va = 0.f, vb = 0.f;
+                for (int sl = 0; sl < kSlots; ++sl) {
+                    if (!act[sl]) continue;
+                    float ax, ay, az;
+                    const float pen = pen_sphere<float>(cx[sl], cy[sl], cz[sl], rr[sl], os, ax, ay, az);
+                    if (pen > 0.f) {
+                        any_hit = true;
+                        pen_sum[sl] += pen;
+                        acc_max = fmaxf(acc_max, pen);
+                        gx[sl] += ax; gy[sl] += ay; gz[sl] += az;
+                    }
+                }
+            }
+        }
+        // context blocks: placed (k < b, movable) and not yet moved (k > b)
+        {
+            const unsigned below = (1u << b) - 1u;
+            unsigned m = (bm_placed & below) | (bm_init & ~below & ~(1u << b));
+            visits += __popc(m);
+            while (m) {
+                const int kb = __ffs(m) - 1;
+                m &= m - 1;
+                const bool placed = kb < b;
+                const float4* cb = placed ? sh.bcub[kb] : sh.icub[kb];
+                const float4 o0 = cb[0], o1 = cb[1], o2 = cb[2], o3 = cb[3];
+                float dax = 0.f, day = 0.f, daz = 0.f, dayaw = 0.f, dbx = 0.f, dby = 0.f, dbz = 0.f, dbyaw = 0.f;
+                bool hit = false;
+                float p0[kSlots], p1[kSlots], p2[kSlots], q0[kSlots], q1[kSlots], q2[kSlots], qm[kSlots];
 #pragma unroll
-        for (int k = 0; k < 7; ++k) if (k == lane) { va = ja[k]; vb = jb[k]; }
-        G_arm[t * 8 + lane] = va;
-        G_blk[t * 8 + lane] = vb;
-    }
-}
+                for (int sl = 0; sl < kSlots; ++sl)
+                    qm[sl] = cub_local<float>(cx[sl], cy[sl], cz[sl], o0, o1, o2, o3, p0[sl], p1[sl], p2[sl], q0[sl],
+                                              q1[sl], q2[sl]);
+#pragma unroll
+                for (int sl = 0; sl < kSlots; ++sl) {
+                    if (!act[sl] || !(qm[sl] < rr[sl])) continue;
+                    float ax, ay, az;
+                    const float pen = pen_finish<float>(p0[sl], p1[sl], p2[sl], q0[sl], q1[sl], q2[sl], qm[sl], rr[sl],
+                                                        o1, o2, o3, ax, ay, az);
+                    if (pen > 0.f) {
+                        any_hit = true;
+                        hit = true;
+                        pen_sum[sl] += pen;
+                        acc_max = fmaxf(acc_max, pen);
+                        gx[sl] += ax; gy[sl] += ay; gz[sl] += az;
+                        // rigid motion of the cuboid: d/dP = -g, d/dyaw = -((c - P) x g)_z
+                        const float dyaw = -((cx[sl] - o0.x) * ay - (cy[sl] - o0.y) * ax);
+                        if (isblk[sl]) { dbx -= ax; dby -= ay; dbz -= az; dbyaw += dyaw; }
+                        else { dax -= ax; day -= ay; daz -= az; dayaw += dyaw; }
+                    }
+                }
+                if (grad && placed && __any_sync(0xffffffffu, hit)) {
+                    dax = warp_sum(dax); day = warp_sum(day); daz = warp_sum(daz); dayaw = warp_sum(dayaw);
+                    dbx = warp_sum(dbx); dby = warp_sum(dby); dbz = warp_sum(dbz); dbyaw = warp_sum(dbyaw);
+                    if (lane == 0) {
+                        tw.wr[0][kb][0] += dax; tw.wr[0][kb][1] += day; tw.wr[0][kb][2] += daz;
+                        tw.wr[0][kb][3] += dayaw;
+                        tw.wr[1][kb][0] += dbx; tw.wr[1][kb][1] += dby; tw.wr[1][kb][2] += dbz;
+                        tw.wr[1][kb][3] += dbyaw;
+                    }
+                }
+            }
+        }
+        n_tests += (unsigned long long)visits * (unsigned)n_items;
+#pragma unroll
+        for (int sl = 0; sl < kSlots; ++sl) {
+            if (isblk[sl]) acc_blk += pen_sum[sl];
+            else acc_arm += pen_sum[sl];
+        }
+        if (!grad) continue;
 
-// One placed pose from the place configuration of block b: (x, y, z, yaw) of the block
-// frame held by the tool.
-__device__ __forceinline__ void placed_pose(const Scalars& sc, int b, const float* q, float pose[4]) {
-    float qq[7];
-    for (int j = 0; j < 7; ++j) qq[j] = q[j];
-    float R[8][9], o[8][3], Rt[9], pt[3], Rb[9], pb[3];
-    fk_full<float>(sc, qq, R, o, Rt, pt);
-    held_block<float>(sc, b, Rt, pt, Rb, pb);
-    pose[0] = pb[0]; pose[1] = pb[1]; pose[2] = pb[2];
-    pose[3] = atan2f(Rb[3], Rb[0]);
+        // backward: dC/dq_k = sum_s z_k . ((c_s - o_k) x g_s) over spheres on links >= k
+        float ja[7], jb[7];
+#pragma unroll
+        for (int k = 0; k < 7; ++k) ja[k] = jb[k] = 0.f;
+        const bool warp_hit = __any_sync(0xffffffffu, any_hit);
+        if (warp_hit) {
+            const float4(*F)[3] = tw.F[ci];
+            if (any_hit) {
+#pragma unroll
+                for (int k = 0; k < 7; ++k) {
+                    const float4 f0 = F[k + 1][0], f1 = F[k + 1][1], f2 = F[k + 1][2];
+                    const float ox = f0.w, oy = f1.w, oz = f2.w;
+                    const float zx = f0.z, zy = f1.z, zz = f2.z;
+#pragma unroll
+                    for (int sl = 0; sl < kSlots; ++sl) {
+                        const int lk = isblk[sl] ? 7 : ls.link[sl];
+                        if (!act[sl] || lk < k + 1) continue;
+                        const float vx = cx[sl] - ox, vy = cy[sl] - oy, vz = cz[sl] - oz;
+                        const float mm = zx * (vy * gz[sl] - vz * gy[sl]) + zy * (vz * gx[sl] - vx * gz[sl]) +
+                                         zz * (vx * gy[sl] - vy * gx[sl]);
+                        if (isblk[sl]) jb[k] += mm; else ja[k] += mm;
+                    }
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < 7; ++k) { ja[k] = warp_sum(ja[k]); jb[k] = warp_sum(jb[k]); }
+        }
+        if (lane < 7) {
+            float va = 0.f, vb = 0.f;
+#pragma unroll
+            for (int k = 0; k < 7; ++k) if (k == lane) { va = ja[k]; vb = jb[k]; }
+            G_arm[t * 8 + lane] = va;
+            G_blk[t * 8 + lane] = vb;
+        }
+    }
 }
 
 // Residuals of the start group at the grasp (which = 0) or place (which = 1) configuration
-// of block b, and, with s_r != nullptr, their weighted joint gradient sum_r s_r dh_r/dq.
-__device__ __forceinline__ void start_terms(const Scalars& sc, int b, int which, const float* q, float* h_out,
+// of block b from that configuration's frames, and, with s_r != nullptr, their weighted
+// joint gradient sum_r s_r dh_r/dq (plus the placed-pose gradient g4 at a place config).
+__device__ __forceinline__ void start_terms(const Scalars& sc, int b, int which, const SpecialFrames& sf, float* h_out,
                                             const float* s_r, float grad_out[7], const float* g4 /*4 or null*/) {
-    float qq[7];
-    for (int j = 0; j < 7; ++j) qq[j] = q[j];
-    float R[8][9], o[8][3], Rt[9], pt[3], Rb[9], pb[3];
-    fk_full<float>(sc, qq, R, o, Rt, pt);
-    held_block<float>(sc, b, Rt, pt, Rb, pb);
+    float Rb[9], pb[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        Rb[3 * r] = sf.H[r].x; Rb[3 * r + 1] = sf.H[r].y; Rb[3 * r + 2] = sf.H[r].z; pb[r] = sf.H[r].w;
+    }
     float roll, pitch, wr[3], wp[3];
     roll_pitch_torque<float>(Rb, roll, pitch, wr, wp);
     if (which == 0) {
@@ -537,13 +562,13 @@ __device__ __forceinline__ void start_terms(const Scalars& sc, int b, int which,
     M[1] += pb[2] * F[0] - pb[0] * F[2];
     M[2] += pb[0] * F[1] - pb[1] * F[0];
     for (int k = 0; k < 7; ++k) {
-        const float* ok = o[k + 1];
-        const float zx = R[k + 1][2], zy = R[k + 1][5], zz = R[k + 1][8];
+        const float4 f0 = sf.F[k + 1][0], f1 = sf.F[k + 1][1], f2 = sf.F[k + 1][2];
+        const float ok[3] = {f0.w, f1.w, f2.w};
         // z . (M - o x F)
         const float tx = M[0] - (ok[1] * F[2] - ok[2] * F[1]);
         const float ty = M[1] - (ok[2] * F[0] - ok[0] * F[2]);
         const float tz = M[2] - (ok[0] * F[1] - ok[1] * F[0]);
-        grad_out[k] = zx * tx + zy * ty + zz * tz;
+        grad_out[k] = f0.z * tx + f1.z * ty + f2.z * tz;
     }
 }
 
@@ -559,38 +584,44 @@ __device__ __forceinline__ void cuboid_aabb(const float4* c, float4* box) {
     box[1] = make_float4(c[0].x + ex, c[0].y + ey, c[0].z + ez, 0.f);
 }
 
-// Evaluate the whole particle: placed poses, configuration loop, residuals, objective;
-// with `grad`, assemble dL/dq into G_arm (G_blk is scratch).
+// Evaluate the whole particle: kinematics of the grasp/place configurations and the placed
+// poses, the configuration loop, residuals and objective; with `grad`, the assembled dL/dq
+// ends up in G_blk (G_arm holds the unscaled arm-group gradient).
 __device__ void traj_evaluate(const Scalars& sc, const LaneSpheres& ls, const float4* cub, const float4* osph,
-                              const float4* aabb, TShared& sh, float* q, float* G_arm, float* G_blk, bool grad,
-                              unsigned long long& n_tests) {
+                              const float4* aabb, TShared& sh, SpecialFrames* sp, float* q, float* G_arm,
+                              float* G_blk, bool grad, unsigned long long& n_tests) {
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const int B = sc.B, S = sc.S, C = sc.C, NR = sc.NR;
 
-    // (1) placed poses of this iteration
-    if (w == 0) {
-        if (lane < B) {
-            float pose[4];
-            placed_pose(sc, lane, q + t_place(S, lane) * 8, pose);
-            for (int i = 0; i < 4; ++i) sh.pose[4 * lane + i] = pose[i];
-            block_cuboid(pose[0], pose[1], pose[2], pose[3], sc.half[lane], sh.bcub[lane]);
-            cuboid_aabb(sh.bcub[lane], sh.baabb[lane]);
-        }
+    // (1) frames of the 2B grasp/place configurations (4 per warp), kept for the epilogue
+    const int n_sp = 2 * B;
+    for (int gi = w; gi * 4 < n_sp; gi += kTWarps) {
+        const int si = 4 * gi + (lane >> 3);
+        const bool ok = si < n_sp;
+        chunk_fk(sc, q, ok ? (si + 1) * S : 1, ok, sp[ok ? si : 0].F, sp[ok ? si : 0].H);
     }
-    // zero per-warp accumulators
     for (int i = lane; i < 2 * kMaxB * 4; i += 32) (&sh.warp[w].wr[0][0][0])[i] = 0.f;
     __syncthreads();
+    // placed poses: the block frame at each place configuration, (x, y, z, yaw)
+    if (w == 0 && lane < B) {
+        const float4* H = sp[2 * lane + 1].H;
+        const float pose[4] = {H[0].w, H[1].w, H[2].w, atan2f(H[1].x, H[0].x)};
+        for (int i = 0; i < 4; ++i) sh.pose[4 * lane + i] = pose[i];
+        block_cuboid(pose[0], pose[1], pose[2], pose[3], sc.half[lane], sh.bcub[lane]);
+        cuboid_aabb(sh.bcub[lane], sh.baabb[lane]);
+    }
+    __syncthreads();
 
-    // (2) configuration loop
+    // (2) configuration loop: chunks of kChunk consecutive configurations per warp
     float acc_arm = 0.f, acc_blk = 0.f, acc_max = 0.f;
     const int n_chunks = (C - 1 + kChunk - 1) / kChunk;
     for (int chk = w; chk < n_chunks; chk += kTWarps) {
         const int t0 = 1 + kChunk * chk;
-        chunk_fk(sc, q, t0, sh.warp[w]);
+        const int c = lane >> 3;
+        chunk_fk(sc, q, t0 + c, true, sh.warp[w].F[c], sh.warp[w].H[c]);
         __syncwarp();
-        for (int ci = 0; ci < kChunk && t0 + ci < C; ++ci)
-            config_collisions(sc, ls, cub, osph, aabb, sh, sh.warp[w], q, G_arm, G_blk, t0 + ci, ci, grad, acc_arm,
-                              acc_blk, acc_max, n_tests);
+        chunk_collisions(sc, ls, cub, osph, aabb, sh, sh.warp[w], G_arm, G_blk, t0, min(kChunk, C - t0), grad,
+                         acc_arm, acc_blk, acc_max, n_tests);
         __syncwarp();
     }
     acc_arm = warp_sum(acc_arm);
@@ -599,13 +630,12 @@ __device__ void traj_evaluate(const Scalars& sc, const LaneSpheres& ls, const fl
     if (lane == 0) { sh.warp[w].part[0] = acc_arm; sh.warp[w].part[1] = acc_blk; sh.warp[w].part[2] = acc_max; }
     __syncthreads();
 
-    // (3) epilogue on warp 0: residuals, objective, pose and start gradients
+    // (3) epilogue.  (a) warp 0: group sums and the placement residuals; warp 1: start residuals
     if (w == 0) {
-        float ca = lane < kTWarps ? sh.warp[lane].part[0] : 0.f;
-        float cb = lane < kTWarps ? sh.warp[lane].part[1] : 0.f;
+        const float ca = lane < kTWarps ? sh.warp[lane].part[0] : 0.f;
+        const float cb = lane < kTWarps ? sh.warp[lane].part[1] : 0.f;
         float cm = lane < kTWarps ? sh.warp[lane].part[2] : 0.f;
-        // fixed-order sums over warps
-        float tot_a = 0.f, tot_b = 0.f;
+        float tot_a = 0.f, tot_b = 0.f;   // fixed-order sums over warps
         for (int i = 0; i < kTWarps; ++i) {
             tot_a += __shfl_sync(0xffffffffu, ca, i);
             tot_b += __shfl_sync(0xffffffffu, cb, i);
@@ -615,8 +645,6 @@ __device__ void traj_evaluate(const Scalars& sc, const LaneSpheres& ls, const fl
         place_eval_warp(sc, cub, sc.n_cub, osph, sc.n_osph, sh.pose, false, kPlaceForward, nullptr, nullptr, 0.f,
                         nullptr, sh.ps, po);
         if (lane < B) {
-            start_terms(sc, lane, 0, q + t_grasp(S, lane) * 8, &sh.h[5 * lane], nullptr, nullptr, nullptr);
-            start_terms(sc, lane, 1, q + t_place(S, lane) * 8, &sh.h[5 * B + 2 * lane], nullptr, nullptr, nullptr);
             sh.h[7 * B + lane] = sh.ps.e[lane];
             sh.h[8 * B + lane] = sh.ps.D[lane];
         }
@@ -628,8 +656,13 @@ __device__ void traj_evaluate(const Scalars& sc, const LaneSpheres& ls, const fl
             sh.c_coll = po.c_coll; sh.c_stable = po.c_stable; sh.c_height = po.c_height;
             sh.pm_pen = po.maxpen; sh.pm_D = po.maxD; sh.pm_dz = po.maxdz;
         }
-        __syncwarp();
-        // start-group values and maxima
+    } else if (w == 1 && lane < B) {
+        start_terms(sc, lane, 0, sp[2 * lane], &sh.h[5 * lane], nullptr, nullptr, nullptr);
+        start_terms(sc, lane, 1, sp[2 * lane + 1], &sh.h[5 * B + 2 * lane], nullptr, nullptr, nullptr);
+    }
+    __syncthreads();
+    // (b) objective and dL/dh
+    if (w == 0) {
         float v_start = 0.f, v_tilt = 0.f;
         if (lane < B) {
             const float* hg = &sh.h[5 * lane];
@@ -639,7 +672,6 @@ __device__ void traj_evaluate(const Scalars& sc, const LaneSpheres& ls, const fl
         }
         const float c_start = warp_sum(v_start + v_tilt);
         const float m_start = warp_max(v_start), m_tilt = warp_max(v_tilt);
-        // objective and dL/dh
         float Lp = 0.f;
         for (int r = lane; r < NR; r += 32) {
             const float sw = residual_sqrt_weight(sc, r), hw = sw * sh.h[r];
@@ -647,31 +679,40 @@ __device__ void traj_evaluate(const Scalars& sc, const LaneSpheres& ls, const fl
             sh.s[r] = (sh.lam[r] + sh.mu * hw) * sw;
         }
         Lp = warp_sum(Lp);
-        if (lane == 0) { sh.L = Lp; sh.c_start = c_start; sh.max_start = m_start; sh.max_tilt = m_tilt; }
-        __syncwarp();
-        if (grad) {
+        if (lane == 0) {
+            sh.L = Lp; sh.c_start = c_start; sh.max_start = m_start; sh.max_tilt = m_tilt;
+            sh.s_arm = sh.s[9 * B + 1]; sh.s_blk = sh.s[9 * B + 2];
+        }
+    }
+    __syncthreads();
+    if (grad) {
+        // (c) warp 0: placement gradient w.r.t. the placed poses; warp 1: grasp gradients
+        if (w == 0) {
+            PlaceOut po;
             place_eval_warp(sc, cub, sc.n_cub, osph, sc.n_osph, sh.pose, false, kPlaceExplicit, &sh.s[8 * B],
                             &sh.s[7 * B], sh.s[9 * B], sh.g4, sh.ps, po);
-            const float s_arm = sh.s[9 * B + 1], s_blk = sh.s[9 * B + 2];
+            const float s_arm = sh.s_arm, s_blk = sh.s_blk;
             for (int i = lane; i < 4 * B; i += 32) {
                 const int kb = i >> 2, c = i & 3;
                 float wa = 0.f, wb = 0.f;
                 for (int ww = 0; ww < kTWarps; ++ww) { wa += sh.warp[ww].wr[0][kb][c]; wb += sh.warp[ww].wr[1][kb][c]; }
                 sh.g4[i] += s_arm * wa + s_blk * wb;
             }
-            if (lane == 0) { sh.s_arm = s_arm; sh.s_blk = s_blk; }
-            __syncwarp();
-            if (lane < B) {
-                float hbuf[5];
-                start_terms(sc, lane, 0, q + t_grasp(S, lane) * 8, hbuf, &sh.s[5 * lane], sh.extra[lane], nullptr);
-                start_terms(sc, lane, 1, q + t_place(S, lane) * 8, hbuf, &sh.s[5 * B + 2 * lane], sh.extra[B + lane],
-                            &sh.g4[4 * lane]);
-            }
+        } else if (w == 1 && lane < B) {
+            float hbuf[5];
+            start_terms(sc, lane, 0, sp[2 * lane], hbuf, &sh.s[5 * lane], sh.extra[lane], nullptr);
         }
+        __syncthreads();
+        // (d) place configurations: tilt residuals and the placed-pose gradient through fk
+        if (w == 1 && lane < B) {
+            float hbuf[5];
+            start_terms(sc, lane, 1, sp[2 * lane + 1], hbuf, &sh.s[5 * B + 2 * lane], sh.extra[B + lane],
+                        &sh.g4[4 * lane]);
+        }
+        __syncthreads();
     }
-    __syncthreads();
 
-    // (4) path length, joint limits; assemble the gradient into G_arm
+    // (4) path length, joint limits; assemble the gradient into G_blk
     float path = 0.f, jl = 0.f;
     for (int i = tid; i < C * 7; i += kTThreads) {
         const int t = i / 7, j = i % 7;
@@ -700,8 +741,8 @@ __device__ void traj_evaluate(const Scalars& sc, const LaneSpheres& ls, const fl
                     gsum += (e & 1) ? sh.extra[B + bb][j] : sh.extra[bb][j];
                 }
             }
+            G_blk[t * 8 + j] = gsum;   // G_blk becomes the assembled gradient
         }
-        if (grad) G_blk[t * 8 + j] = gsum;   // G_blk becomes the assembled gradient
     }
     path = warp_sum(path);
     jl = warp_sum(jl);
@@ -728,6 +769,7 @@ __global__ void __launch_bounds__(kTThreads, 2) k_traj(const __grid_constant__ S
     float* q = reinterpret_cast<float*>(smem_raw + t_q_offset(sc.n_cub, sc.n_osph));
     float* G_arm = q + sc.C * 8;
     float* G_blk = G_arm + sc.C * 8;
+    SpecialFrames* sp = reinterpret_cast<SpecialFrames*>(smem_raw + t_sp_offset(sc.n_cub, sc.n_osph, sc.C));
     if (!stage_tables(cub, tab.cub, (uint32_t)sc.n_cub * 64u, osph, tab.osph, (uint32_t)sc.n_osph * 16u, bar, err))
         return;
     const int p = blockIdx.x;
@@ -759,7 +801,7 @@ __global__ void __launch_bounds__(kTThreads, 2) k_traj(const __grid_constant__ S
     if (mode == kTrajDescend) {
         const int K = io.k_steps;
         for (int k = 1; k <= K; ++k) {
-            traj_evaluate(sc, ls, cub, osph, aabb, sh, q, G_arm, G_blk, true, n_tests);
+            traj_evaluate(sc, ls, cub, osph, aabb, sh, sp, q, G_arm, G_blk, true, n_tests);
             const float eta = sc.eta_traj * (1.f - (float)k / (float)K);
             for (int i = tid; i < C * 7; i += kTThreads) {
                 const int t = i / 7, j = i % 7;
@@ -776,7 +818,7 @@ __global__ void __launch_bounds__(kTThreads, 2) k_traj(const __grid_constant__ S
         }
     }
     const bool want_grad = mode == kTrajEval && io.grad != nullptr;
-    traj_evaluate(sc, ls, cub, osph, aabb, sh, q, G_arm, G_blk, want_grad, n_tests);
+    traj_evaluate(sc, ls, cub, osph, aabb, sh, sp, q, G_arm, G_blk, want_grad, n_tests);
     if (io.tests && (threadIdx.x & 31) == 0) atomicAdd(io.tests, n_tests);
 
     // outputs
