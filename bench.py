@@ -150,6 +150,26 @@ def count_tests(wl) -> dict:
             "flop": FLOP_PER_TEST * tests + FLOP_PER_CONFIG_FK * (C - 1)}
 
 
+def rank_seeds(rank: int, n: int) -> list:
+    """Scene/Philox seeds of one rank's solves: replicas solve different problems."""
+    return [rank * 100000 + i for i in range(n)]
+
+
+def max_over_ranks(value: float, ws: int, device=None) -> float:
+    """The timed region's duration is the slowest rank's (MAX over ranks)."""
+    if ws <= 1:
+        return value
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_throughput(units_per_rank: int, ws: int, max_ms: float) -> float:
+    """Units processed by all ranks / the slowest rank's time (weak scaling)."""
+    return ws * units_per_rank / (max_ms / 1000.0)
+
+
 # ------------------------------------------------------------------------------- native
 def run_native(args, ws, rank, local):
     import torch
@@ -166,7 +186,7 @@ def run_native(args, ws, rank, local):
         k, v = kv.split("=", 1)
         overrides[k] = float(v) if any(ch in v for ch in ".e") else int(v)
     n_total = args.warmup + args.steps
-    seeds = [rank * 100000 + i for i in range(n_total)]
+    seeds = rank_seeds(rank, n_total)
     wls = [scenes.make_problem(WORKLOAD, seed=s, **{k: v for k, v in overrides.items() if k != "max_steps"})
            for s in seeds]
     probs = [S.Problem(w, **overrides) for w in wls]
@@ -208,13 +228,9 @@ def run_native(args, ws, rank, local):
     wall = time.perf_counter() - wall0
     clocks = sampler.stop()
 
-    total_ms = sum(times)
-    if ws > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = t.item()
+    total_ms = max_over_ranks(sum(times), ws, dev)
     ms_per_step = total_ms / args.steps
-    value = ws * args.steps / (total_ms / 1000.0)
+    value = whole_job_throughput(args.steps, ws, total_ms)
 
     tc = count_tests(wls[0])
     traj_ms = sum(s["ms_traj"] for s in stats)
