@@ -283,6 +283,10 @@ def run_native(args, ws, rank, local):
         del res
     e2e_value = ws * len(e2e_times) / sum(e2e_times) if e2e_times else None
 
+    batched = served = None
+    if args.serve_problems > 0:
+        batched, served = run_served(args, rank, overrides)
+
     out = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -305,6 +309,8 @@ def run_native(args, ws, rank, local):
         "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": statistics.mean(h2d) if h2d else 0,
                 "d2h_bytes_per_step": statistics.mean(d2h) if d2h else 0, "steps": len(e2e_times),
                 "path": "spasm_create_problem (host arrays) + spasm_optimize + spasm_result + destroy"},
+        "batched": batched,
+        "served": served,
         "gpu_launches": int(sum(s["kernel_launches"] for s in stats)),
         "clocks": clocks,
         "kernel_sources_sha256_16": kernel_hash(),
@@ -312,6 +318,81 @@ def run_native(args, ws, rank, local):
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(wls[0], args.cpu_budget_s)
     return out
+
+
+def _percentile(xs, q):
+    xs = sorted(xs)
+    return float(xs[min(len(xs) - 1, max(0, math.ceil(q * len(xs)) - 1))])
+
+
+def run_served(args, rank, overrides):
+    """Heterogeneous problems (1-10 blocks, 8-64 cuboids, 1024-4096 trajectory particles,
+    32 waypoints per segment): (a) all submitted at once to the continuous-batching service
+    vs the same problems solved one after another through the plain API; (b) Poisson
+    arrivals at several rates, latency from arrival to completion."""
+    import random
+
+    import torch
+
+    from paper_2510_07674_gb300 import scenes
+    from paper_2510_07674_gb300 import spasm as S
+    n = args.serve_problems
+    wls = scenes.heterogeneous_batch(n, seed=1000 + rank)
+    ov = {"max_steps": overrides.get("max_steps", 1000)}
+    # plain form: one problem at a time
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ok_plain = 0
+    for wl in wls:
+        p = S.Problem(wl, **ov)
+        try:
+            S.spasm_optimize(p)
+        except S.SpasmError as e:
+            if e.status != -4:
+                raise
+        ok_plain += S.spasm_result(p, allow_empty=True)["n_found"] > 0
+        p.close()
+    torch.cuda.synchronize()
+    t_plain = time.perf_counter() - t0
+    # batched: all at once to the service
+    sv = S.Server(budget_bytes=150 << 30, max_inflight=args.serve_slots)
+    t0 = time.perf_counter()
+    tickets = [S.spasm_server_submit(sv, wl, **ov) for wl in wls]
+    for t in tickets:
+        S.spasm_server_wait(sv, t, 600.0)
+    t_batch = time.perf_counter() - t0
+    res = [S.spasm_server_result(sv, t) for t in tickets]
+    for t in tickets:
+        S.spasm_server_release(sv, t)
+    batched = {"problems": n, "slots": args.serve_slots, "plain_solves_per_s": n / t_plain,
+               "batched_solves_per_s": n / t_batch, "speedup_vs_plain": t_plain / t_batch,
+               "success_plain": ok_plain / n, "success_batched": sum(r["n_found"] > 0 for r in res) / n,
+               "workload": "heterogeneous: B~U{1..10}, O~U{8..64}, Q~U{1024..4096}, N=4096->M=1024, 32 waypoints"}
+    # served: Poisson arrivals
+    served = []
+    rng = random.Random(7 + rank)
+    for rate in args.serve_rates:
+        arrivals, tcur = [], 0.0
+        for _ in range(n):
+            tcur += rng.expovariate(rate)
+            arrivals.append(tcur)
+        start = time.perf_counter()
+        tickets = []
+        for i, wl in enumerate(wls):
+            delay = arrivals[i] - (time.perf_counter() - start)
+            if delay > 0:
+                time.sleep(delay)
+            tickets.append(S.spasm_server_submit(sv, wl, **ov))
+        for t in tickets:
+            S.spasm_server_wait(sv, t, 600.0)
+        end = time.perf_counter() - start
+        lat = [S.spasm_server_result(sv, t)["latency_ms"] for t in tickets]
+        for t in tickets:
+            S.spasm_server_release(sv, t)
+        served.append({"rate_per_s": rate, "requests": n, "solves_per_s": n / end,
+                       "latency_ms_p50": _percentile(lat, 0.5), "latency_ms_p99": _percentile(lat, 0.99)})
+    sv.close()
+    return batched, served
 
 
 # ------------------------------------------------------------------------------- oracle
@@ -392,6 +473,10 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--cpu-budget-s", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve-problems", type=int, default=32,
+                    help="heterogeneous problems for the batched / served measurements (0 = skip)")
+    ap.add_argument("--serve-slots", type=int, default=8)
+    ap.add_argument("--serve-rates", type=float, nargs="*", default=[10.0, 50.0, 200.0])
     ap.add_argument("--override", action="append", default=[], metavar="PARAM=VALUE",
                     help="change a solver parameter (profiling of a reduced case only; recorded in config)")
     args = ap.parse_args()

@@ -224,6 +224,33 @@ spasm_status spasm_set_timing(spasm_problem_t problem, int enable);
 spasm_status spasm_get_stats(spasm_problem_t problem, spasm_stats* out);
 spasm_status spasm_reset_stats(spasm_problem_t problem);
 
+/* ---- solver service with continuous batching (not in the paper: the serving form of the
+ * hot path) ----
+ * Requests are whole problems (copied at submission).  They are admitted in arrival order
+ * as soon as one of max_inflight slots is free and their device memory fits budget_bytes
+ * (a request larger than the whole budget runs alone); each runs spasm_create_problem,
+ * spasm_optimize and spasm_result on its own non-blocking CUDA stream of the device that was
+ * current at creation, so requests that arrive while others run overlap with them on the
+ * device.  Results stay with the server until spasm_server_release. */
+typedef struct spasm_server* spasm_server_t;
+spasm_status spasm_server_create(long long budget_bytes, int max_inflight, spasm_server_t* out);
+/* Validates sizes on the host (SPASM_ERR_INVALID) and queues; *ticket identifies the request. */
+spasm_status spasm_server_submit(spasm_server_t server, const spasm_robot* robot, const spasm_obstacles* obstacles,
+                                 const spasm_goal* goal, const spasm_params* params, long long* ticket);
+/* *state = 0 queued, 1 running, 2 done. */
+spasm_status spasm_server_poll(spasm_server_t server, long long ticket, int* state);
+/* Bounded wait for completion: SPASM_ERR_TIMEOUT after timeout_s seconds. */
+spasm_status spasm_server_wait(spasm_server_t server, long long ticket, double timeout_s);
+/* Outputs of a finished request (host buffers sized as for spasm_result; any may be NULL);
+ * *status is the request's own status; latency_ms = submission to completion, queue_ms =
+ * submission to admission.  SPASM_ERR_TIMEOUT if it has not finished. */
+spasm_status spasm_server_result(spasm_server_t server, long long ticket, int* status, int* n_found,
+                                 double* placements, double* traj, double* cost, int* success, double* latency_ms,
+                                 double* queue_ms);
+spasm_status spasm_server_release(spasm_server_t server, long long ticket);
+/* Finishes the queued and running requests, then joins the slots. */
+spasm_status spasm_server_destroy(spasm_server_t server);
+
 #ifdef __cplusplus
 }
 #endif

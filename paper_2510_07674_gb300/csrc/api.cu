@@ -77,11 +77,14 @@ static spasm_status rec(spasm_problem* pr, int i) {
     return SPASM_OK;
 }
 
+// Stream-ordered allocation from the device's default memory pool: unlike cudaMalloc /
+// cudaFree it does not synchronise the device, so problems created and destroyed on
+// their own streams (the solver service) do not stall each other.
 template <typename T>
-static spasm_status dalloc(T** p, size_t count) {
+static spasm_status dalloc(T** p, size_t count, cudaStream_t st) {
     if (count == 0) count = 1;
-    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T));
-    if (e != cudaSuccess) return fail(SPASM_ERR_NOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(p), count * sizeof(T), st);
+    if (e != cudaSuccess) return fail(SPASM_ERR_NOMEM, std::string("cudaMallocAsync: ") + cudaGetErrorString(e));
     return SPASM_OK;
 }
 
@@ -109,7 +112,7 @@ static void free_all(spasm_problem* pr) {
                     pr->d_mu, pr->d_metrics, pr->d_tmasked, pr->d_tsat, pr->d_tnsat, pr->d_tbest, pr->d_rq,
                     pr->d_rcost, pr->d_rsucc, pr->d_user_np, pr->d_cub64, pr->d_osph64, pr->d_rmet64, pr->d_tests};
     for (void* p : ptrs)
-        if (p) cudaFree(p);
+        if (p) cudaFreeAsync(p, pr->stream);
     for (cudaEvent_t e : pr->ev)
         if (e) cudaEventDestroy(e);
 }
@@ -249,7 +252,7 @@ extern "C" spasm_status spasm_create_problem(const spasm_robot* robot, const spa
     const int N = prm->N, M = prm->M, P = prm->P, Q = prm->Q, NR = sc.NR;
     spasm_status st = SPASM_OK;
 #define ALLOC(ptr, count) \
-    if (st == SPASM_OK) st = dalloc(&(ptr), (count))
+    if (st == SPASM_OK) st = dalloc(&(ptr), (count), pr->stream)
     ALLOC(pr->d_cub, cub.size());
     ALLOC(pr->d_osph, osph.size());
     ALLOC(pr->d_err, 1);
@@ -464,13 +467,15 @@ extern "C" spasm_status spasm_optimize(spasm_problem_t pr) {
     SPASM_TRY(check_device_error(pr));
     {
         unsigned long long nt = 0;
-        SPASM_CUDA(cudaMemcpy(&nt, pr->d_tests, sizeof nt, cudaMemcpyDeviceToHost));
+        SPASM_CUDA(cudaMemcpyAsync(&nt, pr->d_tests, sizeof nt, cudaMemcpyDeviceToHost, pr->stream));
+        SPASM_CUDA(cudaStreamSynchronize(pr->stream));
         pr->stats.d2h_bytes += sizeof nt;
         pr->stats.tests_executed += (long long)nt;
     }
     if (found > 0) {
         std::vector<int> succ(sc.P, 0);
-        SPASM_CUDA(cudaMemcpy(succ.data(), pr->d_rsucc, sc.P * sizeof(int), cudaMemcpyDeviceToHost));
+        SPASM_CUDA(cudaMemcpyAsync(succ.data(), pr->d_rsucc, sc.P * sizeof(int), cudaMemcpyDeviceToHost, pr->stream));
+        SPASM_CUDA(cudaStreamSynchronize(pr->stream));
         pr->stats.d2h_bytes += sc.P * sizeof(int);
         int ns = 0;
         for (int r = 0; r < found; ++r) ns += succ[r] != 0;
@@ -492,13 +497,15 @@ extern "C" spasm_status spasm_result(spasm_problem_t pr, int* n_found, double* p
     if (n_found) *n_found = pr->optimized ? pr->n_found : 0;
     if (placements) {
         std::vector<float> tmp((size_t)P * B * 4, 0.f);
-        SPASM_CUDA(cudaMemcpy(tmp.data(), pr->d_place, tmp.size() * sizeof(float), cudaMemcpyDeviceToHost));
+        SPASM_CUDA(cudaMemcpyAsync(tmp.data(), pr->d_place, tmp.size() * sizeof(float), cudaMemcpyDeviceToHost, pr->stream));
+        SPASM_CUDA(cudaStreamSynchronize(pr->stream));
         pr->stats.d2h_bytes += tmp.size() * sizeof(float);
         for (size_t i = 0; i < tmp.size(); ++i) placements[i] = tmp[i];
     }
     if (traj) {
         std::vector<float> tmp((size_t)P * C * 8, 0.f);
-        SPASM_CUDA(cudaMemcpy(tmp.data(), pr->d_rq, tmp.size() * sizeof(float), cudaMemcpyDeviceToHost));
+        SPASM_CUDA(cudaMemcpyAsync(tmp.data(), pr->d_rq, tmp.size() * sizeof(float), cudaMemcpyDeviceToHost, pr->stream));
+        SPASM_CUDA(cudaStreamSynchronize(pr->stream));
         pr->stats.d2h_bytes += tmp.size() * sizeof(float);
         for (int r = 0; r < P; ++r)
             for (int t = 0; t < C; ++t)
@@ -506,12 +513,14 @@ extern "C" spasm_status spasm_result(spasm_problem_t pr, int* n_found, double* p
     }
     if (cost) {
         std::vector<float> tmp(P, 0.f);
-        SPASM_CUDA(cudaMemcpy(tmp.data(), pr->d_rcost, P * sizeof(float), cudaMemcpyDeviceToHost));
+        SPASM_CUDA(cudaMemcpyAsync(tmp.data(), pr->d_rcost, P * sizeof(float), cudaMemcpyDeviceToHost, pr->stream));
+        SPASM_CUDA(cudaStreamSynchronize(pr->stream));
         pr->stats.d2h_bytes += P * sizeof(float);
         for (int r = 0; r < P; ++r) cost[r] = tmp[r];
     }
     if (success) {
-        SPASM_CUDA(cudaMemcpy(success, pr->d_rsucc, P * sizeof(int), cudaMemcpyDeviceToHost));
+        SPASM_CUDA(cudaMemcpyAsync(success, pr->d_rsucc, P * sizeof(int), cudaMemcpyDeviceToHost, pr->stream));
+        SPASM_CUDA(cudaStreamSynchronize(pr->stream));
         pr->stats.d2h_bytes += P * sizeof(int);
     }
     if (!pr->optimized || pr->n_found == 0) return fail(SPASM_ERR_NOSOLUTION, "no solution");

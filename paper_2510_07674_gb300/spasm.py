@@ -24,7 +24,9 @@ STATUS = {0: "SPASM_OK", -1: "SPASM_ERR_INVALID", -2: "SPASM_ERR_NOMEM", -3: "SP
 EXPORTED = ["spasm_create_problem", "spasm_destroy_problem", "spasm_last_error", "spasm_place", "spasm_optimize",
             "spasm_result", "spasm_sizes", "spasm_place_sample", "spasm_place_eval", "spasm_place_descend",
             "spasm_select_topk", "spasm_lift", "spasm_traj_eval", "spasm_traj_descend", "spasm_set_seed",
-            "spasm_set_timing", "spasm_get_stats", "spasm_reset_stats", "spasm_place_select_static"]
+            "spasm_set_timing", "spasm_get_stats", "spasm_reset_stats", "spasm_place_select_static",
+            "spasm_server_create", "spasm_server_submit", "spasm_server_poll", "spasm_server_wait",
+            "spasm_server_result", "spasm_server_release", "spasm_server_destroy"]
 
 
 class SpasmError(RuntimeError):
@@ -100,6 +102,15 @@ def lib():
         L.spasm_get_stats.argtypes = [_V, ctypes.POINTER(_Stats)]
         L.spasm_reset_stats.argtypes = [_V]
         L.spasm_place_select_static.argtypes = [_V, ctypes.c_int, ctypes.c_uint32, ctypes.c_int, _V, _V]
+        LL = ctypes.c_longlong
+        L.spasm_server_create.argtypes = [LL, ctypes.c_int, ctypes.POINTER(_V)]
+        L.spasm_server_submit.argtypes = [_V, ctypes.POINTER(_Robot), ctypes.POINTER(_Obstacles), ctypes.POINTER(_Goal),
+                                          ctypes.POINTER(_Params), ctypes.POINTER(LL)]
+        L.spasm_server_poll.argtypes = [_V, LL, _I]
+        L.spasm_server_wait.argtypes = [_V, LL, ctypes.c_double]
+        L.spasm_server_result.argtypes = [_V, LL, _I, _I, _D, _D, _D, _I, _D, _D]
+        L.spasm_server_release.argtypes = [_V, LL]
+        L.spasm_server_destroy.argtypes = [_V]
         for name in EXPORTED:
             if name != "spasm_last_error":
                 getattr(L, name).restype = ctypes.c_int
@@ -125,10 +136,10 @@ def _f64(a) -> np.ndarray:
     return np.ascontiguousarray(a, dtype=np.float64)
 
 
-class Problem:
-    """Owns one ``spasm_problem_t`` created from a seeded workload description."""
+class ProblemDesc:
+    """The C structs describing one workload (arrays kept alive by this object)."""
 
-    def __init__(self, workload, stream=None, **param_overrides):
+    def __init__(self, workload, **param_overrides):
         r, s = workload.robot, workload.scene
         prm = dict(vars(workload.params))
         prm.update(param_overrides)
@@ -154,17 +165,28 @@ class Problem:
         p.seed = int(prm["seed"]) & 0xFFFFFFFFFFFFFFFF
         p.max_steps = int(prm["max_steps"])
         self._params = p
+        self.B = len(a["half"])
+        self.C = 2 * self.B * (int(prm["W"]) - 1) + 1
+
+    def refs(self):
+        return (ctypes.byref(self._robot), ctypes.byref(self._obs), ctypes.byref(self._goal),
+                ctypes.byref(self._params))
+
+
+class Problem(ProblemDesc):
+    """Owns one ``spasm_problem_t`` created from a seeded workload description."""
+
+    def __init__(self, workload, stream=None, **param_overrides):
+        super().__init__(workload, **param_overrides)
         if stream is None:
             import torch
             stream = torch.cuda.current_stream().cuda_stream
         self.stream = int(stream)
         h = _V()
-        _check(lib().spasm_create_problem(ctypes.byref(self._robot), ctypes.byref(self._obs), ctypes.byref(self._goal),
-                                          ctypes.byref(self._params), _V(self.stream), ctypes.byref(h)))
+        _check(lib().spasm_create_problem(*self.refs(), _V(self.stream), ctypes.byref(h)))
         self.handle = h
         C, NR = ctypes.c_int32(), ctypes.c_int32()
         _check(lib().spasm_sizes(h, ctypes.byref(C), ctypes.byref(NR)))
-        self.B = len(a["half"])
         self.C, self.NR = C.value, NR.value
 
     def close(self):
@@ -256,3 +278,62 @@ def spasm_reset_stats(problem: Problem):
 def spasm_place_select_static(problem: Problem, n: int, attempt: int, m: int, x_elite, cost_elite):
     """Sampling + elite selection with the library's fixed device scratch (no allocation)."""
     _check(lib().spasm_place_select_static(problem.handle, n, attempt, m, _dev(x_elite), _dev(cost_elite)))
+
+
+class Server:
+    """Owns one ``spasm_server_t`` (continuous-batching solver service)."""
+
+    def __init__(self, budget_bytes: int, max_inflight: int):
+        h = _V()
+        _check(lib().spasm_server_create(int(budget_bytes), int(max_inflight), ctypes.byref(h)))
+        self.handle = h
+        self._descs = {}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().spasm_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def spasm_server_submit(server: Server, workload, **overrides) -> int:
+    d = ProblemDesc(workload, **overrides)
+    t = ctypes.c_longlong()
+    _check(lib().spasm_server_submit(server.handle, *d.refs(), ctypes.byref(t)))
+    server._descs[t.value] = d
+    return t.value
+
+
+def spasm_server_poll(server: Server, ticket: int) -> int:
+    st = ctypes.c_int32()
+    _check(lib().spasm_server_poll(server.handle, ticket, ctypes.byref(st)))
+    return st.value
+
+
+def spasm_server_wait(server: Server, ticket: int, timeout_s: float):
+    _check(lib().spasm_server_wait(server.handle, ticket, float(timeout_s)))
+
+
+def spasm_server_result(server: Server, ticket: int) -> dict:
+    d = server._descs[ticket]
+    P, B, C = int(d.params["P"]), d.B, d.C
+    st, nf = ctypes.c_int32(), ctypes.c_int32()
+    place, traj, cost = np.zeros((P, B, 4)), np.zeros((P, C, 7)), np.zeros(P)
+    succ = np.zeros(P, dtype=np.int32)
+    lat, qms = ctypes.c_double(), ctypes.c_double()
+    _check(lib().spasm_server_result(server.handle, ticket, ctypes.byref(st), ctypes.byref(nf), place.ctypes.data_as(_D),
+                                     traj.ctypes.data_as(_D), cost.ctypes.data_as(_D), succ.ctypes.data_as(_I),
+                                     ctypes.byref(lat), ctypes.byref(qms)))
+    n = nf.value
+    return {"status": st.value, "n_found": n, "placements": place, "traj": traj[:n], "cost": cost[:n],
+            "success": succ[:n], "latency_ms": lat.value, "queue_ms": qms.value}
+
+
+def spasm_server_release(server: Server, ticket: int):
+    _check(lib().spasm_server_release(server.handle, ticket))
+    server._descs.pop(ticket, None)
