@@ -51,6 +51,21 @@ struct Scalars {
     unsigned long long seed;
 };
 
+// ------------------------------------------------------------------------------ launches
+// Raise a kernel's dynamic shared-memory cap to the device's opt-in maximum.  Every caller
+// sets the same value, so host threads launching the kernel for problems of different
+// sizes at the same time never lower the cap under one another's launch.
+template <typename K>
+inline cudaError_t allow_max_dynamic_smem(K kernel, size_t need) {
+    int dev = 0, max_optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    if (need > (size_t)max_optin) return cudaErrorInvalidValue;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_optin);
+}
+
 // ------------------------------------------------------------------------------ errors
 // Device error word (per problem): kernels record the first problem they see here and
 // return early instead of trapping; the host reads it after the stream syncs.

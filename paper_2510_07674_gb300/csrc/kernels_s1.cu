@@ -163,11 +163,11 @@ __global__ void k_gather_soa_to_aos(const float* __restrict__ src, int ld_src, i
 // ------------------------------------------------------------------------------ launchers
 static cudaError_t s1_prepare(const Scalars& sc) {
     size_t bytes = s1_smem_bytes(sc);
-    cudaError_t e = cudaFuncSetAttribute(k_place_sample_cost, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    cudaError_t e = allow_max_dynamic_smem(k_place_sample_cost, bytes);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_place_eval, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    e = allow_max_dynamic_smem(k_place_eval, bytes);
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_place_descend, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    return allow_max_dynamic_smem(k_place_descend, bytes);
 }
 
 cudaError_t launch_place_sample_cost(const Scalars& sc, DevTables t, int n, uint32_t attempt, float* x, float* cost,
@@ -216,7 +216,7 @@ cudaError_t launch_topk(const float* cost, int n, int k, int* idx, float* cost_o
     if (k > n) k = n;
     const int kp2 = next_pow2(k);
     const size_t bytes = topk_smem_bytes(n, k);
-    cudaError_t e = cudaFuncSetAttribute(k_topk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    cudaError_t e = allow_max_dynamic_smem(k_topk, bytes);
     if (e != cudaSuccess) return e;
     k_topk<<<1, kSelectThreads, bytes, st>>>(cost, n, k, idx, cost_out, kp2);
     return cudaGetLastError();

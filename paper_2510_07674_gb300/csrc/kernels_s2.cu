@@ -871,7 +871,7 @@ cudaError_t launch_traj(const Scalars& sc, DevTables t, int n, int mode, const T
                         cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
     const size_t bytes = traj_smem_bytes(sc);
-    cudaError_t e = cudaFuncSetAttribute(k_traj, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    cudaError_t e = allow_max_dynamic_smem(k_traj, bytes);
     if (e != cudaSuccess) return e;
     k_traj<<<n, kTThreads, bytes, st>>>(sc, t, n, mode, io, err);
     return cudaGetLastError();

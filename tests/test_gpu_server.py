@@ -25,7 +25,7 @@ def test_results_alone_equal_results_in_the_mix():
     mix = [S.spasm_server_result(sv, t) for t in tickets]
     sv.close()
     for a, m in zip(alone, mix):
-        assert m["status"] == 0 and m["n_found"] == a["n_found"]
+        assert m["status"] == 0 and m["n_found"] == a["n_found"], m["status"]
         np.testing.assert_array_equal(m["traj"], a["traj"])
         np.testing.assert_array_equal(m["cost"], a["cost"])
         np.testing.assert_array_equal(m["placements"], a["placements"])
