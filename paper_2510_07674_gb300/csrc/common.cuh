@@ -62,8 +62,12 @@ inline cudaError_t allow_max_dynamic_smem(K kernel, size_t need) {
     if (e != cudaSuccess) return e;
     e = cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e != cudaSuccess) return e;
-    if (need > (size_t)max_optin) return cudaErrorInvalidValue;
-    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_optin);
+    cudaFuncAttributes fa;
+    e = cudaFuncGetAttributes(&fa, kernel);
+    if (e != cudaSuccess) return e;
+    const int cap = max_optin - (int)fa.sharedSizeBytes;   // static + dynamic <= opt-in maximum
+    if ((long long)need > (long long)cap) return cudaErrorInvalidValue;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
 }
 
 // ------------------------------------------------------------------------------ errors
