@@ -3,7 +3,10 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
+#include <set>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "spasm.h"
@@ -14,6 +17,19 @@
 using namespace spasm;
 
 static thread_local std::string g_last_error;
+
+namespace spasm {
+cudaError_t configure_once_impl(const void* kernel, int dev, cudaError_t (*fn)(void*), void* ctx) {
+    static std::mutex mu;
+    static std::set<std::pair<const void*, int>> done;
+    std::lock_guard<std::mutex> lock(mu);
+    const auto key = std::make_pair(kernel, dev);
+    if (done.count(key)) return cudaSuccess;
+    const cudaError_t e = fn(ctx);
+    if (e == cudaSuccess) done.insert(key);
+    return e;
+}
+}  // namespace spasm
 
 static spasm_status fail(spasm_status st, const std::string& msg) {
     g_last_error = msg;
@@ -39,7 +55,6 @@ struct spasm_problem {
     float *d_xs = nullptr, *d_cost = nullptr, *d_xm = nullptr, *d_costm = nullptr, *d_masked = nullptr;
     int *d_idx = nullptr, *d_sat = nullptr, *d_nsat = nullptr, *d_best = nullptr;
     float* d_place = nullptr;   // P x B x 4
-    int* d_nplace = nullptr;
     bool placed = false;
     int n_place = 0, place_attempts = 0, place_steps = 0;
     // stage 2
@@ -47,9 +62,7 @@ struct spasm_problem {
     int *d_tsat = nullptr, *d_tnsat = nullptr, *d_tbest = nullptr;
     float *d_rq = nullptr, *d_rcost = nullptr;   // returned solutions
     int* d_rsucc = nullptr;
-    int* d_user_np = nullptr;   // placement count of a user-driven lift
     unsigned long long* d_tests = nullptr;   // sphere-obstacle tests run by the trajectory kernel
-    int h_user_np = 0;
     bool optimized = false;
     int n_found = 0, traj_attempts = 0;
     std::vector<double> host_cub, host_osph;
@@ -108,9 +121,9 @@ static spasm_status check_device_error(spasm_problem* pr) {
 
 static void free_all(spasm_problem* pr) {
     void* ptrs[] = {pr->d_cub, pr->d_osph, pr->d_err, pr->d_xs, pr->d_cost, pr->d_xm, pr->d_costm, pr->d_masked,
-                    pr->d_idx, pr->d_sat, pr->d_nsat, pr->d_best, pr->d_place, pr->d_nplace, pr->d_q, pr->d_lam,
+                    pr->d_idx, pr->d_sat, pr->d_nsat, pr->d_best, pr->d_place, pr->d_q, pr->d_lam,
                     pr->d_mu, pr->d_metrics, pr->d_tmasked, pr->d_tsat, pr->d_tnsat, pr->d_tbest, pr->d_rq,
-                    pr->d_rcost, pr->d_rsucc, pr->d_user_np, pr->d_cub64, pr->d_osph64, pr->d_rmet64, pr->d_tests};
+                    pr->d_rcost, pr->d_rsucc, pr->d_cub64, pr->d_osph64, pr->d_rmet64, pr->d_tests};
     for (void* p : ptrs)
         if (p) cudaFreeAsync(p, pr->stream);
     for (cudaEvent_t e : pr->ev)
@@ -266,7 +279,6 @@ extern "C" spasm_status spasm_create_problem(const spasm_robot* robot, const spa
     ALLOC(pr->d_nsat, 1);
     ALLOC(pr->d_best, P);
     ALLOC(pr->d_place, (size_t)P * B * 4);
-    ALLOC(pr->d_nplace, 1);
     ALLOC(pr->d_q, (size_t)Q * C * 8);
     ALLOC(pr->d_lam, (size_t)Q * NR);
     ALLOC(pr->d_mu, Q);
@@ -278,7 +290,6 @@ extern "C" spasm_status spasm_create_problem(const spasm_robot* robot, const spa
     ALLOC(pr->d_rq, (size_t)P * C * 8);
     ALLOC(pr->d_rcost, P);
     ALLOC(pr->d_rsucc, P);
-    ALLOC(pr->d_user_np, 1);
     ALLOC(pr->d_cub64, (size_t)16 * sc.n_cub);
     ALLOC(pr->d_osph64, (size_t)4 * sc.n_osph);
     ALLOC(pr->d_rmet64, (size_t)6 * P);
@@ -372,8 +383,6 @@ extern "C" spasm_status spasm_place(spasm_problem_t pr) {
     pr->place_steps = steps;
     pr->n_place = found;
     pr->stats.place_attempts += attempt;
-    SPASM_CUDA(cudaMemcpyAsync(pr->d_nplace, &pr->n_place, sizeof(int), cudaMemcpyHostToDevice, pr->stream));
-    pr->stats.h2d_bytes += sizeof(int);
     SPASM_TRY(check_device_error(pr));
     if (pr->timing) pr->stats.ms_place += ev_ms(pr->ev[0], pr->ev[1]);
     pr->placed = true;
@@ -386,7 +395,7 @@ static spasm_status traj_attempt(spasm_problem* pr, uint32_t attempt) {
     const Scalars& sc = pr->sc;
     cudaStream_t s = pr->stream;
     SPASM_TRY(rec(pr, 2));
-    SPASM_CUDA(launch_lift(sc, sc.Q, pr->d_place, pr->d_nplace, attempt, pr->d_q, s));
+    SPASM_CUDA(launch_lift(sc, sc.Q, pr->d_place, pr->n_place, attempt, pr->d_q, s));
     SPASM_TRY(rec(pr, 3));
     TrajIO io{};
     io.q = pr->d_q; io.lam = pr->d_lam; io.mu = pr->d_mu; io.metrics = pr->d_metrics; io.sat = pr->d_tsat;
@@ -561,9 +570,7 @@ extern "C" spasm_status spasm_select_topk(spasm_problem_t pr, int n, const float
 extern "C" spasm_status spasm_lift(spasm_problem_t pr, int n, const float* placements, int n_place, uint32_t attempt,
                                    float* q) {
     if (!pr || n < 0 || n_place < 1 || (n > 0 && (!placements || !q))) return fail(SPASM_ERR_INVALID, "bad arguments");
-    pr->h_user_np = n_place;
-    SPASM_CUDA(cudaMemcpyAsync(pr->d_user_np, &pr->h_user_np, sizeof(int), cudaMemcpyHostToDevice, pr->stream));
-    SPASM_CUDA(launch_lift(pr->sc, n, placements, pr->d_user_np, attempt, q, pr->stream));
+    SPASM_CUDA(launch_lift(pr->sc, n, placements, n_place, attempt, q, pr->stream));
     return SPASM_OK;
 }
 

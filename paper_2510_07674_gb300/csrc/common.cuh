@@ -52,9 +52,17 @@ struct Scalars {
 };
 
 // ------------------------------------------------------------------------------ launches
-// Raise a kernel's dynamic shared-memory cap to the device's opt-in maximum.  Every caller
-// sets the same value, so host threads launching the kernel for problems of different
-// sizes at the same time never lower the cap under one another's launch.
+// Raise a kernel's dynamic shared-memory cap to the device's opt-in maximum (minus its
+// static shared memory), once per (kernel, device) under a lock: host threads launching
+// the kernel for problems of different sizes never change the attribute while another
+// thread launches it.
+// Runs `set` once per (kernel, device) while holding a process-wide lock.
+cudaError_t configure_once_impl(const void* kernel, int dev, cudaError_t (*fn)(void*), void* ctx);
+template <typename F>
+inline cudaError_t configure_once(const void* kernel, int dev, F set) {
+    return configure_once_impl(kernel, dev, [](void* c) { return (*static_cast<F*>(c))(); }, &set);
+}
+
 template <typename K>
 inline cudaError_t allow_max_dynamic_smem(K kernel, size_t need) {
     int dev = 0, max_optin = 0;
@@ -67,7 +75,9 @@ inline cudaError_t allow_max_dynamic_smem(K kernel, size_t need) {
     if (e != cudaSuccess) return e;
     const int cap = max_optin - (int)fa.sharedSizeBytes;   // static + dynamic <= opt-in maximum
     if ((long long)need > (long long)cap) return cudaErrorInvalidValue;
-    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
+    return configure_once(reinterpret_cast<const void*>(kernel), dev, [&] {
+        return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
+    });
 }
 
 // ------------------------------------------------------------------------------ errors

@@ -80,12 +80,11 @@ __device__ __forceinline__ void perturbed_home(const Scalars& sc, uint32_t c0, i
 }
 
 // one thread per (particle, block, grasp|place)
-__global__ void k_lift_ik(const __grid_constant__ Scalars sc, int n, const float* __restrict__ place,
-                          const int* __restrict__ n_place, uint32_t attempt, float* __restrict__ q) {
+__global__ void k_lift_ik(const __grid_constant__ Scalars sc, int n, const float* __restrict__ place, int np,
+                          uint32_t attempt, float* __restrict__ q) {
     const int gid = blockIdx.x * blockDim.x + threadIdx.x;
     const int B = sc.B;
     if (gid >= n * 2 * B) return;
-    const int np = *n_place;
     if (np <= 0) return;
     const int p = gid / (2 * B), r = gid % (2 * B), b = r >> 1, which = r & 1;
     const U4 kk = philox4x32_10((uint32_t)b, (uint32_t)p, kTagGrasp, attempt, sc.seed);
@@ -113,11 +112,11 @@ __global__ void k_lift_ik(const __grid_constant__ Scalars sc, int n, const float
 
 // one thread per (particle, configuration): home, or linear interpolation
 // start -> via -> goal within the configuration's segment
-__global__ void k_lift_interp(const __grid_constant__ Scalars sc, int n, const int* __restrict__ n_place,
-                              uint32_t attempt, float* __restrict__ q) {
+__global__ void k_lift_interp(const __grid_constant__ Scalars sc, int n, int np, uint32_t attempt,
+                              float* __restrict__ q) {
     const int gid = blockIdx.x * blockDim.x + threadIdx.x;
     if (gid >= n * sc.C) return;
-    if (*n_place <= 0) return;
+    if (np <= 0) return;
     const int p = gid / sc.C, t = gid % sc.C, S = sc.S;
     float* dst = q + ((size_t)p * sc.C + t) * 8;
     if (t == 0) {
@@ -130,7 +129,9 @@ __global__ void k_lift_interp(const __grid_constant__ Scalars sc, int n, const i
     const int s = t / S, m = S / 2;
     float via[7];
     perturbed_home(sc, (uint32_t)s, p, kTagVia, attempt, 0.3f, via);
-    const float* qa = q + ((size_t)p * sc.C + s * S) * 8;
+    // segment 0 starts at home; this launch writes that row itself (t == 0 above), so it is
+    // taken from the constants rather than read back from q
+    const float* qa = s == 0 ? sc.q_home : q + ((size_t)p * sc.C + s * S) * 8;
     const float* qb = q + ((size_t)p * sc.C + (s + 1) * S) * 8;
     for (int j = 0; j < 7; ++j) {
         float v;
@@ -679,6 +680,7 @@ __device__ void traj_evaluate(const Scalars& sc, const LaneSpheres& ls, const fl
             sh.s[r] = (sh.lam[r] + sh.mu * hw) * sw;
         }
         Lp = warp_sum(Lp);
+        __syncwarp();   // sh.s[] was written by other lanes: order those stores before lane 0 reads them
         if (lane == 0) {
             sh.L = Lp; sh.c_start = c_start; sh.max_start = m_start; sh.max_tilt = m_tilt;
             sh.s_arm = sh.s[9 * B + 1]; sh.s_blk = sh.s[9 * B + 2];
@@ -855,7 +857,7 @@ __global__ void __launch_bounds__(kTThreads, 2) k_traj(const __grid_constant__ S
 }
 
 // ================================================================================== launchers
-cudaError_t launch_lift(const Scalars& sc, int n, const float* place, const int* n_place, uint32_t attempt, float* q,
+cudaError_t launch_lift(const Scalars& sc, int n, const float* place, int n_place, uint32_t attempt, float* q,
                         cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
     const int n_ik = n * 2 * sc.B;

@@ -22,8 +22,8 @@ struct TrajIO {
 enum TrajModeHost { kTrajModeEval = 0, kTrajModeDescend = 1, kTrajModeCheck = 2 };
 
 size_t traj_smem_bytes(const Scalars& sc);
-// IK at grasp/place poses + interpolation; particle p lifts placement p % *n_place.
-cudaError_t launch_lift(const Scalars& sc, int n, const float* place, const int* n_place, uint32_t attempt, float* q,
+// IK at grasp/place poses + interpolation; particle p lifts placement p % n_place.
+cudaError_t launch_lift(const Scalars& sc, int n, const float* place, int n_place, uint32_t attempt, float* q,
                         cudaStream_t st);
 cudaError_t launch_traj(const Scalars& sc, DevTables t, int n, int mode, const TrajIO& io, int* err, cudaStream_t st);
 
