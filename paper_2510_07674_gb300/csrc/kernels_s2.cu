@@ -154,6 +154,7 @@ struct TWarp {
     float4 H[kChunk][3];     // held-block frame of each configuration (same row layout)
     float wr[2][kMaxB][4];   // d/d(placed pose k): group arm, group block
     float part[4];           // C_arm, C_block, max penetration
+    float pc[2];             // placed tower: sum and maximum of its penetrations (this warp's share)
     uint32_t cmask[kMaxCub / 32];    // environment cuboids that may touch the current chunk
     uint32_t smask[kMaxOSph / 32];   // environment spheres that may touch the current chunk
 };
@@ -174,6 +175,8 @@ struct TShared {
     float h[kMaxNR], lam[kMaxNR], s[kMaxNR];
     float extra[2 * kMaxB][8];   // gradient rows of grasp (b) and place (B + b) configurations
     float coef_a[kMaxB], coef_b[kMaxB];
+    float pg[kTWarps][kMaxB][4];   // dC_coll/d(placed pose j), sphere side, per warp
+    float pgc[kMaxB][4];           // dC_coll/d(placed pose i), cuboid side of block pairs
     PlaceScratch ps;
     float s_arm, s_blk, mu, L;
     float c_arm, c_blk, maxpen, c_coll, c_stable, c_height, c_start;
@@ -573,6 +576,97 @@ __device__ __forceinline__ void start_terms(const Scalars& sc, int b, int which,
     }
 }
 
+// Collisions of the placed tower (the C_coll residual of the placement terms), spread over
+// all warps of the CTA: lanes own (block j, sphere m) items, warp w takes the environment
+// obstacles o = w (mod kTWarps) and the lower-block cuboids i = w (mod kTWarps), and a box
+// test screens each pair before the exact one.  Per warp: the sum and maximum of the
+// penetrations (tw.pc); with `grad`, the unscaled pose gradient dC_coll/dx, sphere side in
+// sh.pg[w][j] and cuboid side in sh.pgc[i] (written by the one warp that owns cuboid i).
+__device__ __forceinline__ void placed_collisions(const Scalars& sc, const float4* __restrict__ cub,
+                                                  const float4* __restrict__ osph, const float4* __restrict__ aabb,
+                                                  TShared& sh, bool grad) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int B = sc.B, n_items = 8 * B;
+    float coll = 0.f, maxpen = 0.f;
+    if (grad && lane < 4)
+        for (int i = w; i + 1 < B; i += kTWarps) sh.pgc[i][lane] = 0.f;
+    __syncwarp();
+    for (int base = 0; base < n_items; base += 32) {
+        const int it = base + lane;
+        const bool valid = it < n_items;
+        const int j = valid ? it >> 3 : 0, m = it & 7;
+        const float4 h = sc.half[j];
+        float lx, ly, lz;
+        block_sphere_local(h, m, lx, ly, lz);
+        const float c = sh.bcub[j][1].x, s = sh.bcub[j][1].y;
+        const float cx = sh.pose[4 * j] + c * lx - s * ly;
+        const float cy = sh.pose[4 * j + 1] + s * lx + c * ly;
+        const float cz = sh.pose[4 * j + 2] + lz;
+        const float r = h.w;
+        auto apart = [&](const float4& lo, const float4& hi) {
+            return lo.x > cx + r || hi.x < cx - r || lo.y > cy + r || hi.y < cy - r || lo.z > cz + r || hi.z < cz - r;
+        };
+        float ax = 0.f, ay = 0.f, az = 0.f;   // dC/dc of this item
+        if (valid) {
+            for (int o = w; o < sc.n_cub; o += kTWarps) {
+                if (apart(aabb[2 * o], aabb[2 * o + 1])) continue;
+                float gx, gy, gz;
+                const float pen = pen_cuboid<float>(cx, cy, cz, r, cub[4 * o], cub[4 * o + 1], cub[4 * o + 2],
+                                                    cub[4 * o + 3], gx, gy, gz);
+                if (pen > 0.f) {
+                    coll += pen; maxpen = fmaxf(maxpen, pen);
+                    ax += gx; ay += gy; az += gz;
+                }
+            }
+            for (int o = w; o < sc.n_osph; o += kTWarps) {
+                float gx, gy, gz;
+                const float pen = pen_sphere<float>(cx, cy, cz, r, osph[o], gx, gy, gz);
+                if (pen > 0.f) {
+                    coll += pen; maxpen = fmaxf(maxpen, pen);
+                    ax += gx; ay += gy; az += gz;
+                }
+            }
+        }
+        // blocks below in the stack: sphere of j against the cuboid of i < j
+        for (int i = w; i + 1 < B; i += kTWarps) {
+            float bx = 0.f, by = 0.f, bz = 0.f, byaw = 0.f;   // dC/d(pose i) from this item
+            bool hit = false;
+            if (valid && i < j && !apart(sh.baabb[i][0], sh.baabb[i][1])) {
+                float gx, gy, gz;
+                const float pen = pen_cuboid<float>(cx, cy, cz, r, sh.bcub[i][0], sh.bcub[i][1], sh.bcub[i][2],
+                                                    sh.bcub[i][3], gx, gy, gz);
+                if (pen > 0.f) {
+                    hit = true;
+                    coll += pen; maxpen = fmaxf(maxpen, pen);
+                    ax += gx; ay += gy; az += gz;
+                    // the cuboid moves rigidly: d/dP_i = -g, d/dyaw_i = -((c - P_i) x g)_z
+                    bx = -gx; by = -gy; bz = -gz;
+                    byaw = -((cx - sh.pose[4 * i]) * gy - (cy - sh.pose[4 * i + 1]) * gx);
+                }
+            }
+            if (grad && __any_sync(0xffffffffu, hit)) {
+                bx = warp_sum(bx); by = warp_sum(by); bz = warp_sum(bz); byaw = warp_sum(byaw);
+                if (lane == 0) { sh.pgc[i][0] += bx; sh.pgc[i][1] += by; sh.pgc[i][2] += bz; sh.pgc[i][3] += byaw; }
+            }
+        }
+        if (grad) {
+            float gyaw = ax * (-s * lx - c * ly) + ay * (c * lx - s * ly);   // dc/dyaw_j
+#pragma unroll
+            for (int off = 4; off > 0; off >>= 1) {
+                ax += __shfl_xor_sync(0xffffffffu, ax, off);
+                ay += __shfl_xor_sync(0xffffffffu, ay, off);
+                az += __shfl_xor_sync(0xffffffffu, az, off);
+                gyaw += __shfl_xor_sync(0xffffffffu, gyaw, off);
+            }
+            // one writer per (warp, block j): the lane with m == 0
+            if (valid && m == 0) { sh.pg[w][j][0] = ax; sh.pg[w][j][1] = ay; sh.pg[w][j][2] = az; sh.pg[w][j][3] = gyaw; }
+        }
+    }
+    coll = warp_sum(coll);
+    maxpen = warp_max(maxpen);
+    if (lane == 0) { sh.warp[w].pc[0] = coll; sh.warp[w].pc[1] = maxpen; }
+}
+
 // Modes of the trajectory kernel
 enum TrajMode { kTrajEval = 0, kTrajDescend = 1, kTrajCheck = 2 };
 
@@ -629,6 +723,8 @@ __device__ void traj_evaluate(const Scalars& sc, const LaneSpheres& ls, const fl
     acc_blk = warp_sum(acc_blk);
     acc_max = warp_max(acc_max);
     if (lane == 0) { sh.warp[w].part[0] = acc_arm; sh.warp[w].part[1] = acc_blk; sh.warp[w].part[2] = acc_max; }
+    // collisions of the placed tower, all warps (reads only the placed poses of step 1)
+    placed_collisions(sc, cub, osph, aabb, sh, grad);
     __syncthreads();
 
     // (3) epilogue.  (a) warp 0: group sums and the placement residuals; warp 1: start residuals
@@ -642,20 +738,28 @@ __device__ void traj_evaluate(const Scalars& sc, const LaneSpheres& ls, const fl
             tot_b += __shfl_sync(0xffffffffu, cb, i);
         }
         cm = warp_max(cm);
-        PlaceOut po;
-        place_eval_warp(sc, cub, sc.n_cub, osph, sc.n_osph, sh.pose, false, kPlaceForward, nullptr, nullptr, 0.f,
-                        nullptr, sh.ps, po);
+        const float pcl = lane < kTWarps ? sh.warp[lane].pc[0] : 0.f;
+        float pm = lane < kTWarps ? sh.warp[lane].pc[1] : 0.f;
+        float c_coll = 0.f;
+        for (int i = 0; i < kTWarps; ++i) c_coll += __shfl_sync(0xffffffffu, pcl, i);
+        pm = warp_max(pm);
+        float my_D, my_e;
+        place_stack_warp(sc, sh.pose, kPlaceForward, nullptr, nullptr, nullptr, sh.ps, my_D, my_e);
+        const float c_stable = warp_sum(lane < B ? my_D : 0.f);
+        const float c_height = warp_sum(lane < B ? my_e * my_e : 0.f);
+        const float max_D = warp_max(lane < B ? my_D : 0.f);
+        const float max_dz = warp_max(lane < B ? fabsf(my_e) : 0.f);
         if (lane < B) {
-            sh.h[7 * B + lane] = sh.ps.e[lane];
-            sh.h[8 * B + lane] = sh.ps.D[lane];
+            sh.h[7 * B + lane] = my_e;
+            sh.h[8 * B + lane] = my_D;
         }
         if (lane == 0) {
-            sh.h[9 * B] = po.c_coll;
+            sh.h[9 * B] = c_coll;
             sh.h[9 * B + 1] = tot_a;
             sh.h[9 * B + 2] = tot_b;
             sh.c_arm = tot_a; sh.c_blk = tot_b; sh.maxpen = cm;
-            sh.c_coll = po.c_coll; sh.c_stable = po.c_stable; sh.c_height = po.c_height;
-            sh.pm_pen = po.maxpen; sh.pm_D = po.maxD; sh.pm_dz = po.maxdz;
+            sh.c_coll = c_coll; sh.c_stable = c_stable; sh.c_height = c_height;
+            sh.pm_pen = pm; sh.pm_D = max_D; sh.pm_dz = max_dz;
         }
     } else if (w == 1 && lane < B) {
         start_terms(sc, lane, 0, sp[2 * lane], &sh.h[5 * lane], nullptr, nullptr, nullptr);
@@ -690,15 +794,19 @@ __device__ void traj_evaluate(const Scalars& sc, const LaneSpheres& ls, const fl
     if (grad) {
         // (c) warp 0: placement gradient w.r.t. the placed poses; warp 1: grasp gradients
         if (w == 0) {
-            PlaceOut po;
-            place_eval_warp(sc, cub, sc.n_cub, osph, sc.n_osph, sh.pose, false, kPlaceExplicit, &sh.s[8 * B],
-                            &sh.s[7 * B], sh.s[9 * B], sh.g4, sh.ps, po);
-            const float s_arm = sh.s_arm, s_blk = sh.s_blk;
+            float my_D, my_e;
+            place_stack_warp(sc, sh.pose, kPlaceExplicit, &sh.s[8 * B], &sh.s[7 * B], sh.g4, sh.ps, my_D, my_e);
+            const float s_arm = sh.s_arm, s_blk = sh.s_blk, s_coll = sh.s[9 * B];
             for (int i = lane; i < 4 * B; i += 32) {
                 const int kb = i >> 2, c = i & 3;
-                float wa = 0.f, wb = 0.f;
-                for (int ww = 0; ww < kTWarps; ++ww) { wa += sh.warp[ww].wr[0][kb][c]; wb += sh.warp[ww].wr[1][kb][c]; }
-                sh.g4[i] += s_arm * wa + s_blk * wb;
+                float wa = 0.f, wb = 0.f, gc = 0.f;
+                for (int ww = 0; ww < kTWarps; ++ww) {
+                    wa += sh.warp[ww].wr[0][kb][c];
+                    wb += sh.warp[ww].wr[1][kb][c];
+                    gc += sh.pg[ww][kb][c];
+                }
+                if (kb + 1 < B) gc += sh.pgc[kb][c];
+                sh.g4[i] += s_coll * gc + s_arm * wa + s_blk * wb;
             }
         } else if (w == 1 && lane < B) {
             float hbuf[5];

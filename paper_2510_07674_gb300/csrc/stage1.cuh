@@ -28,19 +28,17 @@ struct PlaceScratch {
 // s_coll = w_coll), or explicit per-residual coefficients (stage 2).
 enum PlaceMode { kPlaceForward = 0, kPlaceStage1 = 1, kPlaceExplicit = 2 };
 
-// x, g: per-warp shared arrays of 4B floats.  With mode != kPlaceForward, writes
-//   g = sum_i a_i dD_i/dx + sum_i b_i de_i/dx + s_coll dC_coll/dx.
-// Must be called by all 32 lanes of the warp.
-__device__ __forceinline__ void place_eval_warp(const Scalars& sc, const float4* __restrict__ cub, int n_cub,
-                                                const float4* __restrict__ osph, int n_osph, const float* x,
-                                                bool quad, int mode, const float* a_in, const float* b_in,
-                                                float s_coll_in, float* g, PlaceScratch& ps, PlaceOut& out) {
+// Per-block terms of the tower (lane i < B owns block i): height residual e_i, support
+// distance D_i and the block cuboids in ps.  With mode != kPlaceForward, sets
+//   g = sum_i a_i dD_i/dx + sum_i b_i de_i/dx   (the collision part is added by the caller).
+// x, g: per-warp shared arrays of 4B floats.  Must be called by all 32 lanes of the warp.
+__device__ __forceinline__ void place_stack_warp(const Scalars& sc, const float* x, int mode, const float* a_in,
+                                                 const float* b_in, float* g, PlaceScratch& ps, float& my_D,
+                                                 float& my_e) {
     const int lane = threadIdx.x & 31;
     const int B = sc.B;
     const bool want_grad = mode != kPlaceForward;
-
-    // -- per-block terms (lane i owns block i)
-    float my_D = 0.f, my_e = 0.f;
+    my_D = 0.f; my_e = 0.f;
     if (lane < B) {
         const int i = lane;
         my_e = x[4 * i + 2] - sc.zt[i];
@@ -81,6 +79,20 @@ __device__ __forceinline__ void place_eval_warp(const Scalars& sc, const float4*
         g[4 * i] = gx; g[4 * i + 1] = gy; g[4 * i + 2] = b; g[4 * i + 3] = ps.stab[i][2];
     }
     __syncwarp();
+}
+
+// x, g: per-warp shared arrays of 4B floats.  With mode != kPlaceForward, writes
+//   g = sum_i a_i dD_i/dx + sum_i b_i de_i/dx + s_coll dC_coll/dx.
+// Must be called by all 32 lanes of the warp.
+__device__ __forceinline__ void place_eval_warp(const Scalars& sc, const float4* __restrict__ cub, int n_cub,
+                                                const float4* __restrict__ osph, int n_osph, const float* x,
+                                                bool quad, int mode, const float* a_in, const float* b_in,
+                                                float s_coll_in, float* g, PlaceScratch& ps, PlaceOut& out) {
+    const int lane = threadIdx.x & 31;
+    const int B = sc.B;
+    const bool want_grad = mode != kPlaceForward;
+    float my_D, my_e;
+    place_stack_warp(sc, x, mode, a_in, b_in, g, ps, my_D, my_e);
 
     // -- collisions: items (block j, sphere m)
     const float s_coll = mode == kPlaceStage1 ? sc.w_coll : s_coll_in;
