@@ -185,6 +185,24 @@ extern "C" spasm_status spasm_create_problem(const spasm_robot* robot, const spa
         sc.rsph[i] = make_float4((float)s[0], (float)s[1], (float)s[2], (float)s[3]);
         sc.rlink[i] = robot->sphere_link[i];
     }
+    for (int l = 0; l < 8; ++l) {
+        double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+        bool any = false;
+        for (int i = 0; i < robot->n_spheres; ++i) {
+            if (robot->sphere_link[i] != l) continue;
+            const double* s = robot->sphere + 4 * i;
+            for (int k = 0; k < 3; ++k) { lo[k] = std::fmin(lo[k], s[k] - s[3]); hi[k] = std::fmax(hi[k], s[k] + s[3]); }
+            any = true;
+        }
+        // the pad keeps the box conservative under the FP32 rounding of its world transform
+        const double pad = 1e-5;
+        sc.lbox_c[l] = any ? make_float4((float)(0.5 * (lo[0] + hi[0])), (float)(0.5 * (lo[1] + hi[1])),
+                                         (float)(0.5 * (lo[2] + hi[2])), 0.f)
+                           : make_float4(0.f, 0.f, 0.f, 0.f);
+        sc.lbox_h[l] = any ? make_float4((float)(0.5 * (hi[0] - lo[0]) + pad), (float)(0.5 * (hi[1] - lo[1]) + pad),
+                                         (float)(0.5 * (hi[2] - lo[2]) + pad), 0.f)
+                           : make_float4(-1.f, -1.f, -1.f, 0.f);
+    }
     double z = goal->z_table;
     for (int i = 0; i < B; ++i) {
         const double* h = goal->half_ext + 3 * i;

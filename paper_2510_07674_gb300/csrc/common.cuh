@@ -37,6 +37,8 @@ struct Scalars {
     float q_home[7];
     float4 rsph[kMaxRobotSpheres];   // x, y, z, r in the link frame
     int rlink[kMaxRobotSpheres];     // 0 = base
+    float4 lbox_c[8], lbox_h[8];     // per link: box of its spheres in the link frame (centre, half
+                                     // extents, slightly padded); half.x < 0 when the link has none
     // blocks in stack order
     float4 half[kMaxB];              // hx, hy, hz, sphere radius min(h)/2
     float4 init[kMaxB];              // x, y, z, yaw

@@ -178,6 +178,9 @@ struct TShared {
     float pg[kTWarps][kMaxB][4];   // dC_coll/d(placed pose j), sphere side, per warp
     float pgc[kMaxB][4];           // dC_coll/d(placed pose i), cuboid side of block pairs
     PlaceScratch ps;
+    float4 dh[8];            // joint j: cos alpha, sin alpha, a, d (per-lane reads in the kinematics)
+    float th0[8];            // joint offsets
+    float4 lbc[8], lbh[8];   // link-frame boxes of each link's spheres (centre, half extents)
     float s_arm, s_blk, mu, L;
     float c_arm, c_blk, maxpen, c_coll, c_stable, c_height, c_start;
     float max_start, max_tilt, pm_pen, pm_D, pm_dz, path, jl;
@@ -229,10 +232,13 @@ __device__ __forceinline__ LaneSpheres lane_spheres(const Scalars& sc) {
 // Forward kinematics of four configurations by one warp: lane 8c + k holds link transform
 // k of configuration t_c (k = 0: identity), and a 3-level inclusive scan of affine products
 // inside each group of 8 lanes gives frame_k = T_1 ... T_k.  Group c writes its frames (rows
-// (R_i0, R_i1, R_i2, o_i)) to F_c and the frame of the block the tool would hold in t_c's
-// segment to H_c, unless `write` is false for that group.
-__device__ __forceinline__ void chunk_fk(const Scalars& sc, const float* __restrict__ q, int t_c, bool write,
-                                         float4 (*F_c)[3], float4* H_c) {
+// (R_i0, R_i1, R_i2, o_i)) to F_c, unless `write` is false for that group, and, when
+// `want_h`, the frame of the block the tool would hold in t_c's segment to H_c.  With `box`,
+// the lane also returns a world box (lo xyz, hi xyz) that holds every sphere of link k (and of
+// the held block, at k = 7 with `want_h`): the link-frame box of those spheres carried by the
+// frame, i.e. centre R c + o and half extents |R| h.
+__device__ __forceinline__ void chunk_fk(const Scalars& sc, const TShared& sh, const float* __restrict__ q, int t_c,
+                                         bool write, bool want_h, float4 (*F_c)[3], float4* H_c, float* box) {
     const int lane = threadIdx.x & 31;
     const int k = lane & 7;
     const int t = min(max(t_c, 1), sc.C - 1);
@@ -240,12 +246,13 @@ __device__ __forceinline__ void chunk_fk(const Scalars& sc, const float* __restr
     if (k > 0) {
         const int j = k - 1;
         float st, ct;
-        sincosf(sc.th0[j] + q[t * 8 + j], &st, &ct);
-        const float ca = sc.ca[j], sa = sc.sa[j];
+        sincosf(sh.th0[j] + q[t * 8 + j], &st, &ct);
+        const float4 row = sh.dh[j];
+        const float ca = row.x, sa = row.y;
         A[0] = ct;      A[1] = -st;     A[2] = 0.f;
         A[3] = ca * st; A[4] = ca * ct; A[5] = -sa;
         A[6] = sa * st; A[7] = sa * ct; A[8] = ca;
-        bv[0] = sc.a[j]; bv[1] = -sa * sc.d[j]; bv[2] = ca * sc.d[j];
+        bv[0] = row.z; bv[1] = -sa * row.w; bv[2] = ca * row.w;
     }
 #pragma unroll
     for (int off = 1; off < 8; off <<= 1) {
@@ -269,16 +276,38 @@ __device__ __forceinline__ void chunk_fk(const Scalars& sc, const float* __restr
             for (int i = 0; i < 3; ++i) bv[i] = nb[i];
         }
     }
+    if (box) {
+        const float4 lc = sh.lbc[k], lh = sh.lbh[k];
+        const bool has = lh.x >= 0.f;
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            const float w = A[3 * r] * lc.x + A[3 * r + 1] * lc.y + A[3 * r + 2] * lc.z + bv[r];
+            const float e = fabsf(A[3 * r]) * lh.x + fabsf(A[3 * r + 1]) * lh.y + fabsf(A[3 * r + 2]) * lh.z;
+            box[r] = has ? w - e : 3.4e38f;
+            box[3 + r] = has ? w + e : -3.4e38f;
+        }
+    }
     if (!write) return;
 #pragma unroll
     for (int r = 0; r < 3; ++r) F_c[k][r] = make_float4(A[3 * r], A[3 * r + 1], A[3 * r + 2], bv[r]);
-    if (k == 7) {
+    if (k == 7 && want_h) {
         const int seg = (t - 1) / sc.S, b = seg >> 1;
         float Rt[9], pt[3], Rb[9], pb[3];
         tool_frame<float>(sc, A, bv, Rt, pt);
         held_block<float>(sc, b, Rt, pt, Rb, pb);
 #pragma unroll
         for (int r = 0; r < 3; ++r) H_c[r] = make_float4(Rb[3 * r], Rb[3 * r + 1], Rb[3 * r + 2], pb[r]);
+        if (box) {
+            // held-block spheres sit at (+-hx/2, +-hy/2, +-hz/2) with radius r_b in the block frame
+            const float4 hb = sc.half[b];
+            const float ex = 0.5f * hb.x + hb.w + 1e-5f, ey = 0.5f * hb.y + hb.w + 1e-5f, ez = 0.5f * hb.z + hb.w + 1e-5f;
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+                const float e = fabsf(Rb[3 * r]) * ex + fabsf(Rb[3 * r + 1]) * ey + fabsf(Rb[3 * r + 2]) * ez;
+                box[r] = fminf(box[r], pb[r] - e);
+                box[3 + r] = fmaxf(box[3 + r], pb[r] + e);
+            }
+        }
     }
 }
 
@@ -320,27 +349,18 @@ __device__ __forceinline__ void sphere_centres(const Scalars& sc, const LaneSphe
 __device__ __forceinline__ void chunk_collisions(const Scalars& sc, const LaneSpheres& ls,
                                                  const float4* __restrict__ cub, const float4* __restrict__ osph,
                                                  const float4* __restrict__ aabb, TShared& sh, TWarp& tw, float* G_arm,
-                                                 float* G_blk, int t0, int nc, bool grad, float& acc_arm, float& acc_blk,
-                                                 float& acc_max, unsigned long long& n_tests) {
+                                                 float* G_blk, int t0, int nc, bool grad, const float* lane_box,
+                                                 float& acc_arm, float& acc_blk, float& acc_max,
+                                                 unsigned long long& n_tests) {
     const int lane = threadIdx.x & 31;
     const int S = sc.S, B = sc.B;
     float cx[kSlots], cy[kSlots], cz[kSlots], rr[kSlots];
     bool act[kSlots], isblk[kSlots];
 
-    // pass 1: box of every sphere of the chunk, candidate obstacles by warp ballots
-    float lo_x = 3.4e38f, lo_y = 3.4e38f, lo_z = 3.4e38f, hi_x = -3.4e38f, hi_y = -3.4e38f, hi_z = -3.4e38f;
-    for (int ci = 0; ci < nc; ++ci) {
-        const int t = t0 + ci, seg = (t - 1) / S, b = seg >> 1, jj = t - seg * S;
-        const int n_items = sc.n_rsph + (((seg & 1) && jj < S) ? 8 : 0);
-        sphere_centres(sc, ls, tw.F[ci], tw.H[ci], n_items, b, cx, cy, cz, rr, act, isblk);
-#pragma unroll
-        for (int sl = 0; sl < kSlots; ++sl) {
-            if (!act[sl]) continue;
-            lo_x = fminf(lo_x, cx[sl] - rr[sl]); hi_x = fmaxf(hi_x, cx[sl] + rr[sl]);
-            lo_y = fminf(lo_y, cy[sl] - rr[sl]); hi_y = fmaxf(hi_y, cy[sl] + rr[sl]);
-            lo_z = fminf(lo_z, cz[sl] - rr[sl]); hi_z = fmaxf(hi_z, cz[sl] + rr[sl]);
-        }
-    }
+    // pass 1: box of every sphere of the chunk (union of the lanes' link boxes), candidate
+    // obstacles by warp ballots
+    float lo_x = lane_box[0], lo_y = lane_box[1], lo_z = lane_box[2];
+    float hi_x = lane_box[3], hi_y = lane_box[4], hi_z = lane_box[5];
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
         lo_x = fminf(lo_x, __shfl_xor_sync(0xffffffffu, lo_x, off));
@@ -693,7 +713,7 @@ __device__ void traj_evaluate(const Scalars& sc, const LaneSpheres& ls, const fl
     for (int gi = w; gi * 4 < n_sp; gi += kTWarps) {
         const int si = 4 * gi + (lane >> 3);
         const bool ok = si < n_sp;
-        chunk_fk(sc, q, ok ? (si + 1) * S : 1, ok, sp[ok ? si : 0].F, sp[ok ? si : 0].H);
+        chunk_fk(sc, sh, q, ok ? (si + 1) * S : 1, ok, true, sp[ok ? si : 0].F, sp[ok ? si : 0].H, nullptr);
     }
     for (int i = lane; i < 2 * kMaxB * 4; i += 32) (&sh.warp[w].wr[0][0][0])[i] = 0.f;
     __syncthreads();
@@ -713,9 +733,13 @@ __device__ void traj_evaluate(const Scalars& sc, const LaneSpheres& ls, const fl
     for (int chk = w; chk < n_chunks; chk += kTWarps) {
         const int t0 = 1 + kChunk * chk;
         const int c = lane >> 3;
-        chunk_fk(sc, q, t0 + c, true, sh.warp[w].F[c], sh.warp[w].H[c]);
+        // the held block's frame matters on transfer-segment interiors only
+        const int tc = min(t0 + c, C - 1), seg_c = (tc - 1) / S;
+        const bool held_c = (seg_c & 1) && tc - seg_c * S < S;
+        float box[6];
+        chunk_fk(sc, sh, q, t0 + c, true, held_c, sh.warp[w].F[c], sh.warp[w].H[c], box);
         __syncwarp();
-        chunk_collisions(sc, ls, cub, osph, aabb, sh, sh.warp[w], G_arm, G_blk, t0, min(kChunk, C - t0), grad,
+        chunk_collisions(sc, ls, cub, osph, aabb, sh, sh.warp[w], G_arm, G_blk, t0, min(kChunk, C - t0), grad, box,
                          acc_arm, acc_blk, acc_max, n_tests);
         __syncwarp();
     }
@@ -894,6 +918,12 @@ __global__ void __launch_bounds__(kTThreads, 2) k_traj(const __grid_constant__ S
     if (tid < B) {
         block_cuboid(sc.init[tid].x, sc.init[tid].y, sc.init[tid].z, sc.init[tid].w, sc.half[tid], sh.icub[tid]);
         cuboid_aabb(sh.icub[tid], sh.iaabb[tid]);
+    }
+    if (tid < 8) {
+        sh.dh[tid] = tid < 7 ? make_float4(sc.ca[tid], sc.sa[tid], sc.a[tid], sc.d[tid]) : make_float4(1.f, 0.f, 0.f, 0.f);
+        sh.th0[tid] = tid < 7 ? sc.th0[tid] : 0.f;
+        sh.lbc[tid] = sc.lbox_c[tid];
+        sh.lbh[tid] = sc.lbox_h[tid];
     }
     for (int o = tid; o < sc.n_cub; o += kTThreads) cuboid_aabb(&cub[4 * o], &aabb[2 * o]);
     for (int o = tid; o < sc.n_osph; o += kTThreads) {

@@ -1,0 +1,79 @@
+"""Writes the oracle side of the end-to-end distribution tests (tests/golden/e2e_*.json).
+
+For each seed of a workload it runs the FP64 oracle's whole method: the stage-1 loop of
+Alg. 1 (sample, elite top-M, K_lin linear and K_quad quadratic steps, satisfying filter, best
+P, retries) and stage 2 (lift, augmented-Lagrangian trajectory descent, satisfying filter,
+best P, retries).  It stores per seed the number of solutions found, their rank costs in
+ascending order and the attempt counts.  Only the oracle and the seeded scene generator are
+called.
+
+    python tests/golden/make_e2e_golden.py tower1 --seeds 100
+    python tests/golden/make_e2e_golden.py tower4 --seeds 100 --override Q=64
+
+The 4-block case keeps its scene, stage-1 sizes and waypoint count, and reduces the number of
+trajectory particles so that the FP64 all-pairs oracle finishes 100 seeds in about an hour.
+"""
+import argparse
+import json
+import os
+import sys
+import time
+
+ROOT = os.path.abspath(os.path.join(os.path.dirname(__file__), "..", ".."))
+sys.path.insert(0, ROOT)
+
+from oracle.oracle import Oracle  # noqa: E402
+from paper_2510_07674_gb300 import scenes  # noqa: E402
+
+
+def parse_overrides(items):
+    out = {}
+    for it in items:
+        k, v = it.split("=", 1)
+        out[k] = float(v) if any(c in v for c in ".e") else int(v)
+    return out
+
+
+def run_seed(name, seed, overrides, threads):
+    wl = scenes.make_problem(name, seed=seed, **overrides)
+    o = Oracle(wl, n_threads=threads)
+    place, place_attempts, place_steps = o.place_solve()
+    if len(place) == 0:
+        return {"seed": seed, "n_place": 0, "n_found": 0, "cost": [], "place_attempts": place_attempts,
+                "traj_attempts": 0}
+    q, cost, traj_attempts = o.traj_solve(place)
+    return {"seed": seed, "n_place": int(len(place)), "n_found": int(len(cost)), "cost": [float(c) for c in cost],
+            "place_attempts": int(place_attempts), "traj_attempts": int(traj_attempts)}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("workload")
+    ap.add_argument("--seeds", type=int, default=100)
+    ap.add_argument("--override", action="append", default=[], metavar="PARAM=VALUE")
+    ap.add_argument("--threads", type=int, default=os.cpu_count() or 1)
+    ap.add_argument("--out", default=None)
+    args = ap.parse_args()
+    overrides = parse_overrides(args.override)
+    tag = args.workload + "".join(f"_{k}{v}" for k, v in sorted(overrides.items()))
+    out = args.out or os.path.join(os.path.dirname(__file__), f"e2e_{tag}.json")
+    rows = []
+    if os.path.exists(out):   # resume
+        with open(out) as f:
+            rows = json.load(f)["seeds"]
+    done = {r["seed"] for r in rows}
+    for seed in range(args.seeds):
+        if seed in done:
+            continue
+        t = time.time()
+        rows.append(run_seed(args.workload, seed, overrides, args.threads))
+        print(f"seed {seed}: found {rows[-1]['n_found']} best "
+              f"{rows[-1]['cost'][0] if rows[-1]['cost'] else None} ({time.time() - t:.1f} s)", flush=True)
+        rows.sort(key=lambda r: r["seed"])
+        with open(out, "w") as f:
+            json.dump({"workload": args.workload, "overrides": overrides,
+                       "source": "oracle/ (FP64), tests/golden/make_e2e_golden.py", "seeds": rows}, f, indent=0)
+
+
+if __name__ == "__main__":
+    main()
