@@ -224,6 +224,37 @@ spasm_status spasm_set_timing(spasm_problem_t problem, int enable);
 spasm_status spasm_get_stats(spasm_problem_t problem, spasm_stats* out);
 spasm_status spasm_reset_stats(spasm_problem_t problem);
 
+/* ---- batched form (not in the paper: the throughput form of the hot path for many
+ * independent problems; the per-particle computation is that of Alg. 1 and Sec. IV as in
+ * spasm_optimize) ----
+ * spasm_optimize_batch solves n problems together on `cuda_stream`, which must be a created
+ * stream (not the legacy default stream: the batch is captured as CUDA graphs).  The first
+ * attempt of stage 1 of every problem not yet placed runs as one graph; stage 2 of every
+ * placed problem (lift, one persistent launch of the trajectory kernel over the particles
+ * of all problems, selection, FP64 check) runs as a second graph.  A problem that needs
+ * further attempts continues alone on its own stream, as spasm_optimize would.  Each
+ * problem's outcome is then read with spasm_result, and equals what spasm_optimize gives
+ * (the same arithmetic for every particle, whatever the schedule).  Returns SPASM_OK unless
+ * an argument is invalid or a CUDA call fails; a problem without a solution reports
+ * SPASM_ERR_NOSOLUTION from spasm_result.  Every problem's own stream is synchronised
+ * first, and the problems must not be used by another thread during the call.
+ * The schedule of the persistent launch: */
+typedef struct {
+    int per_fetch;     /* particles per work item a CTA takes from the shared counter (1..64) */
+    int ctas_per_sm;   /* resident CTAs per SM (0: as many as fit) */
+    int order;         /* 0: the largest problem (particles x configurations) first, 1: as given */
+} spasm_batch_config;
+/* per_fetch 1, ctas_per_sm 0, order 0. */
+spasm_status spasm_batch_default_config(spasm_batch_config* cfg);
+/* cfg NULL: the default schedule. */
+spasm_status spasm_optimize_batch(spasm_problem_t* problems, int n, void* cuda_stream, const spasm_batch_config* cfg);
+/* Autotuner of the schedule: places the problems not yet placed (stage 1, as above), lifts
+ * them, times one evaluation of every particle under each candidate schedule (per_fetch in
+ * {1, 2, 4} x ctas_per_sm in {all, 1} x both orders; CUDA events) and returns the fastest in
+ * *best (and its time in *best_ms when not NULL).  The schedule changes no result. */
+spasm_status spasm_batch_autotune(spasm_problem_t* problems, int n, void* cuda_stream, spasm_batch_config* best,
+                                  double* best_ms);
+
 /* ---- solver service with continuous batching (not in the paper: the serving form of the
  * hot path) ----
  * Requests are whole problems (copied at submission).  They are admitted in arrival order

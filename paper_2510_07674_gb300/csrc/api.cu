@@ -9,10 +9,7 @@
 #include <utility>
 #include <vector>
 
-#include "spasm.h"
-#include "check64.h"
-#include "launch_s2.h"
-#include "stage2.cuh"
+#include "problem.h"
 
 using namespace spasm;
 
@@ -31,63 +28,9 @@ cudaError_t configure_once_impl(const void* kernel, int dev, cudaError_t (*fn)(v
 }
 }  // namespace spasm
 
-static spasm_status fail(spasm_status st, const std::string& msg) {
+spasm_status spasm::fail(spasm_status st, const std::string& msg) {
     g_last_error = msg;
     return st;
-}
-
-#define SPASM_CUDA(call)                                                                              \
-    do {                                                                                              \
-        cudaError_t e_ = (call);                                                                      \
-        if (e_ != cudaSuccess)                                                                        \
-            return fail(SPASM_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));          \
-    } while (0)
-
-struct spasm_problem {
-    Scalars sc;
-    spasm_params prm;
-    cudaStream_t stream = nullptr;
-    DevTables tab{};
-    float4* d_cub = nullptr;
-    float4* d_osph = nullptr;
-    int* d_err = nullptr;
-    // stage 1
-    float *d_xs = nullptr, *d_cost = nullptr, *d_xm = nullptr, *d_costm = nullptr, *d_masked = nullptr;
-    int *d_idx = nullptr, *d_sat = nullptr, *d_nsat = nullptr, *d_best = nullptr;
-    float* d_place = nullptr;   // P x B x 4
-    bool placed = false;
-    int n_place = 0, place_attempts = 0, place_steps = 0;
-    // stage 2
-    float *d_q = nullptr, *d_lam = nullptr, *d_mu = nullptr, *d_metrics = nullptr, *d_tmasked = nullptr;
-    int *d_tsat = nullptr, *d_tnsat = nullptr, *d_tbest = nullptr;
-    float *d_rq = nullptr, *d_rcost = nullptr;   // returned solutions
-    int* d_rsucc = nullptr;
-    unsigned long long* d_tests = nullptr;   // sphere-obstacle tests run by the trajectory kernel
-    bool optimized = false;
-    int n_found = 0, traj_attempts = 0;
-    std::vector<double> host_cub, host_osph;
-    // FP64 final check
-    Scalars64 s64;
-    double* d_cub64 = nullptr;
-    double* d_osph64 = nullptr;
-    double* d_rmet64 = nullptr;
-    // statistics and timing
-    spasm_stats stats{};
-    bool timing = false;
-    cudaEvent_t ev[8] = {};
-};
-
-static void count_launches(spasm_problem* pr, int n) { pr->stats.kernel_launches += n; }
-
-static float ev_ms(cudaEvent_t a, cudaEvent_t b) {
-    float ms = 0.f;
-    if (cudaEventElapsedTime(&ms, a, b) != cudaSuccess) return 0.f;
-    return ms;
-}
-
-static spasm_status rec(spasm_problem* pr, int i) {
-    if (pr->timing) SPASM_CUDA(cudaEventRecord(pr->ev[i], pr->stream));
-    return SPASM_OK;
 }
 
 // Stream-ordered allocation from the device's default memory pool: unlike cudaMalloc /
@@ -101,13 +44,7 @@ static spasm_status dalloc(T** p, size_t count, cudaStream_t st) {
     return SPASM_OK;
 }
 
-#define SPASM_TRY(x)                      \
-    do {                                  \
-        spasm_status s_ = (x);            \
-        if (s_ != SPASM_OK) return s_;    \
-    } while (0)
-
-static spasm_status check_device_error(spasm_problem* pr) {
+spasm_status spasm::check_device_error(spasm_problem* pr) {
     int err = 0;
     SPASM_CUDA(cudaMemcpyAsync(&err, pr->d_err, sizeof(int), cudaMemcpyDeviceToHost, pr->stream));
     SPASM_CUDA(cudaStreamSynchronize(pr->stream));
@@ -123,7 +60,7 @@ static void free_all(spasm_problem* pr) {
     void* ptrs[] = {pr->d_cub, pr->d_osph, pr->d_err, pr->d_xs, pr->d_cost, pr->d_xm, pr->d_costm, pr->d_masked,
                     pr->d_idx, pr->d_sat, pr->d_nsat, pr->d_best, pr->d_place, pr->d_q, pr->d_lam,
                     pr->d_mu, pr->d_metrics, pr->d_tmasked, pr->d_tsat, pr->d_tnsat, pr->d_tbest, pr->d_rq,
-                    pr->d_rcost, pr->d_rsucc, pr->d_cub64, pr->d_osph64, pr->d_rmet64, pr->d_tests};
+                    pr->d_rcost, pr->d_rsucc, pr->d_cub64, pr->d_osph64, pr->d_rmet64, pr->d_tests, pr->d_sc};
     for (void* p : ptrs)
         if (p) cudaFreeAsync(p, pr->stream);
     for (cudaEvent_t e : pr->ev)
@@ -312,6 +249,7 @@ extern "C" spasm_status spasm_create_problem(const spasm_robot* robot, const spa
     ALLOC(pr->d_osph64, (size_t)4 * sc.n_osph);
     ALLOC(pr->d_rmet64, (size_t)6 * P);
     ALLOC(pr->d_tests, 1);
+    ALLOC(pr->d_sc, 1);
 #undef ALLOC
     for (auto& ev : pr->ev)
         if (st == SPASM_OK && cudaEventCreate(&ev) != cudaSuccess) st = fail(SPASM_ERR_CUDA, "cudaEventCreate failed");
@@ -326,6 +264,7 @@ extern "C" spasm_status spasm_create_problem(const spasm_robot* robot, const spa
         e = cudaMemcpyAsync(pr->d_cub64, cub64.data(), cub64.size() * sizeof(double), cudaMemcpyHostToDevice, pr->stream);
     if (e == cudaSuccess && !osph64.empty())
         e = cudaMemcpyAsync(pr->d_osph64, osph64.data(), osph64.size() * sizeof(double), cudaMemcpyHostToDevice, pr->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(pr->d_sc, &pr->sc, sizeof(Scalars), cudaMemcpyHostToDevice, pr->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(pr->d_err, 0, sizeof(int), pr->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(pr->stream);
     if (e != cudaSuccess) {
@@ -366,10 +305,9 @@ extern "C" spasm_status spasm_sizes(spasm_problem_t pr, int* C, int* NR) {
 // ---------------------------------------------------------------------------------- stage 1
 // One attempt of Alg. 1 entirely on the device; the count of satisfying particles lands in
 // d_nsat and the best min(P, count) placements in d_place.
-static spasm_status place_attempt(spasm_problem* pr, uint32_t attempt) {
+spasm_status spasm::place_attempt(spasm_problem* pr, uint32_t attempt, cudaStream_t s) {
     const Scalars& sc = pr->sc;
     const int N = sc.N, M = sc.M, P = sc.P, B = sc.B;
-    cudaStream_t s = pr->stream;
     SPASM_CUDA(launch_place_sample_cost(sc, pr->tab, N, attempt, pr->d_xs, pr->d_cost, pr->d_err, s));
     SPASM_CUDA(launch_topk(pr->d_cost, N, M, pr->d_idx, nullptr, s));
     SPASM_CUDA(launch_place_descend(sc, pr->tab, M, pr->d_xs, N, pr->d_idx, pr->d_xm, sc.K_lin, sc.K_quad,
@@ -377,35 +315,41 @@ static spasm_status place_attempt(spasm_problem* pr, uint32_t attempt) {
     SPASM_CUDA(launch_mask_costs(pr->d_costm, pr->d_sat, M, pr->d_masked, pr->d_nsat, s));
     SPASM_CUDA(launch_topk(pr->d_masked, M, P, pr->d_best, nullptr, s));
     SPASM_CUDA(launch_gather_soa_to_aos(pr->d_xm, M, 4 * B, pr->d_best, P, pr->d_place, s));
+    count_launches(pr, 6);
     return SPASM_OK;
 }
 
-extern "C" spasm_status spasm_place(spasm_problem_t pr) {
-    if (!pr) return fail(SPASM_ERR_INVALID, "null problem");
+spasm_status spasm::place_continue(spasm_problem* pr, int attempt, int steps, int nsat) {
     const int per = pr->sc.K_lin + pr->sc.K_quad;
-    int steps = 0, attempt = 0, found = 0;
-    SPASM_TRY(rec(pr, 0));
-    while (steps < pr->prm.max_steps || attempt == 0) {
-        SPASM_TRY(place_attempt(pr, (uint32_t)attempt));
-        count_launches(pr, 6);
+    while (nsat == 0 && (steps < pr->prm.max_steps || attempt == 0)) {
+        SPASM_TRY(place_attempt(pr, (uint32_t)attempt, pr->stream));
         steps += per;
         ++attempt;
-        int nsat = 0;
         SPASM_CUDA(cudaMemcpyAsync(&nsat, pr->d_nsat, sizeof(int), cudaMemcpyDeviceToHost, pr->stream));
         SPASM_CUDA(cudaStreamSynchronize(pr->stream));
         pr->stats.d2h_bytes += sizeof(int);
-        if (nsat > 0) { found = nsat < pr->sc.P ? nsat : pr->sc.P; break; }
     }
-    SPASM_TRY(rec(pr, 1));
+    const int found = nsat > 0 ? (nsat < pr->sc.P ? nsat : pr->sc.P) : 0;
     pr->place_attempts = attempt;
     pr->place_steps = steps;
     pr->n_place = found;
     pr->stats.place_attempts += attempt;
     SPASM_TRY(check_device_error(pr));
-    if (pr->timing) pr->stats.ms_place += ev_ms(pr->ev[0], pr->ev[1]);
     pr->placed = true;
     if (found == 0) return fail(SPASM_ERR_NOSOLUTION, "stage 1 found no satisfying placement within max_steps");
     return SPASM_OK;
+}
+
+extern "C" spasm_status spasm_place(spasm_problem_t pr) {
+    if (!pr) return fail(SPASM_ERR_INVALID, "null problem");
+    SPASM_TRY(rec(pr, 0));
+    const spasm_status st = place_continue(pr, 0, 0, 0);
+    SPASM_TRY(rec(pr, 1));
+    if (pr->timing) {
+        SPASM_CUDA(cudaEventSynchronize(pr->ev[1]));
+        pr->stats.ms_place += ev_ms(pr->ev[0], pr->ev[1]);
+    }
+    return st;
 }
 
 // ---------------------------------------------------------------------------------- stage 2
@@ -446,26 +390,37 @@ __global__ static void k_gather_solutions(const float* q, const float* metrics, 
     if (threadIdx.x == 0) { rcost[r] = metrics[8 * (size_t)src + 7]; rsucc[r] = 1; }
 }
 
-extern "C" spasm_status spasm_optimize(spasm_problem_t pr) {
-    if (!pr) return fail(SPASM_ERR_INVALID, "null problem");
-    if (!pr->placed) {
-        spasm_status st = spasm_place(pr);
-        if (st != SPASM_OK) return st;
-    }
-    if (pr->n_place <= 0) return fail(SPASM_ERR_NOSOLUTION, "no placements to lift");
+spasm_status spasm::traj_select(spasm_problem* pr, cudaStream_t s) {
+    const Scalars& sc = pr->sc;
+    k_rank_costs<<<(sc.Q + 255) / 256, 256, 0, s>>>(pr->d_metrics, sc.Q, pr->d_tmasked);
+    SPASM_CUDA(cudaGetLastError());
+    SPASM_CUDA(launch_mask_costs(pr->d_tmasked, pr->d_tsat, sc.Q, pr->d_tmasked, pr->d_tnsat, s));
+    count_launches(pr, 2);
+    return SPASM_OK;
+}
+
+spasm_status spasm::finish_enqueue(spasm_problem* pr, cudaStream_t s) {
+    const Scalars& sc = pr->sc;
+    if (sc.Q > 32768) return fail(SPASM_ERR_INVALID, "Q > 32768 unsupported by the selection kernel");
+    SPASM_CUDA(launch_topk(pr->d_tmasked, sc.Q, sc.P, pr->d_tbest, nullptr, s));
+    k_gather_solutions<<<sc.P, 256, 0, s>>>(pr->d_q, pr->d_metrics, pr->d_tbest, pr->d_tnsat, sc.P, sc.C, pr->d_rq,
+                                             pr->d_rcost, pr->d_rsucc);
+    SPASM_CUDA(cudaGetLastError());
+    // FP64 re-evaluation of the returned solutions decides their success flags
+    SPASM_CUDA(launch_check64(pr->s64, pr->d_cub64, pr->d_osph64, pr->d_rq, pr->d_tnsat, sc.P, pr->d_rmet64,
+                              pr->d_rsucc, s));
+    count_launches(pr, 3);
+    return SPASM_OK;
+}
+
+spasm_status spasm::traj_continue(spasm_problem* pr, int attempt, int steps, int nsat, int* found) {
     const Scalars& sc = pr->sc;
     cudaStream_t s = pr->stream;
-    int steps = 0, attempt = 0, found = 0;
-    SPASM_CUDA(cudaMemsetAsync(pr->d_tests, 0, sizeof(unsigned long long), s));
-    while (steps < pr->prm.max_steps || attempt == 0) {
+    while (nsat == 0 && (steps < pr->prm.max_steps || attempt == 0)) {
         SPASM_TRY(traj_attempt(pr, (uint32_t)attempt));
         steps += sc.K_traj;
         ++attempt;
-        k_rank_costs<<<(sc.Q + 255) / 256, 256, 0, s>>>(pr->d_metrics, sc.Q, pr->d_tmasked);
-        SPASM_CUDA(cudaGetLastError());
-        SPASM_CUDA(launch_mask_costs(pr->d_tmasked, pr->d_tsat, sc.Q, pr->d_tmasked, pr->d_tnsat, s));
-        int nsat = 0;
-        count_launches(pr, 2);
+        SPASM_TRY(traj_select(pr, s));
         SPASM_CUDA(cudaMemcpyAsync(&nsat, pr->d_tnsat, sizeof(int), cudaMemcpyDeviceToHost, s));
         SPASM_CUDA(cudaStreamSynchronize(s));
         pr->stats.d2h_bytes += sizeof(int);
@@ -473,22 +428,19 @@ extern "C" spasm_status spasm_optimize(spasm_problem_t pr) {
             pr->stats.ms_lift += ev_ms(pr->ev[2], pr->ev[3]);
             pr->stats.ms_traj += ev_ms(pr->ev[3], pr->ev[4]);
         }
-        if (nsat > 0) { found = nsat < sc.P ? nsat : sc.P; break; }
     }
+    *found = nsat > 0 ? (nsat < sc.P ? nsat : sc.P) : 0;
     pr->traj_attempts = attempt;
     pr->stats.traj_attempts += attempt;
-    if (found > 0) {
-        if (sc.Q > 32768) return fail(SPASM_ERR_INVALID, "Q > 32768 unsupported by the selection kernel");
+    return SPASM_OK;
+}
+
+spasm_status spasm::finish_record(spasm_problem* pr, int found, bool finish_done) {
+    const Scalars& sc = pr->sc;
+    if (found > 0 && !finish_done) {
         SPASM_TRY(rec(pr, 5));
-        SPASM_CUDA(launch_topk(pr->d_tmasked, sc.Q, sc.P, pr->d_tbest, nullptr, s));
-        k_gather_solutions<<<sc.P, 256, 0, s>>>(pr->d_q, pr->d_metrics, pr->d_tbest, pr->d_tnsat, sc.P, sc.C, pr->d_rq,
-                                                 pr->d_rcost, pr->d_rsucc);
-        SPASM_CUDA(cudaGetLastError());
-        // FP64 re-evaluation of the returned solutions decides their success flags
-        SPASM_CUDA(launch_check64(pr->s64, pr->d_cub64, pr->d_osph64, pr->d_rq, pr->d_tnsat, sc.P, pr->d_rmet64,
-                                  pr->d_rsucc, s));
+        SPASM_TRY(finish_enqueue(pr, pr->stream));
         SPASM_TRY(rec(pr, 6));
-        count_launches(pr, 3);
     }
     pr->n_found = found;
     SPASM_TRY(check_device_error(pr));
@@ -507,12 +459,25 @@ extern "C" spasm_status spasm_optimize(spasm_problem_t pr) {
         int ns = 0;
         for (int r = 0; r < found; ++r) ns += succ[r] != 0;
         pr->stats.n_success = ns;
-        if (pr->timing) pr->stats.ms_finish += ev_ms(pr->ev[5], pr->ev[6]);
+        if (pr->timing && !finish_done) pr->stats.ms_finish += ev_ms(pr->ev[5], pr->ev[6]);
     }
     pr->stats.n_found = found;
     pr->optimized = true;
     if (found == 0) return fail(SPASM_ERR_NOSOLUTION, "stage 2 found no satisfying trajectory within max_steps");
     return SPASM_OK;
+}
+
+extern "C" spasm_status spasm_optimize(spasm_problem_t pr) {
+    if (!pr) return fail(SPASM_ERR_INVALID, "null problem");
+    if (!pr->placed) {
+        spasm_status st = spasm_place(pr);
+        if (st != SPASM_OK) return st;
+    }
+    if (pr->n_place <= 0) return fail(SPASM_ERR_NOSOLUTION, "no placements to lift");
+    SPASM_CUDA(cudaMemsetAsync(pr->d_tests, 0, sizeof(unsigned long long), pr->stream));
+    int found = 0;
+    SPASM_TRY(traj_continue(pr, 0, 0, 0, &found));
+    return finish_record(pr, found, false);
 }
 
 extern "C" spasm_status spasm_result(spasm_problem_t pr, int* n_found, double* placements, double* traj, double* cost,
@@ -620,6 +585,8 @@ extern "C" spasm_status spasm_set_seed(spasm_problem_t pr, uint64_t seed) {
     SPASM_CUDA(cudaStreamSynchronize(pr->stream));
     pr->sc.seed = seed;
     pr->prm.seed = seed;
+    SPASM_CUDA(cudaMemcpyAsync(pr->d_sc, &pr->sc, sizeof(Scalars), cudaMemcpyHostToDevice, pr->stream));
+    SPASM_CUDA(cudaStreamSynchronize(pr->stream));
     pr->placed = pr->optimized = false;
     pr->n_place = pr->n_found = 0;
     return SPASM_OK;

@@ -328,9 +328,12 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t phase) {
 }
 
 // Copies up to two tables; every thread of the CTA calls it; returns false on timeout.
+// `init`: initialise the barrier first (its first use in the CTA); `phase`: parity of the
+// barrier phase this copy completes (0 for the first use, then alternating).
 __device__ __forceinline__ bool stage_tables(void* dst0, const void* src0, uint32_t bytes0, void* dst1, const void* src1,
-                                             uint32_t bytes1, uint64_t* bar, int* err) {
-    if (threadIdx.x == 0) {
+                                             uint32_t bytes1, uint64_t* bar, int* err, bool init = true,
+                                             uint32_t phase = 0) {
+    if (init && threadIdx.x == 0) {
         mbar_init(bar, 1);
         fence_mbar_init();
     }
@@ -342,7 +345,7 @@ __device__ __forceinline__ bool stage_tables(void* dst0, const void* src0, uint3
     }
     bool done = false;
     for (int polls = 0; polls < (1 << 22); ++polls) {
-        if (mbar_try_wait(bar, 0)) { done = true; break; }
+        if (mbar_try_wait(bar, phase)) { done = true; break; }
     }
     if (!done) set_error(err, kDevTimeout);
     int all = __syncthreads_and(done ? 1 : 0);

@@ -892,10 +892,11 @@ __device__ void traj_evaluate(const Scalars& sc, const LaneSpheres& ls, const fl
     __syncthreads();
 }
 
-__global__ void __launch_bounds__(kTThreads, 2) k_traj(const __grid_constant__ Scalars sc, DevTables tab, int n, int mode,
-                                                      TrajIO io, int* err) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
+// One particle of the trajectory stage by the whole CTA: load its state, run the descent (or
+// the single evaluation), write the outputs.  The environment tables are already in shared
+// memory (smem_raw, laid out by the t_*_offset functions of this problem).
+__device__ __forceinline__ void traj_particle(const Scalars& sc, int p, int mode, const TrajIO& io,
+                                              unsigned char* smem_raw) {
     float4* cub = reinterpret_cast<float4*>(smem_raw + t_env_offset());
     float4* osph = cub + 4 * sc.n_cub;
     float4* aabb = reinterpret_cast<float4*>(smem_raw + t_aabb_offset(sc.n_cub, sc.n_osph));
@@ -904,10 +905,6 @@ __global__ void __launch_bounds__(kTThreads, 2) k_traj(const __grid_constant__ S
     float* G_arm = q + sc.C * 8;
     float* G_blk = G_arm + sc.C * 8;
     SpecialFrames* sp = reinterpret_cast<SpecialFrames*>(smem_raw + t_sp_offset(sc.n_cub, sc.n_osph, sc.C));
-    if (!stage_tables(cub, tab.cub, (uint32_t)sc.n_cub * 64u, osph, tab.osph, (uint32_t)sc.n_osph * 16u, bar, err))
-        return;
-    const int p = blockIdx.x;
-    if (p >= n) return;
     const int tid = threadIdx.x;
     const int C = sc.C, NR = sc.NR, B = sc.B;
 
@@ -994,6 +991,80 @@ __global__ void __launch_bounds__(kTThreads, 2) k_traj(const __grid_constant__ S
     }
 }
 
+// One CTA per particle of one problem.
+__global__ void __launch_bounds__(kTThreads, 2) k_traj(const __grid_constant__ Scalars sc, DevTables tab, int n, int mode,
+                                                      TrajIO io, int* err) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
+    float4* cub = reinterpret_cast<float4*>(smem_raw + t_env_offset());
+    float4* osph = cub + 4 * sc.n_cub;
+    if (!stage_tables(cub, tab.cub, (uint32_t)sc.n_cub * 64u, osph, tab.osph, (uint32_t)sc.n_osph * 16u, bar, err))
+        return;
+    const int p = blockIdx.x;
+    if (p >= n) return;
+    traj_particle(sc, p, mode, io, smem_raw);
+}
+
+static_assert(sizeof(Scalars) % 16 == 0, "the batched kernel copies Scalars in 16-byte words");
+
+// Batched form: a persistent grid over the particles of several problems.  Work items are
+// runs of `per_fetch` consecutive particles of one problem, numbered problem after problem
+// (jobs[j].first is the first item of problem j); each CTA takes the next item from *next
+// until none is left.  On a change of problem the CTA stages that problem's constants and
+// tables into shared memory.  Every particle runs exactly the code of k_traj, so results
+// equal the single-problem launches bit for bit, whatever the schedule.
+__global__ void __launch_bounds__(kTThreads, 2) k_traj_batch(const TrajJob* __restrict__ jobs, int n_jobs, int n_items,
+                                                            int per_fetch, int mode, int* next) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ __align__(16) Scalars sc_s;
+    __shared__ TrajIO io_s;
+    __shared__ int s_item, s_job;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
+    int cur = -1;
+    uint32_t uses = 0;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const int it = atomicAdd(next, 1);
+            int j = -1;
+            if (it < n_items) {   // last job whose first item is <= it
+                int lo = 0, hi = n_jobs - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (jobs[mid].first <= it) lo = mid; else hi = mid - 1;
+                }
+                j = lo;
+            }
+            s_item = it;
+            s_job = j;
+        }
+        __syncthreads();
+        const int it = s_item, j = s_job;
+        if (j < 0) break;
+        const TrajJob& job = jobs[j];
+        if (j != cur) {
+            // stage the problem's constants (int4 words) and its tables
+            const int4* src = reinterpret_cast<const int4*>(job.sc);
+            int4* dst = reinterpret_cast<int4*>(&sc_s);
+            for (int i = threadIdx.x; i < (int)(sizeof(Scalars) / 16); i += blockDim.x) dst[i] = src[i];
+            if (threadIdx.x == 0) io_s = job.io;
+            __syncthreads();
+            float4* cub = reinterpret_cast<float4*>(smem_raw + t_env_offset());
+            float4* osph = cub + 4 * sc_s.n_cub;
+            if (!stage_tables(cub, job.tab.cub, (uint32_t)sc_s.n_cub * 64u, osph, job.tab.osph,
+                              (uint32_t)sc_s.n_osph * 16u, bar, job.err, uses == 0, uses & 1u))
+                return;
+            ++uses;
+            cur = j;
+        }
+        const int p0 = (it - job.first) * per_fetch;
+        const int p1 = min(p0 + per_fetch, job.n);
+        for (int p = p0; p < p1; ++p) {
+            traj_particle(sc_s, p, mode, io_s, smem_raw);
+            __syncthreads();
+        }
+    }
+}
+
 // ================================================================================== launchers
 cudaError_t launch_lift(const Scalars& sc, int n, const float* place, int n_place, uint32_t attempt, float* q,
                         cudaStream_t st) {
@@ -1005,6 +1076,22 @@ cudaError_t launch_lift(const Scalars& sc, int n, const float* place, int n_plac
     const int n_cfg = n * sc.C;
     k_lift_interp<<<(n_cfg + 255) / 256, 256, 0, st>>>(sc, n, n_place, attempt, q);
     return cudaGetLastError();
+}
+
+cudaError_t launch_traj_batch(const TrajJob* jobs, int n_jobs, int n_items, int per_fetch, int mode, int* next,
+                              size_t smem_bytes, int grid, cudaStream_t st) {
+    if (n_items <= 0) return cudaSuccess;
+    cudaError_t e = allow_max_dynamic_smem(k_traj_batch, smem_bytes);
+    if (e != cudaSuccess) return e;
+    k_traj_batch<<<grid, kTThreads, smem_bytes, st>>>(jobs, n_jobs, n_items, per_fetch, mode, next);
+    return cudaGetLastError();
+}
+
+int traj_batch_ctas_per_sm(size_t smem_bytes) {
+    int n = 0;
+    if (allow_max_dynamic_smem(k_traj_batch, smem_bytes) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_traj_batch, kTThreads, smem_bytes) != cudaSuccess) return 0;
+    return n;
 }
 
 cudaError_t launch_traj(const Scalars& sc, DevTables t, int n, int mode, const TrajIO& io, int* err,

@@ -21,10 +21,26 @@ struct TrajIO {
 };
 enum TrajModeHost { kTrajModeEval = 0, kTrajModeDescend = 1, kTrajModeCheck = 2 };
 
+// One problem of a batched trajectory launch (device array, sorted by `first`).
+struct TrajJob {
+    const Scalars* sc;   // device copy of the problem constants
+    DevTables tab;
+    TrajIO io;
+    int* err;
+    int n;               // particles
+    int first;           // index of the problem's first work item
+};
+
 size_t traj_smem_bytes(const Scalars& sc);
 // IK at grasp/place poses + interpolation; particle p lifts placement p % n_place.
 cudaError_t launch_lift(const Scalars& sc, int n, const float* place, int n_place, uint32_t attempt, float* q,
                         cudaStream_t st);
 cudaError_t launch_traj(const Scalars& sc, DevTables t, int n, int mode, const TrajIO& io, int* err, cudaStream_t st);
+// Persistent batched launch over jobs[0..n_jobs) (n_items work items of per_fetch particles;
+// *next must be 0); smem_bytes = the largest traj_smem_bytes of the jobs.
+cudaError_t launch_traj_batch(const TrajJob* jobs, int n_jobs, int n_items, int per_fetch, int mode, int* next,
+                              size_t smem_bytes, int grid, cudaStream_t st);
+// Resident CTAs per SM of the batched kernel at that shared-memory size (0 on error).
+int traj_batch_ctas_per_sm(size_t smem_bytes);
 
 }  // namespace spasm

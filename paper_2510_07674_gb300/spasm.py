@@ -26,7 +26,8 @@ EXPORTED = ["spasm_create_problem", "spasm_destroy_problem", "spasm_last_error",
             "spasm_select_topk", "spasm_lift", "spasm_traj_eval", "spasm_traj_descend", "spasm_set_seed",
             "spasm_set_timing", "spasm_get_stats", "spasm_reset_stats", "spasm_place_select_static",
             "spasm_server_create", "spasm_server_submit", "spasm_server_poll", "spasm_server_wait",
-            "spasm_server_result", "spasm_server_release", "spasm_server_destroy"]
+            "spasm_server_result", "spasm_server_release", "spasm_server_destroy", "spasm_batch_default_config",
+            "spasm_optimize_batch", "spasm_batch_autotune"]
 
 
 class SpasmError(RuntimeError):
@@ -72,6 +73,10 @@ class _Stats(ctypes.Structure):
                 ("d2h_bytes", ctypes.c_longlong), ("tests_executed", ctypes.c_longlong)]
 
 
+class _BatchConfig(ctypes.Structure):
+    _fields_ = [("per_fetch", ctypes.c_int), ("ctas_per_sm", ctypes.c_int), ("order", ctypes.c_int)]
+
+
 _lib = None
 
 
@@ -111,6 +116,9 @@ def lib():
         L.spasm_server_result.argtypes = [_V, LL, _I, _I, _D, _D, _D, _I, _D, _D]
         L.spasm_server_release.argtypes = [_V, LL]
         L.spasm_server_destroy.argtypes = [_V]
+        L.spasm_batch_default_config.argtypes = [ctypes.POINTER(_BatchConfig)]
+        L.spasm_optimize_batch.argtypes = [ctypes.POINTER(_V), ctypes.c_int, _V, ctypes.POINTER(_BatchConfig)]
+        L.spasm_batch_autotune.argtypes = [ctypes.POINTER(_V), ctypes.c_int, _V, ctypes.POINTER(_BatchConfig), _D]
         for name in EXPORTED:
             if name != "spasm_last_error":
                 getattr(L, name).restype = ctypes.c_int
@@ -278,6 +286,46 @@ def spasm_reset_stats(problem: Problem):
 def spasm_place_select_static(problem: Problem, n: int, attempt: int, m: int, x_elite, cost_elite):
     """Sampling + elite selection with the library's fixed device scratch (no allocation)."""
     _check(lib().spasm_place_select_static(problem.handle, n, attempt, m, _dev(x_elite), _dev(cost_elite)))
+
+
+def _handles(problems):
+    arr = (_V * len(problems))()
+    for i, p in enumerate(problems):
+        arr[i] = p.handle
+    return arr
+
+
+def _batch_stream(stream):
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    if int(stream) == 0:
+        raise ValueError("the batched form needs a created (non-default) CUDA stream")
+    return _V(int(stream))
+
+
+def spasm_batch_default_config() -> dict:
+    c = _BatchConfig()
+    _check(lib().spasm_batch_default_config(ctypes.byref(c)))
+    return {"per_fetch": c.per_fetch, "ctas_per_sm": c.ctas_per_sm, "order": c.order}
+
+
+def spasm_optimize_batch(problems, stream=None, config: Optional[dict] = None):
+    """Solve the problems together (batched form); read each with spasm_result."""
+    cfg = None
+    if config is not None:
+        cfg = _BatchConfig(int(config["per_fetch"]), int(config["ctas_per_sm"]), int(config["order"]))
+    _check(lib().spasm_optimize_batch(_handles(problems), len(problems), _batch_stream(stream),
+                                      ctypes.byref(cfg) if cfg is not None else None))
+
+
+def spasm_batch_autotune(problems, stream=None) -> dict:
+    """Fastest schedule of the batched trajectory launch for these problems (and its time)."""
+    c = _BatchConfig()
+    ms = ctypes.c_double()
+    _check(lib().spasm_batch_autotune(_handles(problems), len(problems), _batch_stream(stream), ctypes.byref(c),
+                                      ctypes.byref(ms)))
+    return {"per_fetch": c.per_fetch, "ctas_per_sm": c.ctas_per_sm, "order": c.order, "ms": ms.value}
 
 
 class Server:
