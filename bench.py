@@ -285,7 +285,7 @@ def run_native(args, ws, rank, local):
 
     batched = served = None
     if args.serve_problems > 0:
-        batched, served = run_served(args, rank, overrides)
+        batched, served = run_forms(args, rank, overrides, peak)
 
     out = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
@@ -325,11 +325,24 @@ def _percentile(xs, q):
     return float(xs[min(len(xs) - 1, max(0, math.ceil(q * len(xs)) - 1))])
 
 
-def run_served(args, rank, overrides):
-    """Heterogeneous problems (1-10 blocks, 8-64 cuboids, 1024-4096 trajectory particles,
-    32 waypoints per segment): (a) all submitted at once to the continuous-batching service
-    vs the same problems solved one after another through the plain API; (b) Poisson
-    arrivals at several rates, latency from arrival to completion."""
+def solve_flop(wl, st) -> float:
+    """Algorithmic trajectory work of one finished solve (the headline roofline's count):
+    executed sphere-obstacle tests, the chunk cull and the forward kinematics of every
+    configuration of every evaluation."""
+    tc = count_tests(wl)
+    evals = wl.params.Q * (wl.params.K_traj + 1) * max(st["traj_launches"], 1)
+    return (FLOP_PER_TEST * st["tests_executed"] + FLOP_PER_CULL * evals * (tc["C"] - 1) * tc["n_obs"]
+            + FLOP_PER_CONFIG_FK * evals * (tc["C"] - 1))
+
+
+def run_forms(args, rank, overrides, peak):
+    """The same heterogeneous problems (1-10 blocks, 8-64 cuboids, 1024-4096 trajectory
+    particles, 32 waypoints per segment) solved (a) one after another through the plain API,
+    (b) as one batch (spasm_optimize_batch: two CUDA graphs, one persistent trajectory
+    launch; schedule from spasm_batch_autotune on a separate copy of the problems), (c) all
+    submitted at once to the continuous-batching service; then (d) Poisson arrivals at each
+    rate to the service, latency from arrival to completion.  Problem creation and the
+    result read-back are inside every timed region."""
     import random
 
     import torch
@@ -339,10 +352,15 @@ def run_served(args, rank, overrides):
     n = args.serve_problems
     wls = scenes.heterogeneous_batch(n, seed=1000 + rank)
     ov = {"max_steps": overrides.get("max_steps", 1000)}
-    # plain form: one problem at a time
+
+    def form(t, ok, flop, **extra):
+        ach = flop / t / 1e12
+        return dict(solves_per_s=n / t, success=ok / n, achieved_tflops=ach, frac_of_alu_peak=ach / peak, **extra)
+
+    # (a) plain form
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    ok_plain = 0
+    ok = flop = 0
     for wl in wls:
         p = S.Problem(wl, **ov)
         try:
@@ -350,25 +368,49 @@ def run_served(args, rank, overrides):
         except S.SpasmError as e:
             if e.status != -4:
                 raise
-        ok_plain += S.spasm_result(p, allow_empty=True)["n_found"] > 0
+        r = S.spasm_result(p, allow_empty=True)
+        ok += int(r["success"].sum() > 0)
+        flop += solve_flop(wl, S.spasm_get_stats(p))
         p.close()
     torch.cuda.synchronize()
-    t_plain = time.perf_counter() - t0
-    # batched: all at once to the service
+    plain = form(time.perf_counter() - t0, ok, flop)
+
+    # (b) batched form
+    stream = torch.cuda.Stream()
+    tune = [S.Problem(wl, stream=stream.cuda_stream, **ov) for wl in wls]
+    sched = S.spasm_batch_autotune(tune, stream=stream.cuda_stream)
+    for p in tune:
+        p.close()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    prs = [S.Problem(wl, stream=stream.cuda_stream, **ov) for wl in wls]
+    S.spasm_optimize_batch(prs, stream=stream.cuda_stream, config=sched)
+    ok = flop = 0
+    for wl, p in zip(wls, prs):
+        r = S.spasm_result(p, allow_empty=True)
+        ok += int(r["success"].sum() > 0)
+        flop += solve_flop(wl, S.spasm_get_stats(p))
+        p.close()
+    torch.cuda.synchronize()
+    batched = form(time.perf_counter() - t0, ok, flop, schedule=sched,
+                   form="spasm_optimize_batch: stage-1 graph + stage-2 graph with one persistent trajectory launch")
+    batched["speedup_vs_plain"] = batched["solves_per_s"] / plain["solves_per_s"]
+
+    # (c) the service, everything submitted at once
     sv = S.Server(budget_bytes=150 << 30, max_inflight=args.serve_slots)
     t0 = time.perf_counter()
     tickets = [S.spasm_server_submit(sv, wl, **ov) for wl in wls]
     for t in tickets:
         S.spasm_server_wait(sv, t, 600.0)
-    t_batch = time.perf_counter() - t0
+    t_all = time.perf_counter() - t0
     res = [S.spasm_server_result(sv, t) for t in tickets]
     for t in tickets:
         S.spasm_server_release(sv, t)
-    batched = {"problems": n, "slots": args.serve_slots, "plain_solves_per_s": n / t_plain,
-               "batched_solves_per_s": n / t_batch, "speedup_vs_plain": t_plain / t_batch,
-               "success_plain": ok_plain / n, "success_batched": sum(r["n_found"] > 0 for r in res) / n,
-               "workload": "heterogeneous: B~U{1..10}, O~U{8..64}, Q~U{1024..4096}, N=4096->M=1024, 32 waypoints"}
-    # served: Poisson arrivals
+    service = dict(solves_per_s=n / t_all, success=sum(int(r["success"].sum() > 0) for r in res) / n,
+                   slots=args.serve_slots, budget_gb=150)
+    service["speedup_vs_plain"] = service["solves_per_s"] / plain["solves_per_s"]
+
+    # (d) served: Poisson arrivals
     served = []
     rng = random.Random(7 + rank)
     for rate in args.serve_rates:
@@ -386,13 +428,17 @@ def run_served(args, rank, overrides):
         for t in tickets:
             S.spasm_server_wait(sv, t, 600.0)
         end = time.perf_counter() - start
-        lat = [S.spasm_server_result(sv, t)["latency_ms"] for t in tickets]
+        rs = [S.spasm_server_result(sv, t) for t in tickets]
+        lat = [r["latency_ms"] for r in rs]
         for t in tickets:
             S.spasm_server_release(sv, t)
         served.append({"rate_per_s": rate, "requests": n, "solves_per_s": n / end,
+                       "success": sum(int(r["success"].sum() > 0) for r in rs) / n,
                        "latency_ms_p50": _percentile(lat, 0.5), "latency_ms_p99": _percentile(lat, 0.99)})
     sv.close()
-    return batched, served
+    forms = {"problems": n, "workload": "heterogeneous: B~U{1..10}, O~U{8..64}, Q~U{1024..4096}, N=4096->M=1024, "
+             "32 waypoints per segment", "plain": plain, "batched": batched, "service_all_at_once": service}
+    return forms, served
 
 
 # ------------------------------------------------------------------------------- oracle
@@ -473,10 +519,10 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--cpu-budget-s", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--serve-problems", type=int, default=32,
+    ap.add_argument("--serve-problems", type=int, default=64,
                     help="heterogeneous problems for the batched / served measurements (0 = skip)")
     ap.add_argument("--serve-slots", type=int, default=8)
-    ap.add_argument("--serve-rates", type=float, nargs="*", default=[10.0, 50.0, 200.0])
+    ap.add_argument("--serve-rates", type=float, nargs="*", default=[10.0, 30.0, 100.0, 300.0, 1000.0, 2000.0])
     ap.add_argument("--override", action="append", default=[], metavar="PARAM=VALUE",
                     help="change a solver parameter (profiling of a reduced case only; recorded in config)")
     args = ap.parse_args()
