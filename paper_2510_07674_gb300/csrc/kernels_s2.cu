@@ -155,8 +155,9 @@ struct TWarp {
     float wr[2][kMaxB][4];   // d/d(placed pose k): group arm, group block
     float part[4];           // C_arm, C_block, max penetration
     float pc[2];             // placed tower: sum and maximum of its penetrations (this warp's share)
-    uint32_t cmask[kMaxCub / 32];    // environment cuboids that may touch the current chunk
-    uint32_t smask[kMaxOSph / 32];   // environment spheres that may touch the current chunk
+    uint32_t cmask[kChunk][kMaxCub / 32];    // environment cuboids that may touch configuration c of the chunk
+    uint32_t smask[kChunk][kMaxOSph / 32];   // environment spheres that may touch configuration c
+    uint32_t bmask[2][kChunk];               // placed / not-yet-moved blocks that may touch configuration c
 };
 
 // Frames of one configuration kept for the epilogue (grasp and place configurations).
@@ -373,20 +374,56 @@ __device__ __forceinline__ void chunk_collisions(const Scalars& sc, const LaneSp
     auto overlaps = [&](const float4& blo, const float4& bhi) {
         return blo.x <= hi_x && bhi.x >= lo_x && blo.y <= hi_y && bhi.y >= lo_y && blo.z <= hi_z && bhi.z >= lo_z;
     };
+    // second level: each candidate of the chunk box against the lanes' own link boxes (lane
+    // 8c + k: link k of configuration c); configuration c keeps the candidate when one of its
+    // link boxes overlaps the candidate's box.  Both levels are exact: no sphere inside the
+    // boxes is dropped.
+    const float* lb = lane_box;
+    auto refine = [&](unsigned m, int base, const float4* boxes, int stride, uint32_t out[kChunk]) {
+#pragma unroll
+        for (int c = 0; c < kChunk; ++c) out[c] = 0u;
+        while (m) {
+            const int bit = __ffs(m) - 1;
+            m &= m - 1;
+            const float4 blo = boxes[stride * (base + bit)], bhi = boxes[stride * (base + bit) + 1];
+            const unsigned bal = __ballot_sync(0xffffffffu, blo.x <= lb[3] && bhi.x >= lb[0] && blo.y <= lb[4] &&
+                                                                bhi.y >= lb[1] && blo.z <= lb[5] && bhi.z >= lb[2]);
+#pragma unroll
+            for (int c = 0; c < kChunk; ++c)
+                if ((bal >> (8 * c)) & 0xffu) out[c] |= 1u << bit;
+        }
+    };
     const int n_cw = (sc.n_cub + 31) >> 5, n_sw = (sc.n_osph + 31) >> 5;
+    uint32_t per[kChunk];
     for (int wd = 0; wd < n_cw; ++wd) {
         const int oi = 32 * wd + lane;
         const unsigned m = __ballot_sync(0xffffffffu, oi < sc.n_cub && overlaps(aabb[2 * oi], aabb[2 * oi + 1]));
-        if (lane == 0) tw.cmask[wd] = m;
+        refine(m, 32 * wd, aabb, 2, per);
+        if (lane == 0)
+#pragma unroll
+            for (int c = 0; c < kChunk; ++c) tw.cmask[c][wd] = per[c];
     }
     for (int wd = 0; wd < n_sw; ++wd) {
         const int oi = 32 * wd + lane;
         const int ai = sc.n_cub + oi;
         const unsigned m = __ballot_sync(0xffffffffu, oi < sc.n_osph && overlaps(aabb[2 * ai], aabb[2 * ai + 1]));
-        if (lane == 0) tw.smask[wd] = m;
+        refine(m, sc.n_cub + 32 * wd, aabb, 2, per);
+        if (lane == 0)
+#pragma unroll
+            for (int c = 0; c < kChunk; ++c) tw.smask[c][wd] = per[c];
     }
-    const unsigned bm_placed = __ballot_sync(0xffffffffu, lane < B && overlaps(sh.baabb[lane][0], sh.baabb[lane][1]));
-    const unsigned bm_init = __ballot_sync(0xffffffffu, lane < B && overlaps(sh.iaabb[lane][0], sh.iaabb[lane][1]));
+    {
+        const unsigned bm_placed = __ballot_sync(0xffffffffu, lane < B && overlaps(sh.baabb[lane][0], sh.baabb[lane][1]));
+        refine(bm_placed, 0, &sh.baabb[0][0], 2, per);
+        if (lane == 0)
+#pragma unroll
+            for (int c = 0; c < kChunk; ++c) tw.bmask[0][c] = per[c];
+        const unsigned bm_init = __ballot_sync(0xffffffffu, lane < B && overlaps(sh.iaabb[lane][0], sh.iaabb[lane][1]));
+        refine(bm_init, 0, &sh.iaabb[0][0], 2, per);
+        if (lane == 0)
+#pragma unroll
+            for (int c = 0; c < kChunk; ++c) tw.bmask[1][c] = per[c];
+    }
     __syncwarp();
 
     // pass 2: every configuration against the candidates
@@ -402,7 +439,7 @@ __device__ __forceinline__ void chunk_collisions(const Scalars& sc, const LaneSp
         int visits = 0;
 
         for (int wd = 0; wd < n_cw; ++wd) {
-            unsigned m = tw.cmask[wd];
+            unsigned m = tw.cmask[ci][wd];
             visits += __popc(m);
             while (m) {
                 const int ob = 32 * wd + __ffs(m) - 1;
@@ -429,7 +466,7 @@ __device__ __forceinline__ void chunk_collisions(const Scalars& sc, const LaneSp
             }
         }
         for (int wd = 0; wd < n_sw; ++wd) {
-            unsigned m = tw.smask[wd];
+            unsigned m = tw.smask[ci][wd];
             visits += __popc(m);
             while (m) {
                 const int ob = 32 * wd + __ffs(m) - 1;
@@ -452,7 +489,7 @@ __device__ __forceinline__ void chunk_collisions(const Scalars& sc, const LaneSp
         // context blocks: placed (k < b, movable) and not yet moved (k > b)
         {
             const unsigned below = (1u << b) - 1u;
-            unsigned m = (bm_placed & below) | (bm_init & ~below & ~(1u << b));
+            unsigned m = (tw.bmask[0][ci] & below) | (tw.bmask[1][ci] & ~below & ~(1u << b));
             visits += __popc(m);
             while (m) {
                 const int kb = __ffs(m) - 1;
