@@ -427,8 +427,12 @@ __device__ __forceinline__ void chunk_collisions(const Scalars& sc, const LaneSp
     __syncwarp();
 
     // pass 2: every configuration against the candidates
+    const int seg0 = (t0 - 1) / S, r0 = (t0 - 1) - seg0 * S;
     for (int ci = 0; ci < nc; ++ci) {
-        const int t = t0 + ci, seg = (t - 1) / S, b = seg >> 1, jj = t - seg * S;
+        const int t = t0 + ci;
+        int seg = seg0, r = r0 + ci;
+        while (r >= S) { r -= S; ++seg; }
+        const int b = seg >> 1, jj = r + 1;
         const bool held = (seg & 1) && jj < S;
         const int n_items = sc.n_rsph + (held ? 8 : 0);
         sphere_centres(sc, ls, tw.F[ci], tw.H[ci], n_items, b, cx, cy, cz, rr, act, isblk);
@@ -543,9 +547,10 @@ __device__ __forceinline__ void chunk_collisions(const Scalars& sc, const LaneSp
         if (!grad) continue;
 
         // backward: dC/dq_k = sum_s z_k . ((c_s - o_k) x g_s) over spheres on links >= k
-        float ja[7], jb[7];
+        // v[k] = arm-group torque of joint k, v[8 + k] = block-group torque (v[7], v[15] unused)
+        float v[16];
 #pragma unroll
-        for (int k = 0; k < 7; ++k) ja[k] = jb[k] = 0.f;
+        for (int k = 0; k < 16; ++k) v[k] = 0.f;
         const bool warp_hit = __any_sync(0xffffffffu, any_hit);
         if (warp_hit) {
             const float4(*F)[3] = tw.F[ci];
@@ -562,19 +567,42 @@ __device__ __forceinline__ void chunk_collisions(const Scalars& sc, const LaneSp
                         const float vx = cx[sl] - ox, vy = cy[sl] - oy, vz = cz[sl] - oz;
                         const float mm = zx * (vy * gz[sl] - vz * gy[sl]) + zy * (vz * gx[sl] - vx * gz[sl]) +
                                          zz * (vx * gy[sl] - vy * gx[sl]);
-                        if (isblk[sl]) jb[k] += mm; else ja[k] += mm;
+                        if (isblk[sl]) v[8 + k] += mm; else v[k] += mm;
                     }
                 }
             }
+            // warp reduce-scatter by recursive halving: at the step of lane bit `off` a lane keeps
+            // the half of its values selected by that bit and adds the partner's copy of it; after
+            // bits 16, 8, 4, 2 lane L holds value 8 b4 + 4 b3 + 2 b2 + b1 summed over 16 lanes, and
+            // the last exchange (bit 1) completes the sum over the warp
 #pragma unroll
-            for (int k = 0; k < 7; ++k) { ja[k] = warp_sum(ja[k]); jb[k] = warp_sum(jb[k]); }
+            for (int i = 0; i < 8; ++i) {
+                const bool up = lane & 16;
+                const float send = up ? v[i] : v[i + 8], keep = up ? v[i + 8] : v[i];
+                v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const bool up = lane & 8;
+                const float send = up ? v[i] : v[i + 4], keep = up ? v[i + 4] : v[i];
+                v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+            }
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                const bool up = lane & 4;
+                const float send = up ? v[i] : v[i + 2], keep = up ? v[i + 2] : v[i];
+                v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+            }
+            {
+                const bool up = lane & 2;
+                const float send = up ? v[0] : v[1], keep = up ? v[1] : v[0];
+                v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+            }
+            v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
         }
-        if (lane < 7) {
-            float va = 0.f, vb = 0.f;
-#pragma unroll
-            for (int k = 0; k < 7; ++k) if (k == lane) { va = ja[k]; vb = jb[k]; }
-            G_arm[t * 8 + lane] = va;
-            G_blk[t * 8 + lane] = vb;
+        {
+            const int j = ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
+            if ((lane & 1) == 0 && (j & 7) != 7) (j < 8 ? G_arm : G_blk)[t * 8 + (j & 7)] = v[0];
         }
     }
 }
