@@ -57,6 +57,8 @@ class _Problem(ctypes.Structure):
         ("w_path", ctypes.c_double), ("w_jl", ctypes.c_double),
         ("mu0", ctypes.c_double), ("mu_max", ctypes.c_double), ("ik_damp", ctypes.c_double),
         ("seed", ctypes.c_uint64), ("max_steps", ctypes.c_int), ("n_threads", ctypes.c_int),
+        ("kind", ctypes.c_int), ("cell_start", _I), ("cell", _D), ("cell_size", ctypes.c_double),
+        ("z_star", ctypes.c_double),
     ]
 
 
@@ -177,6 +179,16 @@ class Oracle:
             setattr(st, name, float(prm[name]))
         st.seed = int(prm["seed"]) & 0xFFFFFFFFFFFFFFFF
         st.n_threads = int(n_threads)
+        pk = getattr(problem, "packing", None)
+        if pk is not None:   # the appendix's packing (Tetris) problem
+            k["cell_start"] = np.ascontiguousarray(np.concatenate([[0], np.cumsum(pk.n_cells)]), np.int32)
+            k["cell"] = _f64(pk.cell).reshape(-1, 2)
+            st.kind = 1
+            st.cell_start = k["cell_start"].ctypes.data_as(_I)
+            st.cell = _dp(k["cell"])
+            st.cell_size, st.z_star = float(pk.cell_size), float(pk.z_star)
+        else:
+            st.kind = 0
         self.st = st
         self.B = st.B
         self.ptr = ctypes.byref(st)

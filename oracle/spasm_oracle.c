@@ -327,6 +327,86 @@ static void block_sphere_world(const double pose[4], const double l[3], double c
     }
 }
 
+/* Penetration of sphere (c, r) into the unit cube of a packing block whose centre is the
+ * block origin plus Rz(yaw) times the cell offset `off`; the gradient with respect to the
+ * block pose goes through that centre (chain rule on pen_block's cube-pose gradient). */
+static double pen_cell(const double c[3], double r, const double pose[4], const double off[2], double u,
+                       double dpen_dc[3], double dpen_dpose[4]) {
+    double cy = cos(pose[3]), sy = sin(pose[3]);
+    double cp[4] = {pose[0] + cy * off[0] - sy * off[1], pose[1] + sy * off[0] + cy * off[1], pose[2], pose[3]};
+    double half[3] = {0.5 * u, 0.5 * u, 0.5 * u};
+    double gp[4];
+    double pen = pen_block(c, r, cp, half, dpen_dc, gp);
+    if (dpen_dpose) {
+        double dcx = -sy * off[0] - cy * off[1], dcy = cy * off[0] - sy * off[1];
+        dpen_dpose[0] = gp[0];
+        dpen_dpose[1] = gp[1];
+        dpen_dpose[2] = gp[2];
+        dpen_dpose[3] = gp[3] + gp[0] * dcx + gp[1] * dcy;
+    }
+    return pen;
+}
+
+/* Packing residuals (appendix, Tetris problem): e[i] = z_i - z*, and the penetration sum
+ * (pen, or pen^2 when `quad`) of every sphere of block j against every unit cube of each
+ * block i < j and against the walls (the environment).  A unit cube of edge u carries 8
+ * spheres of radius u/4 at (+-u/4, +-u/4, +-u/4) from its centre (objects as sphere sets,
+ * Sec. III), so cubes in face contact do not penetrate.  With g != NULL accumulates
+ * g += sum_i b[i] de_i/dx + s_coll dC_coll/dx.  metrics = (largest penetration, 0,
+ * largest |e|). */
+static void pack_residuals(const or_problem *pr, const double *x, int quad, double *e, double *c_coll,
+                           const double *b, double s_coll, double *g, double metrics[3]) {
+    const int B = pr->B;
+    const double u = pr->cell_size, r = 0.25 * u;
+    double cc = 0.0, maxpen = 0.0, maxdz = 0.0;
+    for (int i = 0; i < B; ++i) {
+        e[i] = x[4 * i + 2] - pr->z_star;
+        if (fabs(e[i]) > maxdz) maxdz = fabs(e[i]);
+        if (g) g[4 * i + 2] += b[i];
+    }
+    for (int j = 0; j < B; ++j) {
+        for (int k = pr->cell_start[j]; k < pr->cell_start[j + 1]; ++k) {
+            for (int m = 0; m < 8; ++m) {
+                double l[3] = {pr->cell[2 * k] + ((m & 1) ? 0.25 : -0.25) * u,
+                               pr->cell[2 * k + 1] + ((m & 2) ? 0.25 : -0.25) * u, ((m & 4) ? 0.25 : -0.25) * u};
+                double c[3], dc_dyaw[3];
+                block_sphere_world(x + 4 * j, l, c, dc_dyaw);
+                for (int o = 0; o < pr->n_cub + pr->n_sph; ++o) {
+                    double gc[3], pen;
+                    if (o < pr->n_cub) {
+                        const double *cb = pr->cub + 15 * o;
+                        pen = or_pen_box(c, r, cb, cb + 3, cb + 12, gc, NULL);
+                    } else {
+                        pen = or_pen_sph(c, r, pr->sph + 4 * (o - pr->n_cub), gc);
+                    }
+                    if (pen > maxpen) maxpen = pen;
+                    cc += quad ? pen * pen : pen;
+                    if (g && pen > 0.0) {
+                        double sc = s_coll * (quad ? 2.0 * pen : 1.0);
+                        for (int d = 0; d < 3; ++d) g[4 * j + d] += sc * gc[d];
+                        g[4 * j + 3] += sc * dot3(gc, dc_dyaw);
+                    }
+                }
+                for (int i = 0; i < j; ++i)
+                    for (int kk = pr->cell_start[i]; kk < pr->cell_start[i + 1]; ++kk) {
+                        double gc[3], gp[4];
+                        double pen = pen_cell(c, r, x + 4 * i, pr->cell + 2 * kk, u, gc, gp);
+                        if (pen > maxpen) maxpen = pen;
+                        cc += quad ? pen * pen : pen;
+                        if (g && pen > 0.0) {
+                            double sc = s_coll * (quad ? 2.0 * pen : 1.0);
+                            for (int d = 0; d < 3; ++d) g[4 * j + d] += sc * gc[d];
+                            g[4 * j + 3] += sc * dot3(gc, dc_dyaw);
+                            for (int d = 0; d < 4; ++d) g[4 * i + d] += sc * gp[d];
+                        }
+                    }
+            }
+        }
+    }
+    *c_coll = cc;
+    if (metrics) { metrics[0] = maxpen; metrics[1] = 0.0; metrics[2] = maxdz; }
+}
+
 /* Placement residuals: D[i] = CoM distance for block i (i < B-1; D[B-1] = 0),
  * e[i] = z_i - zt_i, and the collision sum (pen, or pen^2 when `quad`).  With g != NULL
  * accumulates  g += sum_i a[i] dD_i/dx + sum_i b[i] de_i/dx + s_coll dC_coll/dx.
@@ -425,6 +505,21 @@ static void place_residuals(const or_problem *pr, const double *x, int quad, dou
  * (C_stable, C_height, C_coll).  Two passes: residuals, then the gradient. */
 double or_place_cost(const or_problem *pr, const double *x, int quad, double *grad, double terms[3]) {
     const int B = pr->B;
+    if (pr->kind == OR_KIND_PACK) {
+        /* C = w_coll (sum of block-block and block-wall penetrations) + w_height sum |z_i - z*|;
+         * the absolute value keeps its form in both phases (only penetrations turn quadratic) */
+        double e[64], b[64], cc, ch = 0.0;
+        pack_residuals(pr, x, quad, e, &cc, NULL, 0.0, NULL, NULL);
+        for (int i = 0; i < B; ++i) ch += fabs(e[i]);
+        if (grad) {
+            for (int i = 0; i < B; ++i) b[i] = pr->w_height * (e[i] > 0.0 ? 1.0 : (e[i] < 0.0 ? -1.0 : 0.0));
+            memset(grad, 0, sizeof(double) * 4 * B);
+            double e2[64], cc2;
+            pack_residuals(pr, x, quad, e2, &cc2, b, pr->w_coll, grad, NULL);
+        }
+        if (terms) { terms[0] = 0.0; terms[1] = ch; terms[2] = cc; }
+        return pr->w_height * ch + pr->w_coll * cc;
+    }
     double *buf = (double *)malloc(sizeof(double) * 4 * B);
     double *D = buf, *e = buf + B, *a = buf + 2 * B, *b = buf + 3 * B;
     double cc;
@@ -447,7 +542,10 @@ double or_place_cost(const or_problem *pr, const double *x, int quad, double *gr
  * every height error within eps (|f(x)| < eps, Sec. III). */
 int or_place_check(const or_problem *pr, const double *x, double metrics[3]) {
     double D[64], e[64], cc, m[3];
-    place_residuals(pr, x, 0, D, e, &cc, NULL, NULL, 0.0, NULL, m);
+    if (pr->kind == OR_KIND_PACK)
+        pack_residuals(pr, x, 0, e, &cc, NULL, 0.0, NULL, m);
+    else
+        place_residuals(pr, x, 0, D, e, &cc, NULL, NULL, 0.0, NULL, m);
     if (metrics) { metrics[0] = m[0]; metrics[1] = m[1]; metrics[2] = m[2]; }
     return m[0] <= pr->eps && m[1] <= pr->eps && m[2] <= pr->eps;
 }

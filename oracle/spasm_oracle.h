@@ -47,7 +47,17 @@ typedef struct {
     uint64_t seed;
     int max_steps;
     int n_threads;
+    /* goal kind: 0 = tower (the tower stacking costs of the appendix), 1 = packing (the
+     * appendix's Tetris problem).  Packing: block i is a polyomino of unit cubes of edge
+     * cell_size centred at the offsets cell[cell_start[i] .. cell_start[i+1]) (x, y in the
+     * block frame); the walls are the environment cuboids; z_star is the target height. */
+    int kind;
+    const int32_t *cell_start; /* B + 1 */
+    const double *cell;        /* cell_start[B] x 2 */
+    double cell_size, z_star;
 } or_problem;
+
+enum { OR_KIND_TOWER = 0, OR_KIND_PACK = 1 };
 
 /* constraint groups of the stage-2 augmented Lagrangian */
 enum { OR_G_START = 0, OR_G_ARM, OR_G_BLOCK, OR_G_COLL, OR_G_STABLE, OR_G_HEIGHT, OR_NG };
@@ -61,7 +71,7 @@ double or_pen_box(const double c[3], double r, const double centre[3], const dou
                   const double half[3], double dpen_dc[3], double dpen_dp[3]);
 double or_pen_sph(const double c[3], double r, const double *sph, double dpen_dc[3]);
 
-/* stage 1 (Alg. 1 and the tower placement cost of the appendix) */
+/* stage 1 (Alg. 1 and the placement cost of the appendix: tower, or packing when kind = 1) */
 double or_place_cost(const or_problem *pr, const double *x, int quad, double *grad, double terms[3]);
 int    or_place_check(const or_problem *pr, const double *x, double metrics[3]);
 void   or_place_sample(const or_problem *pr, int n, uint32_t attempt, double *x);

@@ -1,4 +1,4 @@
-"""Seeded synthetic workloads for the tower-stacking problem.
+"""Seeded synthetic workloads for the tower-stacking and the packing (Tetris) problems.
 
 This module only *generates inputs*: a 7-revolute-joint arm described by modified
 Denavit-Hartenberg rows and a set of collision spheres, a table, cuboid clutter,
@@ -20,6 +20,13 @@ sphere set are not available, so every instance here is synthetic and seeded:
 * clutter: cuboids with sides U(0.05, 0.3) m and uniform yaw, rejection-sampled to
   stay out of keep-out volumes (robot base, start region, a central tower column and
   a transport corridor), so that a solution is expected to exist.
+
+Packing (the appendix's Tetris problem): blocks are polyominoes of unit cubes that must
+fill a rectangular region on the floor, between four walls, at the resting height z*.
+The generator tiles a gx x gy grid of cells with seeded random tetrominoes, so a packing
+of zero cost exists (the planted one); each block's frame sits at the centroid of its
+cells and is turned by a seeded multiple of 90 degrees.  No benchmark instance is
+reproduced.
 
 All arrays are float64 / int32 numpy arrays in row-major order.
 """
@@ -103,11 +110,22 @@ class Params:
 
 
 @dataclasses.dataclass
+class Packing:
+    n_cells: np.ndarray       # (B,) int32 unit cells of each block
+    cell: np.ndarray          # (sum n_cells, 2) cell-centre offsets (x, y) in the block frame
+    cell_size: float          # edge of the unit cubes
+    region: np.ndarray        # (4,) x_lo, y_lo, x_hi, y_hi (inner faces of the walls)
+    z_star: float             # resting height of the block centres
+    planted: np.ndarray       # (B, 4) a zero-cost packing (the generator's tiling)
+
+
+@dataclasses.dataclass
 class Problem:
     name: str
     robot: Robot
     scene: Scene
     params: Params
+    packing: "Packing | None" = None
 
 
 def _rot_z(yaw: float) -> np.ndarray:
@@ -253,6 +271,107 @@ def make_problem(name: str, seed: int = 0, robot_seed: int = 7, **overrides) -> 
     cfg.setdefault("seed", seed)
     params = Params(**cfg)
     return Problem(name=name, robot=make_robot(robot_seed), scene=make_scene(B, O, seed, n_sph), params=params)
+
+
+# Packing workloads: gx x gy cells of edge 5 cm tiled by tetrominoes (B = gx gy / 4), stage 1
+# only (the paper's 5- and 8-block Tetris problems are stage-1 time-to-first-solution runs).
+PACKINGS: Dict[str, dict] = {
+    "tetris5": dict(gx=5, gy=4, N=4096, M=1024, P=8, K_lin=25, K_quad=5),
+    "tetris8": dict(gx=8, gy=4, N=16384, M=4096, P=8, K_lin=25, K_quad=5),
+}
+PACK_PARAMS = dict(eta_init=0.03, alpha=0.002, w_coll=1.0, w_height=1.0, Q=1, W=3)
+CELL = 0.05
+
+
+def _tile(gx: int, gy: int, size: int, rng) -> np.ndarray:
+    """Random partition of a gx x gy grid into connected pieces of `size` cells: the first
+    free cell in row-major order grows a piece by random frontier picks; a dead end restarts."""
+    for _ in range(100000):
+        lab = -np.ones((gx, gy), dtype=np.int64)
+        pid, ok = 0, True
+        for iy in range(gy):
+            for ix in range(gx):
+                if lab[ix, iy] >= 0:
+                    continue
+                piece = [(ix, iy)]
+                lab[ix, iy] = pid
+                while len(piece) < size:
+                    front = sorted({(a + dx, b + dy) for a, b in piece for dx, dy in ((1, 0), (-1, 0), (0, 1), (0, -1))
+                                    if 0 <= a + dx < gx and 0 <= b + dy < gy and lab[a + dx, b + dy] < 0})
+                    if not front:
+                        ok = False
+                        break
+                    c = front[int(rng.integers(len(front)))]
+                    lab[c] = pid
+                    piece.append(c)
+                if not ok:
+                    break
+                pid += 1
+            if not ok:
+                break
+        if ok:
+            return lab
+    raise RuntimeError("no tiling found")
+
+
+def packing_problem(blocks, gx: int, gy: int, cell_size: float = CELL, z_span: float = 0.0, turns=None,
+                    name: str = "packing", robot_seed: int = 7, **params) -> Problem:
+    """Packing problem from a layout: blocks[b] lists the grid cells (ix, iy) of block b in a
+    gx x gy region.  Block b's frame sits at the centroid of its cells, turned by
+    turns[b] x 90 degrees (default 0), so the layout itself is a zero-cost packing.  The
+    scene's cuboids are the four walls (slabs of thickness and height u just outside the
+    region, u = cell_size); the goal box bounds the block origins (x, y in the region, z in
+    [z*, z* + z_span]); blocks get cube half extents (z_table = 0 is the floor, z* = u/2)."""
+    u = cell_size
+    x_lo, y_lo = 0.45, -0.5 * gy * u
+    x_hi, y_hi = x_lo + gx * u, y_lo + gy * u
+    z_star = 0.5 * u
+    B = len(blocks)
+    turns = [0] * B if turns is None else list(turns)
+    n_cells, cells, planted = [], [], []
+    for b, cl in enumerate(blocks):
+        idx = np.asarray(cl, dtype=np.float64).reshape(-1, 2)
+        centres = np.stack([x_lo + (idx[:, 0] + 0.5) * u, y_lo + (idx[:, 1] + 0.5) * u], axis=1)
+        cen = centres.mean(0)
+        yaw = 0.5 * math.pi * turns[b]
+        Rm = _rot_z(-yaw)[:2, :2]
+        cells.append((centres - cen) @ Rm.T)
+        n_cells.append(len(idx))
+        planted.append([cen[0], cen[1], z_star, (yaw + math.pi) % (2.0 * math.pi) - math.pi])
+    xc, yc = 0.5 * (x_lo + x_hi), 0.5 * (y_lo + y_hi)
+    walls = []
+    for c, h in (((x_lo - 0.5 * u, yc, z_star), (0.5 * u, 0.5 * gy * u + u, 0.5 * u)),
+                 ((x_hi + 0.5 * u, yc, z_star), (0.5 * u, 0.5 * gy * u + u, 0.5 * u)),
+                 ((xc, y_lo - 0.5 * u, z_star), (0.5 * gx * u + u, 0.5 * u, 0.5 * u)),
+                 ((xc, y_hi + 0.5 * u, z_star), (0.5 * gx * u + u, 0.5 * u, 0.5 * u))):
+        walls.append(np.concatenate([np.array(c), np.eye(3).ravel(), np.array(h)]))
+    planted = np.array(planted)
+    scene = Scene(cuboid=np.array(walls), sphere=np.zeros((0, 4)), half=np.full((B, 3), 0.5 * u),
+                  init=planted.copy(), box=np.array([x_lo, y_lo, z_star, x_hi, y_hi, z_star + z_span]),
+                  z_table=0.0, grasp_off=0.0)
+    prm = dict(PACK_PARAMS)
+    prm.update(params)
+    pk = Packing(n_cells=np.array(n_cells, dtype=np.int32), cell=np.concatenate(cells), cell_size=u,
+                 region=np.array([x_lo, y_lo, x_hi, y_hi]), z_star=z_star, planted=planted)
+    return Problem(name=name, robot=make_robot(robot_seed), scene=scene, params=Params(**prm), packing=pk)
+
+
+def make_packing(name: str, seed: int = 0, robot_seed: int = 7, **overrides) -> Problem:
+    """Named packing workload (``tetris5`` / ``tetris8``): a seeded tetromino tiling of the
+    region, each block turned by a seeded multiple of 90 degrees."""
+    cfg = dict(PACKINGS[name])
+    gx, gy = overrides.pop("gx", cfg.pop("gx")), overrides.pop("gy", cfg.pop("gy"))
+    u = overrides.pop("cell_size", CELL)
+    z_span = overrides.pop("zspan", 0.0)
+    rng = np.random.default_rng(np.random.SeedSequence([0x7E7, seed]))
+    lab = _tile(gx, gy, 4, rng)
+    B = int(lab.max()) + 1
+    blocks = [np.argwhere(lab == b) for b in range(B)]
+    turns = [int(rng.integers(4)) for _ in range(B)]
+    cfg.update(overrides)
+    cfg.setdefault("seed", seed)
+    return packing_problem(blocks, gx, gy, cell_size=u, z_span=z_span, turns=turns, name=name,
+                           robot_seed=robot_seed, **cfg)
 
 
 def heterogeneous_batch(n_problems: int, seed: int = 0):
