@@ -36,11 +36,12 @@ WORKLOAD_DESC = ("10-block tower in clutter: 64 random cuboids (sides 0.05-0.3 m
                  "FP32, Philox seeded; seed s = scene + Philox seed")
 # FP32 peak: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x max SM clock
 SM_COUNT, FP32_LANES = 152, 128
-# algorithmic FP32 flop of one sphere-cuboid test (transform to the cuboid frame and the
-# separation test: 3 sub + 9 mul/fma + 3 |p|-h + 2 max + 1 compare, FMA counted as 2)
-FLOP_PER_TEST = 24
-# forward kinematics of one configuration: 7 link transforms (27 fma + sincos each)
-FLOP_PER_CONFIG_FK = 7 * 40
+# algorithmic FP32 work per unit (the per-unit figures of the hot-path analysis): one
+# sphere-cuboid test with its gradient, about 32 instructions = 40 flop (FMA counted as 2)
+FLOP_PER_TEST = 40
+# forward kinematics (about 0.9 kflop) and the backward chain (about 3.3 kflop) of one
+# configuration
+FLOP_PER_CONFIG_FK = 900 + 3300
 # exact box cull of one (configuration, obstacle) pair: 6 comparisons
 FLOP_PER_CULL = 6
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "k_traj_tower10.md")
@@ -286,6 +287,7 @@ def run_native(args, ws, rank, local):
     batched = served = None
     if args.serve_problems > 0:
         batched, served = run_forms(args, rank, overrides, peak)
+    packing = run_packing(args, rank) if args.pack_seeds > 0 else None
 
     out = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
@@ -311,6 +313,7 @@ def run_native(args, ws, rank, local):
                 "path": "spasm_create_problem (host arrays) + spasm_optimize + spasm_result + destroy"},
         "batched": batched,
         "served": served,
+        "packing": packing,
         "gpu_launches": int(sum(s["kernel_launches"] for s in stats)),
         "clocks": clocks,
         "kernel_sources_sha256_16": kernel_hash(),
@@ -441,6 +444,80 @@ def run_forms(args, rank, overrides, peak):
     return forms, served
 
 
+def stage1_first_solution(wl):
+    """(solved, ms, attempts) of one stage-1 solve: CUDA events around spasm_place."""
+    import torch
+
+    from paper_2510_07674_gb300 import spasm as S
+    pr = S.Problem(wl)
+    try:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        try:
+            S.spasm_place(pr)
+        except S.SpasmError as e:
+            if e.status != -4:
+                raise
+        e1.record()
+        torch.cuda.synchronize()
+        st = S.spasm_get_stats(pr)
+        n = S.spasm_placements(pr, allow_empty=True)["n_place"]
+        return n > 0, e0.elapsed_time(e1), st["place_attempts"]
+    finally:
+        pr.close()
+
+
+def _summary(times, ok, att):
+    import numpy as np
+    t = np.array(times)
+    ci = 1.96 * t.std(ddof=1) / math.sqrt(len(t)) if len(t) > 1 else 0.0
+    return {"seeds": len(t), "success": ok / len(t), "ms_mean": float(t.mean()), "ms_ci95": float(ci),
+            "ms_p50": float(np.median(t)), "attempts_mean": float(np.mean(att))}
+
+
+def run_packing(args, rank):
+    """Stage 1 (Alg. 1) on the packing workloads (the appendix's Tetris problem): time to
+    first solution per seed, capped at 30 000 gradient steps as in the paper's runs."""
+    from paper_2510_07674_gb300 import scenes
+    out = {}
+    for name, n in (("tetris5", args.pack_seeds), ("tetris8", max(1, args.pack_seeds // 4))):
+        times, ok, att = [], 0, []
+        for i in range(n):
+            solved, ms, a = stage1_first_solution(scenes.make_packing(name, seed=rank * 1000 + i, max_steps=30000))
+            ok += solved
+            times.append(ms)
+            att.append(a)
+        out[name] = _summary(times, ok, att)
+    out["workload"] = ("seeded tetromino tilings of a 5x4 (5 blocks) and 8x4 (8 blocks) cell region, cell units, "
+                       "stage 1 only; see scenes.PACKINGS for N, M, steps")
+    return out
+
+
+def run_sweep(args):
+    """Hyper-parameter sweep (Sec. IV, Fig. 5 analogue): time to first solution of stage 1
+    over a grid of sampling batch N and optimisation batch M, per workload."""
+    from paper_2510_07674_gb300 import scenes
+    rows = []
+    for name in args.sweep_workloads:
+        for N in [2 ** k for k in range(9, 16)]:
+            for M in [2 ** k for k in range(8, 14)]:
+                if M > N:
+                    continue
+                times, ok, att = [], 0, []
+                for t in range(args.sweep_trials):
+                    kw = dict(seed=t, N=N, M=M, P=min(8, M), max_steps=30000)
+                    wl = scenes.make_packing(name, **kw) if name in scenes.PACKINGS else scenes.make_problem(name, **kw)
+                    solved, ms, a = stage1_first_solution(wl)
+                    ok += solved
+                    times.append(ms)
+                    att.append(a)
+                rows.append(dict(workload=name, N=N, M=M, **_summary(times, ok, att)))
+                print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+    print(json.dumps({"sweep": rows, "trials": args.sweep_trials,
+                      "metric": "stage-1 time to first solution (ms), mean over seeds"}))
+
+
 # ------------------------------------------------------------------------------- oracle
 def cpu_baseline(wl, budget_s: float) -> dict:
     """The FP64 oracle, as it stands, on a bounded sample of the same workload: a stage-1
@@ -522,11 +599,19 @@ def main():
     ap.add_argument("--serve-problems", type=int, default=64,
                     help="heterogeneous problems for the batched / served measurements (0 = skip)")
     ap.add_argument("--serve-slots", type=int, default=8)
+    ap.add_argument("--pack-seeds", type=int, default=12, help="seeds of the 5-block packing leg (0 = skip)")
+    ap.add_argument("--sweep", action="store_true", help="run the N x M stage-1 sweep instead of the benchmark")
+    ap.add_argument("--sweep-workloads", nargs="*", default=["tetris5", "tetris8", "tower10"])
+    ap.add_argument("--sweep-trials", type=int, default=5)
     ap.add_argument("--serve-rates", type=float, nargs="*", default=[10.0, 30.0, 100.0, 300.0, 1000.0, 2000.0])
     ap.add_argument("--override", action="append", default=[], metavar="PARAM=VALUE",
                     help="change a solver parameter (profiling of a reduced case only; recorded in config)")
     args = ap.parse_args()
     ws, rank, local = dist_env()
+    if args.sweep:
+        if rank == 0:
+            run_sweep(args)
+        return
     if args.impl == "reference":
         if rank != 0:
             return

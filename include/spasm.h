@@ -88,6 +88,26 @@ typedef struct {
     double grasp_off;
 } spasm_goal;
 
+/* Packing goal (the appendix's Tetris problem): block i is a polyomino of n_cells[i] unit
+ * cubes of edge cell_size, centred at the offsets cell[2k], cell[2k+1] (k over the block's
+ * cells, in block order) in its frame, the frame origin being the point the block pose
+ * (x, y, z, yaw) places.  The blocks are packed into region = (x_lo, y_lo, x_hi, y_hi)
+ * between four walls (slabs of thickness and height cell_size just outside the region,
+ * centred at height z_star) at the resting height z_star; block origins are clamped to the
+ * region in x, y and to [z_star, z_star + z_span] in z (0: one tight layer).  Cost of a
+ * placement: w_coll (sum over block pairs i < j of the penetration of block j's spheres
+ * into block i's cubes + sum over blocks and walls) + w_height sum |z_i - z_star|, each cube
+ * carrying 8 spheres of radius cell_size/4 at (+-cell_size/4, +-cell_size/4, +-cell_size/4). */
+typedef struct {
+    int n_blocks;                /* 1..16 */
+    const int32_t* n_cells;      /* B: 1..8 each, at most 64 in total */
+    const double* cell;          /* sum(n_cells) x 2 */
+    double cell_size;
+    const double* region;        /* 4 */
+    double z_star;
+    double z_span;               /* >= 0 */
+} spasm_packing;
+
 /* Solver parameters (Alg. 1 and Sec. III-B): N sample / M optimised particles, P
  * returned solutions, Q trajectory particles, W waypoints per motion segment, step
  * counts, learning rates, weights of the appendix cost terms, augmented-Lagrangian
@@ -108,6 +128,15 @@ typedef struct {
  * C <= 1024, N <= 32768, M <= 8192, P <= M, Q >= 1.  Synchronises once. */
 spasm_status spasm_create_problem(const spasm_robot* robot, const spasm_obstacles* obstacles, const spasm_goal* goal,
                                   const spasm_params* params, void* cuda_stream, spasm_problem_t* out);
+/* A packing problem (the appendix's Tetris problem) for stage 1 (spasm_place, the
+ * kernel-level stage-1 entry points); the robot is validated and kept as for
+ * spasm_create_problem, and spasm_optimize reports SPASM_ERR_INVALID (stage 2 is built for
+ * the tower goal).  Limits as spasm_create_problem plus those of spasm_packing. */
+spasm_status spasm_create_packing(const spasm_robot* robot, const spasm_packing* packing, const spasm_params* params,
+                                  void* cuda_stream, spasm_problem_t* out);
+/* Stage-1 result: *n_place satisfying placements found (0 before spasm_place), placements
+ * P x B x 4 (x, y, z, yaw), best first.  SPASM_ERR_NOSOLUTION when none.  Synchronises. */
+spasm_status spasm_placements(spasm_problem_t problem, int* n_place, double* placements);
 spasm_status spasm_destroy_problem(spasm_problem_t problem);
 const char* spasm_last_error(void);
 

@@ -287,6 +287,85 @@ extern "C" spasm_status spasm_create_problem(const spasm_robot* robot, const spa
     return SPASM_OK;
 }
 
+extern "C" spasm_status spasm_create_packing(const spasm_robot* robot, const spasm_packing* pk,
+                                             const spasm_params* prm, void* cuda_stream, spasm_problem_t* out) {
+    if (!pk || !out) return fail(SPASM_ERR_INVALID, "null argument");
+    *out = nullptr;
+    const int B = pk->n_blocks;
+    if (B < 1 || B > kMaxB || !pk->n_cells || !pk->cell || !pk->region)
+        return fail(SPASM_ERR_INVALID, "packing: n_blocks outside 1..16 or a null table");
+    int total = 0;
+    for (int i = 0; i < B; ++i) {
+        if (pk->n_cells[i] < 1 || pk->n_cells[i] > 8) return fail(SPASM_ERR_INVALID, "packing: 1..8 cells per block");
+        total += pk->n_cells[i];
+    }
+    if (total > kMaxCells) return fail(SPASM_ERR_INVALID, "packing: more than 64 cells");
+    const double u = pk->cell_size, zs = pk->z_star;
+    const double* rg = pk->region;
+    if (!(u > 0.0) || !(pk->z_span >= 0.0) || !(rg[2] > rg[0]) || !(rg[3] > rg[1]))
+        return fail(SPASM_ERR_INVALID, "packing: bad cell size, height range or region");
+    // the walls: slabs of thickness u and height u just outside the region
+    const double xc = 0.5 * (rg[0] + rg[2]), yc = 0.5 * (rg[1] + rg[3]);
+    const double hx = 0.5 * (rg[2] - rg[0]) + u, hy = 0.5 * (rg[3] - rg[1]) + u;
+    const double wc[4][3] = {{rg[0] - 0.5 * u, yc, zs}, {rg[2] + 0.5 * u, yc, zs}, {xc, rg[1] - 0.5 * u, zs},
+                             {xc, rg[3] + 0.5 * u, zs}};
+    const double wh[4][3] = {{0.5 * u, hy, 0.5 * u}, {0.5 * u, hy, 0.5 * u}, {hx, 0.5 * u, 0.5 * u}, {hx, 0.5 * u, 0.5 * u}};
+    std::vector<double> walls(4 * 15, 0.0);
+    for (int w = 0; w < 4; ++w) {
+        double* r = walls.data() + 15 * w;
+        for (int k = 0; k < 3; ++k) { r[k] = wc[w][k]; r[12 + k] = wh[w][k]; }
+        r[3] = r[7] = r[11] = 1.0;
+    }
+    std::vector<double> half(3 * B, 0.5 * u), init(4 * B, 0.0);
+    const double box[6] = {rg[0], rg[1], zs, rg[2], rg[3], zs + pk->z_span};
+    spasm_obstacles obs{4, walls.data(), 0, nullptr};
+    spasm_goal goal{B, half.data(), init.data(), box, zs - 0.5 * u, 0.0};
+    spasm_problem_t pr = nullptr;
+    SPASM_TRY(spasm_create_problem(robot, &obs, &goal, prm, cuda_stream, &pr));
+    Scalars& sc = pr->sc;
+    sc.kind = kKindPack;
+    sc.n_cells = total;
+    sc.cell_size = (float)u;
+    sc.z_star = (float)zs;
+    int k = 0;
+    for (int i = 0; i < B; ++i) {
+        sc.cell_start[i] = k;
+        double reach = 0.0;
+        for (int c = 0; c < pk->n_cells[i]; ++c, ++k) {
+            const double ox = pk->cell[2 * k], oy = pk->cell[2 * k + 1];
+            sc.cell[k] = make_float2((float)ox, (float)oy);
+            sc.cell_block[k] = (signed char)i;
+            reach = std::fmax(reach, std::sqrt(ox * ox + oy * oy));
+        }
+        // farthest point of the block's cubes from its origin (padded against rounding)
+        sc.cell_reach[i] = (float)(reach + 0.5 * std::sqrt(3.0) * u + 1e-5);
+    }
+    sc.cell_start[B] = k;
+    cudaError_t e = cudaMemcpyAsync(pr->d_sc, &pr->sc, sizeof(Scalars), cudaMemcpyHostToDevice, pr->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(pr->stream);
+    if (e != cudaSuccess) {
+        spasm_destroy_problem(pr);
+        return fail(SPASM_ERR_CUDA, std::string("create_packing: ") + cudaGetErrorString(e));
+    }
+    *out = pr;
+    return SPASM_OK;
+}
+
+extern "C" spasm_status spasm_placements(spasm_problem_t pr, int* n_place, double* placements) {
+    if (!pr) return fail(SPASM_ERR_INVALID, "null problem");
+    SPASM_CUDA(cudaStreamSynchronize(pr->stream));
+    if (n_place) *n_place = pr->placed ? pr->n_place : 0;
+    if (placements) {
+        std::vector<float> tmp((size_t)pr->sc.P * pr->sc.B * 4, 0.f);
+        SPASM_CUDA(cudaMemcpyAsync(tmp.data(), pr->d_place, tmp.size() * sizeof(float), cudaMemcpyDeviceToHost, pr->stream));
+        SPASM_CUDA(cudaStreamSynchronize(pr->stream));
+        pr->stats.d2h_bytes += tmp.size() * sizeof(float);
+        for (size_t i = 0; i < tmp.size(); ++i) placements[i] = tmp[i];
+    }
+    if (!pr->placed || pr->n_place == 0) return fail(SPASM_ERR_NOSOLUTION, "no placements");
+    return SPASM_OK;
+}
+
 extern "C" spasm_status spasm_destroy_problem(spasm_problem_t pr) {
     if (!pr) return SPASM_OK;
     cudaStreamSynchronize(pr->stream);
@@ -469,6 +548,8 @@ spasm_status spasm::finish_record(spasm_problem* pr, int found, bool finish_done
 
 extern "C" spasm_status spasm_optimize(spasm_problem_t pr) {
     if (!pr) return fail(SPASM_ERR_INVALID, "null problem");
+    if (pr->sc.kind == kKindPack)
+        return fail(SPASM_ERR_INVALID, "stage 2 is implemented for the tower goal only; packing runs stage 1 (spasm_place)");
     if (!pr->placed) {
         spasm_status st = spasm_place(pr);
         if (st != SPASM_OK) return st;

@@ -21,6 +21,8 @@ constexpr int kMaxCub = 256;       // environment cuboids (incl. table)
 constexpr int kMaxOSph = 64;       // environment spheres
 constexpr int kMaxC = 1024;        // configurations per trajectory particle
 constexpr int kMaxNR = 9 * kMaxB + 3;
+constexpr int kMaxCells = 64;      // unit cells over all blocks of a packing problem
+enum GoalKind { kKindTower = 0, kKindPack = 1 };
 constexpr float kPi = 3.14159265358979323846f;
 
 // Scalars, robot tables and block tables: passed by value as a __grid_constant__ kernel
@@ -51,6 +53,16 @@ struct Scalars {
     float w_stable, w_height, w_coll, w_start, w_arm, w_block, w_path, w_jl;
     float mu0, mu_max, ik_damp;
     unsigned long long seed;
+    // packing goal (the appendix's Tetris problem), kind = kKindPack: block i is a polyomino
+    // of unit cubes of edge cell_size centred at cell[cell_start[i] .. cell_start[i+1]) in
+    // its frame; the walls are the environment cuboids; z_star is the resting height
+    int kind;
+    int n_cells;
+    int cell_start[kMaxB + 1];
+    signed char cell_block[kMaxCells];   // block of each cell
+    float2 cell[kMaxCells];
+    float cell_size, z_star;
+    float cell_reach[kMaxB];             // largest distance from a block's origin to a point of its cubes
 };
 
 // ------------------------------------------------------------------------------ launches

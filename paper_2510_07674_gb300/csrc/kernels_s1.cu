@@ -3,6 +3,7 @@
 #include "launch.h"
 #include "select.cuh"
 #include "stage1.cuh"
+#include "stage1_pack.cuh"
 
 namespace spasm {
 
@@ -13,6 +14,7 @@ struct S1Warp {
     float x[4 * kMaxB];
     float g[4 * kMaxB];
     PlaceScratch ps;
+    float4 gcell[kMaxCells];   // per-cube sphere-side gradients of the packing goal
 };
 
 // dynamic shared memory: mbarrier | env cuboids | env spheres | per-warp scratch
@@ -61,8 +63,8 @@ __global__ void __launch_bounds__(kS1Threads) k_place_sample_cost(const __grid_c
     }
     __syncwarp();
     PlaceOut o;
-    place_eval_warp(sc, s.cub, sc.n_cub, s.osph, sc.n_osph, W.x, false, kPlaceForward, nullptr, nullptr, 0.f, nullptr,
-                    W.ps, o);
+    place_eval(sc, s.cub, sc.n_cub, s.osph, sc.n_osph, W.x, false, kPlaceForward, nullptr, W.ps,
+               W.gcell, o);
     for (int v = lane; v < 4 * sc.B; v += 32) x_out[(size_t)v * n + p] = W.x[v];
     if (lane == 0) cost_out[p] = place_cost_value(sc, o);
 }
@@ -81,8 +83,8 @@ __global__ void __launch_bounds__(kS1Threads) k_place_eval(const __grid_constant
     for (int v = lane; v < 4 * sc.B; v += 32) W.x[v] = x[(size_t)v * n + p];
     __syncwarp();
     PlaceOut o;
-    place_eval_warp(sc, s.cub, sc.n_cub, s.osph, sc.n_osph, W.x, quad != 0, grad ? kPlaceStage1 : kPlaceForward,
-                    nullptr, nullptr, 0.f, W.g, W.ps, o);
+    place_eval(sc, s.cub, sc.n_cub, s.osph, sc.n_osph, W.x, quad != 0, grad ? kPlaceStage1 : kPlaceForward, W.g, W.ps,
+               W.gcell, o);
     if (grad)
         for (int v = lane; v < 4 * sc.B; v += 32) grad[(size_t)v * n + p] = W.g[v];
     if (lane == 0) {
@@ -114,19 +116,19 @@ __global__ void __launch_bounds__(kS1Threads) k_place_descend(const __grid_const
     PlaceOut o;
     for (int k = 1; k <= k_lin; ++k) {
         const float eta = sc.eta_init * (1.f - (float)k / (float)k_lin);
-        place_eval_warp(sc, s.cub, sc.n_cub, s.osph, sc.n_osph, W.x, false, kPlaceStage1, nullptr, nullptr, 0.f, W.g,
-                        W.ps, o);
+        place_eval(sc, s.cub, sc.n_cub, s.osph, sc.n_osph, W.x, false, kPlaceStage1, W.g, W.ps,
+               W.gcell, o);
         for (int v = lane; v < nv; v += 32) W.x[v] = place_clamp(sc, v, W.x[v] - eta * W.g[v]);
         __syncwarp();
     }
     for (int k = 1; k <= k_quad; ++k) {
-        place_eval_warp(sc, s.cub, sc.n_cub, s.osph, sc.n_osph, W.x, true, kPlaceStage1, nullptr, nullptr, 0.f, W.g,
-                        W.ps, o);
+        place_eval(sc, s.cub, sc.n_cub, s.osph, sc.n_osph, W.x, true, kPlaceStage1, W.g, W.ps,
+               W.gcell, o);
         for (int v = lane; v < nv; v += 32) W.x[v] = place_clamp(sc, v, W.x[v] - sc.alpha * W.g[v]);
         __syncwarp();
     }
-    place_eval_warp(sc, s.cub, sc.n_cub, s.osph, sc.n_osph, W.x, true, kPlaceForward, nullptr, nullptr, 0.f, nullptr,
-                    W.ps, o);
+    place_eval(sc, s.cub, sc.n_cub, s.osph, sc.n_osph, W.x, true, kPlaceForward, nullptr, W.ps,
+               W.gcell, o);
     for (int v = lane; v < nv; v += 32) x_dst[(size_t)v * m + p] = W.x[v];
     if (lane == 0) {
         if (cost) cost[p] = place_cost_value(sc, o);

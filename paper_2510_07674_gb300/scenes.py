@@ -276,11 +276,15 @@ def make_problem(name: str, seed: int = 0, robot_seed: int = 7, **overrides) -> 
 # Packing workloads: gx x gy cells of edge 5 cm tiled by tetrominoes (B = gx gy / 4), stage 1
 # only (the paper's 5- and 8-block Tetris problems are stage-1 time-to-first-solution runs).
 PACKINGS: Dict[str, dict] = {
-    "tetris5": dict(gx=5, gy=4, N=4096, M=1024, P=8, K_lin=25, K_quad=5),
-    "tetris8": dict(gx=8, gy=4, N=16384, M=4096, P=8, K_lin=25, K_quad=5),
+    # step sizes and batch sizes from a sweep on the GPU (time to first solution, 5 seeds)
+    "tetris5": dict(gx=5, gy=4, N=16384, M=4096, P=8, K_lin=25, K_quad=5, eta_init=0.05, alpha=0.02),
+    "tetris8": dict(gx=8, gy=4, N=32768, M=8192, P=8, K_lin=50, K_quad=10, eta_init=0.03, alpha=0.02),
 }
-PACK_PARAMS = dict(eta_init=0.03, alpha=0.002, w_coll=1.0, w_height=1.0, Q=1, W=3)
-CELL = 0.05
+# Packings are posed in cell units (cube edge 1): plain gradient descent is not unit
+# invariant (the yaw gradient carries a lever arm), and in metres the yaw of a 4-cell block
+# moves an order of magnitude slower than its position.  eps = 0.02 cell is 1 mm at 5 cm cells.
+PACK_PARAMS = dict(eta_init=0.1, alpha=0.05, w_coll=1.0, w_height=1.0, eps=0.02, Q=1, W=3)
+CELL = 1.0
 
 
 def _tile(gx: int, gy: int, size: int, rng) -> np.ndarray:
@@ -315,7 +319,7 @@ def _tile(gx: int, gy: int, size: int, rng) -> np.ndarray:
 
 
 def packing_problem(blocks, gx: int, gy: int, cell_size: float = CELL, z_span: float = 0.0, turns=None,
-                    name: str = "packing", robot_seed: int = 7, **params) -> Problem:
+                    name: str = "packing", robot_seed: int = 7, slack: float = 0.0, **params) -> Problem:
     """Packing problem from a layout: blocks[b] lists the grid cells (ix, iy) of block b in a
     gx x gy region.  Block b's frame sits at the centroid of its cells, turned by
     turns[b] x 90 degrees (default 0), so the layout itself is a zero-cost packing.  The
@@ -323,9 +327,11 @@ def packing_problem(blocks, gx: int, gy: int, cell_size: float = CELL, z_span: f
     region, u = cell_size); the goal box bounds the block origins (x, y in the region, z in
     [z*, z* + z_span]); blocks get cube half extents (z_table = 0 is the floor, z* = u/2)."""
     u = cell_size
-    x_lo, y_lo = 0.45, -0.5 * gy * u
+    x_lo, y_lo = 0.0, -0.5 * gy * u
     x_hi, y_hi = x_lo + gx * u, y_lo + gy * u
     z_star = 0.5 * u
+    # clearance between the tiling and the walls: the region grows by `slack` on every side
+    x_lo, y_lo, x_hi, y_hi = x_lo - slack, y_lo - slack, x_hi + slack, y_hi + slack
     B = len(blocks)
     turns = [0] * B if turns is None else list(turns)
     n_cells, cells, planted = [], [], []
@@ -339,11 +345,13 @@ def packing_problem(blocks, gx: int, gy: int, cell_size: float = CELL, z_span: f
         n_cells.append(len(idx))
         planted.append([cen[0], cen[1], z_star, (yaw + math.pi) % (2.0 * math.pi) - math.pi])
     xc, yc = 0.5 * (x_lo + x_hi), 0.5 * (y_lo + y_hi)
+    hx, hy = 0.5 * (x_hi - x_lo) + u, 0.5 * (y_hi - y_lo) + u
     walls = []
-    for c, h in (((x_lo - 0.5 * u, yc, z_star), (0.5 * u, 0.5 * gy * u + u, 0.5 * u)),
-                 ((x_hi + 0.5 * u, yc, z_star), (0.5 * u, 0.5 * gy * u + u, 0.5 * u)),
-                 ((xc, y_lo - 0.5 * u, z_star), (0.5 * gx * u + u, 0.5 * u, 0.5 * u)),
-                 ((xc, y_hi + 0.5 * u, z_star), (0.5 * gx * u + u, 0.5 * u, 0.5 * u))):
+    hz = 0.5 * u
+    for c, h in (((x_lo - 0.5 * u, yc, z_star), (0.5 * u, hy, hz)),
+                 ((x_hi + 0.5 * u, yc, z_star), (0.5 * u, hy, hz)),
+                 ((xc, y_lo - 0.5 * u, z_star), (hx, 0.5 * u, hz)),
+                 ((xc, y_hi + 0.5 * u, z_star), (hx, 0.5 * u, hz))):
         walls.append(np.concatenate([np.array(c), np.eye(3).ravel(), np.array(h)]))
     planted = np.array(planted)
     scene = Scene(cuboid=np.array(walls), sphere=np.zeros((0, 4)), half=np.full((B, 3), 0.5 * u),

@@ -27,7 +27,7 @@ EXPORTED = ["spasm_create_problem", "spasm_destroy_problem", "spasm_last_error",
             "spasm_set_timing", "spasm_get_stats", "spasm_reset_stats", "spasm_place_select_static",
             "spasm_server_create", "spasm_server_submit", "spasm_server_poll", "spasm_server_wait",
             "spasm_server_result", "spasm_server_release", "spasm_server_destroy", "spasm_batch_default_config",
-            "spasm_optimize_batch", "spasm_batch_autotune"]
+            "spasm_optimize_batch", "spasm_batch_autotune", "spasm_create_packing", "spasm_placements"]
 
 
 class SpasmError(RuntimeError):
@@ -53,6 +53,12 @@ class _Obstacles(ctypes.Structure):
 class _Goal(ctypes.Structure):
     _fields_ = [("n_blocks", ctypes.c_int), ("half_ext", _D), ("init_pose", _D), ("goal_box", _D),
                 ("z_table", ctypes.c_double), ("grasp_off", ctypes.c_double)]
+
+
+class _Packing(ctypes.Structure):
+    _fields_ = [("n_blocks", ctypes.c_int), ("n_cells", ctypes.POINTER(ctypes.c_int32)), ("cell", _D),
+                ("cell_size", ctypes.c_double), ("region", _D), ("z_star", ctypes.c_double),
+                ("z_span", ctypes.c_double)]
 
 
 _INT_PARAMS = ("N", "M", "P", "Q", "W", "K_lin", "K_quad", "K_traj", "K_al", "K_ik")
@@ -117,6 +123,9 @@ def lib():
         L.spasm_server_release.argtypes = [_V, LL]
         L.spasm_server_destroy.argtypes = [_V]
         L.spasm_batch_default_config.argtypes = [ctypes.POINTER(_BatchConfig)]
+        L.spasm_create_packing.argtypes = [ctypes.POINTER(_Robot), ctypes.POINTER(_Packing), ctypes.POINTER(_Params), _V,
+                                           ctypes.POINTER(_V)]
+        L.spasm_placements.argtypes = [_V, _I, _D]
         L.spasm_optimize_batch.argtypes = [ctypes.POINTER(_V), ctypes.c_int, _V, ctypes.POINTER(_BatchConfig)]
         L.spasm_batch_autotune.argtypes = [ctypes.POINTER(_V), ctypes.c_int, _V, ctypes.POINTER(_BatchConfig), _D]
         for name in EXPORTED:
@@ -175,6 +184,15 @@ class ProblemDesc:
         self._params = p
         self.B = len(a["half"])
         self.C = 2 * self.B * (int(prm["W"]) - 1) + 1
+        self._packing = None
+        pk = getattr(workload, "packing", None)
+        if pk is not None:   # the appendix's packing (Tetris) goal
+            a["n_cells"] = np.ascontiguousarray(pk.n_cells, np.int32)
+            a["cell"] = _f64(pk.cell).reshape(-1, 2)
+            a["region"] = _f64(pk.region)
+            z_span = float(s.box[5] - s.box[2])
+            self._packing = _Packing(len(a["n_cells"]), a["n_cells"].ctypes.data_as(_I), dp(a["cell"]),
+                                     float(pk.cell_size), dp(a["region"]), float(pk.z_star), z_span)
 
     def refs(self):
         return (ctypes.byref(self._robot), ctypes.byref(self._obs), ctypes.byref(self._goal),
@@ -191,7 +209,11 @@ class Problem(ProblemDesc):
             stream = torch.cuda.current_stream().cuda_stream
         self.stream = int(stream)
         h = _V()
-        _check(lib().spasm_create_problem(*self.refs(), _V(self.stream), ctypes.byref(h)))
+        if self._packing is not None:
+            _check(lib().spasm_create_packing(ctypes.byref(self._robot), ctypes.byref(self._packing),
+                                              ctypes.byref(self._params), _V(self.stream), ctypes.byref(h)))
+        else:
+            _check(lib().spasm_create_problem(*self.refs(), _V(self.stream), ctypes.byref(h)))
         self.handle = h
         C, NR = ctypes.c_int32(), ctypes.c_int32()
         _check(lib().spasm_sizes(h, ctypes.byref(C), ctypes.byref(NR)))
@@ -216,6 +238,17 @@ def spasm_place(problem: Problem):
 
 def spasm_optimize(problem: Problem):
     _check(lib().spasm_optimize(problem.handle))
+
+
+def spasm_placements(problem: Problem, allow_empty: bool = False) -> dict:
+    """Stage-1 result: the satisfying placements found (best first)."""
+    P, B = int(problem.params["P"]), problem.B
+    n = ctypes.c_int32()
+    place = np.zeros((P, B, 4))
+    st = lib().spasm_placements(problem.handle, ctypes.byref(n), place.ctypes.data_as(_D))
+    if st != SPASM_OK and not (allow_empty and st == -4):
+        _check(st)
+    return {"n_place": n.value, "placements": place[: n.value]}
 
 
 def spasm_result(problem: Problem, allow_empty: bool = False) -> dict:

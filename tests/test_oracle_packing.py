@@ -101,15 +101,15 @@ def test_turned_cube_in_a_tight_cell_against_half_spaces(theta):
 
 
 def test_height_term_is_absolute_and_weighted():
-    pb = one_cell(z_span=0.02, w_height=7.0)
+    pb = one_cell(z_span=0.1, w_height=7.0)
     o = Oracle(pb)
     x = pb.packing.planted.copy()
-    x[0, 2] += 0.013
+    x[0, 2] += 0.043
     c, g, t = o.place_cost(x)
-    assert abs(t[1] - 0.013) < 1e-15 and abs(c - 7.0 * 0.013) < 1e-12
+    assert abs(t[1] - 0.043) < 1e-15 and abs(c - 7.0 * 0.043) < 1e-12
     assert g[0, 2] == pytest.approx(7.0)
     ok, m = o.place_check(x)
-    assert not ok and abs(m[2] - 0.013) < 1e-15
+    assert not ok and abs(m[2] - 0.043) < 1e-15   # above eps
 
 
 @pytest.mark.parametrize("quad", [False, True])
