@@ -187,6 +187,8 @@ class Oracle:
             st.cell_start = k["cell_start"].ctypes.data_as(_I)
             st.cell = _dp(k["cell"])
             st.cell_size, st.z_star = float(pk.cell_size), float(pk.z_star)
+        elif getattr(problem, "p2p", False):   # point-to-point trajectory optimisation
+            st.kind = 2
         else:
             st.kind = 0
         self.st = st

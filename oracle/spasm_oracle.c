@@ -692,7 +692,9 @@ int or_place_solve(const or_problem *pr, double *out, int *n_found, int *attempt
 /*    sqrt of the group weight: L = w_path path + w_jl jl                               */
 /*                                 + sum_r lambda_r hw_r + mu/2 hw_r^2, hw = sqrt(w) h. */
 /* ------------------------------------------------------------------------------------ */
-int or_n_configs(const or_problem *pr) { return 2 * pr->B * (pr->W - 1) + 1; }
+int or_n_configs(const or_problem *pr) {
+    return pr->kind == OR_KIND_P2P ? pr->W : 2 * pr->B * (pr->W - 1) + 1;
+}
 
 static int t_grasp(const or_problem *pr, int b) { return (2 * b + 1) * (pr->W - 1); }
 static int t_place(const or_problem *pr, int b) { return (2 * b + 2) * (pr->W - 1); }
@@ -847,10 +849,11 @@ static void config_collisions(const or_problem *pr, const double *q, int t, doub
 static void traj_evaluate(const or_problem *pr, const double *q, traj_eval *ev, double *h,
                           const double *s, double *grad) {
     const int B = pr->B, C = or_n_configs(pr);
-    double (*P4)[4] = (double (*)[4])malloc(sizeof(double) * 4 * B);
+    const int p2p = pr->kind == OR_KIND_P2P;
+    double (*P4)[4] = (double (*)[4])calloc((size_t)4 * B, sizeof(double));
     double (*g4)[4] = (double (*)[4])calloc((size_t)4 * B, sizeof(double));
     memset(ev, 0, sizeof *ev);
-    for (int b = 0; b < B; ++b) {
+    for (int b = 0; b < B && !p2p; ++b) {
         double fr[8][16], tee[16];
         or_fk(pr, q + 7 * t_place(pr, b), fr, tee);
         pose4_of(pr, b, tee, P4[b]);
@@ -865,8 +868,8 @@ static void traj_evaluate(const or_problem *pr, const double *q, traj_eval *ev, 
     h[9 * B + 1] = ev->c[OR_G_ARM];
     h[9 * B + 2] = ev->c[OR_G_BLOCK];
 
-    /* C_placement residuals on the placed poses */
-    {
+    /* C_placement residuals on the placed poses (none point to point) */
+    if (!p2p) {
         double cc;
         place_residuals(pr, &P4[0][0], 0, h + 8 * B, h + 7 * B, &cc,
                         grad ? s + 8 * B : NULL, grad ? s + 7 * B : NULL, grad ? s[9 * B] : 0.0,
@@ -880,7 +883,7 @@ static void traj_evaluate(const or_problem *pr, const double *q, traj_eval *ev, 
     }
 
     /* placed-pose derivatives -> place configurations */
-    if (grad) {
+    if (grad && !p2p) {
         for (int b = 0; b < B; ++b) {
             int t = t_place(pr, b);
             double fr[8][16], tee[16], J[4][7];
@@ -893,7 +896,7 @@ static void traj_evaluate(const or_problem *pr, const double *q, traj_eval *ev, 
 
     /* C_start residuals: grasp alignment (position, roll, pitch) and upright placement */
     for (int b = 0; b < B; ++b) {
-        for (int which = 0; which < 2; ++which) {
+        for (int which = 0; which < (p2p ? 1 : 2); ++which) {
             int t = which == 0 ? t_grasp(pr, b) : t_place(pr, b);
             double fr[8][16], tee[16], R[9], p[3], roll, pitch, dr[7], dp[7];
             or_fk(pr, q + 7 * t, fr, tee);
@@ -1095,7 +1098,7 @@ static void perturbed_home(const or_problem *pr, uint32_t c0, int particle, uint
  * one intermediate waypoint per segment (q_home perturbed, standing in for a retract
  * configuration), then linear interpolation start -> via -> goal over the segment. */
 void or_lift(const or_problem *pr, const double *place, int particle, uint32_t attempt, double *q) {
-    const int B = pr->B, S = pr->W - 1;
+    const int B = pr->B, S = pr->W - 1, p2p = pr->kind == OR_KIND_P2P;
     memcpy(q, pr->q_home, 7 * sizeof(double));
     for (int b = 0; b < B; ++b) {
         uint32_t k[4];
@@ -1104,12 +1107,13 @@ void or_lift(const or_problem *pr, const double *place, int particle, uint32_t a
         grasp_target(pr, b, pr->init + 4 * b, (int)(k[0] & 3u), T);
         perturbed_home(pr, (uint32_t)(2 * b), particle, TAG_IKSEED, attempt, 0.3, seed);
         or_ik(pr, T, seed, q + 7 * t_grasp(pr, b));
+        if (p2p) continue;   /* one segment: no placement */
         grasp_target(pr, b, place + 4 * b, (int)(k[1] & 3u), T);
         perturbed_home(pr, (uint32_t)(2 * b + 1), particle, TAG_IKSEED, attempt, 0.3, seed);
         or_ik(pr, T, seed, q + 7 * t_place(pr, b));
     }
     int m = S / 2;
-    for (int s = 0; s < 2 * B; ++s) {
+    for (int s = 0; s < (p2p ? 1 : 2 * B); ++s) {
         double via[7];
         perturbed_home(pr, (uint32_t)s, particle, TAG_VIA, attempt, 0.3, via);
         const double *qa = q + 7 * (s * S), *qb = q + 7 * ((s + 1) * S);

@@ -57,7 +57,12 @@ typedef struct {
     double cell_size, z_star;
 } or_problem;
 
-enum { OR_KIND_TOWER = 0, OR_KIND_PACK = 1 };
+enum { OR_KIND_TOWER = 0, OR_KIND_PACK = 1, OR_KIND_P2P = 2 };
+/* Point-to-point trajectory optimisation (kind 2, the paper's motion-planning use of stage
+ * 2): B = 1 and the "block" is a zero-size virtual target at init[0..3]; the trajectory is
+ * one transit segment, C = W configurations from q_home to the target's grasp
+ * configuration; the residuals are the target alignment (position, roll, pitch) and the
+ * arm collisions; there is no placement, no held block and no stage 1. */
 
 /* constraint groups of the stage-2 augmented Lagrangian */
 enum { OR_G_START = 0, OR_G_ARM, OR_G_BLOCK, OR_G_COLL, OR_G_STABLE, OR_G_HEIGHT, OR_NG };

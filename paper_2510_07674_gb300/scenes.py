@@ -126,6 +126,7 @@ class Problem:
     scene: Scene
     params: Params
     packing: "Packing | None" = None
+    p2p: bool = False         # point-to-point: one segment from q_home to the target init[0]
 
 
 def _rot_z(yaw: float) -> np.ndarray:
@@ -380,6 +381,65 @@ def make_packing(name: str, seed: int = 0, robot_seed: int = 7, **overrides) -> 
     cfg.setdefault("seed", seed)
     return packing_problem(blocks, gx, gy, cell_size=u, z_span=z_span, turns=turns, name=name,
                            robot_seed=robot_seed, **cfg)
+
+
+# Point-to-point trajectory optimisation (the paper's motion-planning use of stage 2): from
+# q_home to a top-down tool target in a cluttered tower scene.
+P2P: Dict[str, dict] = {
+    "p2p": dict(O=48, N=256, M=64, P=8, Q=1024, W=32, K_traj=50),
+}
+P2P_LIFT = 0.05   # target height above the top face of a block resting on the table
+
+
+def make_p2p_scene(O: int, seed: int) -> Scene:
+    """Scene of a point-to-point problem: the table, a target over the start region of the
+    tower scenes, and O cuboids, half of them small (sides U(0.05, 0.15) m) inside the volume
+    between the robot and the target, so that the interpolated path is obstructed.  Keep-out
+    volumes: the robot base column and the column above the target."""
+    rng = np.random.default_rng(np.random.SeedSequence([0x2B2, O, seed]))
+    z_table = 0.0
+    table = np.concatenate([[0.55, 0.0, -0.025], np.eye(3).ravel(), [0.45, 0.6, 0.025]])
+    tx, ty = 0.36 + 0.27 * rng.uniform(), 0.22 + 0.18 * rng.uniform()
+    target = np.array([tx, ty, z_table + 2 * BLOCK_HALF + P2P_LIFT, rng.uniform(-math.pi, math.pi)])
+    keep = [
+        (np.array([0.0, 0.0, 0.6]), np.array([0.28, 0.28, 0.7])),                      # robot base column
+        (np.array([tx, ty, 0.45]), np.array([0.09, 0.09, 0.45])),                      # above the target
+    ]
+    cub = [table]
+    tries = 0
+    while len(cub) < O + 1 and tries < 100000:
+        tries += 1
+        inner = len(cub) <= O // 2
+        if inner:   # between the robot and the target
+            hx, hy, hz = rng.uniform(0.025, 0.075, 3)
+            x, y, z = rng.uniform(0.2, 0.75), rng.uniform(-0.15, 0.45), rng.uniform(0.1, 0.8)
+        else:
+            hx, hy, hz = rng.uniform(0.025, 0.15, 3)
+            x, y, z = rng.uniform(-0.5, 1.25), rng.uniform(-1.0, 1.0), rng.uniform(0.0, 1.2)
+        yaw = rng.uniform(-math.pi, math.pi)
+        R = _rot_z(yaw)
+        ext = np.abs(R) @ np.array([hx, hy, hz])
+        c = np.array([x, y, z])
+        if any(_boxes_overlap(c, ext, kc, kh, 0.02) for kc, kh in keep):
+            continue
+        if abs(x - 0.55) < 0.45 + ext[0] and abs(y) < 0.6 + ext[1] and z - ext[2] < z_table:
+            continue   # stays above the table top
+        cub.append(np.concatenate([c, R.ravel(), [hx, hy, hz]]))
+    box = np.array([tx - 0.1, ty - 0.1, target[2], tx + 0.1, ty + 0.1, target[2] + 0.1])
+    return Scene(cuboid=np.array(cub), sphere=np.zeros((0, 4)), half=np.zeros((1, 3)), init=target[None].copy(),
+                 box=box, z_table=z_table, grasp_off=0.0)
+
+
+def make_p2p(name: str = "p2p", seed: int = 0, robot_seed: int = 7, **overrides) -> Problem:
+    """Point-to-point problem: from q_home to the tool target of make_p2p_scene (tool pointing
+    down; any quarter turn of its yaw is accepted by the grasp reading).  The target is a
+    zero-size virtual "block": neither an obstacle nor carried."""
+    cfg = dict(P2P[name])
+    O = overrides.pop("O", cfg.pop("O"))
+    cfg.update(overrides)
+    cfg.setdefault("seed", seed)
+    return Problem(name=name, robot=make_robot(robot_seed), scene=make_p2p_scene(O, seed), params=Params(**cfg),
+                   p2p=True)
 
 
 def heterogeneous_batch(n_problems: int, seed: int = 0):
