@@ -288,6 +288,7 @@ def run_native(args, ws, rank, local):
     if args.serve_problems > 0:
         batched, served = run_forms(args, rank, overrides, peak)
     packing = run_packing(args, rank) if args.pack_seeds > 0 else None
+    p2p = run_p2p(args, rank) if args.p2p_seeds > 0 else None
 
     out = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
@@ -314,6 +315,7 @@ def run_native(args, ws, rank, local):
         "batched": batched,
         "served": served,
         "packing": packing,
+        "p2p": p2p,
         "gpu_launches": int(sum(s["kernel_launches"] for s in stats)),
         "clocks": clocks,
         "kernel_sources_sha256_16": kernel_hash(),
@@ -494,6 +496,40 @@ def run_packing(args, rank):
     return out
 
 
+def run_p2p(args, rank):
+    """Point-to-point trajectory optimisation (stage 2 on one segment, Sec. IV's motion
+    planning use): solve time per seed (CUDA events around spasm_optimize) and success."""
+    import torch
+
+    from paper_2510_07674_gb300 import scenes
+    from paper_2510_07674_gb300 import spasm as S
+    times, ok, att = [], 0, []
+    for i in range(args.p2p_seeds):
+        wl = scenes.make_p2p("p2p", seed=rank * 1000 + i, max_steps=30000)
+        pr = S.Problem(wl)
+        try:
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record()
+            try:
+                S.spasm_optimize(pr)
+            except S.SpasmError as e:
+                if e.status != -4:
+                    raise
+            e1.record()
+            torch.cuda.synchronize()
+            r = S.spasm_result(pr, allow_empty=True)
+            ok += int(r["success"].sum() > 0)
+            times.append(e0.elapsed_time(e1))
+            att.append(S.spasm_get_stats(pr)["traj_attempts"])
+        finally:
+            pr.close()
+    out = _summary(times, ok, att)
+    out["workload"] = ("q_home to a top-down tool target over the table, 48 cuboids (half between robot and target), "
+                       "Q=1024 trajectory particles, 32 waypoints, 50 iterations")
+    return out
+
+
 def run_sweep(args):
     """Hyper-parameter sweep (Sec. IV, Fig. 5 analogue): time to first solution of stage 1
     over a grid of sampling batch N and optimisation batch M, per workload."""
@@ -600,6 +636,7 @@ def main():
                     help="heterogeneous problems for the batched / served measurements (0 = skip)")
     ap.add_argument("--serve-slots", type=int, default=8)
     ap.add_argument("--pack-seeds", type=int, default=12, help="seeds of the 5-block packing leg (0 = skip)")
+    ap.add_argument("--p2p-seeds", type=int, default=10, help="seeds of the point-to-point leg (0 = skip)")
     ap.add_argument("--sweep", action="store_true", help="run the N x M stage-1 sweep instead of the benchmark")
     ap.add_argument("--sweep-workloads", nargs="*", default=["tetris5", "tetris8", "tower10"])
     ap.add_argument("--sweep-trials", type=int, default=5)

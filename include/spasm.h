@@ -134,6 +134,16 @@ spasm_status spasm_create_problem(const spasm_robot* robot, const spasm_obstacle
  * the tower goal).  Limits as spasm_create_problem plus those of spasm_packing. */
 spasm_status spasm_create_packing(const spasm_robot* robot, const spasm_packing* packing, const spasm_params* params,
                                   void* cuda_stream, spasm_problem_t* out);
+/* Point-to-point trajectory optimisation (the paper's motion-planning use of stage 2, Sec.
+ * IV): one transit segment of W configurations from q_home to a configuration whose tool,
+ * pointing down (tool z along -world z), reaches target = (x, y, z, yaw); the yaw is free
+ * up to quarter turns (the lift draws one).  The objective is that of stage 2 with the
+ * target-alignment residuals (tool position, roll, pitch) and the arm-collision group,
+ * without placement, held block or stage 1 (spasm_place reports SPASM_ERR_INVALID).
+ * spasm_optimize, spasm_result (C = W) and spasm_optimize_batch apply.  Limits as
+ * spasm_create_problem. */
+spasm_status spasm_create_p2p(const spasm_robot* robot, const spasm_obstacles* obstacles, const double* target,
+                              const spasm_params* params, void* cuda_stream, spasm_problem_t* out);
 /* Stage-1 result: *n_place satisfying placements found (0 before spasm_place), placements
  * P x B x 4 (x, y, z, yaw), best first.  SPASM_ERR_NOSOLUTION when none.  Synchronises. */
 spasm_status spasm_placements(spasm_problem_t problem, int* n_place, double* placements);

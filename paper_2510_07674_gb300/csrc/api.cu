@@ -351,6 +351,33 @@ extern "C" spasm_status spasm_create_packing(const spasm_robot* robot, const spa
     return SPASM_OK;
 }
 
+extern "C" spasm_status spasm_create_p2p(const spasm_robot* robot, const spasm_obstacles* obs, const double* target,
+                                         const spasm_params* prm, void* cuda_stream, spasm_problem_t* out) {
+    if (!target || !out || !prm) return fail(SPASM_ERR_INVALID, "null argument");
+    *out = nullptr;
+    const double half[3] = {0.0, 0.0, 0.0};
+    const double box[6] = {target[0] - 0.1, target[1] - 0.1, target[2], target[0] + 0.1, target[1] + 0.1, target[2] + 0.1};
+    spasm_goal goal{1, half, target, box, target[2], 0.0};
+    spasm_problem_t pr = nullptr;
+    SPASM_TRY(spasm_create_problem(robot, obs, &goal, prm, cuda_stream, &pr));
+    // one transit segment: C = W configurations; stage 1 does not apply
+    pr->sc.kind = kKindP2P;
+    pr->sc.C = pr->sc.S + 1;
+    pr->s64.C = pr->sc.C;
+    pr->s64.p2p = 1;
+    pr->placed = true;
+    pr->n_place = 1;
+    cudaError_t e = cudaMemsetAsync(pr->d_place, 0, sizeof(float) * 4, pr->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(pr->d_sc, &pr->sc, sizeof(Scalars), cudaMemcpyHostToDevice, pr->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(pr->stream);
+    if (e != cudaSuccess) {
+        spasm_destroy_problem(pr);
+        return fail(SPASM_ERR_CUDA, std::string("create_p2p: ") + cudaGetErrorString(e));
+    }
+    *out = pr;
+    return SPASM_OK;
+}
+
 extern "C" spasm_status spasm_placements(spasm_problem_t pr, int* n_place, double* placements) {
     if (!pr) return fail(SPASM_ERR_INVALID, "null problem");
     SPASM_CUDA(cudaStreamSynchronize(pr->stream));
@@ -421,6 +448,7 @@ spasm_status spasm::place_continue(spasm_problem* pr, int attempt, int steps, in
 
 extern "C" spasm_status spasm_place(spasm_problem_t pr) {
     if (!pr) return fail(SPASM_ERR_INVALID, "null problem");
+    if (pr->sc.kind == kKindP2P) return fail(SPASM_ERR_INVALID, "a point-to-point problem has no stage 1");
     SPASM_TRY(rec(pr, 0));
     const spasm_status st = place_continue(pr, 0, 0, 0);
     SPASM_TRY(rec(pr, 1));
@@ -668,8 +696,10 @@ extern "C" spasm_status spasm_set_seed(spasm_problem_t pr, uint64_t seed) {
     pr->prm.seed = seed;
     SPASM_CUDA(cudaMemcpyAsync(pr->d_sc, &pr->sc, sizeof(Scalars), cudaMemcpyHostToDevice, pr->stream));
     SPASM_CUDA(cudaStreamSynchronize(pr->stream));
-    pr->placed = pr->optimized = false;
-    pr->n_place = pr->n_found = 0;
+    pr->optimized = false;
+    pr->placed = pr->sc.kind == kKindP2P;   // a point-to-point problem has no stage 1
+    pr->n_place = pr->placed ? 1 : 0;
+    pr->n_found = 0;
     return SPASM_OK;
 }
 

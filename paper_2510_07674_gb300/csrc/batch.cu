@@ -51,7 +51,8 @@ spasm_status check_batch(spasm_problem_t* prs, int n, void* stream) {
     if (!stream) return fail(SPASM_ERR_INVALID, "the batched form needs a created (non-default) stream for graph capture");
     for (int i = 0; i < n; ++i) {
         if (!prs[i]) return fail(SPASM_ERR_INVALID, "null problem in the batch");
-        if (prs[i]->sc.kind != kKindTower) return fail(SPASM_ERR_INVALID, "the batched form solves tower problems");
+        if (prs[i]->sc.kind == kKindPack)
+            return fail(SPASM_ERR_INVALID, "the batched form solves tower and point-to-point problems");
         for (int j = 0; j < i; ++j)
             if (prs[j] == prs[i]) return fail(SPASM_ERR_INVALID, "a problem appears twice in the batch");
     }

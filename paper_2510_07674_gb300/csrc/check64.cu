@@ -79,17 +79,19 @@ __global__ void __launch_bounds__(kChkThreads) k_check64(const __grid_constant__
     __shared__ double vstart[kMaxB], vtilt[kMaxB];
     if (tid < B) {
         double qq[7], R[8][9], o[8][3], Rt[9], pt[3], Rb[9], pb[3];
-        // placed pose from the place configuration
-        for (int j = 0; j < 7; ++j) qq[j] = qr[t_place(S, tid) * 8 + j];
-        fk64(s, qq, R, o, Rt, pt);
-        held64(s, tid, Rt, pt, Rb, pb);
-        pose[tid][0] = pb[0]; pose[tid][1] = pb[1]; pose[tid][2] = pb[2]; pose[tid][3] = atan2(Rb[3], Rb[0]);
-        block_cub64(pose[tid], s.half[tid], bcub[tid]);
-        block_cub64(s.init[tid], s.half[tid], icub[tid]);
         vtilt[tid] = 0.0;
-        {
+        block_cub64(s.init[tid], s.half[tid], icub[tid]);
+        if (!s.p2p) {
+            // placed pose from the place configuration
+            for (int j = 0; j < 7; ++j) qq[j] = qr[t_place(S, tid) * 8 + j];
+            fk64(s, qq, R, o, Rt, pt);
+            held64(s, tid, Rt, pt, Rb, pb);
+            pose[tid][0] = pb[0]; pose[tid][1] = pb[1]; pose[tid][2] = pb[2]; pose[tid][3] = atan2(Rb[3], Rb[0]);
+            block_cub64(pose[tid], s.half[tid], bcub[tid]);
             const double roll = atan2(Rb[7], Rb[8]), pitch = atan2(-Rb[6], sqrt(Rb[7] * Rb[7] + Rb[8] * Rb[8]));
             vtilt[tid] = roll * roll + pitch * pitch;
+        } else {
+            for (int i = 0; i < 4; ++i) pose[tid][i] = s.init[tid][i];
         }
         for (int j = 0; j < 7; ++j) qq[j] = qr[t_grasp(S, tid) * 8 + j];
         fk64(s, qq, R, o, Rt, pt);
@@ -176,7 +178,7 @@ __global__ void __launch_bounds__(kChkThreads) k_check64(const __grid_constant__
     }
     // placement: spheres of block j vs the environment and the blocks below
     double place_pen = 0.0;
-    for (int it = tid; it < 8 * B; it += kChkThreads) {
+    for (int it = tid; it < (s.p2p ? 0 : 8 * B); it += kChkThreads) {
         const int j = it >> 3, m = it & 7;
         const double lx = ((m & 1) ? 0.5 : -0.5) * s.half[j][0];
         const double ly = ((m & 2) ? 0.5 : -0.5) * s.half[j][1];
@@ -214,7 +216,7 @@ __global__ void __launch_bounds__(kChkThreads) k_check64(const __grid_constant__
         for (int b = 0; b < B; ++b) {
             ms = fmax(ms, vstart[b]);
             mt = fmax(mt, vtilt[b]);
-            mz = fmax(mz, fabs(pose[b][2] - s.zt[b]));
+            if (!s.p2p) mz = fmax(mz, fabs(pose[b][2] - s.zt[b]));
             if (b + 1 < B) {
                 double mx = 0.0, my = 0.0;
                 for (int j = b + 1; j < B; ++j) { mx += pose[j][0]; my += pose[j][1]; }

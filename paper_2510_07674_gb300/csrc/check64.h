@@ -15,6 +15,7 @@ struct Scalars64 {
     int rlink[kMaxRobotSpheres];
     double half[kMaxB][3], hmin[kMaxB], init[kMaxB][4], zt[kMaxB];
     double grasp_off, eps, eps_start;
+    int p2p;   // point to point: one segment, no placement
 };
 
 // cub: n_cub x 4 x double4 (centre, then R columns with half extents); osph: n_osph x double4.

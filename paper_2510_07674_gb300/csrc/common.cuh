@@ -22,7 +22,7 @@ constexpr int kMaxOSph = 64;       // environment spheres
 constexpr int kMaxC = 1024;        // configurations per trajectory particle
 constexpr int kMaxNR = 9 * kMaxB + 3;
 constexpr int kMaxCells = 64;      // unit cells over all blocks of a packing problem
-enum GoalKind { kKindTower = 0, kKindPack = 1 };
+enum GoalKind { kKindTower = 0, kKindPack = 1, kKindP2P = 2 };
 constexpr float kPi = 3.14159265358979323846f;
 
 // Scalars, robot tables and block tables: passed by value as a __grid_constant__ kernel

@@ -87,6 +87,7 @@ __global__ void k_lift_ik(const __grid_constant__ Scalars sc, int n, const float
     if (gid >= n * 2 * B) return;
     if (np <= 0) return;
     const int p = gid / (2 * B), r = gid % (2 * B), b = r >> 1, which = r & 1;
+    if (which == 1 && sc.kind == kKindP2P) return;   // point to point: no placement
     const U4 kk = philox4x32_10((uint32_t)b, (uint32_t)p, kTagGrasp, attempt, sc.seed);
     float pose[4];
     if (which == 0) {
@@ -767,14 +768,17 @@ __device__ __forceinline__ void cuboid_aabb(const float4* c, float4* box) {
 // Evaluate the whole particle: kinematics of the grasp/place configurations and the placed
 // poses, the configuration loop, residuals and objective; with `grad`, the assembled dL/dq
 // ends up in G_blk (G_arm holds the unscaled arm-group gradient).
+template <bool kP2P>
 __device__ void traj_evaluate(const Scalars& sc, const LaneSpheres& ls, const float4* cub, const float4* osph,
                               const float4* aabb, TShared& sh, SpecialFrames* sp, float* q, float* G_arm,
                               float* G_blk, bool grad, unsigned long long& n_tests) {
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const int B = sc.B, S = sc.S, C = sc.C, NR = sc.NR;
+    // point to point (kP2P): one segment ending at the target's grasp configuration; no placement
+    constexpr bool p2p = kP2P;
 
     // (1) frames of the 2B grasp/place configurations (4 per warp), kept for the epilogue
-    const int n_sp = 2 * B;
+    const int n_sp = p2p ? 1 : 2 * B;
     for (int gi = w; gi * 4 < n_sp; gi += kTWarps) {
         const int si = 4 * gi + (lane >> 3);
         const bool ok = si < n_sp;
@@ -784,11 +788,17 @@ __device__ void traj_evaluate(const Scalars& sc, const LaneSpheres& ls, const fl
     __syncthreads();
     // placed poses: the block frame at each place configuration, (x, y, z, yaw)
     if (w == 0 && lane < B) {
-        const float4* H = sp[2 * lane + 1].H;
-        const float pose[4] = {H[0].w, H[1].w, H[2].w, atan2f(H[1].x, H[0].x)};
-        for (int i = 0; i < 4; ++i) sh.pose[4 * lane + i] = pose[i];
-        block_cuboid(pose[0], pose[1], pose[2], pose[3], sc.half[lane], sh.bcub[lane]);
-        cuboid_aabb(sh.bcub[lane], sh.baabb[lane]);
+        if (!p2p) {
+            const float4* H = sp[2 * lane + 1].H;
+            const float pose[4] = {H[0].w, H[1].w, H[2].w, atan2f(H[1].x, H[0].x)};
+            for (int i = 0; i < 4; ++i) sh.pose[4 * lane + i] = pose[i];
+            block_cuboid(pose[0], pose[1], pose[2], pose[3], sc.half[lane], sh.bcub[lane]);
+            cuboid_aabb(sh.bcub[lane], sh.baabb[lane]);
+        } else {
+            for (int i = 0; i < 4; ++i) sh.pose[4 * lane + i] = 0.f;
+            sh.baabb[lane][0] = make_float4(3.4e38f, 3.4e38f, 3.4e38f, 0.f);   // an empty box: never a candidate
+            sh.baabb[lane][1] = make_float4(-3.4e38f, -3.4e38f, -3.4e38f, 0.f);
+        }
     }
     __syncthreads();
 
@@ -813,7 +823,8 @@ __device__ void traj_evaluate(const Scalars& sc, const LaneSpheres& ls, const fl
     acc_max = warp_max(acc_max);
     if (lane == 0) { sh.warp[w].part[0] = acc_arm; sh.warp[w].part[1] = acc_blk; sh.warp[w].part[2] = acc_max; }
     // collisions of the placed tower, all warps (reads only the placed poses of step 1)
-    placed_collisions(sc, cub, osph, aabb, sh, grad);
+    if (!p2p) placed_collisions(sc, cub, osph, aabb, sh, grad);
+    else if (lane == 0) { sh.warp[w].pc[0] = 0.f; sh.warp[w].pc[1] = 0.f; }
     __syncthreads();
 
     // (3) epilogue.  (a) warp 0: group sums and the placement residuals; warp 1: start residuals
@@ -832,8 +843,8 @@ __device__ void traj_evaluate(const Scalars& sc, const LaneSpheres& ls, const fl
         float c_coll = 0.f;
         for (int i = 0; i < kTWarps; ++i) c_coll += __shfl_sync(0xffffffffu, pcl, i);
         pm = warp_max(pm);
-        float my_D, my_e;
-        place_stack_warp(sc, sh.pose, kPlaceForward, nullptr, nullptr, nullptr, sh.ps, my_D, my_e);
+        float my_D = 0.f, my_e = 0.f;
+        if (!p2p) place_stack_warp(sc, sh.pose, kPlaceForward, nullptr, nullptr, nullptr, sh.ps, my_D, my_e);
         const float c_stable = warp_sum(lane < B ? my_D : 0.f);
         const float c_height = warp_sum(lane < B ? my_e * my_e : 0.f);
         const float max_D = warp_max(lane < B ? my_D : 0.f);
@@ -852,7 +863,8 @@ __device__ void traj_evaluate(const Scalars& sc, const LaneSpheres& ls, const fl
         }
     } else if (w == 1 && lane < B) {
         start_terms(sc, lane, 0, sp[2 * lane], &sh.h[5 * lane], nullptr, nullptr, nullptr);
-        start_terms(sc, lane, 1, sp[2 * lane + 1], &sh.h[5 * B + 2 * lane], nullptr, nullptr, nullptr);
+        if (!p2p) start_terms(sc, lane, 1, sp[2 * lane + 1], &sh.h[5 * B + 2 * lane], nullptr, nullptr, nullptr);
+        else sh.h[5 * B + 2 * lane] = sh.h[5 * B + 2 * lane + 1] = 0.f;
     }
     __syncthreads();
     // (b) objective and dL/dh
@@ -882,7 +894,7 @@ __device__ void traj_evaluate(const Scalars& sc, const LaneSpheres& ls, const fl
     __syncthreads();
     if (grad) {
         // (c) warp 0: placement gradient w.r.t. the placed poses; warp 1: grasp gradients
-        if (w == 0) {
+        if (w == 0 && !p2p) {
             float my_D, my_e;
             place_stack_warp(sc, sh.pose, kPlaceExplicit, &sh.s[8 * B], &sh.s[7 * B], sh.g4, sh.ps, my_D, my_e);
             const float s_arm = sh.s_arm, s_blk = sh.s_blk, s_coll = sh.s[9 * B];
@@ -903,7 +915,7 @@ __device__ void traj_evaluate(const Scalars& sc, const LaneSpheres& ls, const fl
         }
         __syncthreads();
         // (d) place configurations: tilt residuals and the placed-pose gradient through fk
-        if (w == 1 && lane < B) {
+        if (w == 1 && lane < B && !p2p) {
             float hbuf[5];
             start_terms(sc, lane, 1, sp[2 * lane + 1], hbuf, &sh.s[5 * B + 2 * lane], sh.extra[B + lane],
                         &sh.g4[4 * lane]);
@@ -960,6 +972,7 @@ __device__ void traj_evaluate(const Scalars& sc, const LaneSpheres& ls, const fl
 // One particle of the trajectory stage by the whole CTA: load its state, run the descent (or
 // the single evaluation), write the outputs.  The environment tables are already in shared
 // memory (smem_raw, laid out by the t_*_offset functions of this problem).
+template <bool kP2P>
 __device__ __forceinline__ void traj_particle(const Scalars& sc, int p, int mode, const TrajIO& io,
                                               unsigned char* smem_raw) {
     float4* cub = reinterpret_cast<float4*>(smem_raw + t_env_offset());
@@ -1003,7 +1016,7 @@ __device__ __forceinline__ void traj_particle(const Scalars& sc, int p, int mode
     if (mode == kTrajDescend) {
         const int K = io.k_steps;
         for (int k = 1; k <= K; ++k) {
-            traj_evaluate(sc, ls, cub, osph, aabb, sh, sp, q, G_arm, G_blk, true, n_tests);
+            traj_evaluate<kP2P>(sc, ls, cub, osph, aabb, sh, sp, q, G_arm, G_blk, true, n_tests);
             const float eta = sc.eta_traj * (1.f - (float)k / (float)K);
             for (int i = tid; i < C * 7; i += kTThreads) {
                 const int t = i / 7, j = i % 7;
@@ -1020,7 +1033,7 @@ __device__ __forceinline__ void traj_particle(const Scalars& sc, int p, int mode
         }
     }
     const bool want_grad = mode == kTrajEval && io.grad != nullptr;
-    traj_evaluate(sc, ls, cub, osph, aabb, sh, sp, q, G_arm, G_blk, want_grad, n_tests);
+    traj_evaluate<kP2P>(sc, ls, cub, osph, aabb, sh, sp, q, G_arm, G_blk, want_grad, n_tests);
     if (io.tests && (threadIdx.x & 31) == 0) atomicAdd(io.tests, n_tests);
 
     // outputs
@@ -1056,7 +1069,8 @@ __device__ __forceinline__ void traj_particle(const Scalars& sc, int p, int mode
     }
 }
 
-// One CTA per particle of one problem.
+// One CTA per particle of one problem (kP2P: the point-to-point instantiation).
+template <bool kP2P>
 __global__ void __launch_bounds__(kTThreads, 2) k_traj(const __grid_constant__ Scalars sc, DevTables tab, int n, int mode,
                                                       TrajIO io, int* err) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1067,7 +1081,7 @@ __global__ void __launch_bounds__(kTThreads, 2) k_traj(const __grid_constant__ S
         return;
     const int p = blockIdx.x;
     if (p >= n) return;
-    traj_particle(sc, p, mode, io, smem_raw);
+    traj_particle<kP2P>(sc, p, mode, io, smem_raw);
 }
 
 static_assert(sizeof(Scalars) % 16 == 0, "the batched kernel copies Scalars in 16-byte words");
@@ -1124,7 +1138,8 @@ __global__ void __launch_bounds__(kTThreads, 2) k_traj_batch(const TrajJob* __re
         const int p0 = (it - job.first) * per_fetch;
         const int p1 = min(p0 + per_fetch, job.n);
         for (int p = p0; p < p1; ++p) {
-            traj_particle(sc_s, p, mode, io_s, smem_raw);
+            if (sc_s.kind == kKindP2P) traj_particle<true>(sc_s, p, mode, io_s, smem_raw);
+            else traj_particle<false>(sc_s, p, mode, io_s, smem_raw);
             __syncthreads();
         }
     }
@@ -1163,9 +1178,15 @@ cudaError_t launch_traj(const Scalars& sc, DevTables t, int n, int mode, const T
                         cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
     const size_t bytes = traj_smem_bytes(sc);
-    cudaError_t e = allow_max_dynamic_smem(k_traj, bytes);
-    if (e != cudaSuccess) return e;
-    k_traj<<<n, kTThreads, bytes, st>>>(sc, t, n, mode, io, err);
+    if (sc.kind == kKindP2P) {
+        cudaError_t e = allow_max_dynamic_smem(k_traj<true>, bytes);
+        if (e != cudaSuccess) return e;
+        k_traj<true><<<n, kTThreads, bytes, st>>>(sc, t, n, mode, io, err);
+    } else {
+        cudaError_t e = allow_max_dynamic_smem(k_traj<false>, bytes);
+        if (e != cudaSuccess) return e;
+        k_traj<false><<<n, kTThreads, bytes, st>>>(sc, t, n, mode, io, err);
+    }
     return cudaGetLastError();
 }
 

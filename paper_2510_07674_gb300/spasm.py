@@ -27,7 +27,8 @@ EXPORTED = ["spasm_create_problem", "spasm_destroy_problem", "spasm_last_error",
             "spasm_set_timing", "spasm_get_stats", "spasm_reset_stats", "spasm_place_select_static",
             "spasm_server_create", "spasm_server_submit", "spasm_server_poll", "spasm_server_wait",
             "spasm_server_result", "spasm_server_release", "spasm_server_destroy", "spasm_batch_default_config",
-            "spasm_optimize_batch", "spasm_batch_autotune", "spasm_create_packing", "spasm_placements"]
+            "spasm_optimize_batch", "spasm_batch_autotune", "spasm_create_packing", "spasm_placements",
+            "spasm_create_p2p"]
 
 
 class SpasmError(RuntimeError):
@@ -126,6 +127,8 @@ def lib():
         L.spasm_create_packing.argtypes = [ctypes.POINTER(_Robot), ctypes.POINTER(_Packing), ctypes.POINTER(_Params), _V,
                                            ctypes.POINTER(_V)]
         L.spasm_placements.argtypes = [_V, _I, _D]
+        L.spasm_create_p2p.argtypes = [ctypes.POINTER(_Robot), ctypes.POINTER(_Obstacles), _D, ctypes.POINTER(_Params),
+                                       _V, ctypes.POINTER(_V)]
         L.spasm_optimize_batch.argtypes = [ctypes.POINTER(_V), ctypes.c_int, _V, ctypes.POINTER(_BatchConfig)]
         L.spasm_batch_autotune.argtypes = [ctypes.POINTER(_V), ctypes.c_int, _V, ctypes.POINTER(_BatchConfig), _D]
         for name in EXPORTED:
@@ -209,7 +212,12 @@ class Problem(ProblemDesc):
             stream = torch.cuda.current_stream().cuda_stream
         self.stream = int(stream)
         h = _V()
-        if self._packing is not None:
+        if getattr(workload, "p2p", False):   # point-to-point trajectory optimisation
+            self._arrays["target"] = _f64(workload.scene.init[0])
+            _check(lib().spasm_create_p2p(ctypes.byref(self._robot), ctypes.byref(self._obs),
+                                          self._arrays["target"].ctypes.data_as(_D), ctypes.byref(self._params),
+                                          _V(self.stream), ctypes.byref(h)))
+        elif self._packing is not None:
             _check(lib().spasm_create_packing(ctypes.byref(self._robot), ctypes.byref(self._packing),
                                               ctypes.byref(self._params), _V(self.stream), ctypes.byref(h)))
         else:
