@@ -279,7 +279,7 @@ def make_problem(name: str, seed: int = 0, robot_seed: int = 7, **overrides) -> 
 PACKINGS: Dict[str, dict] = {
     # step sizes and batch sizes from a sweep on the GPU (time to first solution, 5 seeds)
     "tetris5": dict(gx=5, gy=4, N=16384, M=4096, P=8, K_lin=25, K_quad=5, eta_init=0.05, alpha=0.02),
-    "tetris8": dict(gx=8, gy=4, N=32768, M=8192, P=8, K_lin=50, K_quad=10, eta_init=0.03, alpha=0.02),
+    "tetris8": dict(gx=8, gy=4, N=16384, M=4096, P=8, K_lin=100, K_quad=20, eta_init=0.05, alpha=0.02),
 }
 # Packings are posed in cell units (cube edge 1): plain gradient descent is not unit
 # invariant (the yaw gradient carries a lever arm), and in metres the yaw of a 4-cell block

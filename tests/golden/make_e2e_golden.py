@@ -9,12 +9,17 @@ called.
 
     python tests/golden/make_e2e_golden.py tower1 --seeds 100
     python tests/golden/make_e2e_golden.py tower4 --seeds 100 --override Q=64
+    python tests/golden/make_e2e_golden.py p2p --seeds 100 --override Q=64 --override max_steps=1000
+
+For the point-to-point workload (one transit segment to a tool target) only stage 2 runs.
 
 The 4-block case keeps its scene, stage-1 sizes and waypoint count, and reduces the number of
 trajectory particles so that the FP64 all-pairs oracle finishes 100 seeds in about an hour.
 """
 import argparse
 import json
+
+import numpy as np
 import os
 import sys
 import time
@@ -35,6 +40,12 @@ def parse_overrides(items):
 
 
 def run_seed(name, seed, overrides, threads):
+    if name in scenes.P2P:
+        wl = scenes.make_p2p(name, seed=seed, **overrides)
+        o = Oracle(wl, n_threads=threads)
+        q, cost, traj_attempts = o.traj_solve(np.zeros((1, 1, 4)))
+        return {"seed": seed, "n_place": 1, "n_found": int(len(cost)), "cost": [float(c) for c in cost],
+                "place_attempts": 0, "traj_attempts": int(traj_attempts)}
     wl = scenes.make_problem(name, seed=seed, **overrides)
     o = Oracle(wl, n_threads=threads)
     place, place_attempts, place_steps = o.place_solve()

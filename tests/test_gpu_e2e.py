@@ -18,12 +18,13 @@ from paper_2510_07674_gb300 import scenes
 from paper_2510_07674_gb300 import spasm as S
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
-CASES = ["e2e_tower1.json", "e2e_tower4_Q64.json"]
+CASES = ["e2e_tower1.json", "e2e_tower4_Q64.json", "e2e_p2p_Q64_max_steps1000.json"]
 
 
 def gpu_best(workload, seed, overrides):
     """(solved, best rank cost among solutions that pass the FP64 check) of one GPU solve."""
-    pr = S.Problem(scenes.make_problem(workload, seed=seed, **overrides))
+    make = scenes.make_p2p if workload in scenes.P2P else scenes.make_problem
+    pr = S.Problem(make(workload, seed=seed, **overrides))
     try:
         try:
             S.spasm_optimize(pr)
