@@ -194,7 +194,9 @@ extern "C" spasm_status spasm_create_problem(const spasm_robot* robot, const spa
         for (int k = 0; k < 7; ++k) {
             const double* row = robot->dh + 4 * k;
             q.a[k] = row[0]; q.ca[k] = std::cos(row[1]); q.sa[k] = std::sin(row[1]); q.d[k] = row[2]; q.th0[k] = row[3];
-            q.qlo[k] = robot->qlim[2 * k]; q.qhi[k] = robot->qlim[2 * k + 1];
+            // the limits as the FP32 path holds them: a joint clamped to its limit in FP32 sits at
+            // the float nearest the limit, which may lie a rounding step beyond the double value
+            q.qlo[k] = (double)(float)robot->qlim[2 * k]; q.qhi[k] = (double)(float)robot->qlim[2 * k + 1];
         }
         for (int i = 0; i < 3; ++i) {
             for (int j = 0; j < 3; ++j) q.ee_R[3 * i + j] = robot->ee[4 * i + j];
