@@ -159,6 +159,7 @@ struct TWarp {
     uint32_t cmask[kChunk][kMaxCub / 32];    // environment cuboids that may touch configuration c of the chunk
     uint32_t smask[kChunk][kMaxOSph / 32];   // environment spheres that may touch configuration c
     uint32_t bmask[2][kChunk];               // placed / not-yet-moved blocks that may touch configuration c
+    uint32_t envany[kChunk];                 // configuration c has an environment candidate
 };
 
 // Frames of one configuration kept for the epilogue (grasp and place configurations).
@@ -395,7 +396,7 @@ __device__ __forceinline__ void chunk_collisions(const Scalars& sc, const LaneSp
         }
     };
     const int n_cw = (sc.n_cub + 31) >> 5, n_sw = (sc.n_osph + 31) >> 5;
-    uint32_t per[kChunk];
+    uint32_t per[kChunk], any[kChunk] = {0u, 0u, 0u, 0u};
     for (int wd = 0; wd < n_cw; ++wd) {
         const int oi = 32 * wd + lane;
         const unsigned m = __ballot_sync(0xffffffffu, oi < sc.n_cub && overlaps(aabb[2 * oi], aabb[2 * oi + 1]));
@@ -403,6 +404,8 @@ __device__ __forceinline__ void chunk_collisions(const Scalars& sc, const LaneSp
         if (lane == 0)
 #pragma unroll
             for (int c = 0; c < kChunk; ++c) tw.cmask[c][wd] = per[c];
+#pragma unroll
+        for (int c = 0; c < kChunk; ++c) any[c] |= per[c];
     }
     for (int wd = 0; wd < n_sw; ++wd) {
         const int oi = 32 * wd + lane;
@@ -412,7 +415,12 @@ __device__ __forceinline__ void chunk_collisions(const Scalars& sc, const LaneSp
         if (lane == 0)
 #pragma unroll
             for (int c = 0; c < kChunk; ++c) tw.smask[c][wd] = per[c];
+#pragma unroll
+        for (int c = 0; c < kChunk; ++c) any[c] |= per[c];
     }
+    if (lane == 0)
+#pragma unroll
+        for (int c = 0; c < kChunk; ++c) tw.envany[c] = any[c];
     {
         const unsigned bm_placed = __ballot_sync(0xffffffffu, lane < B && overlaps(sh.baabb[lane][0], sh.baabb[lane][1]));
         refine(bm_placed, 0, &sh.baabb[0][0], 2, per);
@@ -443,7 +451,8 @@ __device__ __forceinline__ void chunk_collisions(const Scalars& sc, const LaneSp
         bool any_hit = false;
         int visits = 0;
 
-        for (int wd = 0; wd < n_cw; ++wd) {
+        const bool env_c = tw.envany[ci] != 0u;
+        for (int wd = 0; wd < (env_c ? n_cw : 0); ++wd) {
             unsigned m = tw.cmask[ci][wd];
             visits += __popc(m);
             while (m) {
@@ -470,7 +479,7 @@ __device__ __forceinline__ void chunk_collisions(const Scalars& sc, const LaneSp
                 }
             }
         }
-        for (int wd = 0; wd < n_sw; ++wd) {
+        for (int wd = 0; wd < (env_c ? n_sw : 0); ++wd) {
             unsigned m = tw.smask[ci][wd];
             visits += __popc(m);
             while (m) {
