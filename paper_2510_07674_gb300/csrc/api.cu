@@ -60,7 +60,7 @@ static void free_all(spasm_problem* pr) {
     void* ptrs[] = {pr->d_cub, pr->d_osph, pr->d_err, pr->d_xs, pr->d_cost, pr->d_xm, pr->d_costm, pr->d_masked,
                     pr->d_idx, pr->d_sat, pr->d_nsat, pr->d_best, pr->d_place, pr->d_q, pr->d_lam,
                     pr->d_mu, pr->d_metrics, pr->d_tmasked, pr->d_tsat, pr->d_tnsat, pr->d_tbest, pr->d_rq,
-                    pr->d_rcost, pr->d_rsucc, pr->d_cub64, pr->d_osph64, pr->d_rmet64, pr->d_tests, pr->d_sc};
+                    pr->d_rcost, pr->d_rsucc, pr->d_cub64, pr->d_osph64, pr->d_rmet64, pr->d_tests, pr->d_sc, pr->d_chkacc};
     for (void* p : ptrs)
         if (p) cudaFreeAsync(p, pr->stream);
     for (cudaEvent_t e : pr->ev)
@@ -252,6 +252,7 @@ extern "C" spasm_status spasm_create_problem(const spasm_robot* robot, const spa
     ALLOC(pr->d_rmet64, (size_t)6 * P);
     ALLOC(pr->d_tests, 1);
     ALLOC(pr->d_sc, 1);
+    ALLOC(pr->d_chkacc, P);
 #undef ALLOC
     for (auto& ev : pr->ev)
         if (st == SPASM_OK && cudaEventCreate(&ev) != cudaSuccess) st = fail(SPASM_ERR_CUDA, "cudaEventCreate failed");
@@ -268,6 +269,7 @@ extern "C" spasm_status spasm_create_problem(const spasm_robot* robot, const spa
         e = cudaMemcpyAsync(pr->d_osph64, osph64.data(), osph64.size() * sizeof(double), cudaMemcpyHostToDevice, pr->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(pr->d_sc, &pr->sc, sizeof(Scalars), cudaMemcpyHostToDevice, pr->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(pr->d_err, 0, sizeof(int), pr->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(pr->d_chkacc, 0, sizeof(CheckAcc) * (size_t)P, pr->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(pr->stream);
     if (e != cudaSuccess) {
         free_all(pr);
@@ -517,7 +519,7 @@ spasm_status spasm::finish_enqueue(spasm_problem* pr, cudaStream_t s) {
     SPASM_CUDA(cudaGetLastError());
     // FP64 re-evaluation of the returned solutions decides their success flags
     SPASM_CUDA(launch_check64(pr->s64, pr->d_cub64, pr->d_osph64, pr->d_rq, pr->d_tnsat, sc.P, pr->d_rmet64,
-                              pr->d_rsucc, s));
+                              pr->d_rsucc, pr->d_chkacc, s));
     count_launches(pr, 3);
     return SPASM_OK;
 }

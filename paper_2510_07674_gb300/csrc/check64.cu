@@ -1,8 +1,10 @@
 // FP64 feasibility check of returned trajectories (GetSatisfyingParticles applied to the
 // final solutions, |f(x)| < eps of Sec. III), evaluated in double precision on the
-// float32 joint values the optimiser returned.  One CTA per solution: threads over
-// configurations for the arm / held-block penetrations, then the grasp, tilt and
-// placement metrics.
+// float32 joint values the optimiser returned.  `split` CTAs per solution share its
+// configurations (arm / held-block penetrations, joint limits); the first also takes the
+// grasp, tilt and placement metrics.  Each CTA folds its maxima into the solution's
+// accumulator with atomics, and the CTA that arrives last (counter after a fence; nothing
+// waits) turns them into the metrics and the flag and clears the accumulator.
 #include "check64.h"
 #include "stage2.cuh"
 
@@ -58,17 +60,18 @@ __device__ __forceinline__ double pen_env64(const Scalars64& s, const D4* cub, c
 }
 
 constexpr int kChkThreads = 256;
+constexpr int kChkMaxSplit = 8;
 
 __global__ void __launch_bounds__(kChkThreads) k_check64(const __grid_constant__ Scalars64 s, const D4* __restrict__ cub,
                                                         const D4* __restrict__ osph, const float* __restrict__ q,
                                                         const int* __restrict__ n_sol, int P, double* __restrict__ metrics,
-                                                        int* __restrict__ ok) {
-    const int r = blockIdx.x;
+                                                        int* __restrict__ ok, CheckAcc* __restrict__ acc, int split) {
+    const int r = blockIdx.x, slice = blockIdx.y;
     if (r >= P) return;
     const int n = min(*n_sol, P);
     const int tid = threadIdx.x;
     if (r >= n) {
-        if (tid == 0) ok[r] = 0;
+        if (tid == 0 && slice == 0) ok[r] = 0;
         return;
     }
     const int B = s.B, S = s.S, C = s.C;
@@ -106,7 +109,7 @@ __global__ void __launch_bounds__(kChkThreads) k_check64(const __grid_constant__
     // arm and held-block penetrations over every configuration, joint limits
     double maxpen = 0.0;
     int limits_ok = 1;
-    for (int t = 1 + tid; t < C; t += kChkThreads) {
+    for (int t = 1 + tid + slice * kChkThreads; t < C; t += kChkThreads * split) {
         const int seg = (t - 1) / S, b = seg >> 1, jj = t - seg * S;
         const bool held = (seg & 1) && jj < S;
         double qq[7], R[8][9], o[8][3], Rt[9], pt[3];
@@ -178,7 +181,7 @@ __global__ void __launch_bounds__(kChkThreads) k_check64(const __grid_constant__
     }
     // placement: spheres of block j vs the environment and the blocks below
     double place_pen = 0.0;
-    for (int it = tid; it < (s.p2p ? 0 : 8 * B); it += kChkThreads) {
+    for (int it = tid; it < ((s.p2p || slice != 0) ? 0 : 8 * B); it += kChkThreads) {
         const int j = it >> 3, m = it & 7;
         const double lx = ((m & 1) ? 0.5 : -0.5) * s.half[j][0];
         const double ly = ((m & 2) ? 0.5 : -0.5) * s.half[j][1];
@@ -212,36 +215,51 @@ __global__ void __launch_bounds__(kChkThreads) k_check64(const __grid_constant__
     const double pp = red[0];
     const int lim = __syncthreads_and(limits_ok);
     if (tid == 0) {
-        double ms = 0.0, mt = 0.0, mD = 0.0, mz = 0.0;
-        for (int b = 0; b < B; ++b) {
-            ms = fmax(ms, vstart[b]);
-            mt = fmax(mt, vtilt[b]);
-            if (!s.p2p) mz = fmax(mz, fabs(pose[b][2] - s.zt[b]));
-            if (b + 1 < B) {
-                double mx = 0.0, my = 0.0;
-                for (int j = b + 1; j < B; ++j) { mx += pose[j][0]; my += pose[j][1]; }
-                mx /= (double)(B - 1 - b);
-                my /= (double)(B - 1 - b);
-                double sn, cs;
-                sincos(pose[b][3], &sn, &cs);
-                const double vx = mx - pose[b][0], vy = my - pose[b][1];
-                const double ux = cs * vx + sn * vy, uy = -sn * vx + cs * vy;
-                const double ex = fmax(fabs(ux) - s.half[b][0], 0.0), ey = fmax(fabs(uy) - s.half[b][1], 0.0);
-                mD = fmax(mD, sqrt(ex * ex + ey * ey));
+        CheckAcc& A = acc[r];
+        atomicMax(&A.mp, (unsigned long long)__double_as_longlong(mp));   // non-negative: integer order
+        if (!lim) atomicOr(&A.viol, 1);
+        if (slice == 0) {
+            double ms = 0.0, mt = 0.0, mD = 0.0, mz = 0.0;
+            for (int b = 0; b < B; ++b) {
+                ms = fmax(ms, vstart[b]);
+                mt = fmax(mt, vtilt[b]);
+                if (!s.p2p) mz = fmax(mz, fabs(pose[b][2] - s.zt[b]));
+                if (b + 1 < B) {
+                    double mx = 0.0, my = 0.0;
+                    for (int j = b + 1; j < B; ++j) { mx += pose[j][0]; my += pose[j][1]; }
+                    mx /= (double)(B - 1 - b);
+                    my /= (double)(B - 1 - b);
+                    double sn, cs;
+                    sincos(pose[b][3], &sn, &cs);
+                    const double vx = mx - pose[b][0], vy = my - pose[b][1];
+                    const double ux = cs * vx + sn * vy, uy = -sn * vx + cs * vy;
+                    const double ex = fmax(fabs(ux) - s.half[b][0], 0.0), ey = fmax(fabs(uy) - s.half[b][1], 0.0);
+                    mD = fmax(mD, sqrt(ex * ex + ey * ey));
+                }
             }
+            A.pp = pp; A.ms = ms; A.mt = mt; A.mD = mD; A.mz = mz;
         }
-        double* m = metrics + (size_t)r * 6;
-        m[0] = mp; m[1] = ms; m[2] = mt; m[3] = pp; m[4] = mD; m[5] = mz;
-        ok[r] = (mp <= s.eps && ms <= s.eps_start && mt <= s.eps_start && pp <= s.eps && mD <= s.eps && mz <= s.eps &&
-                 lim) ? 1 : 0;
+        __threadfence();
+        if (atomicAdd(&A.count, 1) == split - 1) {   // the last slice of this solution
+            __threadfence();
+            const volatile CheckAcc& V = A;
+            const double mpa = __longlong_as_double((long long)V.mp);
+            const int lim_all = V.viol == 0;
+            double* m = metrics + (size_t)r * 6;
+            m[0] = mpa; m[1] = V.ms; m[2] = V.mt; m[3] = V.pp; m[4] = V.mD; m[5] = V.mz;
+            ok[r] = (mpa <= s.eps && V.ms <= s.eps_start && V.mt <= s.eps_start && V.pp <= s.eps && V.mD <= s.eps &&
+                     V.mz <= s.eps && lim_all) ? 1 : 0;
+            A.mp = 0ull; A.viol = 0; A.count = 0;   // ready for the next check
+        }
     }
 }
 
 cudaError_t launch_check64(const Scalars64& s, const void* cub, const void* osph, const float* q, const int* n_sol, int P,
-                           double* metrics, int* ok, cudaStream_t st) {
+                           double* metrics, int* ok, CheckAcc* acc, cudaStream_t st) {
     if (P <= 0) return cudaSuccess;
-    k_check64<<<P, kChkThreads, 0, st>>>(s, static_cast<const D4*>(cub), static_cast<const D4*>(osph), q, n_sol, P,
-                                         metrics, ok);
+    const int split = max(1, min(kChkMaxSplit, (s.C - 1 + kChkThreads - 1) / kChkThreads));
+    k_check64<<<dim3(P, split), kChkThreads, 0, st>>>(s, static_cast<const D4*>(cub), static_cast<const D4*>(osph), q, n_sol,
+                                                      P, metrics, ok, acc, split);
     return cudaGetLastError();
 }
 

@@ -18,10 +18,19 @@ struct Scalars64 {
     int p2p;   // point to point: one segment, no placement
 };
 
+// Per-solution accumulator of the split check (zeroed once at allocation; the check leaves it
+// zeroed).
+struct CheckAcc {
+    unsigned long long mp;   // largest arm / held-block penetration (bit pattern of a non-negative double)
+    double pp, ms, mt, mD, mz;
+    int viol;                // a joint outside its limits
+    int count;               // slices done
+};
+
 // cub: n_cub x 4 x double4 (centre, then R columns with half extents); osph: n_osph x double4.
 // metrics: P x 6 (max arm/held penetration, max grasp error, max tilt, placement max
 // penetration, max CoM distance, max height error); ok: P flags.
 cudaError_t launch_check64(const Scalars64& s, const void* cub, const void* osph, const float* q, const int* n_sol, int P,
-                           double* metrics, int* ok, cudaStream_t st);
+                           double* metrics, int* ok, CheckAcc* acc, cudaStream_t st);
 
 }  // namespace spasm

@@ -56,6 +56,7 @@ struct spasm_problem {
     double* d_cub64 = nullptr;
     double* d_osph64 = nullptr;
     double* d_rmet64 = nullptr;
+    spasm::CheckAcc* d_chkacc = nullptr;   // accumulators of the split FP64 check (P)
     // statistics and timing
     spasm_stats stats{};
     bool timing = false;
