@@ -59,7 +59,7 @@ __device__ __forceinline__ double pen_env64(const Scalars64& s, const D4* cub, c
     return m;
 }
 
-constexpr int kChkThreads = 256;
+constexpr int kChkThreads = 128;
 constexpr int kChkMaxSplit = 8;
 
 __global__ void __launch_bounds__(kChkThreads) k_check64(const __grid_constant__ Scalars64 s, const D4* __restrict__ cub,
