@@ -58,7 +58,7 @@ class _Problem(ctypes.Structure):
         ("mu0", ctypes.c_double), ("mu_max", ctypes.c_double), ("ik_damp", ctypes.c_double),
         ("seed", ctypes.c_uint64), ("max_steps", ctypes.c_int), ("n_threads", ctypes.c_int),
         ("kind", ctypes.c_int), ("cell_start", _I), ("cell", _D), ("cell_size", ctypes.c_double),
-        ("z_star", ctypes.c_double),
+        ("z_star", ctypes.c_double), ("ik_mode", ctypes.c_int),
     ]
 
 
@@ -91,6 +91,9 @@ def lib():
         L.or_place_solve.argtypes = [P, _D, _I, _I, _I]
         L.or_n_configs.argtypes = [P]
         L.or_ik.argtypes = [P, _D, _D, _D]
+        L.or_ik_analytic_supported.argtypes = [P]
+        L.or_ik_analytic.argtypes = [P, _D, ctypes.c_double, _D]
+        L.or_ik_select.argtypes = [P, _D, _D, _D, ctypes.c_int, _D]
         L.or_lift.argtypes = [P, _D, ctypes.c_int, ctypes.c_uint32, _D]
         L.or_traj_cost.restype = ctypes.c_double
         L.or_n_residuals.argtypes = [P]
@@ -179,6 +182,7 @@ class Oracle:
             setattr(st, name, float(prm[name]))
         st.seed = int(prm["seed"]) & 0xFFFFFFFFFFFFFFFF
         st.n_threads = int(n_threads)
+        st.ik_mode = int(prm.get("ik_mode", 0))
         pk = getattr(problem, "packing", None)
         if pk is not None:   # the appendix's packing (Tetris) problem
             k["cell_start"] = np.ascontiguousarray(np.concatenate([[0], np.cumsum(pk.n_cells)]), np.int32)
@@ -209,6 +213,23 @@ class Oracle:
         q = np.zeros(7)
         lib().or_ik(self.ptr, _dp(t), _dp(q0), _dp(q))
         return q
+
+    def ik_analytic_supported(self) -> bool:
+        return bool(lib().or_ik_analytic_supported(self.ptr))
+
+    def ik_analytic(self, target, q6: float) -> np.ndarray:
+        """All in-limit analytic IK solutions of a tool pose for a given last joint, (n, 7)."""
+        t = _f64(target)
+        sol = np.zeros((8, 7))
+        n = lib().or_ik_analytic(self.ptr, _dp(t), float(q6), _dp(sol))
+        return sol[:n].copy()
+
+    def ik_select(self, target, seed, q6s):
+        """(found, q): the analytic solution nearest to seed over the last-joint values q6s."""
+        t, sd, c = _f64(target), _f64(seed), _f64(q6s)
+        q = np.zeros(7)
+        found = lib().or_ik_select(self.ptr, _dp(t), _dp(sd), _dp(c), len(c), _dp(q))
+        return bool(found), q
 
     # -- stage 1 -----------------------------------------------------------------------
     def place_cost(self, x, quad: bool = False, grad: bool = True):

@@ -13,8 +13,9 @@
  *   - the trajectory cost C_trajopt = C_placement(fk(q_{b,T})) + w_start C_start
  *     + w_arm C_arm + w_block C_block (Appendix), inside an augmented Lagrangian
  *     (Sec. III-B, trajectory optimisation),
- *   - the lift of placements to joint space (Sec. III-B): IK at grasp poses, one
- *     intermediate waypoint per segment, linear interpolation.
+ *   - the lift of placements to joint space (Sec. III-B): IK at grasp poses (damped least
+ *     squares, or the analytic IK of the Franka joint layout), one intermediate waypoint
+ *     per segment, linear interpolation.
  * Robot and objects are sphere sets; collisions are penetration depths (Sec. III).
  * Readings of points where the paper is silent are stated at each function.
  *
@@ -66,7 +67,7 @@ static void philox(const or_problem *pr, uint32_t c0, uint32_t c1, uint32_t c2, 
 }
 
 /* Philox stream tags */
-enum { TAG_SAMPLE = 0, TAG_GRASP = 1, TAG_IKSEED = 2, TAG_VIA = 3 };
+enum { TAG_SAMPLE = 0, TAG_GRASP = 1, TAG_IKSEED = 2, TAG_VIA = 3, TAG_Q6 = 4 };
 
 /* ------------------------------------------------------------------------------------ */
 /* small linear algebra                                                                  */
@@ -1094,6 +1095,179 @@ static void perturbed_home(const or_problem *pr, uint32_t c0, int particle, uint
         q[j] = clampd(pr->q_home[j] + amp * (2.0 * u[j] - 1.0), pr->qlim[2 * j], pr->qlim[2 * j + 1]);
 }
 
+/* ------------------------------------------------------------------------------------ */
+/* Analytic IK (Sec. III-B lifts placements with the analytical IK of He and Liu, 2021,   */
+/* for the Franka arm).  The arm here has that arm's joint layout: alpha = (0, -pi/2,     */
+/* pi/2, pi/2, -pi/2, pi/2, pi/2), a_0 = a_1 = a_2 = a_5 = 0, d_1 = d_3 = d_5 = d_6 = 0;  */
+/* the lengths d_0, d_2, a_3, a_4, d_4, a_6 and the tool are free.  Geometric solution,   */
+/* with the last joint q_6 as the free parameter (written from the geometry):            */
+/*  1. frame 7 = target E^-1, frame 6 = frame 7 T_6(q_6)^-1 (orientation and origin O6). */
+/*  2. the first three axes meet at the shoulder S = (0, 0, d_0); |O6 - S|^2 depends on   */
+/*     theta_3 only: K + 2 (a3 a4 + d2 d4) cos + 2 (d2 a4 - a3 d4) sin -> two theta_3.   */
+/*  3. u = S - O6 in frame 4 is (-a3 c3 - d2 s3 - a4, a3 s3 - d2 c3 - d4, 0); w = S - O6 */
+/*     in frame 6 is known; R_6^4(theta_4, theta_5)^T u = w gives                         */
+/*     w_x sin t5 + w_y cos t5 = u_y (two theta_5), then u_x sin t4 = w_z and             */
+/*     u_x cos t4 = w_x cos t5 - w_y sin t5 (theta_4).                                    */
+/*  4. frame 3's orientation R3 = R6 (R_4^3 R_5^4 R_6^5)^T = Rz(t0) Ry(t1) Rz(t2) is split */
+/*     as z-y-z Euler angles, both signs of sin t1.                                        */
+/* Up to 8 solutions; each is brought into the joint limits by +-2 pi where possible and  */
+/* kept only if every joint is within them.                                              */
+/* ------------------------------------------------------------------------------------ */
+static const double IK_ALPHA[7] = {0.0, -PI / 2, PI / 2, PI / 2, -PI / 2, PI / 2, PI / 2};
+
+int or_ik_analytic_supported(const or_problem *pr) {
+    const double *dh = pr->dh;
+    for (int k = 0; k < 7; ++k)
+        if (fabs(dh[4 * k + 1] - IK_ALPHA[k]) > 1e-9) return 0;
+    const int zero_a[4] = {0, 1, 2, 5}, zero_d[4] = {1, 3, 5, 6};
+    for (int i = 0; i < 4; ++i)
+        if (dh[4 * zero_a[i]] != 0.0 || dh[4 * zero_d[i] + 2] != 0.0) return 0;
+    double a3 = dh[12], a4 = dh[16], d2 = dh[10], d4 = dh[18];
+    return hypot(a3 * a4 + d2 * d4, d2 * a4 - a3 * d4) > 0.0;
+}
+
+/* inverse of a rigid 4x4 transform */
+static void rigid_inverse(const double T[16], double Ti[16]) {
+    mat4_eye(Ti);
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) Ti[4 * i + j] = T[4 * j + i];
+    for (int i = 0; i < 3; ++i) Ti[4 * i + 3] = -(Ti[4 * i] * T[3] + Ti[4 * i + 1] * T[7] + Ti[4 * i + 2] * T[11]);
+}
+
+/* rotation part of a DH row: Rot_x(alpha) Rot_z(theta), 3x3 row-major */
+static void rot_xz(double alpha, double theta, double R[9]) {
+    double ca = cos(alpha), sa = sin(alpha), ct = cos(theta), st = sin(theta);
+    R[0] = ct;      R[1] = -st;     R[2] = 0.0;
+    R[3] = ca * st; R[4] = ca * ct; R[5] = -sa;
+    R[6] = sa * st; R[7] = sa * ct; R[8] = ca;
+}
+
+static void mat3_mul(const double A[9], const double B[9], double C[9]) {
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) C[3 * i + j] = A[3 * i] * B[j] + A[3 * i + 1] * B[3 + j] + A[3 * i + 2] * B[6 + j];
+}
+
+/* C = A B^T */
+static void mat3_mul_bt(const double A[9], const double B[9], double C[9]) {
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) C[3 * i + j] = A[3 * i] * B[3 * j] + A[3 * i + 1] * B[3 * j + 1] + A[3 * i + 2] * B[3 * j + 2];
+}
+
+/* joint angle theta_k -> q_k inside [lo, hi] (shifted by 2 pi where that helps); 0 if outside */
+static int to_limits(const or_problem *pr, int k, double theta, double *q) {
+    double v = wrap_angle(theta - pr->dh[4 * k + 3]);
+    double lo = pr->qlim[2 * k], hi = pr->qlim[2 * k + 1];
+    if (v < lo) v += 2.0 * PI;
+    if (v > hi) v -= 2.0 * PI;
+    *q = v;
+    return v >= lo && v <= hi;
+}
+
+int or_ik_analytic(const or_problem *pr, const double target[16], double q6, double sol[8][7]) {
+    const double *dh = pr->dh;
+    const double d0 = dh[2], d2 = dh[10], a3 = dh[12], a4 = dh[16], d4 = dh[18];
+    double Einv[16], F7[16], T6[16], T6i[16], F6[16];
+    rigid_inverse(pr->ee, Einv);
+    mat4_mul(target, Einv, F7);
+    dh_transform(dh[24], dh[25], dh[26], dh[27] + q6, T6);
+    rigid_inverse(T6, T6i);
+    mat4_mul(F7, T6i, F6);
+    double R6[9];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) R6[3 * i + j] = F6[4 * i + j];
+    const double v[3] = {-F6[3], -F6[7], d0 - F6[11]};            /* S - O6, world */
+    double w[3];                                                /* S - O6, frame 6 */
+    for (int i = 0; i < 3; ++i) w[i] = R6[i] * v[0] + R6[3 + i] * v[1] + R6[6 + i] * v[2];
+    const double A = a3 * a4 + d2 * d4, Bs = d2 * a4 - a3 * d4, Rn = hypot(A, Bs);
+    const double D = 0.5 * (dot3(v, v) - (a3 * a3 + d2 * d2 + a4 * a4 + d4 * d4));
+    if (fabs(D) > Rn) return 0;                                 /* out of reach for this q6 */
+    const double phi = atan2(Bs, A), c_3 = acos(D / Rn);
+    const double rho = hypot(w[0], w[1]), psi = atan2(w[0], w[1]);
+    int n = 0;
+    for (int i3 = 0; i3 < 2; ++i3) {
+        const double t3 = i3 == 0 ? phi + c_3 : phi - c_3;
+        const double ux = -a3 * cos(t3) - d2 * sin(t3) - a4, uy = a3 * sin(t3) - d2 * cos(t3) - d4;
+        if (fabs(uy) > rho) continue;
+        const double c_5 = acos(uy / rho);
+        for (int i5 = 0; i5 < 2; ++i5) {
+            const double t5 = i5 == 0 ? psi + c_5 : psi - c_5;
+            const double sg = ux < 0.0 ? -1.0 : 1.0;
+            const double t4 = atan2(sg * w[2], sg * (cos(t5) * w[0] - sin(t5) * w[1]));
+            double R34[9], R45[9], R56[9], R35[9], R36[9], R3[9];
+            rot_xz(dh[13], t3, R34);
+            rot_xz(dh[17], t4, R45);
+            rot_xz(dh[21], t5, R56);
+            mat3_mul(R34, R45, R35);
+            mat3_mul(R35, R56, R36);
+            mat3_mul_bt(R6, R36, R3);
+            const double sb = hypot(R3[2], R3[5]);
+            for (int sgn = 1; sgn >= -1; sgn -= 2) {
+                double t0, t1, t2;
+                if (sb < 1e-12) {                               /* t1 = 0: only t0 + t2 is fixed */
+                    if (sgn < 0) break;
+                    t0 = 0.0; t1 = atan2(0.0, R3[8]); t2 = atan2(R3[3], R3[0]);
+                } else {
+                    t1 = atan2(sgn * sb, R3[8]);
+                    t0 = atan2(sgn * R3[5], sgn * R3[2]);
+                    t2 = atan2(sgn * R3[7], -sgn * R3[6]);
+                }
+                const double th[6] = {t0, t1, t2, t3, t4, t5};
+                double q[7];
+                int ok = 1;
+                for (int k = 0; k < 6 && ok; ++k) ok = to_limits(pr, k, th[k], &q[k]);
+                if (!ok) continue;
+                q[6] = q6;
+                memcpy(sol[n++], q, sizeof q);
+            }
+        }
+    }
+    return n;
+}
+
+/* The in-limit analytic solution nearest to seed (squared joint distance) over the
+ * candidate values of the last joint, first found on ties; 0 if there is none. */
+int or_ik_select(const or_problem *pr, const double target[16], const double seed[7], const double *q6,
+                 int n_q6, double q[7]) {
+    double best = INFINITY;
+    for (int c = 0; c < n_q6; ++c) {
+        double sol[8][7];
+        const int n = or_ik_analytic(pr, target, q6[c], sol);
+        for (int i = 0; i < n; ++i) {
+            double d = 0.0;
+            for (int j = 0; j < 7; ++j) d += (sol[i][j] - seed[j]) * (sol[i][j] - seed[j]);
+            if (d < best) { best = d; memcpy(q, sol[i], sizeof(double) * 7); }
+        }
+    }
+    return best < INFINITY;
+}
+
+/* Candidate values of the last joint for one IK target: the seed's own value, then
+ * OR_IK_Q6 - 1 uniform draws over its limits (Philox counter (2 c0 + i/4, particle,
+ * TAG_Q6, attempt), word i mod 4). */
+static void q6_candidates(const or_problem *pr, uint32_t c0, int particle, uint32_t attempt, double seed6,
+                          double q6[OR_IK_Q6]) {
+    uint32_t u[8];
+    philox(pr, 2u * c0, (uint32_t)particle, TAG_Q6, attempt, u);
+    philox(pr, 2u * c0 + 1u, (uint32_t)particle, TAG_Q6, attempt, u + 4);
+    const double lo = pr->qlim[12], hi = pr->qlim[13];
+    q6[0] = seed6;
+    for (int i = 1; i < OR_IK_Q6; ++i) q6[i] = lo + or_u01(u[i - 1]) * (hi - lo);
+}
+
+/* IK of one lift target: analytic (ik_mode 1) from the seed's and sampled last-joint
+ * values, else (ik_mode 0, or no in-limit analytic solution) damped least squares. */
+static void lift_ik(const or_problem *pr, const double T[16], uint32_t c0, int particle, uint32_t attempt,
+                    double *q) {
+    double seed[7];
+    perturbed_home(pr, c0, particle, TAG_IKSEED, attempt, 0.3, seed);
+    if (pr->ik_mode == 1) {
+        double q6[OR_IK_Q6];
+        q6_candidates(pr, c0, particle, attempt, seed[6], q6);
+        if (or_ik_select(pr, T, seed, q6, OR_IK_Q6, q)) return;
+    }
+    or_ik(pr, T, seed, q);
+}
+
 /* Lift (Sec. III-B): IK at the grasp of each block's initial pose and at its placement,
  * one intermediate waypoint per segment (q_home perturbed, standing in for a retract
  * configuration), then linear interpolation start -> via -> goal over the segment. */
@@ -1103,14 +1277,12 @@ void or_lift(const or_problem *pr, const double *place, int particle, uint32_t a
     for (int b = 0; b < B; ++b) {
         uint32_t k[4];
         philox(pr, (uint32_t)b, (uint32_t)particle, TAG_GRASP, attempt, k);
-        double T[16], seed[7];
+        double T[16];
         grasp_target(pr, b, pr->init + 4 * b, (int)(k[0] & 3u), T);
-        perturbed_home(pr, (uint32_t)(2 * b), particle, TAG_IKSEED, attempt, 0.3, seed);
-        or_ik(pr, T, seed, q + 7 * t_grasp(pr, b));
+        lift_ik(pr, T, (uint32_t)(2 * b), particle, attempt, q + 7 * t_grasp(pr, b));
         if (p2p) continue;   /* one segment: no placement */
         grasp_target(pr, b, place + 4 * b, (int)(k[1] & 3u), T);
-        perturbed_home(pr, (uint32_t)(2 * b + 1), particle, TAG_IKSEED, attempt, 0.3, seed);
-        or_ik(pr, T, seed, q + 7 * t_place(pr, b));
+        lift_ik(pr, T, (uint32_t)(2 * b + 1), particle, attempt, q + 7 * t_place(pr, b));
     }
     int m = S / 2;
     for (int s = 0; s < (p2p ? 1 : 2 * B); ++s) {

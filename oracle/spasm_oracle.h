@@ -55,7 +55,13 @@ typedef struct {
     const int32_t *cell_start; /* B + 1 */
     const double *cell;        /* cell_start[B] x 2 */
     double cell_size, z_star;
+    /* lift IK: 0 = damped least squares from a perturbed home seed; 1 = analytic IK of the
+     * Franka joint layout over OR_IK_Q6 values of the last joint, nearest to that seed,
+     * damped least squares where no in-limit analytic solution exists */
+    int ik_mode;
 } or_problem;
+
+#define OR_IK_Q6 8   /* last-joint values tried per target by the analytic lift */
 
 enum { OR_KIND_TOWER = 0, OR_KIND_PACK = 1, OR_KIND_P2P = 2 };
 /* Point-to-point trajectory optimisation (kind 2, the paper's motion-planning use of stage
@@ -87,6 +93,10 @@ int    or_place_solve(const or_problem *pr, double *out, int *n_found, int *atte
 /* stage 2 (trajectory optimisation of Sec. III-B and the appendix) */
 int    or_n_configs(const or_problem *pr);
 void   or_ik(const or_problem *pr, const double target[16], const double q0[7], double q[7]);
+int    or_ik_analytic_supported(const or_problem *pr);
+int    or_ik_analytic(const or_problem *pr, const double target[16], double q6, double sol[8][7]);
+int    or_ik_select(const or_problem *pr, const double target[16], const double seed[7], const double *q6,
+                    int n_q6, double q[7]);
 void   or_lift(const or_problem *pr, const double *place, int particle, uint32_t attempt, double *q);
 int    or_n_residuals(const or_problem *pr);
 double or_traj_cost(const or_problem *pr, const double *q, const double *lam, double mu,
