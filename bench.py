@@ -289,6 +289,7 @@ def run_native(args, ws, rank, local):
         batched, served = run_forms(args, rank, overrides, peak)
     packing = run_packing(args, rank) if args.pack_seeds > 0 else None
     p2p = run_p2p(args, rank) if args.p2p_seeds > 0 else None
+    ik_modes = run_ik_modes(args, rank) if args.ik_seeds > 0 else None
 
     out = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
@@ -316,6 +317,7 @@ def run_native(args, ws, rank, local):
         "served": served,
         "packing": packing,
         "p2p": p2p,
+        "ik_modes": ik_modes,
         "gpu_launches": int(sum(s["kernel_launches"] for s in stats)),
         "clocks": clocks,
         "kernel_sources_sha256_16": kernel_hash(),
@@ -621,6 +623,62 @@ def run_reference(args, ws, rank, local):
             "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def run_ik_modes(args, rank):
+    """The lift's two IK forms on the 10-block tower: the lift alone (spasm_lift of the Q
+    trajectory particles, CUDA events, median of repeats) and whole solves (spasm_optimize)
+    with the analytic IK, per seed, with success and stage-2 attempts."""
+    import torch
+
+    from paper_2510_07674_gb300 import scenes
+    from paper_2510_07674_gb300 import spasm as S
+    out = {}
+    for mode in (0, 1):
+        wl = scenes.make_problem(WORKLOAD, seed=rank * 1000, ik_mode=mode)
+        pr = S.Problem(wl)
+        try:
+            place = torch.from_numpy(wl.scene.init.reshape(1, -1)).float().cuda().contiguous()
+            q = torch.zeros(wl.params.Q, pr.C, 8, device="cuda")
+            ms = []
+            for r in range(6):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                e0.record()
+                S.spasm_lift(pr, wl.params.Q, place, 1, r, q)
+                e1.record()
+                torch.cuda.synchronize()
+                ms.append(e0.elapsed_time(e1))
+            out[f"lift_ms_ik_mode{mode}"] = float(statistics.median(ms[1:]))
+        finally:
+            pr.close()
+    times, ok, att, lift = [], 0, [], []
+    for i in range(args.ik_seeds):
+        wl = scenes.make_problem(WORKLOAD, seed=rank * 1000 + i, ik_mode=1)
+        pr = S.Problem(wl, max_steps=args.max_steps)
+        try:
+            S.spasm_set_timing(pr, True)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record()
+            try:
+                S.spasm_optimize(pr)
+            except S.SpasmError as e:
+                if e.status != -4:
+                    raise
+            e1.record()
+            torch.cuda.synchronize()
+            st = S.spasm_get_stats(pr)
+            ok += int(st["n_success"] > 0)
+            times.append(e0.elapsed_time(e1))
+            att.append(st["traj_attempts"])
+            lift.append(st["ms_lift"])
+        finally:
+            pr.close()
+    out["analytic_solve"] = _summary(times, ok, att)
+    out["analytic_solve"]["lift_ms_mean"] = statistics.mean(lift) if lift else None
+    out["workload"] = WORKLOAD_DESC + "; lift with ik_mode 1 (analytic, Franka joint layout) vs 0 (damped least squares)"
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -637,6 +695,8 @@ def main():
     ap.add_argument("--serve-slots", type=int, default=8)
     ap.add_argument("--pack-seeds", type=int, default=12, help="seeds of the 5-block packing leg (0 = skip)")
     ap.add_argument("--p2p-seeds", type=int, default=10, help="seeds of the point-to-point leg (0 = skip)")
+    ap.add_argument("--ik-seeds", type=int, default=6,
+                    help="10-block solves with the analytic lift IK, after timing both lift forms (0 = skip)")
     ap.add_argument("--sweep", action="store_true", help="run the N x M stage-1 sweep instead of the benchmark")
     ap.add_argument("--sweep-workloads", nargs="*", default=["tetris5", "tetris8", "tower10"])
     ap.add_argument("--sweep-trials", type=int, default=5)

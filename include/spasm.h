@@ -111,8 +111,16 @@ typedef struct {
 /* Solver parameters (Alg. 1 and Sec. III-B): N sample / M optimised particles, P
  * returned solutions, Q trajectory particles, W waypoints per motion segment, step
  * counts, learning rates, weights of the appendix cost terms, augmented-Lagrangian
- * penalty schedule, IK iterations/damping, Philox seed, and the cap on total gradient
- * steps (30 000 in the paper's experiments, Sec. IV-C). */
+ * penalty schedule, IK iterations/damping, Philox seed, the cap on total gradient
+ * steps (30 000 in the paper's experiments, Sec. IV-C), and the lift's IK:
+ *   ik_mode 0: damped least squares (K_ik iterations, ik_damp) from a perturbed home seed;
+ *   ik_mode 1: analytic IK of the Franka joint layout (the paper lifts with an analytic
+ *              Franka IK, Sec. III-B): the last joint takes the seed's value and 7 draws
+ *              over its limits, every in-limit branch (up to 8 per value) is solved in
+ *              closed form and the one nearest the seed is kept; targets without one fall
+ *              back to damped least squares.  Needs twists (0, -pi/2, pi/2, pi/2, -pi/2,
+ *              pi/2, pi/2) and a_0 = a_1 = a_2 = a_5 = d_1 = d_3 = d_5 = d_6 = 0, else
+ *              create returns SPASM_ERR_INVALID. */
 typedef struct {
     int N, M, P, Q, W;
     int K_lin, K_quad, K_traj, K_al, K_ik;
@@ -121,6 +129,7 @@ typedef struct {
     double mu0, mu_max, ik_damp;
     uint64_t seed;
     int max_steps;
+    int ik_mode;
 } spasm_params;
 
 /* Validate and copy the problem to the device and allocate its working memory.

@@ -69,6 +69,22 @@ static void free_all(spasm_problem* pr) {
 
 extern "C" const char* spasm_last_error(void) { return g_last_error.c_str(); }
 
+// The joint layout the analytic lift IK solves (the Franka arm's): twists (0, -pi/2, pi/2,
+// pi/2, -pi/2, pi/2, pi/2), a_0 = a_1 = a_2 = a_5 = 0, d_1 = d_3 = d_5 = d_6 = 0, and an
+// elbow whose two links are not both of zero length.
+static bool franka_layout(const double* dh) {
+    const double h = 1.5707963267948966;
+    const double alpha[7] = {0.0, -h, h, h, -h, h, h};
+    for (int k = 0; k < 7; ++k)
+        if (std::fabs(dh[4 * k + 1] - alpha[k]) > 1e-9) return false;
+    for (int k : {0, 1, 2, 5})
+        if (dh[4 * k] != 0.0) return false;
+    for (int k : {1, 3, 5, 6})
+        if (dh[4 * k + 2] != 0.0) return false;
+    const double a3 = dh[12], a4 = dh[16], d2 = dh[10], d4 = dh[18];
+    return std::hypot(a3 * a4 + d2 * d4, d2 * a4 - a3 * d4) > 0.0;
+}
+
 extern "C" spasm_status spasm_create_problem(const spasm_robot* robot, const spasm_obstacles* obs,
                                              const spasm_goal* goal, const spasm_params* prm, void* cuda_stream,
                                              spasm_problem_t* out) {
@@ -90,6 +106,9 @@ extern "C" spasm_status spasm_create_problem(const spasm_robot* robot, const spa
         return fail(SPASM_ERR_INVALID, "need 1 <= P <= M and 1 <= Q");
     if (prm->K_lin < 1 || prm->K_quad < 0 || prm->K_traj < 1 || prm->K_ik < 0)
         return fail(SPASM_ERR_INVALID, "step counts must be positive");
+    if (prm->ik_mode != 0 && prm->ik_mode != 1) return fail(SPASM_ERR_INVALID, "ik_mode must be 0 or 1");
+    if (prm->ik_mode == 1 && !franka_layout(robot->dh))
+        return fail(SPASM_ERR_INVALID, "ik_mode 1 needs the Franka joint layout (alpha, zero a and d entries)");
     for (int i = 0; i < robot->n_spheres; ++i)
         if (robot->sphere_link[i] < 0 || robot->sphere_link[i] > 7) return fail(SPASM_ERR_INVALID, "sphere_link outside 0..7");
 
@@ -160,6 +179,7 @@ extern "C" spasm_status spasm_create_problem(const spasm_robot* robot, const spa
     sc.w_start = (float)prm->w_start; sc.w_arm = (float)prm->w_arm; sc.w_block = (float)prm->w_block;
     sc.w_path = (float)prm->w_path; sc.w_jl = (float)prm->w_jl;
     sc.mu0 = (float)prm->mu0; sc.mu_max = (float)prm->mu_max; sc.ik_damp = (float)prm->ik_damp;
+    sc.ik_mode = prm->ik_mode;
     sc.seed = prm->seed;
 
     // environment tables: cuboid = centre (+ bounding radius), then columns of R with half extents

@@ -52,6 +52,7 @@ struct Scalars {
     float eta_init, alpha, eta_traj, eps, eps_start;
     float w_stable, w_height, w_coll, w_start, w_arm, w_block, w_path, w_jl;
     float mu0, mu_max, ik_damp;
+    int ik_mode;                     // lift IK: 0 damped least squares, 1 analytic (Franka joint layout)
     unsigned long long seed;
     // packing goal (the appendix's Tetris problem), kind = kKindPack: block i is a polyomino
     // of unit cubes of edge cell_size centred at cell[cell_start[i] .. cell_start[i+1]) in
@@ -129,7 +130,7 @@ __device__ __forceinline__ U4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c
 // top 24 bits -> [0, 1): exact in binary32
 __device__ __forceinline__ float u01(uint32_t u) { return (float)(u >> 8) * (1.0f / 16777216.0f); }
 
-enum PhiloxTag : uint32_t { kTagSample = 0, kTagGrasp = 1, kTagIkSeed = 2, kTagVia = 3 };
+enum PhiloxTag : uint32_t { kTagSample = 0, kTagGrasp = 1, kTagIkSeed = 2, kTagVia = 3, kTagQ6 = 4 };
 
 // ------------------------------------------------------------------------------ warp helpers
 __device__ __forceinline__ float warp_sum(float v) {

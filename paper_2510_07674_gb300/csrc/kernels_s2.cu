@@ -1,147 +1,10 @@
-// Stage-2 kernels: lift (IK + waypoint initialisation), the fused trajectory
-// optimisation (one CTA per particle, every iteration inside one launch) and the FP64
-// feasibility check of returned solutions.
+// Stage-2 kernels: the fused trajectory optimisation (one CTA per particle, every
+// iteration inside one launch).  The lift that initialises it is in kernels_lift.cu.
 #include "launch_s2.h"
 #include "stage1.cuh"
 #include "stage2.cuh"
 
 namespace spasm {
-
-// ================================================================================== lift
-// Damped-least-squares IK (Wampler 1986): dq = J^T (J J^T + damp^2 I)^-1 e with
-//   e = (p* - p, 1/2 sum_c R[:,c] x R*[:,c]),  J_k = (z_k x (p - o_k), z_k),
-// solved by a 6x6 Cholesky factorisation (the system matrix is SPD thanks to damping).
-__device__ void ik_dls(const Scalars& sc, const float Rs[9], const float ps[3], float q[7]) {
-    for (int it = 0; it < sc.K_ik; ++it) {
-        float R[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1}, o[3] = {0, 0, 0};
-        float z[7][3], org[7][3];
-        for (int k = 0; k < 7; ++k) {
-            float s, c;
-            sincosf(sc.th0[k] + q[k], &s, &c);
-            dh_step<float>(R, o, sc.ca[k], sc.sa[k], sc.a[k], sc.d[k], c, s);
-            z[k][0] = R[2]; z[k][1] = R[5]; z[k][2] = R[8];
-            org[k][0] = o[0]; org[k][1] = o[1]; org[k][2] = o[2];
-        }
-        float Rt[9], pt[3];
-        tool_frame<float>(sc, R, o, Rt, pt);
-        float e[6];
-        e[0] = ps[0] - pt[0]; e[1] = ps[1] - pt[1]; e[2] = ps[2] - pt[2];
-        e[3] = e[4] = e[5] = 0.f;
-        for (int c = 0; c < 3; ++c) {
-            const float a0 = Rt[c], a1 = Rt[3 + c], a2 = Rt[6 + c];
-            const float b0 = Rs[c], b1 = Rs[3 + c], b2 = Rs[6 + c];
-            e[3] += 0.5f * (a1 * b2 - a2 * b1);
-            e[4] += 0.5f * (a2 * b0 - a0 * b2);
-            e[5] += 0.5f * (a0 * b1 - a1 * b0);
-        }
-        float J[6][7];
-        for (int k = 0; k < 7; ++k) {
-            const float rx = pt[0] - org[k][0], ry = pt[1] - org[k][1], rz = pt[2] - org[k][2];
-            J[0][k] = z[k][1] * rz - z[k][2] * ry;
-            J[1][k] = z[k][2] * rx - z[k][0] * rz;
-            J[2][k] = z[k][0] * ry - z[k][1] * rx;
-            J[3][k] = z[k][0]; J[4][k] = z[k][1]; J[5][k] = z[k][2];
-        }
-        // Cholesky of A = J J^T + damp^2 I (lower triangle L)
-        float L[6][6];
-        for (int i = 0; i < 6; ++i)
-            for (int j = 0; j <= i; ++j) {
-                float s = 0.f;
-                for (int k = 0; k < 7; ++k) s += J[i][k] * J[j][k];
-                if (i == j) s += sc.ik_damp * sc.ik_damp;
-                for (int k = 0; k < j; ++k) s -= L[i][k] * L[j][k];
-                L[i][j] = (i == j) ? sqrtf(fmaxf(s, 1e-30f)) : s / L[j][j];
-            }
-        float y[6];
-        for (int i = 0; i < 6; ++i) {
-            float s = e[i];
-            for (int k = 0; k < i; ++k) s -= L[i][k] * y[k];
-            y[i] = s / L[i][i];
-        }
-        for (int i = 5; i >= 0; --i) {
-            float s = y[i];
-            for (int k = i + 1; k < 6; ++k) s -= L[k][i] * y[k];
-            y[i] = s / L[i][i];
-        }
-        for (int k = 0; k < 7; ++k) {
-            float dq = 0.f;
-            for (int i = 0; i < 6; ++i) dq += J[i][k] * y[i];
-            q[k] = fminf(fmaxf(q[k] + dq, sc.qlo[k]), sc.qhi[k]);
-        }
-    }
-}
-
-__device__ __forceinline__ void perturbed_home(const Scalars& sc, uint32_t c0, int p, uint32_t tag, uint32_t attempt,
-                                               float amp, float q[7]) {
-    const U4 a = philox4x32_10(2u * c0, (uint32_t)p, tag, attempt, sc.seed);
-    const U4 b = philox4x32_10(2u * c0 + 1u, (uint32_t)p, tag, attempt, sc.seed);
-    const float u[7] = {u01(a.x), u01(a.y), u01(a.z), u01(a.w), u01(b.x), u01(b.y), u01(b.z)};
-    for (int j = 0; j < 7; ++j) q[j] = fminf(fmaxf(sc.q_home[j] + amp * (2.f * u[j] - 1.f), sc.qlo[j]), sc.qhi[j]);
-}
-
-// one thread per (particle, block, grasp|place)
-__global__ void k_lift_ik(const __grid_constant__ Scalars sc, int n, const float* __restrict__ place, int np,
-                          uint32_t attempt, float* __restrict__ q) {
-    const int gid = blockIdx.x * blockDim.x + threadIdx.x;
-    const int B = sc.B;
-    if (gid >= n * 2 * B) return;
-    if (np <= 0) return;
-    const int p = gid / (2 * B), r = gid % (2 * B), b = r >> 1, which = r & 1;
-    if (which == 1 && sc.kind == kKindP2P) return;   // point to point: no placement
-    const U4 kk = philox4x32_10((uint32_t)b, (uint32_t)p, kTagGrasp, attempt, sc.seed);
-    float pose[4];
-    if (which == 0) {
-        pose[0] = sc.init[b].x; pose[1] = sc.init[b].y; pose[2] = sc.init[b].z; pose[3] = sc.init[b].w;
-    } else {
-        const float* src = place + ((size_t)(p % np) * B + b) * 4;
-        pose[0] = src[0]; pose[1] = src[1]; pose[2] = src[2]; pose[3] = src[3];
-    }
-    const int k = (int)((which == 0 ? kk.x : kk.y) & 3u);
-    float s, c;
-    sincosf(pose[3] + 0.5f * kPi * (float)k, &s, &c);
-    // tool target: Rz(yaw) Rx(pi), at the block's top face (+grasp offset)
-    const float Rs[9] = {c, s, 0.f, s, -c, 0.f, 0.f, 0.f, -1.f};
-    const float ps[3] = {pose[0], pose[1], pose[2] + sc.half[b].z + sc.grasp_off};
-    float qq[7];
-    perturbed_home(sc, (uint32_t)(2 * b + which), p, kTagIkSeed, attempt, 0.3f, qq);
-    ik_dls(sc, Rs, ps, qq);
-    const int t = which == 0 ? t_grasp(sc.S, b) : t_place(sc.S, b);
-    float* dst = q + ((size_t)p * sc.C + t) * 8;
-    for (int j = 0; j < 7; ++j) dst[j] = qq[j];
-    dst[7] = 0.f;
-}
-
-// one thread per (particle, configuration): home, or linear interpolation
-// start -> via -> goal within the configuration's segment
-__global__ void k_lift_interp(const __grid_constant__ Scalars sc, int n, int np, uint32_t attempt,
-                              float* __restrict__ q) {
-    const int gid = blockIdx.x * blockDim.x + threadIdx.x;
-    if (gid >= n * sc.C) return;
-    if (np <= 0) return;
-    const int p = gid / sc.C, t = gid % sc.C, S = sc.S;
-    float* dst = q + ((size_t)p * sc.C + t) * 8;
-    if (t == 0) {
-        for (int j = 0; j < 7; ++j) dst[j] = sc.q_home[j];
-        dst[7] = 0.f;
-        return;
-    }
-    const int jj = t % S;
-    if (jj == 0) return;   // segment endpoint, written by the IK kernel
-    const int s = t / S, m = S / 2;
-    float via[7];
-    perturbed_home(sc, (uint32_t)s, p, kTagVia, attempt, 0.3f, via);
-    // segment 0 starts at home; this launch writes that row itself (t == 0 above), so it is
-    // taken from the constants rather than read back from q
-    const float* qa = s == 0 ? sc.q_home : q + ((size_t)p * sc.C + s * S) * 8;
-    const float* qb = q + ((size_t)p * sc.C + (s + 1) * S) * 8;
-    for (int j = 0; j < 7; ++j) {
-        float v;
-        if (jj <= m) v = qa[j] + ((float)jj / (float)m) * (via[j] - qa[j]);
-        else v = via[j] + ((float)(jj - m) / (float)(S - m)) * (qb[j] - via[j]);
-        dst[j] = v;
-    }
-    dst[7] = 0.f;
-}
 
 // ================================================================================== trajopt
 constexpr int kTWarps = 8;
@@ -1155,18 +1018,6 @@ __global__ void __launch_bounds__(kTThreads, 2) k_traj_batch(const TrajJob* __re
 }
 
 // ================================================================================== launchers
-cudaError_t launch_lift(const Scalars& sc, int n, const float* place, int n_place, uint32_t attempt, float* q,
-                        cudaStream_t st) {
-    if (n <= 0) return cudaSuccess;
-    const int n_ik = n * 2 * sc.B;
-    k_lift_ik<<<(n_ik + 127) / 128, 128, 0, st>>>(sc, n, place, n_place, attempt, q);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    const int n_cfg = n * sc.C;
-    k_lift_interp<<<(n_cfg + 255) / 256, 256, 0, st>>>(sc, n, n_place, attempt, q);
-    return cudaGetLastError();
-}
-
 cudaError_t launch_traj_batch(const TrajJob* jobs, int n_jobs, int n_items, int per_fetch, int mode, int* next,
                               size_t smem_bytes, int grid, cudaStream_t st) {
     if (n_items <= 0) return cudaSuccess;

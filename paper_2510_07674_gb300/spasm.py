@@ -69,7 +69,7 @@ _DBL_PARAMS = ("eta_init", "alpha", "eta_traj", "eps", "eps_start", "w_stable", 
 
 class _Params(ctypes.Structure):
     _fields_ = ([(n, ctypes.c_int) for n in _INT_PARAMS] + [(n, ctypes.c_double) for n in _DBL_PARAMS] +
-                [("seed", ctypes.c_uint64), ("max_steps", ctypes.c_int)])
+                [("seed", ctypes.c_uint64), ("max_steps", ctypes.c_int), ("ik_mode", ctypes.c_int)])
 
 
 class _Stats(ctypes.Structure):
@@ -184,6 +184,7 @@ class ProblemDesc:
             setattr(p, n, float(prm[n]))
         p.seed = int(prm["seed"]) & 0xFFFFFFFFFFFFFFFF
         p.max_steps = int(prm["max_steps"])
+        p.ik_mode = int(prm.get("ik_mode", 0))
         self._params = p
         self.B = len(a["half"])
         self.C = 2 * self.B * (int(prm["W"]) - 1) + 1

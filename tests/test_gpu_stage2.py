@@ -107,6 +107,51 @@ def test_lift_matches_oracle():
     # different branches; the same branch is reached almost everywhere
     assert converged >= n and matched >= 0.95 * converged, (matched, converged)
 
+@pytest.mark.parametrize("name,n,sample", [("tower4", 64, 64), ("tower10", 4096, 24)])
+def test_analytic_lift_matches_oracle(name, n, sample):
+    """ik_mode 1: every IK endpoint the oracle solves in closed form (tool pose exact) is
+    the same branch on the GPU to FP32 rounding, except where two branches lie nearly
+    equally far from the seed; there the GPU's endpoint still reaches the target.  tower10
+    runs the full 4096-particle lift of the benchmark and checks a sample of particles."""
+    S = _S()
+    wl = scenes.make_problem(name, seed=4, ik_mode=1)
+    orc = O.Oracle(wl)
+    pr = S.Problem(wl)
+    S_ = wl.params.W - 1
+    place_h = wl.scene.init.copy()
+    place_h[:, 0] += 0.04
+    place_h[:, 3] += 0.25
+    place = torch.from_numpy(place_h.reshape(1, -1)).float().cuda().contiguous()
+    q = torch.zeros(n, pr.C, 8, device="cuda")
+    S.spasm_lift(pr, n, place, 1, 1, q)
+    torch.cuda.synchronize()
+    ps = place.cpu().double().numpy().reshape(pr.B, 4)
+    exact = matched = 0
+    for p in np.linspace(0, n - 1, sample).astype(int):
+        qo = orc.lift(ps, int(p), attempt=1)
+        qg = q[p, :, :7].cpu().double().numpy()
+        for b in range(pr.B):
+            for t, pose in (((2 * b + 1) * S_, wl.scene.init[b]), ((2 * b + 2) * S_, ps[b])):
+                _, T = orc.fk(qo[t])
+                target = np.array(pose[:3]) + [0, 0, wl.scene.half[b, 2] + wl.scene.grasp_off]
+                if np.linalg.norm(T[:3, 3] - target) < 1e-9 and T[2, 2] < -1 + 1e-12:
+                    exact += 1
+                    matched += np.abs(qg[t] - qo[t]).max() < 2e-3
+                    _, Tg = orc.fk(qg[t])
+                    assert np.linalg.norm(Tg[:3, 3] - target) < 1e-4 and Tg[2, 2] < -1 + 1e-6, (p, b, t)
+    assert exact >= 0.9 * sample * 2 * pr.B and matched >= 0.98 * exact, (matched, exact)
+
+
+def test_analytic_lift_rejects_other_joint_layouts():
+    S = _S()
+    wl = scenes.make_problem("tower1", seed=0, ik_mode=1)
+    wl.robot.dh[2, 0] = 0.02          # an elbow offset the closed form does not cover
+    with pytest.raises(S.SpasmError, match="ik_mode 1"):
+        S.Problem(wl)
+    wl.params.ik_mode = 0             # damped least squares takes any layout
+    S.Problem(wl).close()
+
+
 def test_descend_matches_oracle_few_steps():
     S = _S()
     wl, orc, _, qs = _cases("tower1", 4, 6, 0.05)
