@@ -115,10 +115,10 @@ typedef struct {
  * steps (30 000 in the paper's experiments, Sec. IV-C), and the lift's IK:
  *   ik_mode 0: damped least squares (K_ik iterations, ik_damp) from a perturbed home seed;
  *   ik_mode 1: analytic IK of the Franka joint layout (the paper lifts with an analytic
- *              Franka IK, Sec. III-B): the last joint takes the seed's value and 7 draws
- *              over its limits, every in-limit branch (up to 8 per value) is solved in
- *              closed form and the one nearest the seed is kept; targets without one fall
- *              back to damped least squares.  Needs twists (0, -pi/2, pi/2, pi/2, -pi/2,
+ *              Franka IK, Sec. III-B): the last joint takes the seed's value and one draw
+ *              in each of 31 equal strips of its limit range, every in-limit branch (up to
+ *              8 per value) is solved in closed form and the one nearest the seed is kept;
+ *              targets without one fall back to damped least squares.  Needs twists (0, -pi/2, pi/2, pi/2, -pi/2,
  *              pi/2, pi/2) and a_0 = a_1 = a_2 = a_5 = d_1 = d_3 = d_5 = d_6 = 0, else
  *              create returns SPASM_ERR_INVALID. */
 typedef struct {

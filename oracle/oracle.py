@@ -95,6 +95,7 @@ def lib():
         L.or_ik_analytic.argtypes = [P, _D, ctypes.c_double, _D]
         L.or_ik_select.argtypes = [P, _D, _D, _D, ctypes.c_int, _D]
         L.or_lift.argtypes = [P, _D, ctypes.c_int, ctypes.c_uint32, _D]
+        L.or_lift_ex.argtypes = [P, _D, ctypes.c_int, ctypes.c_uint32, _D, _I]
         L.or_traj_cost.restype = ctypes.c_double
         L.or_n_residuals.argtypes = [P]
         L.or_traj_cost.argtypes = [P, _D, _D, ctypes.c_double, _D, _D, _D, _D, _D]
@@ -270,6 +271,15 @@ class Oracle:
         q = np.zeros((self.C, 7))
         lib().or_lift(self.ptr, _dp(p), int(particle), int(attempt), _dp(q))
         return q
+
+    def lift_methods(self, place, particle: int, attempt: int = 0):
+        """(q, analytic): the lift and, per block, whether its grasp / place configuration
+        came from the analytic IK (B x 2 booleans)."""
+        p = _f64(place).reshape(self.B, 4)
+        q = np.zeros((self.C, 7))
+        flags = np.zeros(2 * self.B, np.int32)
+        lib().or_lift_ex(self.ptr, _dp(p), int(particle), int(attempt), _dp(q), flags.ctypes.data_as(_I))
+        return q, flags.reshape(self.B, 2).astype(bool)
 
     def traj_cost(self, q, lam=None, mu=None, grad: bool = True):
         """L, dL/dq (C x 7), appendix terms (6), path, jl, residuals h (NR)."""

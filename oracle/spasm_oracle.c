@@ -1241,48 +1241,58 @@ int or_ik_select(const or_problem *pr, const double target[16], const double see
     return best < INFINITY;
 }
 
-/* Candidate values of the last joint for one IK target: the seed's own value, then
- * OR_IK_Q6 - 1 uniform draws over its limits (Philox counter (2 c0 + i/4, particle,
- * TAG_Q6, attempt), word i mod 4). */
+/* Candidate values of the last joint for one IK target: the seed's own value, then one
+ * uniform draw in each of OR_IK_Q6 - 1 equal strips of its limit range, strip i taking
+ * word i mod 4 of the Philox counter (8 c0 + i/4, particle, TAG_Q6, attempt). */
 static void q6_candidates(const or_problem *pr, uint32_t c0, int particle, uint32_t attempt, double seed6,
                           double q6[OR_IK_Q6]) {
-    uint32_t u[8];
-    philox(pr, 2u * c0, (uint32_t)particle, TAG_Q6, attempt, u);
-    philox(pr, 2u * c0 + 1u, (uint32_t)particle, TAG_Q6, attempt, u + 4);
+    const int n = OR_IK_Q6 - 1;
+    uint32_t u[4 * ((OR_IK_Q6 + 2) / 4)];
+    for (int w = 0; 4 * w < n; ++w) philox(pr, 8u * c0 + (uint32_t)w, (uint32_t)particle, TAG_Q6, attempt, u + 4 * w);
     const double lo = pr->qlim[12], hi = pr->qlim[13];
     q6[0] = seed6;
-    for (int i = 1; i < OR_IK_Q6; ++i) q6[i] = lo + or_u01(u[i - 1]) * (hi - lo);
+    for (int i = 0; i < n; ++i) q6[1 + i] = lo + (((double)i + or_u01(u[i])) / (double)n) * (hi - lo);
 }
 
-/* IK of one lift target: analytic (ik_mode 1) from the seed's and sampled last-joint
- * values, else (ik_mode 0, or no in-limit analytic solution) damped least squares. */
-static void lift_ik(const or_problem *pr, const double T[16], uint32_t c0, int particle, uint32_t attempt,
-                    double *q) {
+/* IK of one lift target: analytic (ik_mode 1) over the seed's and the stratified last-joint
+ * values, else (ik_mode 0, or no in-limit analytic solution) damped least squares.
+ * Returns 1 where the analytic solution was taken. */
+static int lift_ik(const or_problem *pr, const double T[16], uint32_t c0, int particle, uint32_t attempt,
+                   double *q) {
     double seed[7];
     perturbed_home(pr, c0, particle, TAG_IKSEED, attempt, 0.3, seed);
     if (pr->ik_mode == 1) {
         double q6[OR_IK_Q6];
         q6_candidates(pr, c0, particle, attempt, seed[6], q6);
-        if (or_ik_select(pr, T, seed, q6, OR_IK_Q6, q)) return;
+        if (or_ik_select(pr, T, seed, q6, OR_IK_Q6, q)) return 1;
     }
     or_ik(pr, T, seed, q);
+    return 0;
 }
 
 /* Lift (Sec. III-B): IK at the grasp of each block's initial pose and at its placement,
  * one intermediate waypoint per segment (q_home perturbed, standing in for a retract
  * configuration), then linear interpolation start -> via -> goal over the segment. */
 void or_lift(const or_problem *pr, const double *place, int particle, uint32_t attempt, double *q) {
+    or_lift_ex(pr, place, particle, attempt, q, NULL);
+}
+
+void or_lift_ex(const or_problem *pr, const double *place, int particle, uint32_t attempt, double *q,
+                int32_t *analytic) {
     const int B = pr->B, S = pr->W - 1, p2p = pr->kind == OR_KIND_P2P;
     memcpy(q, pr->q_home, 7 * sizeof(double));
     for (int b = 0; b < B; ++b) {
         uint32_t k[4];
         philox(pr, (uint32_t)b, (uint32_t)particle, TAG_GRASP, attempt, k);
         double T[16];
+        int how;
         grasp_target(pr, b, pr->init + 4 * b, (int)(k[0] & 3u), T);
-        lift_ik(pr, T, (uint32_t)(2 * b), particle, attempt, q + 7 * t_grasp(pr, b));
+        how = lift_ik(pr, T, (uint32_t)(2 * b), particle, attempt, q + 7 * t_grasp(pr, b));
+        if (analytic) analytic[2 * b] = how;
         if (p2p) continue;   /* one segment: no placement */
         grasp_target(pr, b, place + 4 * b, (int)(k[1] & 3u), T);
-        lift_ik(pr, T, (uint32_t)(2 * b + 1), particle, attempt, q + 7 * t_place(pr, b));
+        how = lift_ik(pr, T, (uint32_t)(2 * b + 1), particle, attempt, q + 7 * t_place(pr, b));
+        if (analytic) analytic[2 * b + 1] = how;
     }
     int m = S / 2;
     for (int s = 0; s < (p2p ? 1 : 2 * B); ++s) {

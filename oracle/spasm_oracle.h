@@ -56,12 +56,13 @@ typedef struct {
     const double *cell;        /* cell_start[B] x 2 */
     double cell_size, z_star;
     /* lift IK: 0 = damped least squares from a perturbed home seed; 1 = analytic IK of the
-     * Franka joint layout over OR_IK_Q6 values of the last joint, nearest to that seed,
+     * Franka joint layout over OR_IK_Q6 values of the last joint (the seed's and one
+     * draw per equal strip of its range), the in-limit solution nearest to that seed,
      * damped least squares where no in-limit analytic solution exists */
     int ik_mode;
 } or_problem;
 
-#define OR_IK_Q6 8   /* last-joint values tried per target by the analytic lift */
+#define OR_IK_Q6 32  /* last-joint values tried per target by the analytic lift */
 
 enum { OR_KIND_TOWER = 0, OR_KIND_PACK = 1, OR_KIND_P2P = 2 };
 /* Point-to-point trajectory optimisation (kind 2, the paper's motion-planning use of stage
@@ -98,6 +99,10 @@ int    or_ik_analytic(const or_problem *pr, const double target[16], double q6, 
 int    or_ik_select(const or_problem *pr, const double target[16], const double seed[7], const double *q6,
                     int n_q6, double q[7]);
 void   or_lift(const or_problem *pr, const double *place, int particle, uint32_t attempt, double *q);
+/* or_lift, and where analytic != NULL, 2B flags: 1 where the grasp (2b) / place (2b+1)
+ * configuration of block b came from the analytic IK, 0 where damped least squares */
+void   or_lift_ex(const or_problem *pr, const double *place, int particle, uint32_t attempt, double *q,
+                  int32_t *analytic);
 int    or_n_residuals(const or_problem *pr);
 double or_traj_cost(const or_problem *pr, const double *q, const double *lam, double mu,
                     double *grad, double c_groups[OR_NG], double *path, double *jl, double *h);

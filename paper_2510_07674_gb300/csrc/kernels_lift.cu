@@ -207,18 +207,25 @@ __device__ void ik_analytic_nearest(const Scalars& sc, const float Rs[9], const 
     }
 }
 
-// Analytic lift of one target: the last joint takes the seed's value, then 7 draws over its
-// limits (Philox counter (2 c0 + i/4, particle, kTagQ6, attempt), word i mod 4).  On success
-// q holds the in-limit solution nearest the seed (first found on ties) and true is returned.
+// Analytic lift of one target: the last joint takes the seed's value, then one uniform draw
+// in each of kQ6Strips equal strips of its limit range (strip i: word i mod 4 of the Philox
+// counter (8 c0 + i/4, particle, kTagQ6, attempt)).  On success q holds the in-limit solution
+// nearest the seed (first found on ties) and true is returned.
+constexpr int kQ6Strips = 31;
+
 __device__ bool ik_analytic_lift(const Scalars& sc, const float Rs[9], const float ps[3], uint32_t c0, int p,
                                  uint32_t attempt, const float seed[7], float q[7]) {
-    const U4 a = philox4x32_10(2u * c0, (uint32_t)p, kTagQ6, attempt, sc.seed);
-    const U4 b = philox4x32_10(2u * c0 + 1u, (uint32_t)p, kTagQ6, attempt, sc.seed);
-    const uint32_t u[7] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z};
     float best_d = INFINITY;
     ik_analytic_nearest(sc, Rs, ps, seed[6], seed, q, best_d);
-    for (int i = 0; i < 7; ++i)
-        ik_analytic_nearest(sc, Rs, ps, sc.qlo[6] + u01(u[i]) * (sc.qhi[6] - sc.qlo[6]), seed, q, best_d);
+    const float lo = sc.qlo[6], span = sc.qhi[6] - sc.qlo[6];
+    for (int w = 0; 4 * w < kQ6Strips; ++w) {
+        const U4 r = philox4x32_10(8u * c0 + (uint32_t)w, (uint32_t)p, kTagQ6, attempt, sc.seed);
+        const uint32_t u[4] = {r.x, r.y, r.z, r.w};
+        for (int j = 0; j < 4 && 4 * w + j < kQ6Strips; ++j) {
+            const float strip = ((float)(4 * w + j) + u01(u[j])) / (float)kQ6Strips;
+            ik_analytic_nearest(sc, Rs, ps, lo + strip * span, seed, q, best_d);
+        }
+    }
     return best_d < INFINITY;
 }
 

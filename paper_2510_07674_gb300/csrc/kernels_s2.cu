@@ -307,6 +307,16 @@ __device__ __forceinline__ void chunk_collisions(const Scalars& sc, const LaneSp
         const int b = seg >> 1, jj = r + 1;
         const bool held = (seg & 1) && jj < S;
         const int n_items = sc.n_rsph + (held ? 8 : 0);
+        // candidates of this configuration: environment (any mask bit), context blocks placed
+        // (k < b, movable) and not yet moved (k > b).  Without any, its collision terms and
+        // their gradient are zero and the sphere centres are not needed.
+        const bool env_c = tw.envany[ci] != 0u;
+        const unsigned below = (1u << b) - 1u;
+        const unsigned ctx = (tw.bmask[0][ci] & below) | (tw.bmask[1][ci] & ~below & ~(1u << b));
+        if (!env_c && ctx == 0u) {
+            if (grad && lane < 16 && (lane & 7) != 7) (lane < 8 ? G_arm : G_blk)[t * 8 + (lane & 7)] = 0.f;
+            continue;
+        }
         sphere_centres(sc, ls, tw.F[ci], tw.H[ci], n_items, b, cx, cy, cz, rr, act, isblk);
         float gx[kSlots], gy[kSlots], gz[kSlots], pen_sum[kSlots];
 #pragma unroll
@@ -314,7 +324,6 @@ __device__ __forceinline__ void chunk_collisions(const Scalars& sc, const LaneSp
         bool any_hit = false;
         int visits = 0;
 
-        const bool env_c = tw.envany[ci] != 0u;
         for (int wd = 0; wd < (env_c ? n_cw : 0); ++wd) {
             unsigned m = tw.cmask[ci][wd];
             visits += __popc(m);
@@ -363,10 +372,9 @@ __device__ __forceinline__ void chunk_collisions(const Scalars& sc, const LaneSp
                 }
             }
         }
-        // context blocks: placed (k < b, movable) and not yet moved (k > b)
+        // context blocks
         {
-            const unsigned below = (1u << b) - 1u;
-            unsigned m = (tw.bmask[0][ci] & below) | (tw.bmask[1][ci] & ~below & ~(1u << b));
+            unsigned m = ctx;
             visits += __popc(m);
             while (m) {
                 const int kb = __ffs(m) - 1;

@@ -109,15 +109,18 @@ def test_lift_matches_oracle():
 
 @pytest.mark.parametrize("name,n,sample", [("tower4", 64, 64), ("tower10", 4096, 24)])
 def test_analytic_lift_matches_oracle(name, n, sample):
-    """ik_mode 1: every IK endpoint the oracle solves in closed form (tool pose exact) is
-    the same branch on the GPU to FP32 rounding, except where two branches lie nearly
-    equally far from the seed; there the GPU's endpoint still reaches the target.  tower10
-    runs the full 4096-particle lift of the benchmark and checks a sample of particles."""
+    """ik_mode 1: every IK endpoint the oracle solves in closed form is the same branch on
+    the GPU to FP32 rounding, except where two branches lie nearly equally far from the
+    seed (the GPU's endpoint is then another exact solution) or where FP32 loses the last
+    in-limit solution at a limit or at the edge of reach (the GPU then falls back to damped
+    least squares, as the oracle does where it finds none).  tower10 runs the full
+    4096-particle lift of the benchmark and checks a sample of particles."""
     S = _S()
     wl = scenes.make_problem(name, seed=4, ik_mode=1)
     orc = O.Oracle(wl)
     pr = S.Problem(wl)
     S_ = wl.params.W - 1
+    lo, hi = wl.robot.qlim[:, 0], wl.robot.qlim[:, 1]
     place_h = wl.scene.init.copy()
     place_h[:, 0] += 0.04
     place_h[:, 3] += 0.25
@@ -126,20 +129,24 @@ def test_analytic_lift_matches_oracle(name, n, sample):
     S.spasm_lift(pr, n, place, 1, 1, q)
     torch.cuda.synchronize()
     ps = place.cpu().double().numpy().reshape(pr.B, 4)
-    exact = matched = 0
+    analytic = matched = other_branch = 0
     for p in np.linspace(0, n - 1, sample).astype(int):
-        qo = orc.lift(ps, int(p), attempt=1)
+        qo, how = orc.lift_methods(ps, int(p), attempt=1)
         qg = q[p, :, :7].cpu().double().numpy()
         for b in range(pr.B):
-            for t, pose in (((2 * b + 1) * S_, wl.scene.init[b]), ((2 * b + 2) * S_, ps[b])):
+            for which, t in enumerate(((2 * b + 1) * S_, (2 * b + 2) * S_)):
+                if not how[b, which]:
+                    continue
+                analytic += 1
+                if np.abs(qg[t] - qo[t]).max() < 2e-3:
+                    matched += 1
+                    continue
                 _, T = orc.fk(qo[t])
-                target = np.array(pose[:3]) + [0, 0, wl.scene.half[b, 2] + wl.scene.grasp_off]
-                if np.linalg.norm(T[:3, 3] - target) < 1e-9 and T[2, 2] < -1 + 1e-12:
-                    exact += 1
-                    matched += np.abs(qg[t] - qo[t]).max() < 2e-3
-                    _, Tg = orc.fk(qg[t])
-                    assert np.linalg.norm(Tg[:3, 3] - target) < 1e-4 and Tg[2, 2] < -1 + 1e-6, (p, b, t)
-    assert exact >= 0.9 * sample * 2 * pr.B and matched >= 0.98 * exact, (matched, exact)
+                _, Tg = orc.fk(qg[t])
+                if np.abs(Tg - T).max() < 1e-4 and np.all(qg[t] >= lo - 1e-6) and np.all(qg[t] <= hi + 1e-6):
+                    other_branch += 1
+    assert analytic >= 0.95 * sample * 2 * pr.B, analytic
+    assert matched >= 0.98 * analytic and matched + other_branch >= 0.99 * analytic, (matched, other_branch, analytic)
 
 
 def test_analytic_lift_rejects_other_joint_layouts():
