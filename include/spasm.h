@@ -261,6 +261,9 @@ typedef struct {
     long long d2h_bytes;       /* device -> host bytes copied by place / optimize / result */
     long long tests_executed;  /* sphere-obstacle tests run by the trajectory kernels after the
                                   exact box cull (pairs whose boxes are disjoint are skipped) */
+    long long cull_configs;    /* configurations whose kinematics and cull the trajectory kernels
+                                  ran (the others kept a candidate-free cull from an earlier
+                                  iteration, valid while they moved less than its margin) */
 } spasm_stats;
 
 /* Replace the Philox seed (the key of every random stream) and forget previous results;

@@ -159,6 +159,37 @@ extern "C" spasm_status spasm_create_problem(const spasm_robot* robot, const spa
                                          (float)(0.5 * (hi[2] - lo[2]) + pad), 0.f)
                            : make_float4(-1.f, -1.f, -1.f, 0.f);
     }
+    {
+        // Joint j turns about the axis through the origin of frame j+1; a point of link l > j lies
+        // within sum_{k=j+1}^{l-1} |t_k| + |p| of that origin (t_k: origin of frame k+1 in frame
+        // k, |t_k| = hypot(a_k, d_k); p: the point in frame l), and a held-block sphere centre
+        // within |ee_p| + h_z + grasp_off + |h|/2 of frame 7's origin.  Moving one joint at a time,
+        // a point travels at most |dq_j| times its distance from axis j.
+        double reach[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        bool has[8] = {false, false, false, false, false, false, false, false};
+        for (int i = 0; i < robot->n_spheres; ++i) {
+            const double* v = robot->sphere + 4 * i;
+            const int l = robot->sphere_link[i];
+            reach[l] = std::fmax(reach[l], std::sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]));
+            has[l] = true;
+        }
+        const double* E = robot->ee;
+        double held = 0.0;
+        for (int i = 0; i < B; ++i) {
+            const double* h = goal->half_ext + 3 * i;
+            held = std::fmax(held, h[2] + goal->grasp_off + 0.5 * std::sqrt(h[0] * h[0] + h[1] * h[1] + h[2] * h[2]));
+        }
+        reach[7] = std::fmax(reach[7], std::sqrt(E[3] * E[3] + E[7] * E[7] + E[11] * E[11]) + held);
+        has[7] = true;
+        for (int j = 0; j < 7; ++j) {
+            double L = 0.0, path = 0.0;
+            for (int l = j + 1; l <= 7; ++l) {
+                if (l > j + 1) path += std::hypot(robot->dh[4 * (l - 1)], robot->dh[4 * (l - 1) + 2]);
+                if (has[l]) L = std::fmax(L, path + reach[l]);
+            }
+            sc.sweep[j] = (float)(L * (1.0 + 1e-5) + 1e-5);
+        }
+    }
     double z = goal->z_table;
     for (int i = 0; i < B; ++i) {
         const double* h = goal->half_ext + 3 * i;
@@ -270,7 +301,7 @@ extern "C" spasm_status spasm_create_problem(const spasm_robot* robot, const spa
     ALLOC(pr->d_cub64, (size_t)16 * sc.n_cub);
     ALLOC(pr->d_osph64, (size_t)4 * sc.n_osph);
     ALLOC(pr->d_rmet64, (size_t)6 * P);
-    ALLOC(pr->d_tests, 1);
+    ALLOC(pr->d_tests, 2);
     ALLOC(pr->d_sc, 1);
     ALLOC(pr->d_chkacc, P);
 #undef ALLOC
@@ -576,11 +607,12 @@ spasm_status spasm::finish_record(spasm_problem* pr, int found, bool finish_done
     pr->n_found = found;
     SPASM_TRY(check_device_error(pr));
     {
-        unsigned long long nt = 0;
-        SPASM_CUDA(cudaMemcpyAsync(&nt, pr->d_tests, sizeof nt, cudaMemcpyDeviceToHost, pr->stream));
+        unsigned long long nt[2] = {0, 0};
+        SPASM_CUDA(cudaMemcpyAsync(nt, pr->d_tests, sizeof nt, cudaMemcpyDeviceToHost, pr->stream));
         SPASM_CUDA(cudaStreamSynchronize(pr->stream));
         pr->stats.d2h_bytes += sizeof nt;
-        pr->stats.tests_executed += (long long)nt;
+        pr->stats.tests_executed += (long long)nt[0];
+        pr->stats.cull_configs += (long long)nt[1];
     }
     if (found > 0) {
         std::vector<int> succ(sc.P, 0);
@@ -607,7 +639,7 @@ extern "C" spasm_status spasm_optimize(spasm_problem_t pr) {
         if (st != SPASM_OK) return st;
     }
     if (pr->n_place <= 0) return fail(SPASM_ERR_NOSOLUTION, "no placements to lift");
-    SPASM_CUDA(cudaMemsetAsync(pr->d_tests, 0, sizeof(unsigned long long), pr->stream));
+    SPASM_CUDA(cudaMemsetAsync(pr->d_tests, 0, 2 * sizeof(unsigned long long), pr->stream));
     int found = 0;
     SPASM_TRY(traj_continue(pr, 0, 0, 0, &found));
     return finish_record(pr, found, false);

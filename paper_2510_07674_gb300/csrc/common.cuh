@@ -41,6 +41,9 @@ struct Scalars {
     int rlink[kMaxRobotSpheres];     // 0 = base
     float4 lbox_c[8], lbox_h[8];     // per link: box of its spheres in the link frame (centre, half
                                      // extents, slightly padded); half.x < 0 when the link has none
+    float sweep[7];                  // per joint: bound on the distance from its axis to any robot or
+                                     // held-block sphere centre it moves, so a step dq moves every
+                                     // such centre by at most sum_j |dq_j| sweep[j]
     // blocks in stack order
     float4 half[kMaxB];              // hx, hy, hz, sphere radius min(h)/2
     float4 init[kMaxB];              // x, y, z, yaw
@@ -141,6 +144,12 @@ __device__ __forceinline__ float warp_sum(float v) {
 __device__ __forceinline__ float warp_max(float v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+__device__ __forceinline__ float warp_min(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
     return v;
 }
 

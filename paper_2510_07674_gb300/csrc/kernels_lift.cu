@@ -154,6 +154,8 @@ __device__ void ik_analytic_nearest(const Scalars& sc, const float Rs[9], const 
         const float t3 = i3 == 0 ? phi + c_3 : phi - c_3;
         float s3, c3;
         sincosf(t3, &s3, &c3);
+        float q3, q4, q5;
+        if (!into_limits(sc, 3, t3, q3)) continue;   // each joint is rejected as soon as it is known
         const float ux = -a3 * c3 - d2 * s3 - a4, uy = a3 * s3 - d2 * c3 - d4;
         if (fabsf(uy) > rho) continue;
         const float c_5 = acosf(uy / rho);
@@ -161,10 +163,12 @@ __device__ void ik_analytic_nearest(const Scalars& sc, const float Rs[9], const 
         rot_xz(sc.ca[3], sc.sa[3], t3, R34);
         for (int i5 = 0; i5 < 2; ++i5) {
             const float t5 = i5 == 0 ? psi + c_5 : psi - c_5;
+            if (!into_limits(sc, 5, t5, q5)) continue;
             float s5, c5;
             sincosf(t5, &s5, &c5);
             const float sg = ux < 0.f ? -1.f : 1.f;
             const float t4 = atan2f(sg * w[2], sg * (c5 * w[0] - s5 * w[1]));
+            if (!into_limits(sc, 4, t4, q4)) continue;
             float R45[9], R56[9], R35[9], R36[9], R3[9];
             rot_xz(sc.ca[4], sc.sa[4], t4, R45);
             rot_xz(sc.ca[5], sc.sa[5], t5, R56);
@@ -178,7 +182,7 @@ __device__ void ik_analytic_nearest(const Scalars& sc, const float Rs[9], const 
             }
             const float sb = sqrtf(R3[2] * R3[2] + R3[5] * R3[5]);
             for (int sgn = 1; sgn >= -1; sgn -= 2) {
-                float th[6];
+                float th[3];
                 if (sb < 1e-6f) {                                         // t1 = 0: only t0 + t2 is fixed
                     if (sgn < 0) break;
                     th[0] = 0.f; th[1] = atan2f(0.f, R3[8]); th[2] = atan2f(R3[3], R3[0]);
@@ -188,12 +192,11 @@ __device__ void ik_analytic_nearest(const Scalars& sc, const float Rs[9], const 
                     th[0] = atan2f(g * R3[5], g * R3[2]);
                     th[2] = atan2f(g * R3[7], -g * R3[6]);
                 }
-                th[3] = t3; th[4] = t4; th[5] = t5;
                 float q[7];
                 bool ok = true;
-                for (int k = 0; k < 6 && ok; ++k) ok = into_limits(sc, k, th[k], q[k]);
+                for (int k = 0; k < 3 && ok; ++k) ok = into_limits(sc, k, th[k], q[k]);
                 if (!ok) continue;
-                q[6] = q6;
+                q[3] = q3; q[4] = q4; q[5] = q5; q[6] = q6;
                 float d = 0.f;
 #pragma unroll
                 for (int j = 0; j < 7; ++j) d += (q[j] - seed[j]) * (q[j] - seed[j]);

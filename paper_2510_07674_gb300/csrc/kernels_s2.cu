@@ -13,6 +13,14 @@ constexpr int kSlots = 2;   // sphere items per lane: up to 56 robot + 8 held-bl
 
 constexpr int kChunk = 4;   // configurations whose kinematics one warp evaluates together
 
+// Cached cull.  When a chunk's cull finds no candidate for any of its configurations, it
+// also returns the chunk's clearance: the smallest separation (largest per-axis gap) between
+// any of its link boxes and any obstacle or block box that could touch it.  Later iterations
+// skip the chunk (kinematics, cull and tests: its terms are zero) while the bound on how far
+// its spheres moved since, plus how far the placed blocks moved, stays below the clearance,
+// so the skipped work is exactly the work whose result is zero.
+constexpr float kClearSlack = 1e-5f;   // FP32 rounding of the boxes, metres
+
 struct TWarp {
     float4 F[kChunk][8][3];  // frames 0..7 of each configuration of the chunk: rows (R_i0, R_i1, R_i2, o_i)
     float4 H[kChunk][3];     // held-block frame of each configuration (same row layout)
@@ -48,6 +56,9 @@ struct TShared {
     float th0[8];            // joint offsets
     float4 lbc[8], lbh[8];   // link-frame boxes of each link's spheres (centre, half extents)
     float s_arm, s_blk, mu, L;
+    float pose_prev[4 * kMaxB];   // placed poses of the previous evaluation
+    float blk_moved;              // running bound on how far the placed cuboids have moved
+    int pose_prev_ok;
     float c_arm, c_blk, maxpen, c_coll, c_stable, c_height, c_start;
     float max_start, max_tilt, pm_pen, pm_D, pm_dz, path, jl;
     TWarp warp[kTWarps];
@@ -66,8 +77,15 @@ __host__ __device__ inline size_t t_q_offset(int n_cub, int n_osph) {
 __host__ __device__ inline size_t t_sp_offset(int n_cub, int n_osph, int C) {
     return t_q_offset(n_cub, n_osph) + (size_t)3 * C * 8 * sizeof(float);
 }
+__host__ __device__ inline int t_n_chunks(int C) { return (C - 1 + kChunk - 1) / kChunk; }
+// cached cull state: per configuration the motion bound since its chunk's last cull; per
+// chunk the placed-block motion at that cull, its clearance and whether it found no candidate
+__host__ __device__ inline size_t t_cache_offset(int n_cub, int n_osph, int C, int B) {
+    return (t_sp_offset(n_cub, n_osph, C) + (size_t)2 * B * sizeof(SpecialFrames) + 15) & ~(size_t)15;
+}
 size_t traj_smem_bytes(const Scalars& sc) {
-    return t_sp_offset(sc.n_cub, sc.n_osph, sc.C) + (size_t)2 * sc.B * sizeof(SpecialFrames);
+    return t_cache_offset(sc.n_cub, sc.n_osph, sc.C, sc.B) + (size_t)sc.C * sizeof(float) +
+           (size_t)t_n_chunks(sc.C) * (2 * sizeof(float) + sizeof(int));
 }
 
 // The robot spheres a lane owns (item lane + 32 k), loaded once per kernel launch: link-
@@ -212,12 +230,12 @@ __device__ __forceinline__ void sphere_centres(const Scalars& sc, const LaneSphe
 // per configuration lanes own sphere items, screen both slots branch-free and evaluate the
 // penetration only where the separation test fails.  With `grad`, writes the unscaled group
 // gradients G_arm[t], G_blk[t] and accumulates placed-pose derivatives in the warp scratch.
-__device__ __forceinline__ void chunk_collisions(const Scalars& sc, const LaneSpheres& ls,
+__device__ __forceinline__ bool chunk_collisions(const Scalars& sc, const LaneSpheres& ls,
                                                  const float4* __restrict__ cub, const float4* __restrict__ osph,
                                                  const float4* __restrict__ aabb, TShared& sh, TWarp& tw, float* G_arm,
                                                  float* G_blk, int t0, int nc, bool grad, const float* lane_box,
                                                  float& acc_arm, float& acc_blk, float& acc_max,
-                                                 unsigned long long& n_tests) {
+                                                 unsigned long long& n_tests, float& clearance) {
     const int lane = threadIdx.x & 31;
     const int S = sc.S, B = sc.B;
     float cx[kSlots], cy[kSlots], cz[kSlots], rr[kSlots];
@@ -236,34 +254,43 @@ __device__ __forceinline__ void chunk_collisions(const Scalars& sc, const LaneSp
         hi_y = fmaxf(hi_y, __shfl_xor_sync(0xffffffffu, hi_y, off));
         hi_z = fmaxf(hi_z, __shfl_xor_sync(0xffffffffu, hi_z, off));
     }
-    auto overlaps = [&](const float4& blo, const float4& bhi) {
-        return blo.x <= hi_x && bhi.x >= lo_x && blo.y <= hi_y && bhi.y >= lo_y && blo.z <= hi_z && bhi.z >= lo_z;
+    // separation of a box from the chunk box: the largest per-axis gap, > 0 iff they are apart
+    auto sep_chunk = [&](const float4& blo, const float4& bhi) {
+        return fmaxf(fmaxf(fmaxf(blo.x - hi_x, lo_x - bhi.x), fmaxf(blo.y - hi_y, lo_y - bhi.y)),
+                     fmaxf(blo.z - hi_z, lo_z - bhi.z));
     };
     // second level: each candidate of the chunk box against the lanes' own link boxes (lane
     // 8c + k: link k of configuration c); configuration c keeps the candidate when one of its
     // link boxes overlaps the candidate's box.  Both levels are exact: no sphere inside the
-    // boxes is dropped.
+    // boxes is dropped.  Every box apart from the chunk box, or from a lane's link box, that
+    // the lane's configuration could touch lowers the lane's clearance to that separation.
     const float* lb = lane_box;
-    auto refine = [&](unsigned m, int base, const float4* boxes, int stride, uint32_t out[kChunk]) {
+    float clear = 3.4e38f;
+    auto refine = [&](unsigned m, int base, const float4* boxes, int stride, uint32_t out[kChunk], auto relevant) {
 #pragma unroll
         for (int c = 0; c < kChunk; ++c) out[c] = 0u;
         while (m) {
             const int bit = __ffs(m) - 1;
             m &= m - 1;
             const float4 blo = boxes[stride * (base + bit)], bhi = boxes[stride * (base + bit) + 1];
-            const unsigned bal = __ballot_sync(0xffffffffu, blo.x <= lb[3] && bhi.x >= lb[0] && blo.y <= lb[4] &&
-                                                                bhi.y >= lb[1] && blo.z <= lb[5] && bhi.z >= lb[2]);
+            const float s2 = fmaxf(fmaxf(fmaxf(blo.x - lb[3], lb[0] - bhi.x), fmaxf(blo.y - lb[4], lb[1] - bhi.y)),
+                                   fmaxf(blo.z - lb[5], lb[2] - bhi.z));
+            if (relevant(bit)) clear = fminf(clear, s2);
+            const unsigned bal = __ballot_sync(0xffffffffu, s2 <= 0.f);
 #pragma unroll
             for (int c = 0; c < kChunk; ++c)
                 if ((bal >> (8 * c)) & 0xffu) out[c] |= 1u << bit;
         }
     };
+    auto always = [](int) { return true; };
     const int n_cw = (sc.n_cub + 31) >> 5, n_sw = (sc.n_osph + 31) >> 5;
     uint32_t per[kChunk], any[kChunk] = {0u, 0u, 0u, 0u};
     for (int wd = 0; wd < n_cw; ++wd) {
         const int oi = 32 * wd + lane;
-        const unsigned m = __ballot_sync(0xffffffffu, oi < sc.n_cub && overlaps(aabb[2 * oi], aabb[2 * oi + 1]));
-        refine(m, 32 * wd, aabb, 2, per);
+        const float s1 = oi < sc.n_cub ? sep_chunk(aabb[2 * oi], aabb[2 * oi + 1]) : 3.4e38f;
+        clear = fminf(clear, s1 > 0.f ? s1 : 3.4e38f);
+        const unsigned m = __ballot_sync(0xffffffffu, s1 <= 0.f);
+        refine(m, 32 * wd, aabb, 2, per, always);
         if (lane == 0)
 #pragma unroll
             for (int c = 0; c < kChunk; ++c) tw.cmask[c][wd] = per[c];
@@ -273,8 +300,10 @@ __device__ __forceinline__ void chunk_collisions(const Scalars& sc, const LaneSp
     for (int wd = 0; wd < n_sw; ++wd) {
         const int oi = 32 * wd + lane;
         const int ai = sc.n_cub + oi;
-        const unsigned m = __ballot_sync(0xffffffffu, oi < sc.n_osph && overlaps(aabb[2 * ai], aabb[2 * ai + 1]));
-        refine(m, sc.n_cub + 32 * wd, aabb, 2, per);
+        const float s1 = oi < sc.n_osph ? sep_chunk(aabb[2 * ai], aabb[2 * ai + 1]) : 3.4e38f;
+        clear = fminf(clear, s1 > 0.f ? s1 : 3.4e38f);
+        const unsigned m = __ballot_sync(0xffffffffu, s1 <= 0.f);
+        refine(m, sc.n_cub + 32 * wd, aabb, 2, per, always);
         if (lane == 0)
 #pragma unroll
             for (int c = 0; c < kChunk; ++c) tw.smask[c][wd] = per[c];
@@ -285,13 +314,21 @@ __device__ __forceinline__ void chunk_collisions(const Scalars& sc, const LaneSp
 #pragma unroll
         for (int c = 0; c < kChunk; ++c) tw.envany[c] = any[c];
     {
-        const unsigned bm_placed = __ballot_sync(0xffffffffu, lane < B && overlaps(sh.baabb[lane][0], sh.baabb[lane][1]));
-        refine(bm_placed, 0, &sh.baabb[0][0], 2, per);
+        // a configuration of block b's segments can touch the placed blocks k < b and the
+        // blocks k > b still at their initial poses (the chunk: any of its configurations)
+        const int b_lane = (min(t0 + (lane >> 3), sc.C - 1) - 1) / S >> 1;
+        const int b_first = (t0 - 1) / S >> 1, b_last = (min(t0 + nc - 1, sc.C - 1) - 1) / S >> 1;
+        const float sp = lane < B ? sep_chunk(sh.baabb[lane][0], sh.baabb[lane][1]) : 3.4e38f;
+        if (lane < b_last && sp > 0.f) clear = fminf(clear, sp);
+        const unsigned bm_placed = __ballot_sync(0xffffffffu, sp <= 0.f);
+        refine(bm_placed, 0, &sh.baabb[0][0], 2, per, [&](int k) { return k < b_lane; });
         if (lane == 0)
 #pragma unroll
             for (int c = 0; c < kChunk; ++c) tw.bmask[0][c] = per[c];
-        const unsigned bm_init = __ballot_sync(0xffffffffu, lane < B && overlaps(sh.iaabb[lane][0], sh.iaabb[lane][1]));
-        refine(bm_init, 0, &sh.iaabb[0][0], 2, per);
+        const float si = lane < B ? sep_chunk(sh.iaabb[lane][0], sh.iaabb[lane][1]) : 3.4e38f;
+        if (lane < B && lane > b_first && si > 0.f) clear = fminf(clear, si);
+        const unsigned bm_init = __ballot_sync(0xffffffffu, si <= 0.f);
+        refine(bm_init, 0, &sh.iaabb[0][0], 2, per, [&](int k) { return k > b_lane; });
         if (lane == 0)
 #pragma unroll
             for (int c = 0; c < kChunk; ++c) tw.bmask[1][c] = per[c];
@@ -300,6 +337,7 @@ __device__ __forceinline__ void chunk_collisions(const Scalars& sc, const LaneSp
 
     // pass 2: every configuration against the candidates
     const int seg0 = (t0 - 1) / S, r0 = (t0 - 1) - seg0 * S;
+    bool none = true;
     for (int ci = 0; ci < nc; ++ci) {
         const int t = t0 + ci;
         int seg = seg0, r = r0 + ci;
@@ -317,6 +355,7 @@ __device__ __forceinline__ void chunk_collisions(const Scalars& sc, const LaneSp
             if (grad && lane < 16 && (lane & 7) != 7) (lane < 8 ? G_arm : G_blk)[t * 8 + (lane & 7)] = 0.f;
             continue;
         }
+        none = false;
         sphere_centres(sc, ls, tw.F[ci], tw.H[ci], n_items, b, cx, cy, cz, rr, act, isblk);
         float gx[kSlots], gy[kSlots], gz[kSlots], pen_sum[kSlots];
 #pragma unroll
@@ -486,6 +525,8 @@ __device__ __forceinline__ void chunk_collisions(const Scalars& sc, const LaneSp
             if ((lane & 1) == 0 && (j & 7) != 7) (j < 8 ? G_arm : G_blk)[t * 8 + (j & 7)] = v[0];
         }
     }
+    clearance = warp_min(clear);
+    return none;
 }
 
 // Residuals of the start group at the grasp (which = 0) or place (which = 1) configuration
@@ -651,7 +692,8 @@ __device__ __forceinline__ void cuboid_aabb(const float4* c, float4* box) {
 template <bool kP2P>
 __device__ void traj_evaluate(const Scalars& sc, const LaneSpheres& ls, const float4* cub, const float4* osph,
                               const float4* aabb, TShared& sh, SpecialFrames* sp, float* q, float* G_arm,
-                              float* G_blk, bool grad, unsigned long long& n_tests) {
+                              float* G_blk, float* disp, float* cblk, float* cgap, int* cempty, bool grad,
+                              unsigned long long& n_tests, unsigned long long& n_cull) {
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const int B = sc.B, S = sc.S, C = sc.C, NR = sc.NR;
     // point to point (kP2P): one segment ending at the target's grasp configuration; no placement
@@ -667,17 +709,33 @@ __device__ void traj_evaluate(const Scalars& sc, const LaneSpheres& ls, const fl
     for (int i = lane; i < 2 * kMaxB * 4; i += 32) (&sh.warp[w].wr[0][0][0])[i] = 0.f;
     __syncthreads();
     // placed poses: the block frame at each place configuration, (x, y, z, yaw)
-    if (w == 0 && lane < B) {
-        if (!p2p) {
+    if (w == 0) {
+        float moved = 0.f;
+        if (lane < B && !p2p) {
             const float4* H = sp[2 * lane + 1].H;
             const float pose[4] = {H[0].w, H[1].w, H[2].w, atan2f(H[1].x, H[0].x)};
-            for (int i = 0; i < 4; ++i) sh.pose[4 * lane + i] = pose[i];
+            // how far any point of the placed cuboid moved since the previous evaluation:
+            // |d position| + |d yaw| times its horizontal half diagonal
+            if (sh.pose_prev_ok) {
+                const float* pp = &sh.pose_prev[4 * lane];
+                const float dx = pose[0] - pp[0], dy = pose[1] - pp[1], dz = pose[2] - pp[2];
+                float dyaw = fabsf(pose[3] - pp[3]);
+                dyaw = fminf(dyaw, 2.f * kPi - dyaw);
+                const float4 h = sc.half[lane];
+                moved = (sqrtf(dx * dx + dy * dy + dz * dz) + dyaw * sqrtf(h.x * h.x + h.y * h.y)) * 1.0001f + 1e-6f;
+            }
+            for (int i = 0; i < 4; ++i) sh.pose[4 * lane + i] = sh.pose_prev[4 * lane + i] = pose[i];
             block_cuboid(pose[0], pose[1], pose[2], pose[3], sc.half[lane], sh.bcub[lane]);
             cuboid_aabb(sh.bcub[lane], sh.baabb[lane]);
-        } else {
+        } else if (lane < B) {
             for (int i = 0; i < 4; ++i) sh.pose[4 * lane + i] = 0.f;
             sh.baabb[lane][0] = make_float4(3.4e38f, 3.4e38f, 3.4e38f, 0.f);   // an empty box: never a candidate
             sh.baabb[lane][1] = make_float4(-3.4e38f, -3.4e38f, -3.4e38f, 0.f);
+        }
+        moved = warp_sum(moved);
+        if (lane == 0) {
+            sh.blk_moved += moved;
+            sh.pose_prev_ok = 1;
         }
     }
     __syncthreads();
@@ -685,8 +743,21 @@ __device__ void traj_evaluate(const Scalars& sc, const LaneSpheres& ls, const fl
     // (2) configuration loop: chunks of kChunk consecutive configurations per warp
     float acc_arm = 0.f, acc_blk = 0.f, acc_max = 0.f;
     const int n_chunks = (C - 1 + kChunk - 1) / kChunk;
+    const float blk_moved = sh.blk_moved;
     for (int chk = w; chk < n_chunks; chk += kTWarps) {
         const int t0 = 1 + kChunk * chk;
+        const int nc = min(kChunk, C - t0);
+        // cached cull: no candidate at the last cull, and everything moved less than its margin
+        if (cempty[chk]) {
+            float d = lane < nc ? disp[t0 + lane] : 0.f;
+            d = fmaxf(d, __shfl_xor_sync(0xffffffffu, d, 1));
+            d = fmaxf(d, __shfl_xor_sync(0xffffffffu, d, 2));
+            d = __shfl_sync(0xffffffffu, d, 0);
+            if (d + (blk_moved - cblk[chk]) < cgap[chk]) {
+                if (grad && lane < 7 * nc) G_blk[(t0 + lane / 7) * 8 + lane % 7] = 0.f;
+                continue;
+            }
+        }
         const int c = lane >> 3;
         // the held block's frame matters on transfer-segment interiors only
         const int tc = min(t0 + c, C - 1), seg_c = (tc - 1) / S;
@@ -694,8 +765,16 @@ __device__ void traj_evaluate(const Scalars& sc, const LaneSpheres& ls, const fl
         float box[6];
         chunk_fk(sc, sh, q, t0 + c, true, held_c, sh.warp[w].F[c], sh.warp[w].H[c], box);
         __syncwarp();
-        chunk_collisions(sc, ls, cub, osph, aabb, sh, sh.warp[w], G_arm, G_blk, t0, min(kChunk, C - t0), grad, box,
-                         acc_arm, acc_blk, acc_max, n_tests);
+        float clearance;
+        const bool none = chunk_collisions(sc, ls, cub, osph, aabb, sh, sh.warp[w], G_arm, G_blk, t0, nc, grad, box,
+                                           acc_arm, acc_blk, acc_max, n_tests, clearance);
+        n_cull += (unsigned)nc;
+        if (lane == 0) {
+            cempty[chk] = none ? 1 : 0;
+            cblk[chk] = blk_moved;
+            cgap[chk] = clearance - kClearSlack;
+        }
+        if (lane < nc) disp[t0 + lane] = 0.f;
         __syncwarp();
     }
     acc_arm = warp_sum(acc_arm);
@@ -863,8 +942,16 @@ __device__ __forceinline__ void traj_particle(const Scalars& sc, int p, int mode
     float* G_arm = q + sc.C * 8;
     float* G_blk = G_arm + sc.C * 8;
     SpecialFrames* sp = reinterpret_cast<SpecialFrames*>(smem_raw + t_sp_offset(sc.n_cub, sc.n_osph, sc.C));
+    float* disp = reinterpret_cast<float*>(smem_raw + t_cache_offset(sc.n_cub, sc.n_osph, sc.C, sc.B));
+    const int n_chunks = t_n_chunks(sc.C);
+    float* cblk = disp + sc.C;
+    float* cgap = cblk + n_chunks;
+    int* cempty = reinterpret_cast<int*>(cgap + n_chunks);
     const int tid = threadIdx.x;
     const int C = sc.C, NR = sc.NR, B = sc.B;
+    for (int i = tid; i < C; i += kTThreads) disp[i] = 0.f;
+    for (int i = tid; i < n_chunks; i += kTThreads) { cblk[i] = 0.f; cgap[i] = 0.f; cempty[i] = 0; }
+    if (tid == 0) { sh.blk_moved = 0.f; sh.pose_prev_ok = 0; }
 
     // particle state -> shared memory (coalesced float4)
     const float4* qg = reinterpret_cast<const float4*>(io.q + (size_t)p * C * 8);
@@ -886,7 +973,7 @@ __device__ __forceinline__ void traj_particle(const Scalars& sc, int p, int mode
         aabb[2 * (sc.n_cub + o)] = make_float4(sp.x - sp.w, sp.y - sp.w, sp.z - sp.w, 0.f);
         aabb[2 * (sc.n_cub + o) + 1] = make_float4(sp.x + sp.w, sp.y + sp.w, sp.z + sp.w, 0.f);
     }
-    unsigned long long n_tests = 0;
+    unsigned long long n_tests = 0, n_cull = 0;
     const LaneSpheres ls = lane_spheres(sc);
     const bool fresh = mode == kTrajDescend && io.init_multipliers;
     for (int r = tid; r < NR; r += kTThreads) sh.lam[r] = (fresh || !io.lam) ? 0.f : io.lam[(size_t)p * NR + r];
@@ -896,13 +983,26 @@ __device__ __forceinline__ void traj_particle(const Scalars& sc, int p, int mode
     if (mode == kTrajDescend) {
         const int K = io.k_steps;
         for (int k = 1; k <= K; ++k) {
-            traj_evaluate<kP2P>(sc, ls, cub, osph, aabb, sh, sp, q, G_arm, G_blk, true, n_tests);
+            traj_evaluate<kP2P>(sc, ls, cub, osph, aabb, sh, sp, q, G_arm, G_blk, disp, cblk, cgap, cempty, true, n_tests,
+                                n_cull);
             const float eta = sc.eta_traj * (1.f - (float)k / (float)K);
-            for (int i = tid; i < C * 7; i += kTThreads) {
-                const int t = i / 7, j = i % 7;
-                if (t == 0) continue;
-                const float v = q[t * 8 + j] - eta * G_blk[t * 8 + j];
-                q[t * 8 + j] = fminf(fmaxf(v, sc.qlo[j]), sc.qhi[j]);
+            // q <- clamp(q - eta g) per configuration, and the bound on how far its spheres moved
+            for (int t = 1 + tid; t < C; t += kTThreads) {
+                float4* qv = reinterpret_cast<float4*>(q + t * 8);
+                const float4* gv = reinterpret_cast<const float4*>(G_blk + t * 8);
+                const float4 qa = qv[0], qb = qv[1], ga = gv[0], gb = gv[1];
+                const float old[7] = {qa.x, qa.y, qa.z, qa.w, qb.x, qb.y, qb.z};
+                const float g[7] = {ga.x, ga.y, ga.z, ga.w, gb.x, gb.y, gb.z};
+                float nw[7], moved = 0.f;
+#pragma unroll
+                for (int j = 0; j < 7; ++j) {
+                    const float v = old[j] - eta * g[j];
+                    nw[j] = fminf(fmaxf(v, sc.qlo[j]), sc.qhi[j]);
+                    moved += fabsf(nw[j] - old[j]) * sc.sweep[j];
+                }
+                qv[0] = make_float4(nw[0], nw[1], nw[2], nw[3]);
+                qv[1] = make_float4(nw[4], nw[5], nw[6], qb.w);
+                disp[t] += moved * 1.0001f + 1e-7f;
             }
             if (sc.K_al > 0 && k % sc.K_al == 0) {
                 for (int r = tid; r < NR; r += kTThreads) sh.lam[r] += sh.mu * residual_sqrt_weight(sc, r) * sh.h[r];
@@ -913,8 +1013,12 @@ __device__ __forceinline__ void traj_particle(const Scalars& sc, int p, int mode
         }
     }
     const bool want_grad = mode == kTrajEval && io.grad != nullptr;
-    traj_evaluate<kP2P>(sc, ls, cub, osph, aabb, sh, sp, q, G_arm, G_blk, want_grad, n_tests);
-    if (io.tests && (threadIdx.x & 31) == 0) atomicAdd(io.tests, n_tests);
+    traj_evaluate<kP2P>(sc, ls, cub, osph, aabb, sh, sp, q, G_arm, G_blk, disp, cblk, cgap, cempty, want_grad, n_tests,
+                        n_cull);
+    if (io.tests && (threadIdx.x & 31) == 0) {
+        atomicAdd(io.tests, n_tests);
+        atomicAdd(io.tests + 1, n_cull);
+    }
 
     // outputs
     if (mode == kTrajDescend) {

@@ -47,7 +47,7 @@ struct spasm_problem {
     int *d_tsat = nullptr, *d_tnsat = nullptr, *d_tbest = nullptr;
     float *d_rq = nullptr, *d_rcost = nullptr;   // returned solutions
     int* d_rsucc = nullptr;
-    unsigned long long* d_tests = nullptr;   // sphere-obstacle tests run by the trajectory kernel
+    unsigned long long* d_tests = nullptr;   // [tests run, configurations culled] by the trajectory kernel
     bool optimized = false;
     int n_found = 0, traj_attempts = 0;
     std::vector<double> host_cub, host_osph;
