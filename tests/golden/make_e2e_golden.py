@@ -10,6 +10,10 @@ called.
     python tests/golden/make_e2e_golden.py tower1 --seeds 100
     python tests/golden/make_e2e_golden.py tower4 --seeds 100 --override Q=64
     python tests/golden/make_e2e_golden.py p2p --seeds 100 --override Q=64 --override max_steps=1000
+    python tests/golden/make_e2e_golden.py tower1 --seeds 100 --override ik_mode=1
+    python tests/golden/make_e2e_golden.py tower4 --seeds 50 --override Q=64 --override ik_mode=1
+
+ik_mode=1 lifts with the analytic IK of the Franka joint layout instead of damped least squares.
 
 For the point-to-point workload (one transit segment to a tool target) only stage 2 runs.
 
