@@ -39,11 +39,15 @@ SM_COUNT, FP32_LANES = 152, 128
 # algorithmic FP32 work per unit (the per-unit figures of the hot-path analysis): one
 # sphere-cuboid test with its gradient, about 32 instructions = 40 flop (FMA counted as 2)
 FLOP_PER_TEST = 40
-# forward kinematics (about 0.9 kflop) and the backward chain (about 3.3 kflop) of one
-# configuration
-FLOP_PER_CONFIG_FK = 900 + 3300
+# forward kinematics of one configuration (about 0.9 kflop), run where its chunk is culled
+FLOP_PER_CONFIG_FK = 900
 # exact box cull of one (configuration, obstacle) pair: 6 comparisons
 FLOP_PER_CULL = 6
+# sphere centres and the backward chain of a configuration with a candidate (about 3.3 kflop)
+FLOP_PER_CONFIG_CAND = 3300
+# every configuration, every evaluation: the descent update with its motion bound, and the
+# path, joint-limit and gradient assembly terms (about 120 flop)
+FLOP_PER_CONFIG_STEP = 120
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "k_traj_tower10.md")
 KERNEL_SOURCES = ["paper_2510_07674_gb300/csrc/kernels_s2.cu", "paper_2510_07674_gb300/csrc/stage2.cuh",
                   "paper_2510_07674_gb300/csrc/common.cuh", "paper_2510_07674_gb300/csrc/stage1.cuh"]
@@ -147,8 +151,7 @@ def count_tests(wl) -> dict:
     n_rsph = len(wl.robot.sphere)
     held_cfgs = B * (S - 1)
     tests = (C - 1) * n_rsph * n_obs + held_cfgs * 8 * n_obs
-    return {"C": C, "tests": tests, "n_obs": n_obs,
-            "flop": FLOP_PER_TEST * tests + FLOP_PER_CONFIG_FK * (C - 1)}
+    return {"C": C, "tests": tests, "n_obs": n_obs}
 
 
 def rank_seeds(rank: int, n: int) -> list:
@@ -244,8 +247,9 @@ def run_native(args, ws, rank, local):
     # itself and the forward kinematics; the all-pairs count is reported as effective tests/s.
     evals = Q * (K + 1) * max(traj_launches, 1)
     tests_exec = sum(s["tests_executed"] for s in stats)
-    flop_total = (FLOP_PER_TEST * tests_exec + FLOP_PER_CULL * evals * (tc["C"] - 1) * tc["n_obs"]
-                  + FLOP_PER_CONFIG_FK * evals * (tc["C"] - 1))
+    cull_cfg = sum(s["cull_configs"] for s in stats)
+    cand_cfg = sum(s["cand_configs"] for s in stats)
+    flop_total = traj_flop(tc, evals, tests_exec, cull_cfg, cand_cfg)
     flop_per_launch = flop_total / max(traj_launches, 1)
     avg_launch_s = traj_ms / max(traj_launches, 1) / 1000.0
     achieved = flop_per_launch / avg_launch_s / 1e12 if avg_launch_s > 0 else None
@@ -258,6 +262,8 @@ def run_native(args, ws, rank, local):
                 "flop_per_launch": flop_per_launch, "avg_launch_ms": avg_launch_s * 1e3,
                 "tests_per_particle_iter_all_pairs": tc["tests"],
                 "tests_per_particle_iter_executed": tests_exec / max(evals, 1),
+                "culled_configs_per_particle_iter": cull_cfg / max(evals, 1),
+                "candidate_configs_per_particle_iter": cand_cfg / max(evals, 1),
                 "effective_pair_tests_per_s": tc["tests"] * evals / max(traj_ms / 1000.0, 1e-9)}
     succ = [s["n_success"] > 0 for s in stats]
 
@@ -332,14 +338,20 @@ def _percentile(xs, q):
     return float(xs[min(len(xs) - 1, max(0, math.ceil(q * len(xs)) - 1))])
 
 
+def traj_flop(tc, evals, tests, cull_configs, cand_configs) -> float:
+    """FP32 work the trajectory kernel executes: the sphere-obstacle tests left by the exact
+    cull, the kinematics and cull of the configurations whose chunk was culled (the others
+    kept an earlier cull, valid by their clearance), sphere centres and gradient chain where a
+    configuration has a candidate, and the per-configuration step terms of every evaluation."""
+    return (FLOP_PER_TEST * tests + (FLOP_PER_CONFIG_FK + FLOP_PER_CULL * tc["n_obs"]) * cull_configs
+            + FLOP_PER_CONFIG_CAND * cand_configs + FLOP_PER_CONFIG_STEP * evals * (tc["C"] - 1))
+
+
 def solve_flop(wl, st) -> float:
-    """Algorithmic trajectory work of one finished solve (the headline roofline's count):
-    executed sphere-obstacle tests, the chunk cull and the forward kinematics of every
-    configuration of every evaluation."""
+    """Executed trajectory work of one finished solve (the headline roofline's count)."""
     tc = count_tests(wl)
     evals = wl.params.Q * (wl.params.K_traj + 1) * max(st["traj_launches"], 1)
-    return (FLOP_PER_TEST * st["tests_executed"] + FLOP_PER_CULL * evals * (tc["C"] - 1) * tc["n_obs"]
-            + FLOP_PER_CONFIG_FK * evals * (tc["C"] - 1))
+    return traj_flop(tc, evals, st["tests_executed"], st["cull_configs"], st["cand_configs"])
 
 
 def run_forms(args, rank, overrides, peak):

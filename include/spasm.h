@@ -263,7 +263,9 @@ typedef struct {
                                   exact box cull (pairs whose boxes are disjoint are skipped) */
     long long cull_configs;    /* configurations whose kinematics and cull the trajectory kernels
                                   ran (the others kept a candidate-free cull from an earlier
-                                  iteration, valid while they moved less than its margin) */
+                                  iteration, valid while they moved less than its clearance) */
+    long long cand_configs;    /* of those, configurations with a candidate obstacle, whose sphere
+                                  centres, tests and gradient chain ran */
 } spasm_stats;
 
 /* Replace the Philox seed (the key of every random stream) and forget previous results;

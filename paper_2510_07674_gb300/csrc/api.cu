@@ -301,7 +301,7 @@ extern "C" spasm_status spasm_create_problem(const spasm_robot* robot, const spa
     ALLOC(pr->d_cub64, (size_t)16 * sc.n_cub);
     ALLOC(pr->d_osph64, (size_t)4 * sc.n_osph);
     ALLOC(pr->d_rmet64, (size_t)6 * P);
-    ALLOC(pr->d_tests, 2);
+    ALLOC(pr->d_tests, 3);
     ALLOC(pr->d_sc, 1);
     ALLOC(pr->d_chkacc, P);
 #undef ALLOC
@@ -607,12 +607,13 @@ spasm_status spasm::finish_record(spasm_problem* pr, int found, bool finish_done
     pr->n_found = found;
     SPASM_TRY(check_device_error(pr));
     {
-        unsigned long long nt[2] = {0, 0};
+        unsigned long long nt[3] = {0, 0, 0};
         SPASM_CUDA(cudaMemcpyAsync(nt, pr->d_tests, sizeof nt, cudaMemcpyDeviceToHost, pr->stream));
         SPASM_CUDA(cudaStreamSynchronize(pr->stream));
         pr->stats.d2h_bytes += sizeof nt;
         pr->stats.tests_executed += (long long)nt[0];
         pr->stats.cull_configs += (long long)nt[1];
+        pr->stats.cand_configs += (long long)nt[2];
     }
     if (found > 0) {
         std::vector<int> succ(sc.P, 0);
@@ -639,7 +640,7 @@ extern "C" spasm_status spasm_optimize(spasm_problem_t pr) {
         if (st != SPASM_OK) return st;
     }
     if (pr->n_place <= 0) return fail(SPASM_ERR_NOSOLUTION, "no placements to lift");
-    SPASM_CUDA(cudaMemsetAsync(pr->d_tests, 0, 2 * sizeof(unsigned long long), pr->stream));
+    SPASM_CUDA(cudaMemsetAsync(pr->d_tests, 0, 3 * sizeof(unsigned long long), pr->stream));
     int found = 0;
     SPASM_TRY(traj_continue(pr, 0, 0, 0, &found));
     return finish_record(pr, found, false);

@@ -204,7 +204,7 @@ extern "C" spasm_status spasm_optimize_batch(spasm_problem_t* prs, int n, void* 
     SPASM_TRY(run_as_graph(s, [&]() -> spasm_status {
         for (int i : live) {
             spasm_problem* pr = prs[i];
-            SPASM_CUDA(cudaMemsetAsync(pr->d_tests, 0, 2 * sizeof(unsigned long long), s));
+            SPASM_CUDA(cudaMemsetAsync(pr->d_tests, 0, 3 * sizeof(unsigned long long), s));
             SPASM_CUDA(launch_lift(pr->sc, pr->sc.Q, pr->d_place, pr->n_place, 0u, pr->d_q, s));
         }
         SPASM_CUDA(cudaMemsetAsync(dj.next, 0, sizeof(int), s));

@@ -57,6 +57,8 @@ struct TShared {
     float4 lbc[8], lbh[8];   // link-frame boxes of each link's spheres (centre, half extents)
     float s_arm, s_blk, mu, L;
     float pose_prev[4 * kMaxB];   // placed poses of the previous evaluation
+    short active[(kMaxC + kChunk - 1) / kChunk];   // chunks to evaluate, in chunk order
+    int n_active;
     float blk_moved;              // running bound on how far the placed cuboids have moved
     int pose_prev_ok;
     float c_arm, c_blk, maxpen, c_coll, c_stable, c_height, c_start;
@@ -235,7 +237,8 @@ __device__ __forceinline__ bool chunk_collisions(const Scalars& sc, const LaneSp
                                                  const float4* __restrict__ aabb, TShared& sh, TWarp& tw, float* G_arm,
                                                  float* G_blk, int t0, int nc, bool grad, const float* lane_box,
                                                  float& acc_arm, float& acc_blk, float& acc_max,
-                                                 unsigned long long& n_tests, float& clearance) {
+                                                 unsigned long long& n_tests, unsigned long long& n_cand,
+                                                 float& clearance) {
     const int lane = threadIdx.x & 31;
     const int S = sc.S, B = sc.B;
     float cx[kSlots], cy[kSlots], cz[kSlots], rr[kSlots];
@@ -356,6 +359,7 @@ __device__ __forceinline__ bool chunk_collisions(const Scalars& sc, const LaneSp
             continue;
         }
         none = false;
+        ++n_cand;
         sphere_centres(sc, ls, tw.F[ci], tw.H[ci], n_items, b, cx, cy, cz, rr, act, isblk);
         float gx[kSlots], gy[kSlots], gz[kSlots], pen_sum[kSlots];
 #pragma unroll
@@ -693,7 +697,8 @@ template <bool kP2P>
 __device__ void traj_evaluate(const Scalars& sc, const LaneSpheres& ls, const float4* cub, const float4* osph,
                               const float4* aabb, TShared& sh, SpecialFrames* sp, float* q, float* G_arm,
                               float* G_blk, float* disp, float* cblk, float* cgap, int* cempty, bool grad,
-                              unsigned long long& n_tests, unsigned long long& n_cull) {
+                              unsigned long long& n_tests, unsigned long long& n_cull,
+                              unsigned long long& n_cand) {
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const int B = sc.B, S = sc.S, C = sc.C, NR = sc.NR;
     // point to point (kP2P): one segment ending at the target's grasp configuration; no placement
@@ -743,21 +748,42 @@ __device__ void traj_evaluate(const Scalars& sc, const LaneSpheres& ls, const fl
     // (2) configuration loop: chunks of kChunk consecutive configurations per warp
     float acc_arm = 0.f, acc_blk = 0.f, acc_max = 0.f;
     const int n_chunks = (C - 1 + kChunk - 1) / kChunk;
+    // Chunks to evaluate: those without a valid cached cull (none at its last cull, and
+    // everything moved less than its clearance since).  Warp 0 lists them in chunk order and
+    // zeroes the block-group gradient rows of the skipped ones (their arm-group rows are still
+    // zero from their last cull); the list is dealt to the warps round-robin, which keeps
+    // the per-warp sums deterministic and the warps' shares of the remaining work even.
     const float blk_moved = sh.blk_moved;
-    for (int chk = w; chk < n_chunks; chk += kTWarps) {
-        const int t0 = 1 + kChunk * chk;
-        const int nc = min(kChunk, C - t0);
-        // cached cull: no candidate at the last cull, and everything moved less than its margin
-        if (cempty[chk]) {
-            float d = lane < nc ? disp[t0 + lane] : 0.f;
-            d = fmaxf(d, __shfl_xor_sync(0xffffffffu, d, 1));
-            d = fmaxf(d, __shfl_xor_sync(0xffffffffu, d, 2));
-            d = __shfl_sync(0xffffffffu, d, 0);
-            if (d + (blk_moved - cblk[chk]) < cgap[chk]) {
-                if (grad && lane < 7 * nc) G_blk[(t0 + lane / 7) * 8 + lane % 7] = 0.f;
-                continue;
+    if (w == 0) {
+        int count = 0;
+        for (int base = 0; base < n_chunks; base += 32) {
+            const int chk = base + lane;
+            const int t0 = 1 + kChunk * chk, nc = min(kChunk, C - t0);
+            bool active = chk < n_chunks;
+            if (active && cempty[chk]) {
+                float d = 0.f;
+                for (int i = 0; i < nc; ++i) d = fmaxf(d, disp[t0 + i]);
+                active = !(d + (blk_moved - cblk[chk]) < cgap[chk]);
+            }
+            const unsigned bal = __ballot_sync(0xffffffffu, active);
+            if (active) sh.active[count + __popc(bal & ((1u << lane) - 1u))] = (short)chk;
+            count += __popc(bal);
+            unsigned skipped = __ballot_sync(0xffffffffu, chk < n_chunks && !active);
+            while (grad && skipped) {
+                const int k = base + __ffs(skipped) - 1;
+                skipped &= skipped - 1;
+                const int tk = 1 + kChunk * k, nk = min(kChunk, C - tk);
+                if (lane < 7 * nk) G_blk[(tk + lane / 7) * 8 + lane % 7] = 0.f;
             }
         }
+        if (lane == 0) sh.n_active = count;
+    }
+    __syncthreads();
+    const int n_active = sh.n_active;
+    for (int ai = w; ai < n_active; ai += kTWarps) {
+        const int chk = sh.active[ai];
+        const int t0 = 1 + kChunk * chk;
+        const int nc = min(kChunk, C - t0);
         const int c = lane >> 3;
         // the held block's frame matters on transfer-segment interiors only
         const int tc = min(t0 + c, C - 1), seg_c = (tc - 1) / S;
@@ -767,7 +793,7 @@ __device__ void traj_evaluate(const Scalars& sc, const LaneSpheres& ls, const fl
         __syncwarp();
         float clearance;
         const bool none = chunk_collisions(sc, ls, cub, osph, aabb, sh, sh.warp[w], G_arm, G_blk, t0, nc, grad, box,
-                                           acc_arm, acc_blk, acc_max, n_tests, clearance);
+                                           acc_arm, acc_blk, acc_max, n_tests, n_cand, clearance);
         n_cull += (unsigned)nc;
         if (lane == 0) {
             cempty[chk] = none ? 1 : 0;
@@ -973,7 +999,7 @@ __device__ __forceinline__ void traj_particle(const Scalars& sc, int p, int mode
         aabb[2 * (sc.n_cub + o)] = make_float4(sp.x - sp.w, sp.y - sp.w, sp.z - sp.w, 0.f);
         aabb[2 * (sc.n_cub + o) + 1] = make_float4(sp.x + sp.w, sp.y + sp.w, sp.z + sp.w, 0.f);
     }
-    unsigned long long n_tests = 0, n_cull = 0;
+    unsigned long long n_tests = 0, n_cull = 0, n_cand = 0;
     const LaneSpheres ls = lane_spheres(sc);
     const bool fresh = mode == kTrajDescend && io.init_multipliers;
     for (int r = tid; r < NR; r += kTThreads) sh.lam[r] = (fresh || !io.lam) ? 0.f : io.lam[(size_t)p * NR + r];
@@ -984,7 +1010,7 @@ __device__ __forceinline__ void traj_particle(const Scalars& sc, int p, int mode
         const int K = io.k_steps;
         for (int k = 1; k <= K; ++k) {
             traj_evaluate<kP2P>(sc, ls, cub, osph, aabb, sh, sp, q, G_arm, G_blk, disp, cblk, cgap, cempty, true, n_tests,
-                                n_cull);
+                                n_cull, n_cand);
             const float eta = sc.eta_traj * (1.f - (float)k / (float)K);
             // q <- clamp(q - eta g) per configuration, and the bound on how far its spheres moved
             for (int t = 1 + tid; t < C; t += kTThreads) {
@@ -1014,10 +1040,11 @@ __device__ __forceinline__ void traj_particle(const Scalars& sc, int p, int mode
     }
     const bool want_grad = mode == kTrajEval && io.grad != nullptr;
     traj_evaluate<kP2P>(sc, ls, cub, osph, aabb, sh, sp, q, G_arm, G_blk, disp, cblk, cgap, cempty, want_grad, n_tests,
-                        n_cull);
+                        n_cull, n_cand);
     if (io.tests && (threadIdx.x & 31) == 0) {
         atomicAdd(io.tests, n_tests);
         atomicAdd(io.tests + 1, n_cull);
+        atomicAdd(io.tests + 2, n_cand);
     }
 
     // outputs

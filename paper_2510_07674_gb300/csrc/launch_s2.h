@@ -16,7 +16,8 @@ struct TrajIO {
     float* metrics;    // [n][8] max pen, max grasp error, max tilt, placement max pen / CoM / height, path, rank cost
     int* sat;          // [n] satisfying flag
     unsigned long long* tests;   // [0] sphere-obstacle tests executed (after the exact cull), [1]
-                                 // configurations whose kinematics and cull ran; accumulated
+                                 // configurations whose kinematics and cull ran, [2] of those, the
+                                 // ones with a candidate obstacle (sphere-level work); accumulated
     int k_steps;       // descent steps
     int init_multipliers;   // descent starts from lambda = 0, mu = mu0
 };

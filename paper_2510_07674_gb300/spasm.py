@@ -78,7 +78,7 @@ class _Stats(ctypes.Structure):
                 ("particle_iters", ctypes.c_longlong), ("ms_place", ctypes.c_double), ("ms_lift", ctypes.c_double),
                 ("ms_traj", ctypes.c_double), ("ms_finish", ctypes.c_double), ("h2d_bytes", ctypes.c_longlong),
                 ("d2h_bytes", ctypes.c_longlong), ("tests_executed", ctypes.c_longlong),
-                ("cull_configs", ctypes.c_longlong)]
+                ("cull_configs", ctypes.c_longlong), ("cand_configs", ctypes.c_longlong)]
 
 
 class _BatchConfig(ctypes.Structure):
