@@ -57,8 +57,8 @@ struct TShared {
     float4 lbc[8], lbh[8];   // link-frame boxes of each link's spheres (centre, half extents)
     float s_arm, s_blk, mu, L;
     float pose_prev[4 * kMaxB];   // placed poses of the previous evaluation
-    short active[(kMaxC + kChunk - 1) / kChunk];   // chunks to evaluate, in chunk order
-    int n_active;
+    short active[(kMaxC + kChunk - 1) / kChunk];   // chunks to evaluate: group g (chunks 32g..32g+31) at 32g..
+    int n_group[kTWarps];                           // chunks to evaluate in group g
     float blk_moved;              // running bound on how far the placed cuboids have moved
     int pose_prev_ok;
     float c_arm, c_blk, maxpen, c_coll, c_stable, c_height, c_start;
@@ -749,59 +749,63 @@ __device__ void traj_evaluate(const Scalars& sc, const LaneSpheres& ls, const fl
     float acc_arm = 0.f, acc_blk = 0.f, acc_max = 0.f;
     const int n_chunks = (C - 1 + kChunk - 1) / kChunk;
     // Chunks to evaluate: those without a valid cached cull (none at its last cull, and
-    // everything moved less than its clearance since).  Warp 0 lists them in chunk order and
-    // zeroes the block-group gradient rows of the skipped ones (their arm-group rows are still
-    // zero from their last cull); the list is dealt to the warps round-robin, which keeps
-    // the per-warp sums deterministic and the warps' shares of the remaining work even.
+    // everything moved less than its clearance since).  Warp g lists those of chunks
+    // 32g .. 32g+31 in chunk order and zeroes the block-group gradient rows of the skipped ones
+    // (their arm-group rows are still zero from their last cull); the concatenated list is
+    // dealt to the warps round-robin, which keeps the per-warp sums deterministic and the
+    // warps' shares of the remaining work even.
+    static_assert((kMaxC + kChunk - 1) / kChunk <= 32 * kTWarps && (kTWarps & (kTWarps - 1)) == 0,
+                  "one 32-chunk group per warp");
     const float blk_moved = sh.blk_moved;
-    if (w == 0) {
-        int count = 0;
-        for (int base = 0; base < n_chunks; base += 32) {
-            const int chk = base + lane;
-            const int t0 = 1 + kChunk * chk, nc = min(kChunk, C - t0);
-            bool active = chk < n_chunks;
-            if (active && cempty[chk]) {
-                float d = 0.f;
-                for (int i = 0; i < nc; ++i) d = fmaxf(d, disp[t0 + i]);
-                active = !(d + (blk_moved - cblk[chk]) < cgap[chk]);
-            }
-            const unsigned bal = __ballot_sync(0xffffffffu, active);
-            if (active) sh.active[count + __popc(bal & ((1u << lane) - 1u))] = (short)chk;
-            count += __popc(bal);
-            unsigned skipped = __ballot_sync(0xffffffffu, chk < n_chunks && !active);
-            while (grad && skipped) {
-                const int k = base + __ffs(skipped) - 1;
-                skipped &= skipped - 1;
-                const int tk = 1 + kChunk * k, nk = min(kChunk, C - tk);
-                if (lane < 7 * nk) G_blk[(tk + lane / 7) * 8 + lane % 7] = 0.f;
-            }
+    {
+        const int chk = 32 * w + lane;
+        const int t0 = 1 + kChunk * chk, nc = min(kChunk, C - t0);
+        bool active = chk < n_chunks;
+        if (active && cempty[chk]) {
+            float d = 0.f;
+            for (int i = 0; i < nc; ++i) d = fmaxf(d, disp[t0 + i]);
+            active = !(d + (blk_moved - cblk[chk]) < cgap[chk]);
         }
-        if (lane == 0) sh.n_active = count;
+        const unsigned bal = __ballot_sync(0xffffffffu, active);
+        if (active) sh.active[32 * w + __popc(bal & ((1u << lane) - 1u))] = (short)chk;
+        if (lane == 0) sh.n_group[w] = __popc(bal);
+        unsigned skipped = __ballot_sync(0xffffffffu, chk < n_chunks && !active);
+        while (grad && skipped) {
+            const int k = 32 * w + __ffs(skipped) - 1;
+            skipped &= skipped - 1;
+            const int tk = 1 + kChunk * k, nk = min(kChunk, C - tk);
+            if (lane < 7 * nk) G_blk[(tk + lane / 7) * 8 + lane % 7] = 0.f;
+        }
     }
     __syncthreads();
-    const int n_active = sh.n_active;
-    for (int ai = w; ai < n_active; ai += kTWarps) {
-        const int chk = sh.active[ai];
-        const int t0 = 1 + kChunk * chk;
-        const int nc = min(kChunk, C - t0);
-        const int c = lane >> 3;
-        // the held block's frame matters on transfer-segment interiors only
-        const int tc = min(t0 + c, C - 1), seg_c = (tc - 1) / S;
-        const bool held_c = (seg_c & 1) && tc - seg_c * S < S;
-        float box[6];
-        chunk_fk(sc, sh, q, t0 + c, true, held_c, sh.warp[w].F[c], sh.warp[w].H[c], box);
-        __syncwarp();
-        float clearance;
-        const bool none = chunk_collisions(sc, ls, cub, osph, aabb, sh, sh.warp[w], G_arm, G_blk, t0, nc, grad, box,
-                                           acc_arm, acc_blk, acc_max, n_tests, n_cand, clearance);
-        n_cull += (unsigned)nc;
-        if (lane == 0) {
-            cempty[chk] = none ? 1 : 0;
-            cblk[chk] = blk_moved;
-            cgap[chk] = clearance - kClearSlack;
+    // warp w takes positions w, w + 8, ... of the concatenated list, group by group
+    int start = 0;
+    for (int g = 0; g < kTWarps; ++g) {
+        const int n_g = sh.n_group[g];
+        for (int i = (w - start) & (kTWarps - 1); i < n_g; i += kTWarps) {
+            const int chk = sh.active[32 * g + i];
+            const int t0 = 1 + kChunk * chk;
+            const int nc = min(kChunk, C - t0);
+            const int c = lane >> 3;
+            // the held block's frame matters on transfer-segment interiors only
+            const int tc = min(t0 + c, C - 1), seg_c = (tc - 1) / S;
+            const bool held_c = (seg_c & 1) && tc - seg_c * S < S;
+            float box[6];
+            chunk_fk(sc, sh, q, t0 + c, true, held_c, sh.warp[w].F[c], sh.warp[w].H[c], box);
+            __syncwarp();
+            float clearance;
+            const bool none = chunk_collisions(sc, ls, cub, osph, aabb, sh, sh.warp[w], G_arm, G_blk, t0, nc, grad, box,
+                                               acc_arm, acc_blk, acc_max, n_tests, n_cand, clearance);
+            n_cull += (unsigned)nc;
+            if (lane == 0) {
+                cempty[chk] = none ? 1 : 0;
+                cblk[chk] = blk_moved;
+                cgap[chk] = clearance - kClearSlack;
+            }
+            if (lane < nc) disp[t0 + lane] = 0.f;
+            __syncwarp();
         }
-        if (lane < nc) disp[t0 + lane] = 0.f;
-        __syncwarp();
+        start += n_g;
     }
     acc_arm = warp_sum(acc_arm);
     acc_blk = warp_sum(acc_blk);
