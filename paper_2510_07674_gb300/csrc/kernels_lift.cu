@@ -1,7 +1,8 @@
-// Lift of Sec. III-B: placements -> joint-space trajectory particles.  One thread per IK
-// target (the grasp of each block's initial pose and its placement) solves the tool pose,
-// by damped least squares or by the closed-form IK of the Franka joint layout; one thread
-// per remaining configuration interpolates start -> intermediate waypoint -> goal.
+// Lift of Sec. III-B: placements -> joint-space trajectory particles.  The IK targets (the
+// grasp of each block's initial pose and its placement) are solved by the closed-form IK of
+// the Franka joint layout, one warp per target with a lane per value of the free last joint
+// (ik_mode 1), or by damped least squares, one thread per target (ik_mode 0); one thread per
+// remaining configuration interpolates start -> intermediate waypoint -> goal.
 #include "launch_s2.h"
 #include "stage2.cuh"
 
@@ -210,37 +211,17 @@ __device__ void ik_analytic_nearest(const Scalars& sc, const float Rs[9], const 
     }
 }
 
-// Analytic lift of one target: the last joint takes the seed's value, then one uniform draw
-// in each of kQ6Strips equal strips of its limit range (strip i: word i mod 4 of the Philox
-// counter (8 c0 + i/4, particle, kTagQ6, attempt)).  On success q holds the in-limit solution
-// nearest the seed (first found on ties) and true is returned.
+// The analytic lift tries, per target, the seed's value of the last joint and one uniform
+// draw in each of kQ6Strips equal strips of its limit range (strip i: word i mod 4 of the
+// Philox counter (8 c0 + i/4, particle, kTagQ6, attempt)), and keeps the in-limit solution
+// nearest the seed, the first in that order on ties.
 constexpr int kQ6Strips = 31;
 
-__device__ bool ik_analytic_lift(const Scalars& sc, const float Rs[9], const float ps[3], uint32_t c0, int p,
-                                 uint32_t attempt, const float seed[7], float q[7]) {
-    float best_d = INFINITY;
-    ik_analytic_nearest(sc, Rs, ps, seed[6], seed, q, best_d);
-    const float lo = sc.qlo[6], span = sc.qhi[6] - sc.qlo[6];
-    for (int w = 0; 4 * w < kQ6Strips; ++w) {
-        const U4 r = philox4x32_10(8u * c0 + (uint32_t)w, (uint32_t)p, kTagQ6, attempt, sc.seed);
-        const uint32_t u[4] = {r.x, r.y, r.z, r.w};
-        for (int j = 0; j < 4 && 4 * w + j < kQ6Strips; ++j) {
-            const float strip = ((float)(4 * w + j) + u01(u[j])) / (float)kQ6Strips;
-            ik_analytic_nearest(sc, Rs, ps, lo + strip * span, seed, q, best_d);
-        }
-    }
-    return best_d < INFINITY;
-}
-
-// one thread per (particle, block, grasp|place)
-__global__ void k_lift_ik(const __grid_constant__ Scalars sc, int n, const float* __restrict__ place, int np,
-                          uint32_t attempt, float* __restrict__ q) {
-    const int gid = blockIdx.x * blockDim.x + threadIdx.x;
+// Tool target of IK target r = 2b + which of particle p: Rz(yaw + k pi/2) Rx(pi) at the top
+// face of block b (+ grasp offset), at its initial pose (which = 0) or its placement (1).
+__device__ __forceinline__ void lift_target(const Scalars& sc, const float* __restrict__ place, int np, int p, int b,
+                                            int which, uint32_t attempt, float Rs[9], float ps[3]) {
     const int B = sc.B;
-    if (gid >= n * 2 * B) return;
-    if (np <= 0) return;
-    const int p = gid / (2 * B), r = gid % (2 * B), b = r >> 1, which = r & 1;
-    if (which == 1 && sc.kind == kKindP2P) return;   // point to point: no placement
     const U4 kk = philox4x32_10((uint32_t)b, (uint32_t)p, kTagGrasp, attempt, sc.seed);
     float pose[4];
     if (which == 0) {
@@ -252,16 +233,76 @@ __global__ void k_lift_ik(const __grid_constant__ Scalars sc, int n, const float
     const int k = (int)((which == 0 ? kk.x : kk.y) & 3u);
     float s, c;
     sincosf(pose[3] + 0.5f * kPi * (float)k, &s, &c);
-    // tool target: Rz(yaw) Rx(pi), at the block's top face (+grasp offset)
-    const float Rs[9] = {c, s, 0.f, s, -c, 0.f, 0.f, 0.f, -1.f};
-    const float ps[3] = {pose[0], pose[1], pose[2] + sc.half[b].z + sc.grasp_off};
-    float qq[7], seed[7];
-    perturbed_home(sc, (uint32_t)(2 * b + which), p, kTagIkSeed, attempt, 0.3f, seed);
-    const bool analytic = sc.ik_mode == 1 && ik_analytic_lift(sc, Rs, ps, (uint32_t)(2 * b + which), p, attempt, seed, qq);
-    if (!analytic) {   // damped least squares (ik_mode 0, or no in-limit analytic solution)
+    Rs[0] = c;   Rs[1] = s;   Rs[2] = 0.f;
+    Rs[3] = s;   Rs[4] = -c;  Rs[5] = 0.f;
+    Rs[6] = 0.f; Rs[7] = 0.f; Rs[8] = -1.f;
+    ps[0] = pose[0]; ps[1] = pose[1]; ps[2] = pose[2] + sc.half[b].z + sc.grasp_off;
+}
+
+// Analytic lift, one warp per IK target: lane 0 takes the seed's last-joint value, lane
+// 1 + i strip i of ik_analytic_lift; each lane keeps its nearest in-limit branch and the warp
+// takes the nearest over lanes, the lowest lane on ties, which is the choice of the
+// sequential scan.  A target without an in-limit solution falls back to damped least
+// squares on lane 0.
+__global__ void k_lift_ik_analytic(const __grid_constant__ Scalars sc, int n, const float* __restrict__ place, int np,
+                                   uint32_t attempt, float* __restrict__ q) {
+    const int lane = threadIdx.x & 31;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int B = sc.B;
+    if (gw >= n * 2 * B || np <= 0) return;   // warp-uniform
+    const int p = gw / (2 * B), r = gw % (2 * B), b = r >> 1, which = r & 1;
+    if (which == 1 && sc.kind == kKindP2P) return;   // point to point: no placement
+    float Rs[9], ps[3], seed[7], best[7];
+    lift_target(sc, place, np, p, b, which, attempt, Rs, ps);
+    const uint32_t c0 = (uint32_t)(2 * b + which);
+    perturbed_home(sc, c0, p, kTagIkSeed, attempt, 0.3f, seed);
+#pragma unroll
+    for (int j = 0; j < 7; ++j) best[j] = seed[j];
+    float q6 = seed[6];
+    if (lane >= 1 && lane <= kQ6Strips) {
+        const int i = lane - 1;
+        const U4 u = philox4x32_10(8u * c0 + (uint32_t)(i >> 2), (uint32_t)p, kTagQ6, attempt, sc.seed);
+        const uint32_t word = (i & 3) == 0 ? u.x : (i & 3) == 1 ? u.y : (i & 3) == 2 ? u.z : u.w;
+        const float strip = ((float)i + u01(word)) / (float)kQ6Strips;
+        q6 = sc.qlo[6] + strip * (sc.qhi[6] - sc.qlo[6]);
+    }
+    float d = INFINITY;
+    if (lane <= kQ6Strips) ik_analytic_nearest(sc, Rs, ps, q6, seed, best, d);
+    int win = lane;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const float od = __shfl_xor_sync(0xffffffffu, d, off);
+        const int ow = __shfl_xor_sync(0xffffffffu, win, off);
+        if (od < d || (od == d && ow < win)) { d = od; win = ow; }
+    }
+    float qq[7];
+#pragma unroll
+    for (int j = 0; j < 7; ++j) qq[j] = __shfl_sync(0xffffffffu, best[j], win);
+    if (lane != 0) return;
+    if (!(d < INFINITY)) {
         for (int j = 0; j < 7; ++j) qq[j] = seed[j];
         ik_dls(sc, Rs, ps, qq);
     }
+    const int t = which == 0 ? t_grasp(sc.S, b) : t_place(sc.S, b);
+    float* dst = q + ((size_t)p * sc.C + t) * 8;
+    for (int j = 0; j < 7; ++j) dst[j] = qq[j];
+    dst[7] = 0.f;
+}
+
+// Damped-least-squares lift (ik_mode 0), one thread per (particle, block, grasp|place)
+__global__ void k_lift_ik(const __grid_constant__ Scalars sc, int n, const float* __restrict__ place, int np,
+                          uint32_t attempt, float* __restrict__ q) {
+    const int gid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int B = sc.B;
+    if (gid >= n * 2 * B) return;
+    if (np <= 0) return;
+    const int p = gid / (2 * B), r = gid % (2 * B), b = r >> 1, which = r & 1;
+    if (which == 1 && sc.kind == kKindP2P) return;   // point to point: no placement
+    float Rs[9], ps[3];
+    lift_target(sc, place, np, p, b, which, attempt, Rs, ps);
+    float qq[7];
+    perturbed_home(sc, (uint32_t)(2 * b + which), p, kTagIkSeed, attempt, 0.3f, qq);
+    ik_dls(sc, Rs, ps, qq);
     const int t = which == 0 ? t_grasp(sc.S, b) : t_place(sc.S, b);
     float* dst = q + ((size_t)p * sc.C + t) * 8;
     for (int j = 0; j < 7; ++j) dst[j] = qq[j];
@@ -305,7 +346,12 @@ cudaError_t launch_lift(const Scalars& sc, int n, const float* place, int n_plac
                         cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
     const int n_ik = n * 2 * sc.B;
-    k_lift_ik<<<(n_ik + 127) / 128, 128, 0, st>>>(sc, n, place, n_place, attempt, q);
+    if (sc.ik_mode == 1) {
+        const long long threads = 32LL * n_ik;   // a warp per target
+        k_lift_ik_analytic<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(sc, n, place, n_place, attempt, q);
+    } else {
+        k_lift_ik<<<(n_ik + 127) / 128, 128, 0, st>>>(sc, n, place, n_place, attempt, q);
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int n_cfg = n * sc.C;

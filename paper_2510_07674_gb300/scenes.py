@@ -104,7 +104,7 @@ class Params:
     mu0: float = 1.0
     mu_max: float = 8.0
     ik_damp: float = 1e-2
-    ik_mode: int = 0          # lift IK: 0 damped least squares, 1 analytic (Franka joint layout)
+    ik_mode: int = 1          # lift IK: 1 analytic (Franka joint layout, as the paper), 0 damped least squares
     seed: int = 0
     max_steps: int = 30000
     n_threads: int = 1

@@ -18,8 +18,8 @@ from paper_2510_07674_gb300 import scenes
 from paper_2510_07674_gb300 import spasm as S
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
-CASES = ["e2e_tower1.json", "e2e_tower4_Q64.json", "e2e_p2p_Q64_max_steps1000.json", "e2e_tower1_ik_mode1.json",
-         "e2e_tower4_Q64_ik_mode1.json"]
+CASES = ["e2e_tower1_ik_mode1.json", "e2e_tower4_Q64_ik_mode1.json", "e2e_p2p_Q64_ik_mode1_max_steps1000.json",
+         "e2e_tower1_ik_mode0.json", "e2e_tower4_Q64_ik_mode0.json", "e2e_p2p_Q64_ik_mode0_max_steps1000.json"]
 
 
 def gpu_best(workload, seed, overrides):

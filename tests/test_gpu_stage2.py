@@ -73,12 +73,12 @@ def test_traj_eval_matches_oracle(name, seed, n, sigma, kw):
 
 
 def test_lift_matches_oracle():
-    """Interpolated waypoints are exact functions of the endpoints and via points; every IK
+    """ik_mode 0 (damped least squares).  Interpolated waypoints are exact functions of the endpoints and via points; every IK
     endpoint that converges in the oracle (tool pose within 1e-6 of its target) lands on
     the same joint solution on the GPU.  Endpoints where damped least squares stalls (a
     joint limit, a singular direction) may stop at different points in FP32 and FP64."""
     S = _S()
-    wl = scenes.make_problem("tower4", seed=3, B=3, O=8, W=10)
+    wl = scenes.make_problem("tower4", seed=3, B=3, O=8, W=10, ik_mode=0)
     orc = O.Oracle(wl)
     sol, _, _ = orc.place_solve()
     pr = S.Problem(wl)

@@ -37,7 +37,7 @@ def test_lift_endpoint_reaches_the_target(case):
             hits += 1
             L, g, cg, path, jl, h = o.traj_cost(q)
             assert np.abs(h[:5]).max() < 1e-6   # aligned: position and tilt residuals vanish
-    assert hits >= 4   # damped least squares can stall (a joint limit, a singular direction)
+    assert hits >= 4   # a target without an in-limit closed-form solution falls back to damped least squares
 
 
 def test_gradient_matches_central_differences(case):
