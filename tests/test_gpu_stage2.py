@@ -175,6 +175,43 @@ def test_descend_matches_oracle_few_steps():
         assert err < 1e-4, (p, err)
 
 
+def test_descend_full_schedule_matches_oracle():
+    """All K_traj = 50 steps in one launch, over which the cached cull skips and re-culls
+    chunks: the trajectories stay with the FP64 oracle's (FP32 rounding accumulates over
+    the steps, and a contact switching on or off in one precision only can move a particle)."""
+    S = _S()
+    wl, orc, _, qs = _cases("tower4", 2, 8, 0.05)
+    pr = S.Problem(wl)
+    n = len(qs)
+    q = _to_dev(qs, pr.C)
+    q0 = np.stack([q[p, :, :7].cpu().double().numpy() for p in range(n)])
+    lam = torch.zeros(n, pr.NR, device="cuda")
+    mu = torch.full((n,), float(wl.params.mu0), device="cuda")
+    K = wl.params.K_traj
+    S.spasm_traj_descend(pr, n, q, lam, mu, K, 1)
+    torch.cuda.synchronize()
+    qr, _, _ = orc.traj_descend(q0, k_steps=K)
+    err = np.array([np.abs(q[p, :, :7].cpu().double().numpy() - qr[p]).max() for p in range(n)])
+    assert np.median(err) < 1e-3 and np.mean(err < 1e-2) >= 0.75, np.sort(err)
+
+
+def test_cached_cull_engages_and_counts():
+    """The trajectory kernel's counters: some configurations keep their cull between
+    iterations (fewer culled than evaluated), and only culled configurations can have a
+    candidate."""
+    S = _S()
+    wl = scenes.make_problem("tower4", seed=1)
+    pr = S.Problem(wl)
+    try:
+        S.spasm_optimize(pr)
+        st = S.spasm_get_stats(pr)
+    finally:
+        pr.close()
+    evals = wl.params.Q * (wl.params.K_traj + 1) * st["traj_launches"]
+    assert 0 < st["cand_configs"] <= st["cull_configs"] < evals * (pr.C - 1), st
+    assert st["tests_executed"] > 0
+
+
 def test_optimize_end_to_end_tower1():
     """Both stages on the device; every returned trajectory passes the FP64 oracle check."""
     S = _S()
