@@ -882,7 +882,8 @@ __device__ void traj_evaluate(const Scalars& sc, const LaneSpheres& ls, const fl
     }
     __syncthreads();
     if (grad) {
-        // (c) warp 0: placement gradient w.r.t. the placed poses; warp 1: grasp gradients
+        // (c) warp 0: placement gradient w.r.t. the placed poses, then (d) the place configurations'
+        // gradient rows; warp 1: grasp gradients
         if (w == 0 && !p2p) {
             float my_D, my_e;
             place_stack_warp(sc, sh.pose, kPlaceExplicit, &sh.s[8 * B], &sh.s[7 * B], sh.g4, sh.ps, my_D, my_e);
@@ -898,16 +899,16 @@ __device__ void traj_evaluate(const Scalars& sc, const LaneSpheres& ls, const fl
                 if (kb + 1 < B) gc += sh.pgc[kb][c];
                 sh.g4[i] += s_coll * gc + s_arm * wa + s_blk * wb;
             }
+            __syncwarp();
+            // (d) place configurations: tilt residuals and the placed-pose gradient through fk
+            if (lane < B) {
+                float hbuf[5];
+                start_terms(sc, lane, 1, sp[2 * lane + 1], hbuf, &sh.s[5 * B + 2 * lane], sh.extra[B + lane],
+                            &sh.g4[4 * lane]);
+            }
         } else if (w == 1 && lane < B) {
             float hbuf[5];
             start_terms(sc, lane, 0, sp[2 * lane], hbuf, &sh.s[5 * lane], sh.extra[lane], nullptr);
-        }
-        __syncthreads();
-        // (d) place configurations: tilt residuals and the placed-pose gradient through fk
-        if (w == 1 && lane < B && !p2p) {
-            float hbuf[5];
-            start_terms(sc, lane, 1, sp[2 * lane + 1], hbuf, &sh.s[5 * B + 2 * lane], sh.extra[B + lane],
-                        &sh.g4[4 * lane]);
         }
         __syncthreads();
     }
