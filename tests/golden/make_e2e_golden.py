@@ -12,10 +12,13 @@ called.
     python tests/golden/make_e2e_golden.py p2p --seeds 100 --override Q=64 --override max_steps=1000
     python tests/golden/make_e2e_golden.py tower1 --seeds 100 --override ik_mode=1
     python tests/golden/make_e2e_golden.py tower4 --seeds 50 --override Q=64 --override ik_mode=1
+    python tests/golden/make_e2e_golden.py tetris5 --seeds 100 --override N=2048 --override M=512 --override max_steps=3000
 
 ik_mode=1 lifts with the analytic IK of the Franka joint layout instead of damped least squares.
 
-For the point-to-point workload (one transit segment to a tool target) only stage 2 runs.
+For the point-to-point workload (one transit segment to a tool target) only stage 2 runs; for
+the packing workloads (the appendix's Tetris problem) only stage 1, and the stored costs are the
+stage-1 costs of the returned placements.
 
 The 4-block case keeps its scene, stage-1 sizes and waypoint count, and reduces the number of
 trajectory particles so that the FP64 all-pairs oracle finishes 100 seeds in about an hour.
@@ -44,6 +47,13 @@ def parse_overrides(items):
 
 
 def run_seed(name, seed, overrides, threads):
+    if name in scenes.PACKINGS:
+        wl = scenes.make_packing(name, seed=seed, **overrides)
+        o = Oracle(wl, n_threads=threads)
+        place, place_attempts, _ = o.place_solve()
+        cost = sorted(float(o.place_cost(x, grad=False)[0]) for x in place)
+        return {"seed": seed, "n_place": int(len(place)), "n_found": int(len(place)), "cost": cost,
+                "place_attempts": int(place_attempts), "traj_attempts": 0}
     if name in scenes.P2P:
         wl = scenes.make_p2p(name, seed=seed, **overrides)
         o = Oracle(wl, n_threads=threads)
