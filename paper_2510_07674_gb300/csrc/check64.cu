@@ -60,7 +60,9 @@ __device__ __forceinline__ double pen_env64(const Scalars64& s, const D4* cub, c
 }
 
 constexpr int kChkThreads = 128;
-constexpr int kChkMaxSplit = 8;
+constexpr int kChkLanes = 4;                            // lanes sharing one configuration's spheres
+constexpr int kChkCfgs = kChkThreads / kChkLanes;       // configurations per CTA pass
+constexpr int kChkMaxSplit = (1024 + kChkCfgs - 1) / kChkCfgs;
 
 __global__ void __launch_bounds__(kChkThreads) k_check64(const __grid_constant__ Scalars64 s, const D4* __restrict__ cub,
                                                         const D4* __restrict__ osph, const float* __restrict__ q,
@@ -106,16 +108,23 @@ __global__ void __launch_bounds__(kChkThreads) k_check64(const __grid_constant__
     }
     __syncthreads();
 
-    // arm and held-block penetrations over every configuration, joint limits
+    // arm and held-block penetrations over every configuration, joint limits.  A quad of
+    // lanes takes one configuration: each lane runs the kinematics and a quarter of its
+    // spheres; every lane of a warp takes the same number of passes, so the quad shuffles
+    // see all lanes.
     double maxpen = 0.0;
     int limits_ok = 1;
-    for (int t = 1 + tid + slice * kChkThreads; t < C; t += kChkThreads * split) {
-        const int seg = (t - 1) / S, b = seg >> 1, jj = t - seg * S;
+    const int quad = tid & (kChkLanes - 1);
+    for (int base = slice * kChkCfgs; base < C - 1; base += kChkCfgs * split) {
+        const int t = 1 + base + tid / kChkLanes;
+        const bool valid = t < C;
+        const int tt = valid ? t : C - 1;
+        const int seg = (tt - 1) / S, b = seg >> 1, jj = tt - seg * S;
         const bool held = (seg & 1) && jj < S;
         double qq[7], R[8][9], o[8][3], Rt[9], pt[3];
         for (int j = 0; j < 7; ++j) {
-            qq[j] = qr[t * 8 + j];
-            if (qq[j] < s.qlo[j] || qq[j] > s.qhi[j]) limits_ok = 0;
+            qq[j] = qr[tt * 8 + j];
+            if (valid && (qq[j] < s.qlo[j] || qq[j] > s.qhi[j])) limits_ok = 0;
         }
         fk64(s, qq, R, o, Rt, pt);
         const int n_items = s.n_rsph + (held ? 8 : 0);
@@ -140,14 +149,23 @@ __global__ void __launch_bounds__(kChkThreads) k_check64(const __grid_constant__
                 rad = s.hmin[b] * 0.5;
             }
         };
-        // exact cull: box of all spheres of this configuration against each obstacle's box
+        // exact cull: box of all spheres of this configuration (the quad's four shares)
+        // against each obstacle's box
         double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
-        for (int it = 0; it < n_items; ++it) {
+        for (int it = quad; it < n_items; it += kChkLanes) {
             double cx, cy, cz, rad;
             centre(it, cx, cy, cz, rad);
             lo[0] = fmin(lo[0], cx - rad); lo[1] = fmin(lo[1], cy - rad); lo[2] = fmin(lo[2], cz - rad);
             hi[0] = fmax(hi[0], cx + rad); hi[1] = fmax(hi[1], cy + rad); hi[2] = fmax(hi[2], cz + rad);
         }
+#pragma unroll
+        for (int off = 1; off < kChkLanes; off <<= 1)
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                lo[a] = fmin(lo[a], __shfl_xor_sync(0xffffffffu, lo[a], off));
+                hi[a] = fmax(hi[a], __shfl_xor_sync(0xffffffffu, hi[a], off));
+            }
+        if (!valid) continue;
         auto visit = [&](const D4* c) {
             // box of a cuboid record: centre +- |R| h
             double e[3];
@@ -156,7 +174,7 @@ __global__ void __launch_bounds__(kChkThreads) k_check64(const __grid_constant__
             if (c[0].x - e[0] > hi[0] || c[0].x + e[0] < lo[0] || c[0].y - e[1] > hi[1] || c[0].y + e[1] < lo[1] ||
                 c[0].z - e[2] > hi[2] || c[0].z + e[2] < lo[2])
                 return;
-            for (int it = 0; it < n_items; ++it) {
+            for (int it = quad; it < n_items; it += kChkLanes) {
                 double cx, cy, cz, rad, gx, gy, gz;
                 centre(it, cx, cy, cz, rad);
                 maxpen = fmax(maxpen, pen_cuboid<double>(cx, cy, cz, rad, c[0], c[1], c[2], c[3], gx, gy, gz));
@@ -168,7 +186,7 @@ __global__ void __launch_bounds__(kChkThreads) k_check64(const __grid_constant__
             if (sp.x - sp.w > hi[0] || sp.x + sp.w < lo[0] || sp.y - sp.w > hi[1] || sp.y + sp.w < lo[1] ||
                 sp.z - sp.w > hi[2] || sp.z + sp.w < lo[2])
                 continue;
-            for (int it = 0; it < n_items; ++it) {
+            for (int it = quad; it < n_items; it += kChkLanes) {
                 double cx, cy, cz, rad, gx, gy, gz;
                 centre(it, cx, cy, cz, rad);
                 maxpen = fmax(maxpen, pen_sphere<double>(cx, cy, cz, rad, sp, gx, gy, gz));
@@ -257,7 +275,7 @@ __global__ void __launch_bounds__(kChkThreads) k_check64(const __grid_constant__
 cudaError_t launch_check64(const Scalars64& s, const void* cub, const void* osph, const float* q, const int* n_sol, int P,
                            double* metrics, int* ok, CheckAcc* acc, cudaStream_t st) {
     if (P <= 0) return cudaSuccess;
-    const int split = max(1, min(kChkMaxSplit, (s.C - 1 + kChkThreads - 1) / kChkThreads));
+    const int split = max(1, min(kChkMaxSplit, (s.C - 1 + kChkCfgs - 1) / kChkCfgs));
     k_check64<<<dim3(P, split), kChkThreads, 0, st>>>(s, static_cast<const D4*>(cub), static_cast<const D4*>(osph), q, n_sol,
                                                       P, metrics, ok, acc, split);
     return cudaGetLastError();
