@@ -10,13 +10,13 @@
 
 namespace spasm {
 
-__device__ __forceinline__ void fk64(const Scalars64& s, const double q[7], double R[8][9], double o[8][3],
-                                     double Rt[9], double pt[3]) {
+// Kinematics from the joint angles' sines and cosines.
+__device__ __forceinline__ void fk64_sc(const Scalars64& s, const double sn7[7], const double cs7[7], double R[8][9],
+                                        double o[8][3], double Rt[9], double pt[3]) {
     for (int i = 0; i < 9; ++i) R[0][i] = (i % 4 == 0) ? 1.0 : 0.0;
     o[0][0] = o[0][1] = o[0][2] = 0.0;
     for (int k = 0; k < 7; ++k) {
-        double sn, cs;
-        sincos(s.th0[k] + q[k], &sn, &cs);
+        const double sn = sn7[k], cs = cs7[k];
         for (int i = 0; i < 9; ++i) R[k + 1][i] = R[k][i];
         for (int i = 0; i < 3; ++i) o[k + 1][i] = o[k][i];
         dh_step<double>(R[k + 1], o[k + 1], s.ca[k], s.sa[k], s.a[k], s.d[k], cs, sn);
@@ -26,6 +26,13 @@ __device__ __forceinline__ void fk64(const Scalars64& s, const double q[7], doub
             Rt[3 * i + j] = R[7][3 * i] * s.ee_R[j] + R[7][3 * i + 1] * s.ee_R[3 + j] + R[7][3 * i + 2] * s.ee_R[6 + j];
         pt[i] = o[7][i] + R[7][3 * i] * s.ee_p[0] + R[7][3 * i + 1] * s.ee_p[1] + R[7][3 * i + 2] * s.ee_p[2];
     }
+}
+
+__device__ __forceinline__ void fk64(const Scalars64& s, const double q[7], double R[8][9], double o[8][3],
+                                     double Rt[9], double pt[3]) {
+    double sn[7], cs[7];
+    for (int k = 0; k < 7; ++k) sincos(s.th0[k] + q[k], &sn[k], &cs[k]);
+    fk64_sc(s, sn, cs, R, o, Rt, pt);
 }
 
 __device__ __forceinline__ void held64(const Scalars64& s, int b, const double Rt[9], const double pt[3], double Rb[9],
@@ -63,6 +70,7 @@ constexpr int kChkThreads = 128;
 constexpr int kChkLanes = 4;                            // lanes sharing one configuration's spheres
 constexpr int kChkCfgs = kChkThreads / kChkLanes;       // configurations per CTA pass
 constexpr int kChkMaxSplit = (1024 + kChkCfgs - 1) / kChkCfgs;
+static_assert(kChkLanes == 4, "a quad computes the seven joints' sines and cosines as joints q and q + 4");
 
 __global__ void __launch_bounds__(kChkThreads) k_check64(const __grid_constant__ Scalars64 s, const D4* __restrict__ cub,
                                                         const D4* __restrict__ osph, const float* __restrict__ q,
@@ -126,7 +134,21 @@ __global__ void __launch_bounds__(kChkThreads) k_check64(const __grid_constant__
             qq[j] = qr[tt * 8 + j];
             if (valid && (qq[j] < s.qlo[j] || qq[j] > s.qhi[j])) limits_ok = 0;
         }
-        fk64(s, qq, R, o, Rt, pt);
+        // the quad shares the joint angles' sines and cosines: lane `quad` takes joints quad and
+        // quad + 4
+        double sn7[7], cs7[7];
+        {
+            double s1, c1, s2 = 0.0, c2 = 1.0;
+            sincos(s.th0[quad] + qq[quad], &s1, &c1);
+            if (quad + 4 < 7) sincos(s.th0[quad + 4] + qq[quad + 4], &s2, &c2);
+            const int first = (tid & 31) & ~(kChkLanes - 1);
+#pragma unroll
+            for (int k = 0; k < 7; ++k) {
+                sn7[k] = __shfl_sync(0xffffffffu, k < 4 ? s1 : s2, first + (k & 3));
+                cs7[k] = __shfl_sync(0xffffffffu, k < 4 ? c1 : c2, first + (k & 3));
+            }
+        }
+        fk64_sc(s, sn7, cs7, R, o, Rt, pt);
         const int n_items = s.n_rsph + (held ? 8 : 0);
         double Rb[9], pb[3];
         if (held) held64(s, b, Rt, pt, Rb, pb);
