@@ -72,6 +72,77 @@ def test_traj_eval_matches_oracle(name, seed, n, sigma, kw):
     assert active > 0
 
 
+def test_traj_eval_and_descent_at_the_compiled_maxima():
+    """The largest problem the kernels take: 16 blocks, 256 cuboids (255 + table), 64
+    obstacle spheres, 993 configurations (W = 32), NR = 147 residuals, so 8 cuboid mask words,
+    2 sphere mask words, 16-bit block masks and one CTA per SM.  Objective, groups, residuals
+    and gradient against the oracle, then a few descent steps."""
+    S = _S()
+    wl = scenes.make_problem("tower10", seed=0, B=16, O=255, W=32, n_obstacle_spheres=64, Q=4)
+    orc = O.Oracle(wl, n_threads=8)
+    pr = S.Problem(wl)
+    C, NR = pr.C, pr.NR
+    assert (C, NR, len(wl.scene.cuboid), len(wl.scene.sphere)) == (993, 147, 256, 64)
+    rng = np.random.default_rng(3)
+    qs = []
+    for p, sigma in enumerate((0.1, 0.3, 0.6)):
+        qp = np.tile(wl.robot.q_home, (C, 1)) + rng.normal(0, sigma, (C, 7))
+        qp = np.clip(qp, wl.robot.qlim[:, 0], wl.robot.qlim[:, 1])
+        qp[0] = wl.robot.q_home
+        qs.append(qp)
+    n = len(qs)
+    q = _to_dev(qs, C)
+    lam_np = rng.uniform(0, 2, (n, NR)).astype(np.float32)
+    mu_np = rng.uniform(0.5, 4, n).astype(np.float32)
+    lam, mu = torch.from_numpy(lam_np).cuda(), torch.from_numpy(mu_np).cuda()
+    L, grad = torch.empty(n, device="cuda"), torch.empty(n, C, 8, device="cuda")
+    groups, h = torch.empty(n, 6, device="cuda"), torch.empty(n, NR, device="cuda")
+    S.spasm_traj_eval(pr, n, q, lam, mu, L, grad, groups, h)
+    torch.cuda.synchronize()
+    for p in range(n):
+        qp = q[p, :, :7].cpu().double().numpy()
+        Lo, go, cgo, path, jl, ho = orc.traj_cost(qp, lam_np[p].astype(np.float64), float(mu_np[p]))
+        assert cgo[1] > 0   # the arm collides: every mask word and candidate path is exercised
+        assert abs(L[p].item() - Lo) <= RTOL * max(abs(Lo), 1e-2), (p, L[p].item(), Lo)
+        np.testing.assert_allclose(groups[p].cpu().double().numpy(), cgo, rtol=1e-3, atol=1e-6)
+        np.testing.assert_allclose(h[p].cpu().double().numpy(), ho, rtol=1e-3, atol=1e-5)
+        gd = grad[p, :, :7].cpu().double().numpy()
+        assert np.linalg.norm(gd - go) / max(np.linalg.norm(go), 1e-2) <= RTOL, p
+    q0 = np.stack([q[p, :, :7].cpu().double().numpy() for p in range(n)])
+    lam0, mu0 = torch.zeros(n, NR, device="cuda"), torch.full((n,), float(wl.params.mu0), device="cuda")
+    S.spasm_traj_descend(pr, n, q, lam0, mu0, 3, 1)
+    torch.cuda.synchronize()
+    qr, _, _ = orc.traj_descend(q0, k_steps=3)
+    # these states collide hard (objective ~1e4), so a step moves joints by up to the limits and
+    # FP32 rounding of the gradient (~1e-5 relative) shows at the 1e-3 level on a few entries,
+    # more where a contact switches between the two precisions
+    err = np.abs(np.stack([q[p, :, :7].cpu().double().numpy() for p in range(n)]) - qr)
+    assert np.quantile(err, 0.99) < 1e-3 and err.max() < 2e-2, (np.quantile(err, 0.99), err.max())
+
+
+def test_empty_calls_do_nothing():
+    """n = 0 at every kernel-level entry point: success, no work, outputs untouched."""
+    S = _S()
+    wl = scenes.make_problem("tower1", seed=0)
+    pr = S.Problem(wl)
+    try:
+        x = torch.full((4 * pr.B, 1), 7.0, device="cuda")
+        cost = torch.full((1,), 7.0, device="cuda")
+        S.spasm_place_sample(pr, 0, 0, x, cost)
+        S.spasm_place_eval(pr, 0, x, 0, cost, None, None, None)
+        S.spasm_place_descend(pr, 0, x, 2, 1)
+        q = torch.full((1, pr.C, 8), 7.0, device="cuda")
+        place = torch.zeros(1, 4 * pr.B, device="cuda")
+        S.spasm_lift(pr, 0, place, 1, 0, q)
+        L = torch.full((1,), 7.0, device="cuda")
+        S.spasm_traj_eval(pr, 0, q, None, None, L, None, None, None)
+        S.spasm_traj_descend(pr, 0, q, None, None, 2, 1)
+        torch.cuda.synchronize()
+        assert torch.all(x == 7.0) and torch.all(cost == 7.0) and torch.all(q == 7.0) and torch.all(L == 7.0)
+    finally:
+        pr.close()
+
+
 def test_lift_matches_oracle():
     """ik_mode 0 (damped least squares).  Interpolated waypoints are exact functions of the endpoints and via points; every IK
     endpoint that converges in the oracle (tool pose within 1e-6 of its target) lands on
