@@ -21,10 +21,15 @@ def _soa_to_particles(x, B):
     return x.detach().cpu().double().numpy().T.reshape(-1, B, 4)
 
 
-@pytest.mark.parametrize("name,n", [("tower1", 77), ("tower4", 333), ("tower10", 141)])
-def test_sample_and_cost_match_oracle(name, n):
+# the last case is the largest problem the kernels take (16 blocks, 256 cuboids, 64 spheres)
+MAXIMA = {"B": 16, "O": 255, "n_obstacle_spheres": 64}
+
+
+@pytest.mark.parametrize("name,n,kw", [("tower1", 77, {}), ("tower4", 333, {}), ("tower10", 141, {}),
+                                       ("tower10", 65, MAXIMA)])
+def test_sample_and_cost_match_oracle(name, n, kw):
     S = _S()
-    wl = scenes.make_problem(name, seed=1)
+    wl = scenes.make_problem(name, seed=1, **kw)
     orc = O.Oracle(wl)
     pr = S.Problem(wl)
     x = torch.empty(4 * pr.B, n, device="cuda")
@@ -40,10 +45,10 @@ def test_sample_and_cost_match_oracle(name, n):
 
 
 @pytest.mark.parametrize("quad", [0, 1])
-@pytest.mark.parametrize("name", ["tower4", "tower10"])
-def test_eval_cost_grad_terms_match_oracle(name, quad):
+@pytest.mark.parametrize("name,kw", [("tower4", {}), ("tower10", {}), ("tower10", MAXIMA)])
+def test_eval_cost_grad_terms_match_oracle(name, kw, quad):
     S = _S()
-    wl = scenes.make_problem(name, seed=2)
+    wl = scenes.make_problem(name, seed=2, **kw)
     orc = O.Oracle(wl)
     pr = S.Problem(wl)
     n, B = 203, pr.B
