@@ -61,22 +61,39 @@ def kernel_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def traffic_from_profile():
-    """DRAM bytes per k_traj launch recorded by the committed ncu summary, if it was taken
-    on the current kernel sources (else None)."""
+def profile_values() -> dict:
+    """Entries of the committed ncu summary of k_traj, if it was taken on the current kernel
+    sources (else {})."""
     if not os.path.exists(PROFILE_SUMMARY):
-        return None
+        return {}
     vals = {}
     for line in open(PROFILE_SUMMARY):
         if ":" in line and line.strip().startswith("- "):
             k, v = line.strip()[2:].split(":", 1)
             vals[k.strip()] = v.strip()
-    if vals.get("kernel_sources_sha256_16") != kernel_hash():
-        return None
+    return vals if vals.get("kernel_sources_sha256_16") == kernel_hash() else {}
+
+
+def traffic_from_profile():
+    """DRAM bytes per k_traj launch recorded by the committed ncu summary (None if stale)."""
     try:
-        return float(vals["dram_bytes_per_full_launch"])
+        return float(profile_values()["dram_bytes_per_full_launch"])
     except (KeyError, ValueError):
         return None
+
+
+def issue_from_profile() -> dict:
+    """Issue activity and top stall of k_traj from the committed ncu summary ({} if stale):
+    the kernel is bound by instruction issue and latency, which the ALU fraction does not show."""
+    vals = profile_values()
+    out = {}
+    try:
+        out["issue_active_pct"] = float(vals["issue_active_pct"])
+    except (KeyError, ValueError):
+        pass
+    if "top stalls per issued instruction" in vals:
+        out["top_stalls_per_issue"] = vals["top stalls per issued instruction"]
+    return out
 
 
 def dist_env():
@@ -264,7 +281,8 @@ def run_native(args, ws, rank, local):
                 "tests_per_particle_iter_executed": tests_exec / max(evals, 1),
                 "culled_configs_per_particle_iter": cull_cfg / max(evals, 1),
                 "candidate_configs_per_particle_iter": cand_cfg / max(evals, 1),
-                "effective_pair_tests_per_s": tc["tests"] * evals / max(traj_ms / 1000.0, 1e-9)}
+                "effective_pair_tests_per_s": tc["tests"] * evals / max(traj_ms / 1000.0, 1e-9),
+                "ncu": issue_from_profile()}
     succ = [s["n_success"] > 0 for s in stats]
 
     # ---- end to end through the public API with host buffers
