@@ -285,7 +285,10 @@ __device__ __forceinline__ bool chunk_collisions(const Scalars& sc, const LaneSp
                 if ((bal >> (8 * c)) & 0xffu) out[c] |= 1u << bit;
         }
     };
-    auto always = [](int) { return true; };
+    // link 0 (lane k = 0) is the fixed base: its gaps to static boxes (the environment, blocks
+    // at their initial poses) never shrink and do not bound the clearance
+    const bool moving_link = (lane & 7) != 0;
+    auto moving = [&](int) { return moving_link; };
     const int n_cw = (sc.n_cub + 31) >> 5, n_sw = (sc.n_osph + 31) >> 5;
     uint32_t per[kChunk], any[kChunk] = {0u, 0u, 0u, 0u};
     for (int wd = 0; wd < n_cw; ++wd) {
@@ -293,7 +296,7 @@ __device__ __forceinline__ bool chunk_collisions(const Scalars& sc, const LaneSp
         const float s1 = oi < sc.n_cub ? sep_chunk(aabb[2 * oi], aabb[2 * oi + 1]) : 3.4e38f;
         clear = fminf(clear, s1 > 0.f ? s1 : 3.4e38f);
         const unsigned m = __ballot_sync(0xffffffffu, s1 <= 0.f);
-        refine(m, 32 * wd, aabb, 2, per, always);
+        refine(m, 32 * wd, aabb, 2, per, moving);
         if (lane == 0)
 #pragma unroll
             for (int c = 0; c < kChunk; ++c) tw.cmask[c][wd] = per[c];
@@ -306,7 +309,7 @@ __device__ __forceinline__ bool chunk_collisions(const Scalars& sc, const LaneSp
         const float s1 = oi < sc.n_osph ? sep_chunk(aabb[2 * ai], aabb[2 * ai + 1]) : 3.4e38f;
         clear = fminf(clear, s1 > 0.f ? s1 : 3.4e38f);
         const unsigned m = __ballot_sync(0xffffffffu, s1 <= 0.f);
-        refine(m, sc.n_cub + 32 * wd, aabb, 2, per, always);
+        refine(m, sc.n_cub + 32 * wd, aabb, 2, per, moving);
         if (lane == 0)
 #pragma unroll
             for (int c = 0; c < kChunk; ++c) tw.smask[c][wd] = per[c];
@@ -331,7 +334,7 @@ __device__ __forceinline__ bool chunk_collisions(const Scalars& sc, const LaneSp
         const float si = lane < B ? sep_chunk(sh.iaabb[lane][0], sh.iaabb[lane][1]) : 3.4e38f;
         if (lane < B && lane > b_first && si > 0.f) clear = fminf(clear, si);
         const unsigned bm_init = __ballot_sync(0xffffffffu, si <= 0.f);
-        refine(bm_init, 0, &sh.iaabb[0][0], 2, per, [&](int k) { return k > b_lane; });
+        refine(bm_init, 0, &sh.iaabb[0][0], 2, per, [&](int k) { return k > b_lane && moving_link; });
         if (lane == 0)
 #pragma unroll
             for (int c = 0; c < kChunk; ++c) tw.bmask[1][c] = per[c];
