@@ -57,8 +57,8 @@ struct TShared {
     float4 lbc[8], lbh[8];   // link-frame boxes of each link's spheres (centre, half extents)
     float s_arm, s_blk, mu, L;
     float pose_prev[4 * kMaxB];   // placed poses of the previous evaluation
-    short active[(kMaxC + kChunk - 1) / kChunk];   // chunks to evaluate: group g (chunks 32g..32g+31) at 32g..
-    int n_group[kTWarps];                           // chunks to evaluate in group g
+    short active[2][(kMaxC + kChunk - 1) / kChunk];   // chunks to evaluate, [heavy|light][32g + i] for group g
+    int n_group[2][kTWarps];                           // chunks to evaluate in group g, heavy and light
     float blk_moved;              // running bound on how far the placed cuboids have moved
     int pose_prev_ok;
     float c_arm, c_blk, maxpen, c_coll, c_stable, c_height, c_start;
@@ -753,10 +753,12 @@ __device__ void traj_evaluate(const Scalars& sc, const LaneSpheres& ls, const fl
     const int n_chunks = (C - 1 + kChunk - 1) / kChunk;
     // Chunks to evaluate: those without a valid cached cull (none at its last cull, and
     // everything moved less than its clearance since).  Warp g lists those of chunks
-    // 32g .. 32g+31 in chunk order and zeroes the block-group gradient rows of the skipped ones
-    // (their arm-group rows are still zero from their last cull); the concatenated list is
-    // dealt to the warps round-robin, which keeps the per-warp sums deterministic and the
-    // warps' shares of the remaining work even.
+    // 32g .. 32g+31 in chunk order, in two tiers: heavy (candidates at the last cull: tests
+    // and the gradient chain) and light (a candidate-free chunk to cull again), and zeroes the
+    // block-group gradient rows of the skipped ones (their arm-group rows are still zero from
+    // their last cull).  The heavy list, then the light one, is dealt to the warps
+    // round-robin, which keeps the per-warp sums deterministic and the warps' shares of the
+    // remaining work even.
     static_assert((kMaxC + kChunk - 1) / kChunk <= 32 * kTWarps && (kTWarps & (kTWarps - 1)) == 0,
                   "one 32-chunk group per warp");
     const float blk_moved = sh.blk_moved;
@@ -769,9 +771,14 @@ __device__ void traj_evaluate(const Scalars& sc, const LaneSpheres& ls, const fl
             for (int i = 0; i < nc; ++i) d = fmaxf(d, disp[t0 + i]);
             active = !(d + (blk_moved - cblk[chk]) < cgap[chk]);
         }
-        const unsigned bal = __ballot_sync(0xffffffffu, active);
-        if (active) sh.active[32 * w + __popc(bal & ((1u << lane) - 1u))] = (short)chk;
-        if (lane == 0) sh.n_group[w] = __popc(bal);
+        const bool light = active && cempty[chk];
+        const unsigned bal_h = __ballot_sync(0xffffffffu, active && !light);
+        const unsigned bal_l = __ballot_sync(0xffffffffu, light);
+        if (active) {
+            const unsigned bal = light ? bal_l : bal_h;
+            sh.active[light ? 1 : 0][32 * w + __popc(bal & ((1u << lane) - 1u))] = (short)chk;
+        }
+        if (lane == 0) { sh.n_group[0][w] = __popc(bal_h); sh.n_group[1][w] = __popc(bal_l); }
         unsigned skipped = __ballot_sync(0xffffffffu, chk < n_chunks && !active);
         while (grad && skipped) {
             const int k = 32 * w + __ffs(skipped) - 1;
@@ -781,12 +788,13 @@ __device__ void traj_evaluate(const Scalars& sc, const LaneSpheres& ls, const fl
         }
     }
     __syncthreads();
-    // warp w takes positions w, w + 8, ... of the concatenated list, group by group
+    // warp w takes positions w, w + 8, ... of the concatenated lists, tier by tier, group by group
     int start = 0;
-    for (int g = 0; g < kTWarps; ++g) {
-        const int n_g = sh.n_group[g];
+    for (int tg = 0; tg < 2 * kTWarps; ++tg) {
+        const int tier = tg / kTWarps, g = tg % kTWarps;
+        const int n_g = sh.n_group[tier][g];
         for (int i = (w - start) & (kTWarps - 1); i < n_g; i += kTWarps) {
-            const int chk = sh.active[32 * g + i];
+            const int chk = sh.active[tier][32 * g + i];
             const int t0 = 1 + kChunk * chk;
             const int nc = min(kChunk, C - t0);
             const int c = lane >> 3;
