@@ -57,8 +57,10 @@ struct TShared {
     float4 lbc[8], lbh[8];   // link-frame boxes of each link's spheres (centre, half extents)
     float s_arm, s_blk, mu, L;
     float pose_prev[4 * kMaxB];   // placed poses of the previous evaluation
-    short active[2][(kMaxC + kChunk - 1) / kChunk];   // chunks to evaluate, [heavy|light][32g + i] for group g
-    int n_group[2][kTWarps];                           // chunks to evaluate in group g, heavy and light
+    // chunks to evaluate by tier (kChunk .. 1 configurations with candidates at the last cull, then the
+    // candidate-free ones to cull again): active[tier][32g + i] for group g
+    short active[kChunk + 1][(kMaxC + kChunk - 1) / kChunk];
+    int n_group[kChunk + 1][kTWarps];
     float blk_moved;              // running bound on how far the placed cuboids have moved
     int pose_prev_ok;
     float c_arm, c_blk, maxpen, c_coll, c_stable, c_height, c_start;
@@ -87,7 +89,7 @@ __host__ __device__ inline size_t t_cache_offset(int n_cub, int n_osph, int C, i
 }
 size_t traj_smem_bytes(const Scalars& sc) {
     return t_cache_offset(sc.n_cub, sc.n_osph, sc.C, sc.B) + (size_t)sc.C * sizeof(float) +
-           (size_t)t_n_chunks(sc.C) * (2 * sizeof(float) + sizeof(int));
+           (size_t)t_n_chunks(sc.C) * (2 * sizeof(float) + 2 * sizeof(int));
 }
 
 // The robot spheres a lane owns (item lane + 32 k), loaded once per kernel launch: link-
@@ -699,7 +701,8 @@ __device__ __forceinline__ void cuboid_aabb(const float4* c, float4* box) {
 template <bool kP2P>
 __device__ void traj_evaluate(const Scalars& sc, const LaneSpheres& ls, const float4* cub, const float4* osph,
                               const float4* aabb, TShared& sh, SpecialFrames* sp, float* q, float* G_arm,
-                              float* G_blk, float* disp, float* cblk, float* cgap, int* cempty, bool grad,
+                              float* G_blk, float* disp, float* cblk, float* cgap, int* cempty, int* ccand,
+                              bool grad,
                               unsigned long long& n_tests, unsigned long long& n_cull,
                               unsigned long long& n_cand) {
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
@@ -753,12 +756,12 @@ __device__ void traj_evaluate(const Scalars& sc, const LaneSpheres& ls, const fl
     const int n_chunks = (C - 1 + kChunk - 1) / kChunk;
     // Chunks to evaluate: those without a valid cached cull (none at its last cull, and
     // everything moved less than its clearance since).  Warp g lists those of chunks
-    // 32g .. 32g+31 in chunk order, in two tiers: heavy (candidates at the last cull: tests
-    // and the gradient chain) and light (a candidate-free chunk to cull again), and zeroes the
-    // block-group gradient rows of the skipped ones (their arm-group rows are still zero from
-    // their last cull).  The heavy list, then the light one, is dealt to the warps
-    // round-robin, which keeps the per-warp sums deterministic and the warps' shares of the
-    // remaining work even.
+    // 32g .. 32g+31 in chunk order, by tier: the chunks with 4, 3, 2, 1 configurations with
+    // candidates at the last cull (tests and the gradient chain), then the candidate-free
+    // chunks to cull again; it zeroes the block-group gradient rows of the skipped ones (their
+    // arm-group rows are still zero from their last cull).  The tiers, in that order, are
+    // dealt to the warps round-robin, which keeps the per-warp sums deterministic and the
+    // warps' shares of the remaining work even.
     static_assert((kMaxC + kChunk - 1) / kChunk <= 32 * kTWarps && (kTWarps & (kTWarps - 1)) == 0,
                   "one 32-chunk group per warp");
     const float blk_moved = sh.blk_moved;
@@ -771,14 +774,14 @@ __device__ void traj_evaluate(const Scalars& sc, const LaneSpheres& ls, const fl
             for (int i = 0; i < nc; ++i) d = fmaxf(d, disp[t0 + i]);
             active = !(d + (blk_moved - cblk[chk]) < cgap[chk]);
         }
-        const bool light = active && cempty[chk];
-        const unsigned bal_h = __ballot_sync(0xffffffffu, active && !light);
-        const unsigned bal_l = __ballot_sync(0xffffffffu, light);
-        if (active) {
-            const unsigned bal = light ? bal_l : bal_h;
-            sh.active[light ? 1 : 0][32 * w + __popc(bal & ((1u << lane) - 1u))] = (short)chk;
+        // tier: kChunk - (configurations with candidates), kChunk for a chunk to cull again
+        const int tier = active ? (cempty[chk] ? kChunk : kChunk - ccand[chk]) : -1;
+#pragma unroll
+        for (int tr = 0; tr <= kChunk; ++tr) {
+            const unsigned bal = __ballot_sync(0xffffffffu, tier == tr);
+            if (tier == tr) sh.active[tr][32 * w + __popc(bal & ((1u << lane) - 1u))] = (short)chk;
+            if (lane == 0) sh.n_group[tr][w] = __popc(bal);
         }
-        if (lane == 0) { sh.n_group[0][w] = __popc(bal_h); sh.n_group[1][w] = __popc(bal_l); }
         unsigned skipped = __ballot_sync(0xffffffffu, chk < n_chunks && !active);
         while (grad && skipped) {
             const int k = 32 * w + __ffs(skipped) - 1;
@@ -790,7 +793,7 @@ __device__ void traj_evaluate(const Scalars& sc, const LaneSpheres& ls, const fl
     __syncthreads();
     // warp w takes positions w, w + 8, ... of the concatenated lists, tier by tier, group by group
     int start = 0;
-    for (int tg = 0; tg < 2 * kTWarps; ++tg) {
+    for (int tg = 0; tg < (kChunk + 1) * kTWarps; ++tg) {
         const int tier = tg / kTWarps, g = tg % kTWarps;
         const int n_g = sh.n_group[tier][g];
         for (int i = (w - start) & (kTWarps - 1); i < n_g; i += kTWarps) {
@@ -805,11 +808,13 @@ __device__ void traj_evaluate(const Scalars& sc, const LaneSpheres& ls, const fl
             chunk_fk(sc, sh, q, t0 + c, true, held_c, sh.warp[w].F[c], sh.warp[w].H[c], box);
             __syncwarp();
             float clearance;
+            const unsigned long long cand0 = n_cand;
             const bool none = chunk_collisions(sc, ls, cub, osph, aabb, sh, sh.warp[w], G_arm, G_blk, t0, nc, grad, box,
                                                acc_arm, acc_blk, acc_max, n_tests, n_cand, clearance);
             n_cull += (unsigned)nc;
             if (lane == 0) {
                 cempty[chk] = none ? 1 : 0;
+                ccand[chk] = (int)(n_cand - cand0);
                 cblk[chk] = blk_moved;
                 cgap[chk] = clearance - kClearSlack;
             }
@@ -989,10 +994,11 @@ __device__ __forceinline__ void traj_particle(const Scalars& sc, int p, int mode
     float* cblk = disp + sc.C;
     float* cgap = cblk + n_chunks;
     int* cempty = reinterpret_cast<int*>(cgap + n_chunks);
+    int* ccand = cempty + n_chunks;
     const int tid = threadIdx.x;
     const int C = sc.C, NR = sc.NR, B = sc.B;
     for (int i = tid; i < C; i += kTThreads) disp[i] = 0.f;
-    for (int i = tid; i < n_chunks; i += kTThreads) { cblk[i] = 0.f; cgap[i] = 0.f; cempty[i] = 0; }
+    for (int i = tid; i < n_chunks; i += kTThreads) { cblk[i] = 0.f; cgap[i] = 0.f; cempty[i] = 0; ccand[i] = kChunk; }
     if (tid == 0) { sh.blk_moved = 0.f; sh.pose_prev_ok = 0; }
 
     // particle state -> shared memory (coalesced float4)
@@ -1025,7 +1031,8 @@ __device__ __forceinline__ void traj_particle(const Scalars& sc, int p, int mode
     if (mode == kTrajDescend) {
         const int K = io.k_steps;
         for (int k = 1; k <= K; ++k) {
-            traj_evaluate<kP2P>(sc, ls, cub, osph, aabb, sh, sp, q, G_arm, G_blk, disp, cblk, cgap, cempty, true, n_tests,
+            traj_evaluate<kP2P>(sc, ls, cub, osph, aabb, sh, sp, q, G_arm, G_blk, disp, cblk, cgap, cempty, ccand, true,
+                                n_tests,
                                 n_cull, n_cand);
             const float eta = sc.eta_traj * (1.f - (float)k / (float)K);
             // q <- clamp(q - eta g) per configuration, and the bound on how far its spheres moved
@@ -1055,7 +1062,8 @@ __device__ __forceinline__ void traj_particle(const Scalars& sc, int p, int mode
         }
     }
     const bool want_grad = mode == kTrajEval && io.grad != nullptr;
-    traj_evaluate<kP2P>(sc, ls, cub, osph, aabb, sh, sp, q, G_arm, G_blk, disp, cblk, cgap, cempty, want_grad, n_tests,
+    traj_evaluate<kP2P>(sc, ls, cub, osph, aabb, sh, sp, q, G_arm, G_blk, disp, cblk, cgap, cempty, ccand,
+                        want_grad, n_tests,
                         n_cull, n_cand);
     if (io.tests && (threadIdx.x & 31) == 0) {
         atomicAdd(io.tests, n_tests);
