@@ -60,7 +60,7 @@ struct TShared {
     // chunks to evaluate by tier (kChunk .. 1 configurations with candidates at the last cull, then the
     // candidate-free ones to cull again): active[tier][32g + i] for group g
     short active[kChunk + 1][(kMaxC + kChunk - 1) / kChunk];
-    int n_group[kChunk + 1][kTWarps];
+    short n_group[kChunk + 1][kTWarps];
     float blk_moved;              // running bound on how far the placed cuboids have moved
     int pose_prev_ok;
     float c_arm, c_blk, maxpen, c_coll, c_stable, c_height, c_start;
@@ -83,13 +83,14 @@ __host__ __device__ inline size_t t_sp_offset(int n_cub, int n_osph, int C) {
 }
 __host__ __device__ inline int t_n_chunks(int C) { return (C - 1 + kChunk - 1) / kChunk; }
 // cached cull state: per configuration the motion bound since its chunk's last cull; per
-// chunk the placed-block motion at that cull, its clearance and whether it found no candidate
+// chunk the placed-block motion at that cull, its clearance and how many of its configurations had a
+// candidate (0: none, the chunk's cull is cacheable)
 __host__ __device__ inline size_t t_cache_offset(int n_cub, int n_osph, int C, int B) {
     return (t_sp_offset(n_cub, n_osph, C) + (size_t)2 * B * sizeof(SpecialFrames) + 15) & ~(size_t)15;
 }
 size_t traj_smem_bytes(const Scalars& sc) {
     return t_cache_offset(sc.n_cub, sc.n_osph, sc.C, sc.B) + (size_t)sc.C * sizeof(float) +
-           (size_t)t_n_chunks(sc.C) * (2 * sizeof(float) + 2 * sizeof(int));
+           (size_t)t_n_chunks(sc.C) * (2 * sizeof(float) + sizeof(int));
 }
 
 // The robot spheres a lane owns (item lane + 32 k), loaded once per kernel launch: link-
@@ -701,8 +702,7 @@ __device__ __forceinline__ void cuboid_aabb(const float4* c, float4* box) {
 template <bool kP2P>
 __device__ void traj_evaluate(const Scalars& sc, const LaneSpheres& ls, const float4* cub, const float4* osph,
                               const float4* aabb, TShared& sh, SpecialFrames* sp, float* q, float* G_arm,
-                              float* G_blk, float* disp, float* cblk, float* cgap, int* cempty, int* ccand,
-                              bool grad,
+                              float* G_blk, float* disp, float* cblk, float* cgap, int* ccand, bool grad,
                               unsigned long long& n_tests, unsigned long long& n_cull,
                               unsigned long long& n_cand) {
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
@@ -769,18 +769,18 @@ __device__ void traj_evaluate(const Scalars& sc, const LaneSpheres& ls, const fl
         const int chk = 32 * w + lane;
         const int t0 = 1 + kChunk * chk, nc = min(kChunk, C - t0);
         bool active = chk < n_chunks;
-        if (active && cempty[chk]) {
+        if (active && ccand[chk] == 0) {
             float d = 0.f;
             for (int i = 0; i < nc; ++i) d = fmaxf(d, disp[t0 + i]);
             active = !(d + (blk_moved - cblk[chk]) < cgap[chk]);
         }
         // tier: kChunk - (configurations with candidates), kChunk for a chunk to cull again
-        const int tier = active ? (cempty[chk] ? kChunk : kChunk - ccand[chk]) : -1;
+        const int tier = active ? (ccand[chk] == 0 ? kChunk : kChunk - ccand[chk]) : -1;
 #pragma unroll
         for (int tr = 0; tr <= kChunk; ++tr) {
             const unsigned bal = __ballot_sync(0xffffffffu, tier == tr);
             if (tier == tr) sh.active[tr][32 * w + __popc(bal & ((1u << lane) - 1u))] = (short)chk;
-            if (lane == 0) sh.n_group[tr][w] = __popc(bal);
+            if (lane == 0) sh.n_group[tr][w] = (short)__popc(bal);
         }
         unsigned skipped = __ballot_sync(0xffffffffu, chk < n_chunks && !active);
         while (grad && skipped) {
@@ -813,8 +813,7 @@ __device__ void traj_evaluate(const Scalars& sc, const LaneSpheres& ls, const fl
                                                acc_arm, acc_blk, acc_max, n_tests, n_cand, clearance);
             n_cull += (unsigned)nc;
             if (lane == 0) {
-                cempty[chk] = none ? 1 : 0;
-                ccand[chk] = (int)(n_cand - cand0);
+                ccand[chk] = none ? 0 : (int)(n_cand - cand0);   // 0: a candidate-free (cacheable) chunk
                 cblk[chk] = blk_moved;
                 cgap[chk] = clearance - kClearSlack;
             }
@@ -993,12 +992,11 @@ __device__ __forceinline__ void traj_particle(const Scalars& sc, int p, int mode
     const int n_chunks = t_n_chunks(sc.C);
     float* cblk = disp + sc.C;
     float* cgap = cblk + n_chunks;
-    int* cempty = reinterpret_cast<int*>(cgap + n_chunks);
-    int* ccand = cempty + n_chunks;
+    int* ccand = reinterpret_cast<int*>(cgap + n_chunks);
     const int tid = threadIdx.x;
     const int C = sc.C, NR = sc.NR, B = sc.B;
     for (int i = tid; i < C; i += kTThreads) disp[i] = 0.f;
-    for (int i = tid; i < n_chunks; i += kTThreads) { cblk[i] = 0.f; cgap[i] = 0.f; cempty[i] = 0; ccand[i] = kChunk; }
+    for (int i = tid; i < n_chunks; i += kTThreads) { cblk[i] = 0.f; cgap[i] = 0.f; ccand[i] = kChunk; }
     if (tid == 0) { sh.blk_moved = 0.f; sh.pose_prev_ok = 0; }
 
     // particle state -> shared memory (coalesced float4)
@@ -1031,7 +1029,7 @@ __device__ __forceinline__ void traj_particle(const Scalars& sc, int p, int mode
     if (mode == kTrajDescend) {
         const int K = io.k_steps;
         for (int k = 1; k <= K; ++k) {
-            traj_evaluate<kP2P>(sc, ls, cub, osph, aabb, sh, sp, q, G_arm, G_blk, disp, cblk, cgap, cempty, ccand, true,
+            traj_evaluate<kP2P>(sc, ls, cub, osph, aabb, sh, sp, q, G_arm, G_blk, disp, cblk, cgap, ccand, true,
                                 n_tests,
                                 n_cull, n_cand);
             const float eta = sc.eta_traj * (1.f - (float)k / (float)K);
@@ -1062,8 +1060,7 @@ __device__ __forceinline__ void traj_particle(const Scalars& sc, int p, int mode
         }
     }
     const bool want_grad = mode == kTrajEval && io.grad != nullptr;
-    traj_evaluate<kP2P>(sc, ls, cub, osph, aabb, sh, sp, q, G_arm, G_blk, disp, cblk, cgap, cempty, ccand,
-                        want_grad, n_tests,
+    traj_evaluate<kP2P>(sc, ls, cub, osph, aabb, sh, sp, q, G_arm, G_blk, disp, cblk, cgap, ccand, want_grad, n_tests,
                         n_cull, n_cand);
     if (io.tests && (threadIdx.x & 31) == 0) {
         atomicAdd(io.tests, n_tests);
