@@ -15,6 +15,7 @@ struct S1Warp {
     float g[4 * kMaxB];
     PlaceScratch ps;
     float4 gcell[kMaxCells];   // per-cube sphere-side gradients of the packing goal
+    uint32_t cand[kMaxCub / 32 + kMaxOSph / 32];   // candidate obstacles of the particle (tower goal)
 };
 
 // dynamic shared memory: mbarrier | env cuboids | env spheres | per-warp scratch
@@ -64,7 +65,7 @@ __global__ void __launch_bounds__(kS1Threads) k_place_sample_cost(const __grid_c
     __syncwarp();
     PlaceOut o;
     place_eval(sc, s.cub, sc.n_cub, s.osph, sc.n_osph, W.x, false, kPlaceForward, nullptr, W.ps,
-               W.gcell, o);
+               W.gcell, W.cand, o);
     for (int v = lane; v < 4 * sc.B; v += 32) x_out[(size_t)v * n + p] = W.x[v];
     if (lane == 0) cost_out[p] = place_cost_value(sc, o);
 }
@@ -84,7 +85,7 @@ __global__ void __launch_bounds__(kS1Threads) k_place_eval(const __grid_constant
     __syncwarp();
     PlaceOut o;
     place_eval(sc, s.cub, sc.n_cub, s.osph, sc.n_osph, W.x, quad != 0, grad ? kPlaceStage1 : kPlaceForward, W.g, W.ps,
-               W.gcell, o);
+               W.gcell, W.cand, o);
     if (grad)
         for (int v = lane; v < 4 * sc.B; v += 32) grad[(size_t)v * n + p] = W.g[v];
     if (lane == 0) {
@@ -117,18 +118,18 @@ __global__ void __launch_bounds__(kS1Threads) k_place_descend(const __grid_const
     for (int k = 1; k <= k_lin; ++k) {
         const float eta = sc.eta_init * (1.f - (float)k / (float)k_lin);
         place_eval(sc, s.cub, sc.n_cub, s.osph, sc.n_osph, W.x, false, kPlaceStage1, W.g, W.ps,
-               W.gcell, o);
+               W.gcell, W.cand, o);
         for (int v = lane; v < nv; v += 32) W.x[v] = place_clamp(sc, v, W.x[v] - eta * W.g[v]);
         __syncwarp();
     }
     for (int k = 1; k <= k_quad; ++k) {
         place_eval(sc, s.cub, sc.n_cub, s.osph, sc.n_osph, W.x, true, kPlaceStage1, W.g, W.ps,
-               W.gcell, o);
+               W.gcell, W.cand, o);
         for (int v = lane; v < nv; v += 32) W.x[v] = place_clamp(sc, v, W.x[v] - sc.alpha * W.g[v]);
         __syncwarp();
     }
     place_eval(sc, s.cub, sc.n_cub, s.osph, sc.n_osph, W.x, true, kPlaceForward, nullptr, W.ps,
-               W.gcell, o);
+               W.gcell, W.cand, o);
     for (int v = lane; v < nv; v += 32) x_dst[(size_t)v * m + p] = W.x[v];
     if (lane == 0) {
         if (cost) cost[p] = place_cost_value(sc, o);

@@ -84,10 +84,12 @@ __device__ __forceinline__ void place_stack_warp(const Scalars& sc, const float*
 // x, g: per-warp shared arrays of 4B floats.  With mode != kPlaceForward, writes
 //   g = sum_i a_i dD_i/dx + sum_i b_i de_i/dx + s_coll dC_coll/dx.
 // Must be called by all 32 lanes of the warp.
+// cand: per-warp scratch of kMaxCub/32 + kMaxOSph/32 words (the candidate obstacles of the particle).
 __device__ __forceinline__ void place_eval_warp(const Scalars& sc, const float4* __restrict__ cub, int n_cub,
                                                 const float4* __restrict__ osph, int n_osph, const float* x,
                                                 bool quad, int mode, const float* a_in, const float* b_in,
-                                                float s_coll_in, float* g, PlaceScratch& ps, PlaceOut& out) {
+                                                float s_coll_in, float* g, PlaceScratch& ps, uint32_t* cand,
+                                                PlaceOut& out) {
     const int lane = threadIdx.x & 31;
     const int B = sc.B;
     const bool want_grad = mode != kPlaceForward;
@@ -98,6 +100,62 @@ __device__ __forceinline__ void place_eval_warp(const Scalars& sc, const float4*
     const float s_coll = mode == kPlaceStage1 ? sc.w_coll : s_coll_in;
     float coll = 0.f, maxpen = 0.f;
     const int n_items = 8 * B;
+    // exact cull: the box of every block sphere of the particle (padded by 1e-5 against the
+    // rounding of the boxes) against each obstacle's box; only the obstacles that overlap it
+    // can touch a sphere, and they are visited in the same order as without the cull
+    const int n_cw = (n_cub + 31) >> 5, n_sw = (n_osph + 31) >> 5;
+    {
+        float lo_x = 3.4e38f, lo_y = 3.4e38f, lo_z = 3.4e38f, hi_x = -3.4e38f, hi_y = -3.4e38f, hi_z = -3.4e38f;
+        for (int base = 0; base < n_items; base += 32) {
+            const int it = base + lane;
+            if (it < n_items) {
+                const int j = it >> 3, m = it & 7;
+                const float4 h = sc.half[j];
+                float lx, ly, lz;
+                block_sphere_local(h, m, lx, ly, lz);
+                const float c = ps.bc[j][1].x, s = ps.bc[j][1].y;
+                const float cx = x[4 * j] + c * lx - s * ly, cy = x[4 * j + 1] + s * lx + c * ly, cz = x[4 * j + 2] + lz;
+                const float r = h.w + 1e-5f;
+                lo_x = fminf(lo_x, cx - r); lo_y = fminf(lo_y, cy - r); lo_z = fminf(lo_z, cz - r);
+                hi_x = fmaxf(hi_x, cx + r); hi_y = fmaxf(hi_y, cy + r); hi_z = fmaxf(hi_z, cz + r);
+            }
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            lo_x = fminf(lo_x, __shfl_xor_sync(0xffffffffu, lo_x, off));
+            lo_y = fminf(lo_y, __shfl_xor_sync(0xffffffffu, lo_y, off));
+            lo_z = fminf(lo_z, __shfl_xor_sync(0xffffffffu, lo_z, off));
+            hi_x = fmaxf(hi_x, __shfl_xor_sync(0xffffffffu, hi_x, off));
+            hi_y = fmaxf(hi_y, __shfl_xor_sync(0xffffffffu, hi_y, off));
+            hi_z = fmaxf(hi_z, __shfl_xor_sync(0xffffffffu, hi_z, off));
+        }
+        for (int wd = 0; wd < n_cw; ++wd) {
+            const int o = 32 * wd + lane;
+            bool near = false;
+            if (o < n_cub) {
+                const float4 c0 = cub[4 * o], c1 = cub[4 * o + 1], c2 = cub[4 * o + 2], c3 = cub[4 * o + 3];
+                const float ex = fabsf(c1.x) * c1.w + fabsf(c2.x) * c2.w + fabsf(c3.x) * c3.w;
+                const float ey = fabsf(c1.y) * c1.w + fabsf(c2.y) * c2.w + fabsf(c3.y) * c3.w;
+                const float ez = fabsf(c1.z) * c1.w + fabsf(c2.z) * c2.w + fabsf(c3.z) * c3.w;
+                near = c0.x - ex <= hi_x && c0.x + ex >= lo_x && c0.y - ey <= hi_y && c0.y + ey >= lo_y &&
+                       c0.z - ez <= hi_z && c0.z + ez >= lo_z;
+            }
+            const unsigned mk = __ballot_sync(0xffffffffu, near);
+            if (lane == 0) cand[wd] = mk;
+        }
+        for (int wd = 0; wd < n_sw; ++wd) {
+            const int o = 32 * wd + lane;
+            bool near = false;
+            if (o < n_osph) {
+                const float4 sp = osph[o];
+                near = sp.x - sp.w <= hi_x && sp.x + sp.w >= lo_x && sp.y - sp.w <= hi_y && sp.y + sp.w >= lo_y &&
+                       sp.z - sp.w <= hi_z && sp.z + sp.w >= lo_z;
+            }
+            const unsigned mk = __ballot_sync(0xffffffffu, near);
+            if (lane == 0) cand[kMaxCub / 32 + wd] = mk;
+        }
+        __syncwarp();
+    }
     for (int base = 0; base < n_items; base += 32) {
         const int it = base + lane;
         const bool valid = it < n_items;
@@ -119,25 +177,35 @@ __device__ __forceinline__ void place_eval_warp(const Scalars& sc, const float4*
         }
         float ax = 0.f, ay = 0.f, az = 0.f;   // dC/dc of this item (scaled by 2 pen in quad form)
         if (valid) {
-            for (int o = 0; o < n_cub; ++o) {
-                float gx, gy, gz;
-                const float pen = pen_cuboid<float>(cx, cy, cz, r, cub[4 * o], cub[4 * o + 1], cub[4 * o + 2], cub[4 * o + 3],
-                                                    gx, gy, gz);
-                if (pen > 0.f) {
-                    maxpen = fmaxf(maxpen, pen);
-                    coll += quad ? pen * pen : pen;
-                    const float sgrad = quad ? 2.f * pen : 1.f;
-                    ax += sgrad * gx; ay += sgrad * gy; az += sgrad * gz;
+            for (int wd = 0; wd < n_cw; ++wd) {
+                unsigned mk = cand[wd];
+                while (mk) {
+                    const int o = 32 * wd + __ffs(mk) - 1;
+                    mk &= mk - 1;
+                    float gx, gy, gz;
+                    const float pen = pen_cuboid<float>(cx, cy, cz, r, cub[4 * o], cub[4 * o + 1], cub[4 * o + 2],
+                                                        cub[4 * o + 3], gx, gy, gz);
+                    if (pen > 0.f) {
+                        maxpen = fmaxf(maxpen, pen);
+                        coll += quad ? pen * pen : pen;
+                        const float sgrad = quad ? 2.f * pen : 1.f;
+                        ax += sgrad * gx; ay += sgrad * gy; az += sgrad * gz;
+                    }
                 }
             }
-            for (int o = 0; o < n_osph; ++o) {
-                float gx, gy, gz;
-                const float pen = pen_sphere<float>(cx, cy, cz, r, osph[o], gx, gy, gz);
-                if (pen > 0.f) {
-                    maxpen = fmaxf(maxpen, pen);
-                    coll += quad ? pen * pen : pen;
-                    const float sgrad = quad ? 2.f * pen : 1.f;
-                    ax += sgrad * gx; ay += sgrad * gy; az += sgrad * gz;
+            for (int wd = 0; wd < n_sw; ++wd) {
+                unsigned mk = cand[kMaxCub / 32 + wd];
+                while (mk) {
+                    const int o = 32 * wd + __ffs(mk) - 1;
+                    mk &= mk - 1;
+                    float gx, gy, gz;
+                    const float pen = pen_sphere<float>(cx, cy, cz, r, osph[o], gx, gy, gz);
+                    if (pen > 0.f) {
+                        maxpen = fmaxf(maxpen, pen);
+                        coll += quad ? pen * pen : pen;
+                        const float sgrad = quad ? 2.f * pen : 1.f;
+                        ax += sgrad * gx; ay += sgrad * gy; az += sgrad * gz;
+                    }
                 }
             }
         }

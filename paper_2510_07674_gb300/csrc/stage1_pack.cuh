@@ -150,11 +150,12 @@ __device__ __forceinline__ void place_eval_pack_warp(const Scalars& sc, const fl
 // The placement cost of the problem's goal (tower or packing).
 __device__ __forceinline__ void place_eval(const Scalars& sc, const float4* __restrict__ cub, int n_cub,
                                            const float4* __restrict__ osph, int n_osph, const float* x, bool quad,
-                                           int mode, float* g, PlaceScratch& ps, float4* gcell, PlaceOut& out) {
+                                           int mode, float* g, PlaceScratch& ps, float4* gcell, uint32_t* cand,
+                                           PlaceOut& out) {
     if (sc.kind == kKindPack)
         place_eval_pack_warp(sc, cub, n_cub, osph, n_osph, x, quad, mode, nullptr, 0.f, g, ps, gcell, out);
     else
-        place_eval_warp(sc, cub, n_cub, osph, n_osph, x, quad, mode, nullptr, nullptr, 0.f, g, ps, out);
+        place_eval_warp(sc, cub, n_cub, osph, n_osph, x, quad, mode, nullptr, nullptr, 0.f, g, ps, cand, out);
 }
 
 }  // namespace spasm
