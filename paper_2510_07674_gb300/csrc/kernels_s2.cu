@@ -1,5 +1,7 @@
 // Stage-2 kernels: the fused trajectory optimisation (one CTA per particle, every
 // iteration inside one launch).  The lift that initialises it is in kernels_lift.cu.
+#include <cuda_fp16.h>
+
 #include "launch_s2.h"
 #include "stage1.cuh"
 #include "stage2.cuh"
@@ -14,11 +16,13 @@ constexpr int kSlots = 2;   // sphere items per lane: up to 56 robot + 8 held-bl
 constexpr int kChunk = 4;   // configurations whose kinematics one warp evaluates together
 
 // Cached cull.  When a chunk's cull finds no candidate for any of its configurations, it
-// also returns the chunk's clearance: the smallest separation (largest per-axis gap) between
-// any of its link boxes and any obstacle or block box that could touch it.  Later iterations
+// also returns the chunk's clearances: the smallest separation (largest per-axis gap) between
+// any of its link boxes and any static box that could touch it (the environment, blocks at
+// their initial poses), and the same for the placed blocks, which move.  Later iterations
 // skip the chunk (kinematics, cull and tests: its terms are zero) while the bound on how far
-// its spheres moved since, plus how far the placed blocks moved, stays below the clearance,
-// so the skipped work is exactly the work whose result is zero.
+// its spheres moved since stays below the static clearance and, plus how far the placed
+// blocks moved, below the moving one, so the skipped work is exactly the work whose result
+// is zero.
 constexpr float kClearSlack = 1e-5f;   // FP32 rounding of the boxes, metres
 
 struct TWarp {
@@ -241,7 +245,7 @@ __device__ __forceinline__ bool chunk_collisions(const Scalars& sc, const LaneSp
                                                  float* G_blk, int t0, int nc, bool grad, const float* lane_box,
                                                  float& acc_arm, float& acc_blk, float& acc_max,
                                                  unsigned long long& n_tests, unsigned long long& n_cand,
-                                                 float& clearance) {
+                                                 float& clearance, float& clearance_moving) {
     const int lane = threadIdx.x & 31;
     const int S = sc.S, B = sc.B;
     float cx[kSlots], cy[kSlots], cz[kSlots], rr[kSlots];
@@ -327,13 +331,8 @@ __device__ __forceinline__ bool chunk_collisions(const Scalars& sc, const LaneSp
         // blocks k > b still at their initial poses (the chunk: any of its configurations)
         const int b_lane = (min(t0 + (lane >> 3), sc.C - 1) - 1) / S >> 1;
         const int b_first = (t0 - 1) / S >> 1, b_last = (min(t0 + nc - 1, sc.C - 1) - 1) / S >> 1;
-        const float sp = lane < B ? sep_chunk(sh.baabb[lane][0], sh.baabb[lane][1]) : 3.4e38f;
-        if (lane < b_last && sp > 0.f) clear = fminf(clear, sp);
-        const unsigned bm_placed = __ballot_sync(0xffffffffu, sp <= 0.f);
-        refine(bm_placed, 0, &sh.baabb[0][0], 2, per, [&](int k) { return k < b_lane; });
-        if (lane == 0)
-#pragma unroll
-            for (int c = 0; c < kChunk; ++c) tw.bmask[0][c] = per[c];
+        // blocks at their initial poses (static), then the placed blocks (moving): the clearance
+        // so far is the static one, and the placed blocks' gaps form the moving one
         const float si = lane < B ? sep_chunk(sh.iaabb[lane][0], sh.iaabb[lane][1]) : 3.4e38f;
         if (lane < B && lane > b_first && si > 0.f) clear = fminf(clear, si);
         const unsigned bm_init = __ballot_sync(0xffffffffu, si <= 0.f);
@@ -341,6 +340,16 @@ __device__ __forceinline__ bool chunk_collisions(const Scalars& sc, const LaneSp
         if (lane == 0)
 #pragma unroll
             for (int c = 0; c < kChunk; ++c) tw.bmask[1][c] = per[c];
+        clearance = warp_min(clear);
+        clear = 3.4e38f;
+        const float sp = lane < B ? sep_chunk(sh.baabb[lane][0], sh.baabb[lane][1]) : 3.4e38f;
+        if (lane < b_last && sp > 0.f) clear = fminf(clear, sp);
+        const unsigned bm_placed = __ballot_sync(0xffffffffu, sp <= 0.f);
+        refine(bm_placed, 0, &sh.baabb[0][0], 2, per, [&](int k) { return k < b_lane; });
+        if (lane == 0)
+#pragma unroll
+            for (int c = 0; c < kChunk; ++c) tw.bmask[0][c] = per[c];
+        clearance_moving = warp_min(clear);
     }
     __syncwarp();
 
@@ -535,7 +544,6 @@ __device__ __forceinline__ bool chunk_collisions(const Scalars& sc, const LaneSp
             if ((lane & 1) == 0 && (j & 7) != 7) (j < 8 ? G_arm : G_blk)[t * 8 + (j & 7)] = v[0];
         }
     }
-    clearance = warp_min(clear);
     return none;
 }
 
@@ -702,7 +710,7 @@ __device__ __forceinline__ void cuboid_aabb(const float4* c, float4* box) {
 template <bool kP2P>
 __device__ void traj_evaluate(const Scalars& sc, const LaneSpheres& ls, const float4* cub, const float4* osph,
                               const float4* aabb, TShared& sh, SpecialFrames* sp, float* q, float* G_arm,
-                              float* G_blk, float* disp, float* cblk, float* cgap, int* ccand, bool grad,
+                              float* G_blk, float* disp, float* cblk, __half2* cgap, int* ccand, bool grad,
                               unsigned long long& n_tests, unsigned long long& n_cull,
                               unsigned long long& n_cand) {
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
@@ -772,7 +780,8 @@ __device__ void traj_evaluate(const Scalars& sc, const LaneSpheres& ls, const fl
         if (active && ccand[chk] == 0) {
             float d = 0.f;
             for (int i = 0; i < nc; ++i) d = fmaxf(d, disp[t0 + i]);
-            active = !(d + (blk_moved - cblk[chk]) < cgap[chk]);
+            const __half2 cg = cgap[chk];
+            active = !(d < __low2float(cg) && d + (blk_moved - cblk[chk]) < __high2float(cg));
         }
         // tier: kChunk - (configurations with candidates), kChunk for a chunk to cull again
         const int tier = active ? (ccand[chk] == 0 ? kChunk : kChunk - ccand[chk]) : -1;
@@ -807,15 +816,18 @@ __device__ void traj_evaluate(const Scalars& sc, const LaneSpheres& ls, const fl
             float box[6];
             chunk_fk(sc, sh, q, t0 + c, true, held_c, sh.warp[w].F[c], sh.warp[w].H[c], box);
             __syncwarp();
-            float clearance;
+            float clearance, clearance_moving;
             const unsigned long long cand0 = n_cand;
             const bool none = chunk_collisions(sc, ls, cub, osph, aabb, sh, sh.warp[w], G_arm, G_blk, t0, nc, grad, box,
-                                               acc_arm, acc_blk, acc_max, n_tests, n_cand, clearance);
+                                               acc_arm, acc_blk, acc_max, n_tests, n_cand, clearance,
+                                               clearance_moving);
             n_cull += (unsigned)nc;
             if (lane == 0) {
                 ccand[chk] = none ? 0 : (int)(n_cand - cand0);   // 0: a candidate-free (cacheable) chunk
                 cblk[chk] = blk_moved;
-                cgap[chk] = clearance - kClearSlack;
+                // fp16, rounded down: still a lower bound on either clearance
+                cgap[chk] = __halves2half2(__float2half_rd(clearance - kClearSlack),
+                                           __float2half_rd(clearance_moving - kClearSlack));
             }
             if (lane < nc) disp[t0 + lane] = 0.f;
             __syncwarp();
@@ -991,12 +1003,12 @@ __device__ __forceinline__ void traj_particle(const Scalars& sc, int p, int mode
     float* disp = reinterpret_cast<float*>(smem_raw + t_cache_offset(sc.n_cub, sc.n_osph, sc.C, sc.B));
     const int n_chunks = t_n_chunks(sc.C);
     float* cblk = disp + sc.C;
-    float* cgap = cblk + n_chunks;
+    __half2* cgap = reinterpret_cast<__half2*>(cblk + n_chunks);   // (static, moving) clearances
     int* ccand = reinterpret_cast<int*>(cgap + n_chunks);
     const int tid = threadIdx.x;
     const int C = sc.C, NR = sc.NR, B = sc.B;
     for (int i = tid; i < C; i += kTThreads) disp[i] = 0.f;
-    for (int i = tid; i < n_chunks; i += kTThreads) { cblk[i] = 0.f; cgap[i] = 0.f; ccand[i] = kChunk; }
+    for (int i = tid; i < n_chunks; i += kTThreads) { cblk[i] = 0.f; cgap[i] = __float2half2_rn(0.f); ccand[i] = kChunk; }
     if (tid == 0) { sh.blk_moved = 0.f; sh.pose_prev_ok = 0; }
 
     // particle state -> shared memory (coalesced float4)
