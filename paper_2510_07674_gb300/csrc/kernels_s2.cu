@@ -65,7 +65,7 @@ struct TShared {
     // candidate-free ones to cull again): active[tier][32g + i] for group g
     short active[kChunk + 1][(kMaxC + kChunk - 1) / kChunk];
     short n_group[kChunk + 1][kTWarps];
-    float blk_moved;              // running bound on how far the placed cuboids have moved
+    float blk_cum[kMaxB];         // [k]: running bound on how far the placed blocks 0..k have moved, summed
     int pose_prev_ok;
     float c_arm, c_blk, maxpen, c_coll, c_stable, c_height, c_start;
     float max_start, max_tilt, pm_pen, pm_D, pm_dz, path, jl;
@@ -751,11 +751,14 @@ __device__ void traj_evaluate(const Scalars& sc, const LaneSpheres& ls, const fl
             sh.baabb[lane][0] = make_float4(3.4e38f, 3.4e38f, 3.4e38f, 0.f);   // an empty box: never a candidate
             sh.baabb[lane][1] = make_float4(-3.4e38f, -3.4e38f, -3.4e38f, 0.f);
         }
-        moved = warp_sum(moved);
-        if (lane == 0) {
-            sh.blk_moved += moved;
-            sh.pose_prev_ok = 1;
+        // inclusive scan over the blocks: blk_cum[k] accumulates the motion of blocks 0..k
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const float up = __shfl_up_sync(0xffffffffu, moved, off);
+            if (lane >= off) moved += up;
         }
+        if (lane < B) sh.blk_cum[lane] += moved;
+        if (lane == 0) sh.pose_prev_ok = 1;
     }
     __syncthreads();
 
@@ -772,7 +775,10 @@ __device__ void traj_evaluate(const Scalars& sc, const LaneSpheres& ls, const fl
     // warps' shares of the remaining work even.
     static_assert((kMaxC + kChunk - 1) / kChunk <= 32 * kTWarps && (kTWarps & (kTWarps - 1)) == 0,
                   "one 32-chunk group per warp");
-    const float blk_moved = sh.blk_moved;
+    // motion of the blocks placed before block b: the only placed blocks the configurations of a
+    // chunk whose last configuration belongs to block b's segments can touch
+    auto blk_before = [&](int b) { return b > 0 ? sh.blk_cum[b - 1] : 0.f; };
+    auto chunk_block = [&](int t0c) { return (min(t0c + kChunk - 1, C - 1) - 1) / S >> 1; };
     {
         const int chk = 32 * w + lane;
         const int t0 = 1 + kChunk * chk, nc = min(kChunk, C - t0);
@@ -781,7 +787,7 @@ __device__ void traj_evaluate(const Scalars& sc, const LaneSpheres& ls, const fl
             float d = 0.f;
             for (int i = 0; i < nc; ++i) d = fmaxf(d, disp[t0 + i]);
             const __half2 cg = cgap[chk];
-            active = !(d < __low2float(cg) && d + (blk_moved - cblk[chk]) < __high2float(cg));
+            active = !(d < __low2float(cg) && d + (blk_before(chunk_block(t0)) - cblk[chk]) < __high2float(cg));
         }
         // tier: kChunk - (configurations with candidates), kChunk for a chunk to cull again
         const int tier = active ? (ccand[chk] == 0 ? kChunk : kChunk - ccand[chk]) : -1;
@@ -824,7 +830,7 @@ __device__ void traj_evaluate(const Scalars& sc, const LaneSpheres& ls, const fl
             n_cull += (unsigned)nc;
             if (lane == 0) {
                 ccand[chk] = none ? 0 : (int)(n_cand - cand0);   // 0: a candidate-free (cacheable) chunk
-                cblk[chk] = blk_moved;
+                cblk[chk] = blk_before(chunk_block(t0));
                 // fp16, rounded down: still a lower bound on either clearance
                 cgap[chk] = __halves2half2(__float2half_rd(clearance - kClearSlack),
                                            __float2half_rd(clearance_moving - kClearSlack));
@@ -1009,7 +1015,8 @@ __device__ __forceinline__ void traj_particle(const Scalars& sc, int p, int mode
     const int C = sc.C, NR = sc.NR, B = sc.B;
     for (int i = tid; i < C; i += kTThreads) disp[i] = 0.f;
     for (int i = tid; i < n_chunks; i += kTThreads) { cblk[i] = 0.f; cgap[i] = __float2half2_rn(0.f); ccand[i] = kChunk; }
-    if (tid == 0) { sh.blk_moved = 0.f; sh.pose_prev_ok = 0; }
+    if (tid < kMaxB) sh.blk_cum[tid] = 0.f;
+    if (tid == 0) sh.pose_prev_ok = 0;
 
     // particle state -> shared memory (coalesced float4)
     const float4* qg = reinterpret_cast<const float4*>(io.q + (size_t)p * C * 8);
