@@ -53,11 +53,34 @@ KERNEL_SOURCES = ["paper_2510_07674_gb300/csrc/kernels_s2.cu", "paper_2510_07674
                   "paper_2510_07674_gb300/csrc/common.cuh", "paper_2510_07674_gb300/csrc/stage1.cuh"]
 
 
+def code_text(src: str) -> str:
+    """Source text without comments and blank lines: what the compiler sees of a kernel file,
+    so that editing a comment does not make a profile summary of the same code stale."""
+    out, i, n = [], 0, len(src)
+    while i < n:
+        if src.startswith("//", i):
+            i = src.find("\n", i)
+            i = n if i < 0 else i
+        elif src.startswith("/*", i):
+            j = src.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+        elif src[i] == '"':   # string literal: copied as is
+            j = i + 1
+            while j < n and src[j] != '"':
+                j += 2 if src[j] == "\\" else 1
+            out.append(src[i:j + 1])
+            i = j + 1
+        else:
+            out.append(src[i])
+            i += 1
+    return "\n".join(line.rstrip() for line in "".join(out).splitlines() if line.strip())
+
+
 def kernel_hash() -> str:
     h = hashlib.sha256()
     for f in KERNEL_SOURCES:
-        with open(os.path.join(ROOT, f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, f), encoding="utf-8") as fh:
+            h.update(code_text(fh.read()).encode())
     return h.hexdigest()[:16]
 
 
@@ -71,7 +94,8 @@ def profile_values() -> dict:
         if ":" in line and line.strip().startswith("- "):
             k, v = line.strip()[2:].split(":", 1)
             vals[k.strip()] = v.strip()
-    return vals if vals.get("kernel_sources_sha256_16") == kernel_hash() else {}
+    recorded = (vals.get("kernel_sources_sha256_16") or "").split()
+    return vals if recorded and recorded[0] == kernel_hash() else {}
 
 
 def traffic_from_profile():

@@ -20,9 +20,9 @@ constexpr int kChunk = 4;   // configurations whose kinematics one warp evaluate
 // any of its link boxes and any static box that could touch it (the environment, blocks at
 // their initial poses), and the same for the placed blocks, which move.  Later iterations
 // skip the chunk (kinematics, cull and tests: its terms are zero) while the bound on how far
-// its spheres moved since stays below the static clearance and, plus how far the placed
-// blocks moved, below the moving one, so the skipped work is exactly the work whose result
-// is zero.
+// its spheres moved since stays below the static clearance and, plus how far the blocks
+// placed before the chunk's own block moved, below the moving one, so the skipped work is
+// exactly the work whose result is zero.
 constexpr float kClearSlack = 1e-5f;   // FP32 rounding of the boxes, metres
 
 struct TWarp {
@@ -87,8 +87,9 @@ __host__ __device__ inline size_t t_sp_offset(int n_cub, int n_osph, int C) {
 }
 __host__ __device__ inline int t_n_chunks(int C) { return (C - 1 + kChunk - 1) / kChunk; }
 // cached cull state: per configuration the motion bound since its chunk's last cull; per
-// chunk the placed-block motion at that cull, its clearance and how many of its configurations had a
-// candidate (0: none, the chunk's cull is cacheable)
+// chunk the motion of the blocks placed before its own at that cull, its (static, moving)
+// clearances as an fp16 pair and how many of its configurations had a candidate (0: none,
+// the chunk's cull is cacheable)
 __host__ __device__ inline size_t t_cache_offset(int n_cub, int n_osph, int C, int B) {
     return (t_sp_offset(n_cub, n_osph, C) + (size_t)2 * B * sizeof(SpecialFrames) + 15) & ~(size_t)15;
 }
@@ -765,8 +766,8 @@ __device__ void traj_evaluate(const Scalars& sc, const LaneSpheres& ls, const fl
     // (2) configuration loop: chunks of kChunk consecutive configurations per warp
     float acc_arm = 0.f, acc_blk = 0.f, acc_max = 0.f;
     const int n_chunks = (C - 1 + kChunk - 1) / kChunk;
-    // Chunks to evaluate: those without a valid cached cull (none at its last cull, and
-    // everything moved less than its clearance since).  Warp g lists those of chunks
+    // Chunks to evaluate: those without a valid cached cull (none at its last cull, and the
+    // motion since below its clearances).  Warp g lists those of chunks
     // 32g .. 32g+31 in chunk order, by tier: the chunks with 4, 3, 2, 1 configurations with
     // candidates at the last cull (tests and the gradient chain), then the candidate-free
     // chunks to cull again; it zeroes the block-group gradient rows of the skipped ones (their
