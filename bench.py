@@ -54,8 +54,9 @@ KERNEL_SOURCES = ["paper_2510_07674_gb300/csrc/kernels_s2.cu", "paper_2510_07674
 
 
 def code_text(src: str) -> str:
-    """Source text without comments and blank lines: what the compiler sees of a kernel file,
-    so that editing a comment does not make a profile summary of the same code stale."""
+    """Source text without comments, blank lines and layout whitespace: what the compiler sees
+    of a kernel file, so that editing a comment does not make a profile summary of the same
+    code stale."""
     out, i, n = [], 0, len(src)
     while i < n:
         if src.startswith("//", i):
@@ -73,7 +74,7 @@ def code_text(src: str) -> str:
         else:
             out.append(src[i])
             i += 1
-    return "\n".join(line.rstrip() for line in "".join(out).splitlines() if line.strip())
+    return "\n".join(" ".join(line.split()) for line in "".join(out).splitlines() if line.strip())
 
 
 def kernel_hash() -> str:

@@ -46,3 +46,15 @@ def test_two_gloo_ranks_take_the_slowest_time():
     assert m0 == m1 == 2500.0
     assert v0 == v1 == pytest.approx(2 * 10 / 2.5)
     assert not set(s0) & set(s1)
+
+
+def test_kernel_hash_ignores_comments_only():
+    """The hash tying a profile summary to the kernel code skips comments and blank lines and
+    keeps everything else, string literals included."""
+    import bench
+    a = "int f(int x) {  // first\n  /* block\n comment */ return x + 1;\n}\n"
+    b = "int f(int x) {\n\n  return x + 1;   // other words\n}\n"
+    c = "int f(int x) {\n  return x + 2;\n}\n"
+    assert bench.code_text(a) == bench.code_text(b) != bench.code_text(c)
+    assert "//kept" in bench.code_text('const char* s = "//kept"; // dropped\n')
+    assert "dropped" not in bench.code_text('const char* s = "//kept"; // dropped\n')

@@ -62,6 +62,21 @@ def test_create_rejects_bad_sizes_on_host(libpath):
     assert "configurations" in str(e.value)
 
 
+def test_analytic_ik_mode_checked_on_host(libpath):
+    """ik_mode must be 0 or 1, and 1 needs the Franka joint layout; both are refused before
+    any device work."""
+    from paper_2510_07674_gb300 import spasm as S
+    wl = scenes.make_problem("tower1", seed=0)
+    with pytest.raises(S.SpasmError) as e:
+        S.Problem(wl, stream=0, ik_mode=2)
+    assert e.value.status == -1 and "ik_mode" in str(e.value)
+    bent = scenes.make_problem("tower1", seed=0, ik_mode=1)
+    bent.robot.dh[2, 0] = 0.02
+    with pytest.raises(S.SpasmError) as e:
+        S.Problem(bent, stream=0)
+    assert e.value.status == -1 and "Franka" in str(e.value)
+
+
 def test_no_cpu_fallback_when_library_missing(monkeypatch, tmp_path):
     from paper_2510_07674_gb300 import spasm as S
     monkeypatch.setattr(S, "_lib", None)
