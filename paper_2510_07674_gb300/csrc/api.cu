@@ -44,10 +44,16 @@ static spasm_status dalloc(T** p, size_t count, cudaStream_t st) {
     return SPASM_OK;
 }
 
+spasm_status spasm::host_wait(spasm_problem* pr) {
+    SPASM_CUDA(cudaStreamSynchronize(pr->stream));
+    pr->stats.host_waits += 1;
+    return SPASM_OK;
+}
+
 spasm_status spasm::check_device_error(spasm_problem* pr) {
     int err = 0;
     SPASM_CUDA(cudaMemcpyAsync(&err, pr->d_err, sizeof(int), cudaMemcpyDeviceToHost, pr->stream));
-    SPASM_CUDA(cudaStreamSynchronize(pr->stream));
+    SPASM_TRY(host_wait(pr));
     pr->stats.d2h_bytes += sizeof(int);
     if (err != 0) {
         const char* what = err == kDevTimeout ? "a bounded device wait gave up" : "a kernel rejected its sizes";
@@ -57,14 +63,29 @@ spasm_status spasm::check_device_error(spasm_problem* pr) {
 }
 
 static void free_all(spasm_problem* pr) {
+    drop_graphs(pr);
     void* ptrs[] = {pr->d_cub, pr->d_osph, pr->d_err, pr->d_xs, pr->d_cost, pr->d_xm, pr->d_costm, pr->d_masked,
                     pr->d_idx, pr->d_sat, pr->d_nsat, pr->d_best, pr->d_place, pr->d_q, pr->d_lam,
                     pr->d_mu, pr->d_metrics, pr->d_tmasked, pr->d_tsat, pr->d_tnsat, pr->d_tbest, pr->d_rq,
-                    pr->d_rcost, pr->d_rsucc, pr->d_cub64, pr->d_osph64, pr->d_rmet64, pr->d_tests, pr->d_sc, pr->d_chkacc};
+                    pr->d_rcost, pr->d_rsucc, pr->d_cub64, pr->d_osph64, pr->d_rmet64, pr->d_tests, pr->d_sc, pr->d_chkacc,
+                    pr->d_ctl};
     for (void* p : ptrs)
         if (p) cudaFreeAsync(p, pr->stream);
     for (cudaEvent_t e : pr->ev)
         if (e) cudaEventDestroy(e);
+    if (pr->cap) cudaStreamDestroy(pr->cap);
+    if (pr->cap_body) cudaStreamDestroy(pr->cap_body);
+}
+
+// Zeroes the attempt-loop counters; a point-to-point problem has its one "placement" (the
+// target) from the start.
+static cudaError_t reset_loops(spasm_problem* pr) {
+    LoopCtl c{};
+    c.n_place = pr->sc.kind == kKindP2P ? 1 : 0;
+    c.seed = pr->sc.seed;
+    cudaError_t e = cudaMemcpyAsync(pr->d_ctl, &c, sizeof c, cudaMemcpyHostToDevice, pr->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(pr->stream);   // c lives on this stack frame
+    return e;
 }
 
 extern "C" const char* spasm_last_error(void) { return g_last_error.c_str(); }
@@ -85,9 +106,8 @@ static bool franka_layout(const double* dh) {
     return std::hypot(a3 * a4 + d2 * d4, d2 * a4 - a3 * d4) > 0.0;
 }
 
-extern "C" spasm_status spasm_create_problem(const spasm_robot* robot, const spasm_obstacles* obs,
-                                             const spasm_goal* goal, const spasm_params* prm, void* cuda_stream,
-                                             spasm_problem_t* out) {
+static spasm_status create_problem_impl(const spasm_robot* robot, const spasm_obstacles* obs, const spasm_goal* goal,
+                                        const spasm_params* prm, void* cuda_stream, spasm_problem_t* out) {
     if (!robot || !obs || !goal || !prm || !out) return fail(SPASM_ERR_INVALID, "null argument");
     *out = nullptr;
     if (robot->dof != 7) return fail(SPASM_ERR_INVALID, "dof must be 7");
@@ -304,9 +324,15 @@ extern "C" spasm_status spasm_create_problem(const spasm_robot* robot, const spa
     ALLOC(pr->d_tests, 3);
     ALLOC(pr->d_sc, 1);
     ALLOC(pr->d_chkacc, P);
+    ALLOC(pr->d_ctl, 1);
 #undef ALLOC
     for (auto& ev : pr->ev)
         if (st == SPASM_OK && cudaEventCreate(&ev) != cudaSuccess) st = fail(SPASM_ERR_CUDA, "cudaEventCreate failed");
+    // streams the attempt-loop graphs are captured on (the problem's own stream may be the
+    // legacy default stream, which cannot be captured)
+    if (st == SPASM_OK && (cudaStreamCreateWithFlags(&pr->cap, cudaStreamNonBlocking) != cudaSuccess ||
+                           cudaStreamCreateWithFlags(&pr->cap_body, cudaStreamNonBlocking) != cudaSuccess))
+        st = fail(SPASM_ERR_CUDA, "cudaStreamCreateWithFlags failed");
     if (st != SPASM_OK) { free_all(pr); delete pr; return st; }
     pr->tab.cub = pr->d_cub;
     pr->tab.osph = pr->d_osph;
@@ -321,7 +347,7 @@ extern "C" spasm_status spasm_create_problem(const spasm_robot* robot, const spa
     if (e == cudaSuccess) e = cudaMemcpyAsync(pr->d_sc, &pr->sc, sizeof(Scalars), cudaMemcpyHostToDevice, pr->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(pr->d_err, 0, sizeof(int), pr->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(pr->d_chkacc, 0, sizeof(CheckAcc) * (size_t)P, pr->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(pr->stream);
+    if (e == cudaSuccess) e = reset_loops(pr);
     if (e != cudaSuccess) {
         free_all(pr);
         delete pr;
@@ -340,6 +366,27 @@ extern "C" spasm_status spasm_create_problem(const spasm_robot* robot, const spa
     }
     *out = pr;
     return SPASM_OK;
+}
+
+// Builds the stage graphs of a new problem (a failure destroys it).
+static spasm_status finish_create(spasm_problem_t pr, spasm_problem_t* out) {
+    const spasm_status st = prepare_graphs(pr);
+    if (st != SPASM_OK) {
+        const std::string msg = spasm_last_error();
+        spasm_destroy_problem(pr);
+        return fail(st, msg);
+    }
+    *out = pr;
+    return SPASM_OK;
+}
+
+extern "C" spasm_status spasm_create_problem(const spasm_robot* robot, const spasm_obstacles* obs,
+                                             const spasm_goal* goal, const spasm_params* prm, void* cuda_stream,
+                                             spasm_problem_t* out) {
+    if (!out) return fail(SPASM_ERR_INVALID, "null argument");
+    spasm_problem_t pr = nullptr;
+    SPASM_TRY(create_problem_impl(robot, obs, goal, prm, cuda_stream, &pr));
+    return finish_create(pr, out);
 }
 
 extern "C" spasm_status spasm_create_packing(const spasm_robot* robot, const spasm_packing* pk,
@@ -376,7 +423,7 @@ extern "C" spasm_status spasm_create_packing(const spasm_robot* robot, const spa
     spasm_obstacles obs{4, walls.data(), 0, nullptr};
     spasm_goal goal{B, half.data(), init.data(), box, zs - 0.5 * u, 0.0};
     spasm_problem_t pr = nullptr;
-    SPASM_TRY(spasm_create_problem(robot, &obs, &goal, prm, cuda_stream, &pr));
+    SPASM_TRY(create_problem_impl(robot, &obs, &goal, prm, cuda_stream, &pr));
     Scalars& sc = pr->sc;
     sc.kind = kKindPack;
     sc.n_cells = total;
@@ -402,8 +449,7 @@ extern "C" spasm_status spasm_create_packing(const spasm_robot* robot, const spa
         spasm_destroy_problem(pr);
         return fail(SPASM_ERR_CUDA, std::string("create_packing: ") + cudaGetErrorString(e));
     }
-    *out = pr;
-    return SPASM_OK;
+    return finish_create(pr, out);
 }
 
 extern "C" spasm_status spasm_create_p2p(const spasm_robot* robot, const spasm_obstacles* obs, const double* target,
@@ -414,7 +460,7 @@ extern "C" spasm_status spasm_create_p2p(const spasm_robot* robot, const spasm_o
     const double box[6] = {target[0] - 0.1, target[1] - 0.1, target[2], target[0] + 0.1, target[1] + 0.1, target[2] + 0.1};
     spasm_goal goal{1, half, target, box, target[2], 0.0};
     spasm_problem_t pr = nullptr;
-    SPASM_TRY(spasm_create_problem(robot, obs, &goal, prm, cuda_stream, &pr));
+    SPASM_TRY(create_problem_impl(robot, obs, &goal, prm, cuda_stream, &pr));
     // one transit segment: C = W configurations; stage 1 does not apply
     pr->sc.kind = kKindP2P;
     pr->sc.C = pr->sc.S + 1;
@@ -424,26 +470,25 @@ extern "C" spasm_status spasm_create_p2p(const spasm_robot* robot, const spasm_o
     pr->n_place = 1;
     cudaError_t e = cudaMemsetAsync(pr->d_place, 0, sizeof(float) * 4, pr->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(pr->d_sc, &pr->sc, sizeof(Scalars), cudaMemcpyHostToDevice, pr->stream);
+    if (e == cudaSuccess) e = reset_loops(pr);
     if (e == cudaSuccess) e = cudaStreamSynchronize(pr->stream);
     if (e != cudaSuccess) {
         spasm_destroy_problem(pr);
         return fail(SPASM_ERR_CUDA, std::string("create_p2p: ") + cudaGetErrorString(e));
     }
-    *out = pr;
-    return SPASM_OK;
+    return finish_create(pr, out);
 }
 
 extern "C" spasm_status spasm_placements(spasm_problem_t pr, int* n_place, double* placements) {
     if (!pr) return fail(SPASM_ERR_INVALID, "null problem");
-    SPASM_CUDA(cudaStreamSynchronize(pr->stream));
-    if (n_place) *n_place = pr->placed ? pr->n_place : 0;
-    if (placements) {
-        std::vector<float> tmp((size_t)pr->sc.P * pr->sc.B * 4, 0.f);
+    SPASM_TRY(finalize(pr));
+    std::vector<float> tmp(placements ? (size_t)pr->sc.P * pr->sc.B * 4 : 0);
+    if (placements)
         SPASM_CUDA(cudaMemcpyAsync(tmp.data(), pr->d_place, tmp.size() * sizeof(float), cudaMemcpyDeviceToHost, pr->stream));
-        SPASM_CUDA(cudaStreamSynchronize(pr->stream));
-        pr->stats.d2h_bytes += tmp.size() * sizeof(float);
-        for (size_t i = 0; i < tmp.size(); ++i) placements[i] = tmp[i];
-    }
+    SPASM_TRY(host_wait(pr));
+    pr->stats.d2h_bytes += (long long)(tmp.size() * sizeof(float));
+    if (n_place) *n_place = pr->placed ? pr->n_place : 0;
+    for (size_t i = 0; i < tmp.size(); ++i) placements[i] = tmp[i];
     if (!pr->placed || pr->n_place == 0) return fail(SPASM_ERR_NOSOLUTION, "no placements");
     return SPASM_OK;
 }
@@ -463,224 +508,27 @@ extern "C" spasm_status spasm_sizes(spasm_problem_t pr, int* C, int* NR) {
     return SPASM_OK;
 }
 
-// ---------------------------------------------------------------------------------- stage 1
-// One attempt of Alg. 1 entirely on the device; the count of satisfying particles lands in
-// d_nsat and the best min(P, count) placements in d_place.
-spasm_status spasm::place_attempt(spasm_problem* pr, uint32_t attempt, cudaStream_t s) {
-    const Scalars& sc = pr->sc;
-    const int N = sc.N, M = sc.M, P = sc.P, B = sc.B;
-    SPASM_CUDA(launch_place_sample_cost(sc, pr->tab, N, attempt, pr->d_xs, pr->d_cost, pr->d_err, s));
-    SPASM_CUDA(launch_topk(pr->d_cost, N, M, pr->d_idx, nullptr, s));
-    SPASM_CUDA(launch_place_descend(sc, pr->tab, M, pr->d_xs, N, pr->d_idx, pr->d_xm, sc.K_lin, sc.K_quad,
-                                    pr->d_costm, pr->d_sat, nullptr, pr->d_err, s));
-    SPASM_CUDA(launch_mask_costs(pr->d_costm, pr->d_sat, M, pr->d_masked, pr->d_nsat, s));
-    SPASM_CUDA(launch_topk(pr->d_masked, M, P, pr->d_best, nullptr, s));
-    SPASM_CUDA(launch_gather_soa_to_aos(pr->d_xm, M, 4 * B, pr->d_best, P, pr->d_place, s));
-    count_launches(pr, 6);
-    return SPASM_OK;
-}
-
-spasm_status spasm::place_continue(spasm_problem* pr, int attempt, int steps, int nsat) {
-    const int per = pr->sc.K_lin + pr->sc.K_quad;
-    while (nsat == 0 && (steps < pr->prm.max_steps || attempt == 0)) {
-        SPASM_TRY(place_attempt(pr, (uint32_t)attempt, pr->stream));
-        steps += per;
-        ++attempt;
-        SPASM_CUDA(cudaMemcpyAsync(&nsat, pr->d_nsat, sizeof(int), cudaMemcpyDeviceToHost, pr->stream));
-        SPASM_CUDA(cudaStreamSynchronize(pr->stream));
-        pr->stats.d2h_bytes += sizeof(int);
-    }
-    const int found = nsat > 0 ? (nsat < pr->sc.P ? nsat : pr->sc.P) : 0;
-    pr->place_attempts = attempt;
-    pr->place_steps = steps;
-    pr->n_place = found;
-    pr->stats.place_attempts += attempt;
-    SPASM_TRY(check_device_error(pr));
-    pr->placed = true;
-    if (found == 0) return fail(SPASM_ERR_NOSOLUTION, "stage 1 found no satisfying placement within max_steps");
-    return SPASM_OK;
-}
-
-extern "C" spasm_status spasm_place(spasm_problem_t pr) {
-    if (!pr) return fail(SPASM_ERR_INVALID, "null problem");
-    if (pr->sc.kind == kKindP2P) return fail(SPASM_ERR_INVALID, "a point-to-point problem has no stage 1");
-    SPASM_TRY(rec(pr, 0));
-    const spasm_status st = place_continue(pr, 0, 0, 0);
-    SPASM_TRY(rec(pr, 1));
-    if (pr->timing) {
-        SPASM_CUDA(cudaEventSynchronize(pr->ev[1]));
-        pr->stats.ms_place += ev_ms(pr->ev[0], pr->ev[1]);
-    }
-    return st;
-}
-
-// ---------------------------------------------------------------------------------- stage 2
-static spasm_status traj_attempt(spasm_problem* pr, uint32_t attempt) {
-    const Scalars& sc = pr->sc;
-    cudaStream_t s = pr->stream;
-    SPASM_TRY(rec(pr, 2));
-    SPASM_CUDA(launch_lift(sc, sc.Q, pr->d_place, pr->n_place, attempt, pr->d_q, s));
-    SPASM_TRY(rec(pr, 3));
-    TrajIO io{};
-    io.q = pr->d_q; io.lam = pr->d_lam; io.mu = pr->d_mu; io.metrics = pr->d_metrics; io.sat = pr->d_tsat;
-    io.k_steps = sc.K_traj; io.init_multipliers = 1;
-    io.tests = pr->d_tests;
-    SPASM_CUDA(launch_traj(sc, pr->tab, sc.Q, kTrajModeDescend, io, pr->d_err, s));
-    SPASM_TRY(rec(pr, 4));
-    count_launches(pr, 3);
-    pr->stats.traj_launches += 1;
-    pr->stats.particle_iters += (long long)sc.Q * sc.K_traj;
-    return SPASM_OK;
-}
-
-__global__ static void k_rank_costs(const float* metrics, int n, float* out) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) out[i] = metrics[8 * (size_t)i + 7];
-}
-
-__global__ static void k_gather_solutions(const float* q, const float* metrics, const int* best, const int* nsat, int P,
-                                          int C, float* rq, float* rcost, int* rsucc) {
-    const int r = blockIdx.x;
-    const int n = min(*nsat, P);
-    if (r >= P) return;
-    if (r >= n) {
-        if (threadIdx.x == 0) { rcost[r] = 0.f; rsucc[r] = 0; }
-        return;
-    }
-    const int src = best[r];
-    for (int i = threadIdx.x; i < C * 8; i += blockDim.x) rq[(size_t)r * C * 8 + i] = q[(size_t)src * C * 8 + i];
-    if (threadIdx.x == 0) { rcost[r] = metrics[8 * (size_t)src + 7]; rsucc[r] = 1; }
-}
-
-spasm_status spasm::traj_select(spasm_problem* pr, cudaStream_t s) {
-    const Scalars& sc = pr->sc;
-    k_rank_costs<<<(sc.Q + 255) / 256, 256, 0, s>>>(pr->d_metrics, sc.Q, pr->d_tmasked);
-    SPASM_CUDA(cudaGetLastError());
-    SPASM_CUDA(launch_mask_costs(pr->d_tmasked, pr->d_tsat, sc.Q, pr->d_tmasked, pr->d_tnsat, s));
-    count_launches(pr, 2);
-    return SPASM_OK;
-}
-
-spasm_status spasm::finish_enqueue(spasm_problem* pr, cudaStream_t s) {
-    const Scalars& sc = pr->sc;
-    if (sc.Q > 32768) return fail(SPASM_ERR_INVALID, "Q > 32768 unsupported by the selection kernel");
-    SPASM_CUDA(launch_topk(pr->d_tmasked, sc.Q, sc.P, pr->d_tbest, nullptr, s));
-    k_gather_solutions<<<sc.P, 256, 0, s>>>(pr->d_q, pr->d_metrics, pr->d_tbest, pr->d_tnsat, sc.P, sc.C, pr->d_rq,
-                                             pr->d_rcost, pr->d_rsucc);
-    SPASM_CUDA(cudaGetLastError());
-    // FP64 re-evaluation of the returned solutions decides their success flags
-    SPASM_CUDA(launch_check64(pr->s64, pr->d_cub64, pr->d_osph64, pr->d_rq, pr->d_tnsat, sc.P, pr->d_rmet64,
-                              pr->d_rsucc, pr->d_chkacc, s));
-    count_launches(pr, 3);
-    return SPASM_OK;
-}
-
-spasm_status spasm::traj_continue(spasm_problem* pr, int attempt, int steps, int nsat, int* found) {
-    const Scalars& sc = pr->sc;
-    cudaStream_t s = pr->stream;
-    while (nsat == 0 && (steps < pr->prm.max_steps || attempt == 0)) {
-        SPASM_TRY(traj_attempt(pr, (uint32_t)attempt));
-        steps += sc.K_traj;
-        ++attempt;
-        SPASM_TRY(traj_select(pr, s));
-        SPASM_CUDA(cudaMemcpyAsync(&nsat, pr->d_tnsat, sizeof(int), cudaMemcpyDeviceToHost, s));
-        SPASM_CUDA(cudaStreamSynchronize(s));
-        pr->stats.d2h_bytes += sizeof(int);
-        if (pr->timing) {
-            pr->stats.ms_lift += ev_ms(pr->ev[2], pr->ev[3]);
-            pr->stats.ms_traj += ev_ms(pr->ev[3], pr->ev[4]);
-        }
-    }
-    *found = nsat > 0 ? (nsat < sc.P ? nsat : sc.P) : 0;
-    pr->traj_attempts = attempt;
-    pr->stats.traj_attempts += attempt;
-    return SPASM_OK;
-}
-
-spasm_status spasm::finish_record(spasm_problem* pr, int found, bool finish_done) {
-    const Scalars& sc = pr->sc;
-    if (found > 0 && !finish_done) {
-        SPASM_TRY(rec(pr, 5));
-        SPASM_TRY(finish_enqueue(pr, pr->stream));
-        SPASM_TRY(rec(pr, 6));
-    }
-    pr->n_found = found;
-    SPASM_TRY(check_device_error(pr));
-    {
-        unsigned long long nt[3] = {0, 0, 0};
-        SPASM_CUDA(cudaMemcpyAsync(nt, pr->d_tests, sizeof nt, cudaMemcpyDeviceToHost, pr->stream));
-        SPASM_CUDA(cudaStreamSynchronize(pr->stream));
-        pr->stats.d2h_bytes += sizeof nt;
-        pr->stats.tests_executed += (long long)nt[0];
-        pr->stats.cull_configs += (long long)nt[1];
-        pr->stats.cand_configs += (long long)nt[2];
-    }
-    if (found > 0) {
-        std::vector<int> succ(sc.P, 0);
-        SPASM_CUDA(cudaMemcpyAsync(succ.data(), pr->d_rsucc, sc.P * sizeof(int), cudaMemcpyDeviceToHost, pr->stream));
-        SPASM_CUDA(cudaStreamSynchronize(pr->stream));
-        pr->stats.d2h_bytes += sc.P * sizeof(int);
-        int ns = 0;
-        for (int r = 0; r < found; ++r) ns += succ[r] != 0;
-        pr->stats.n_success = ns;
-        if (pr->timing && !finish_done) pr->stats.ms_finish += ev_ms(pr->ev[5], pr->ev[6]);
-    }
-    pr->stats.n_found = found;
-    pr->optimized = true;
-    if (found == 0) return fail(SPASM_ERR_NOSOLUTION, "stage 2 found no satisfying trajectory within max_steps");
-    return SPASM_OK;
-}
-
-extern "C" spasm_status spasm_optimize(spasm_problem_t pr) {
-    if (!pr) return fail(SPASM_ERR_INVALID, "null problem");
-    if (pr->sc.kind == kKindPack)
-        return fail(SPASM_ERR_INVALID, "stage 2 is implemented for the tower goal only; packing runs stage 1 (spasm_place)");
-    if (!pr->placed) {
-        spasm_status st = spasm_place(pr);
-        if (st != SPASM_OK) return st;
-    }
-    if (pr->n_place <= 0) return fail(SPASM_ERR_NOSOLUTION, "no placements to lift");
-    SPASM_CUDA(cudaMemsetAsync(pr->d_tests, 0, 3 * sizeof(unsigned long long), pr->stream));
-    int found = 0;
-    SPASM_TRY(traj_continue(pr, 0, 0, 0, &found));
-    return finish_record(pr, found, false);
-}
-
 extern "C" spasm_status spasm_result(spasm_problem_t pr, int* n_found, double* placements, double* traj, double* cost,
                                      int* success) {
     if (!pr) return fail(SPASM_ERR_INVALID, "null problem");
     const Scalars& sc = pr->sc;
     const int P = sc.P, B = sc.B, C = sc.C;
-    SPASM_CUDA(cudaStreamSynchronize(pr->stream));
+    SPASM_TRY(finalize(pr));
+    std::vector<float> tp(placements ? (size_t)P * B * 4 : 0), tq(traj ? (size_t)P * C * 8 : 0), tc(cost ? P : 0);
+    if (placements)
+        SPASM_CUDA(cudaMemcpyAsync(tp.data(), pr->d_place, tp.size() * sizeof(float), cudaMemcpyDeviceToHost, pr->stream));
+    if (traj) SPASM_CUDA(cudaMemcpyAsync(tq.data(), pr->d_rq, tq.size() * sizeof(float), cudaMemcpyDeviceToHost, pr->stream));
+    if (cost) SPASM_CUDA(cudaMemcpyAsync(tc.data(), pr->d_rcost, tc.size() * sizeof(float), cudaMemcpyDeviceToHost, pr->stream));
+    if (success) SPASM_CUDA(cudaMemcpyAsync(success, pr->d_rsucc, P * sizeof(int), cudaMemcpyDeviceToHost, pr->stream));
+    SPASM_TRY(host_wait(pr));
+    pr->stats.d2h_bytes += (long long)((tp.size() + tq.size() + tc.size()) * sizeof(float) + (success ? P * sizeof(int) : 0));
     if (n_found) *n_found = pr->optimized ? pr->n_found : 0;
-    if (placements) {
-        std::vector<float> tmp((size_t)P * B * 4, 0.f);
-        SPASM_CUDA(cudaMemcpyAsync(tmp.data(), pr->d_place, tmp.size() * sizeof(float), cudaMemcpyDeviceToHost, pr->stream));
-        SPASM_CUDA(cudaStreamSynchronize(pr->stream));
-        pr->stats.d2h_bytes += tmp.size() * sizeof(float);
-        for (size_t i = 0; i < tmp.size(); ++i) placements[i] = tmp[i];
-    }
-    if (traj) {
-        std::vector<float> tmp((size_t)P * C * 8, 0.f);
-        SPASM_CUDA(cudaMemcpyAsync(tmp.data(), pr->d_rq, tmp.size() * sizeof(float), cudaMemcpyDeviceToHost, pr->stream));
-        SPASM_CUDA(cudaStreamSynchronize(pr->stream));
-        pr->stats.d2h_bytes += tmp.size() * sizeof(float);
+    for (size_t i = 0; i < tp.size(); ++i) placements[i] = tp[i];
+    if (traj)
         for (int r = 0; r < P; ++r)
             for (int t = 0; t < C; ++t)
-                for (int j = 0; j < 7; ++j) traj[((size_t)r * C + t) * 7 + j] = tmp[((size_t)r * C + t) * 8 + j];
-    }
-    if (cost) {
-        std::vector<float> tmp(P, 0.f);
-        SPASM_CUDA(cudaMemcpyAsync(tmp.data(), pr->d_rcost, P * sizeof(float), cudaMemcpyDeviceToHost, pr->stream));
-        SPASM_CUDA(cudaStreamSynchronize(pr->stream));
-        pr->stats.d2h_bytes += P * sizeof(float);
-        for (int r = 0; r < P; ++r) cost[r] = tmp[r];
-    }
-    if (success) {
-        SPASM_CUDA(cudaMemcpyAsync(success, pr->d_rsucc, P * sizeof(int), cudaMemcpyDeviceToHost, pr->stream));
-        SPASM_CUDA(cudaStreamSynchronize(pr->stream));
-        pr->stats.d2h_bytes += P * sizeof(int);
-    }
+                for (int j = 0; j < 7; ++j) traj[((size_t)r * C + t) * 7 + j] = tq[((size_t)r * C + t) * 8 + j];
+    for (size_t r = 0; r < tc.size(); ++r) cost[r] = tc[r];
     if (!pr->optimized || pr->n_found == 0) return fail(SPASM_ERR_NOSOLUTION, "no solution");
     return SPASM_OK;
 }
@@ -746,13 +594,27 @@ extern "C" spasm_status spasm_traj_descend(spasm_problem_t pr, int n, float* q, 
     return SPASM_OK;
 }
 
+extern "C" spasm_status spasm_traj_check(spasm_problem_t pr, int n, const float* q, double* metrics, int* ok) {
+    if (!pr || n < 0 || (n > 0 && (!q || !metrics || !ok))) return fail(SPASM_ERR_INVALID, "bad arguments");
+    // the accumulators of the split check hold P rows: check in chunks of at most P
+    const int P = pr->sc.P, C = pr->sc.C;
+    for (int off = 0; off < n; off += P) {
+        const int k = n - off < P ? n - off : P;
+        SPASM_CUDA(launch_check64(pr->s64, pr->d_cub64, pr->d_osph64, q + (size_t)off * C * 8, nullptr, k,
+                                  metrics + (size_t)off * 6, ok + off, pr->d_chkacc, pr->stream));
+    }
+    return SPASM_OK;
+}
+
 extern "C" spasm_status spasm_set_seed(spasm_problem_t pr, uint64_t seed) {
     if (!pr) return fail(SPASM_ERR_INVALID, "null problem");
+    SPASM_TRY(finalize(pr));
     SPASM_CUDA(cudaStreamSynchronize(pr->stream));
     pr->sc.seed = seed;
     pr->prm.seed = seed;
+    // the stage graphs read the key from the loop block on the device, so they stay valid
     SPASM_CUDA(cudaMemcpyAsync(pr->d_sc, &pr->sc, sizeof(Scalars), cudaMemcpyHostToDevice, pr->stream));
-    SPASM_CUDA(cudaStreamSynchronize(pr->stream));
+    SPASM_CUDA(reset_loops(pr));
     pr->optimized = false;
     pr->placed = pr->sc.kind == kKindP2P;   // a point-to-point problem has no stage 1
     pr->n_place = pr->placed ? 1 : 0;
@@ -768,6 +630,7 @@ extern "C" spasm_status spasm_set_timing(spasm_problem_t pr, int enable) {
 
 extern "C" spasm_status spasm_get_stats(spasm_problem_t pr, spasm_stats* out) {
     if (!pr || !out) return fail(SPASM_ERR_INVALID, "null argument");
+    SPASM_TRY(finalize(pr));
     *out = pr->stats;
     return SPASM_OK;
 }

@@ -1,10 +1,11 @@
 // Batched form of the two-stage solve (not in the paper: the throughput form of the hot path
-// for many independent problems).  The first attempt of stage 1 of every problem is one CUDA
-// graph; stage 2 (lift of every problem, one persistent launch of the trajectory kernel over
-// the particles of all problems, selection and FP64 check of every problem) is a second
-// graph.  The rare problem that needs a further attempt continues alone on its own stream
-// with the code of spasm_optimize.  Every particle runs the same arithmetic as in the
-// single-problem launches, so each problem's result equals its spasm_optimize result.
+// for many independent problems).  One CUDA graph holds the whole batch: stage 1 of every
+// problem not yet placed (each with its own device-side attempt loop, in parallel branches),
+// the first stage-2 lift of every problem, one persistent launch of the trajectory kernel
+// over the particles of all problems, then per problem (in parallel branches) the
+// satisfying selection, its device-side re-lift loop and the FP64 check.  Every particle
+// runs the same arithmetic as in the single-problem launches, so each problem's result
+// equals its spasm_optimize result.
 #include <algorithm>
 #include <chrono>
 #include <cstring>
@@ -17,34 +18,50 @@ using namespace spasm;
 
 namespace {
 
-// Capture what `enqueue` puts on stream s into a graph, run it once and wait for it.
-template <typename F>
-spasm_status run_as_graph(cudaStream_t s, F enqueue) {
-    SPASM_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));
-    const spasm_status st = enqueue();
-    cudaGraph_t g = nullptr;
-    cudaError_t e = cudaStreamEndCapture(s, &g);
-    if (st != SPASM_OK) {
-        if (g) cudaGraphDestroy(g);
-        return st;
+// Parallel branches of a capture on stream s: fork() makes every branch stream depend on
+// s's work so far, join() makes s depend on everything the branches enqueued since.
+struct Branches {
+    std::vector<cudaStream_t> st;
+    std::vector<cudaEvent_t> ev;
+    cudaStream_t s = nullptr;
+    ~Branches() {
+        for (cudaEvent_t e : ev) cudaEventDestroy(e);
+        for (cudaStream_t b : st) cudaStreamDestroy(b);
     }
-    if (e != cudaSuccess) return fail(SPASM_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
-    cudaGraphExec_t x = nullptr;
-    e = cudaGraphInstantiate(&x, g, 0);
-    if (e == cudaSuccess) e = cudaGraphLaunch(x, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (x) cudaGraphExecDestroy(x);
-    cudaGraphDestroy(g);
-    if (e != cudaSuccess) return fail(SPASM_ERR_CUDA, std::string("graph launch: ") + cudaGetErrorString(e));
-    return SPASM_OK;
-}
-
-struct PinnedInts {
-    int* p = nullptr;
-    ~PinnedInts() {
-        if (p) cudaFreeHost(p);
+    spasm_status init(cudaStream_t main, int n) {
+        s = main;
+        for (int i = 0; i < n; ++i) {
+            cudaStream_t b = nullptr;
+            SPASM_CUDA(cudaStreamCreateWithFlags(&b, cudaStreamNonBlocking));
+            st.push_back(b);
+        }
+        return SPASM_OK;
     }
+    spasm_status event(cudaEvent_t* e) {
+        SPASM_CUDA(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+        ev.push_back(*e);
+        return SPASM_OK;
+    }
+    spasm_status fork() {
+        cudaEvent_t e;
+        SPASM_TRY(event(&e));
+        SPASM_CUDA(cudaEventRecord(e, s));
+        for (cudaStream_t b : st) SPASM_CUDA(cudaStreamWaitEvent(b, e, 0));
+        return SPASM_OK;
+    }
+    spasm_status join() {
+        for (cudaStream_t b : st) {
+            cudaEvent_t e;
+            SPASM_TRY(event(&e));
+            SPASM_CUDA(cudaEventRecord(e, b));
+            SPASM_CUDA(cudaStreamWaitEvent(s, e, 0));
+        }
+        return SPASM_OK;
+    }
+    cudaStream_t operator[](size_t i) const { return st[i % st.size()]; }
 };
+
+constexpr int kMaxBranches = 16;
 
 spasm_status check_batch(spasm_problem_t* prs, int n, void* stream) {
     if (!prs || n < 1 || n > 4096) return fail(SPASM_ERR_INVALID, "batch of 1..4096 problems expected");
@@ -59,31 +76,48 @@ spasm_status check_batch(spasm_problem_t* prs, int n, void* stream) {
     return SPASM_OK;
 }
 
-// Stage 1 of every problem not yet placed: attempt 0 of all of them as one graph, then any
-// further attempts per problem.  status[i] records each problem's outcome.
-spasm_status place_all(spasm_problem_t* prs, int n, cudaStream_t s, std::vector<spasm_status>& status) {
-    std::vector<int> todo;
-    for (int i = 0; i < n; ++i)
-        if (!prs[i]->placed) todo.push_back(i);
-    status.assign(n, SPASM_OK);
-    if (todo.empty()) return SPASM_OK;
-    PinnedInts h;
-    SPASM_CUDA(cudaMallocHost(reinterpret_cast<void**>(&h.p), sizeof(int) * n));
-    SPASM_TRY(run_as_graph(s, [&]() -> spasm_status {
-        for (int i : todo) {
-            SPASM_TRY(place_attempt(prs[i], 0u, s));
-            SPASM_CUDA(cudaMemcpyAsync(&h.p[i], prs[i]->d_nsat, sizeof(int), cudaMemcpyDeviceToHost, s));
-        }
-        return SPASM_OK;
-    }));
-    for (int i : todo) {
-        spasm_problem* pr = prs[i];
-        pr->stats.d2h_bytes += sizeof(int);
-        const spasm_status st = place_continue(pr, 1, pr->sc.K_lin + pr->sc.K_quad, h.p[i]);
-        if (st != SPASM_OK && st != SPASM_ERR_NOSOLUTION) return st;
-        status[i] = st;
+// Captures `enqueue` (given the capture stream) into a graph, launches it on `launch_on`.
+template <typename F>
+spasm_status run_graph(cudaStream_t launch_on, F enqueue) {
+    cudaStream_t cap = nullptr;
+    SPASM_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    struct S { cudaStream_t c; ~S() { cudaStreamDestroy(c); } } guard{cap};
+    SPASM_CUDA(cudaStreamBeginCapture(cap, cudaStreamCaptureModeRelaxed));
+    const spasm_status st = enqueue(cap);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(cap, &g);
+    if (st != SPASM_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
     }
+    if (e != cudaSuccess) return fail(SPASM_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    cudaGraphExec_t x = nullptr;
+    e = cudaGraphInstantiate(&x, g, 0);
+    if (e == cudaSuccess) e = cudaGraphLaunch(x, launch_on);
+    // the executable graph is released only after its launch has finished
+    if (e == cudaSuccess) e = cudaStreamSynchronize(launch_on);
+    if (x) cudaGraphExecDestroy(x);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(SPASM_ERR_CUDA, std::string("graph launch: ") + cudaGetErrorString(e));
     return SPASM_OK;
+}
+
+// Stage 1 (with its device-side attempt loop) of the problems `todo`, in parallel branches
+// of the capture on s (br: not yet initialised; it must outlive the capture).
+spasm_status enqueue_place_all(spasm_problem_t* prs, const std::vector<int>& todo, cudaStream_t s, Branches& br) {
+    if (todo.empty()) return SPASM_OK;
+    SPASM_TRY(br.init(s, std::min<int>((int)todo.size(), kMaxBranches)));
+    SPASM_TRY(br.fork());
+    for (size_t k = 0; k < todo.size(); ++k) SPASM_TRY(enqueue_place(prs[todo[k]], br[k]));
+    return br.join();
+}
+
+void mark_placed(spasm_problem_t* prs, const std::vector<int>& todo) {
+    for (int i : todo) {
+        prs[i]->placed = true;
+        prs[i]->place_pending = true;
+        prs[i]->place_timed = false;
+    }
 }
 
 // Work list of a batched trajectory launch over the problems `live` (in `order`).
@@ -105,6 +139,7 @@ JobList make_jobs(spasm_problem_t* prs, const std::vector<int>& live, int per_fe
         if (mode == kTrajModeDescend) {
             j.io.lam = pr->d_lam; j.io.mu = pr->d_mu; j.io.metrics = pr->d_metrics; j.io.sat = pr->d_tsat;
             j.io.tests = pr->d_tests;
+            j.io.active = &pr->d_ctl->n_place;
         }
         j.io.k_steps = k_steps;
         j.io.init_multipliers = init_multipliers ? 1 : 0;
@@ -183,61 +218,46 @@ extern "C" spasm_status spasm_optimize_batch(spasm_problem_t* prs, int n, void* 
     if (cfg_in) cfg = *cfg_in;
     SPASM_TRY(check_config(cfg));
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
-    for (int i = 0; i < n; ++i) SPASM_CUDA(cudaStreamSynchronize(prs[i]->stream));
-
-    std::vector<spasm_status> status;
-    SPASM_TRY(place_all(prs, n, s, status));
-    std::vector<int> live;
-    for (int i = 0; i < n; ++i)
-        if (status[i] == SPASM_OK && prs[i]->n_place > 0) live.push_back(i);
-    if (live.empty()) return SPASM_OK;
-
-    const std::vector<int> order = job_order(prs, live, cfg.order);
+    std::vector<int> todo, all(n);
+    for (int i = 0; i < n; ++i) {
+        SPASM_TRY(finalize(prs[i]));
+        SPASM_CUDA(cudaStreamSynchronize(prs[i]->stream));
+        if (!prs[i]->placed) todo.push_back(i);
+        all[i] = i;
+    }
+    const std::vector<int> order = job_order(prs, all, cfg.order);
     JobList L = make_jobs(prs, order, cfg.per_fetch, kTrajModeDescend, 0, true);
     for (size_t k = 0; k < order.size(); ++k) L.jobs[k].io.k_steps = prs[order[k]]->sc.K_traj;
     int grid = 0;
     SPASM_TRY(batch_grid(cfg, L.smem, &grid));
     DeviceJobs dj;
     SPASM_TRY(upload_jobs(L, s, dj));
-    PinnedInts h;
-    SPASM_CUDA(cudaMallocHost(reinterpret_cast<void**>(&h.p), sizeof(int) * n));
-    SPASM_TRY(run_as_graph(s, [&]() -> spasm_status {
-        for (int i : live) {
-            spasm_problem* pr = prs[i];
-            SPASM_CUDA(cudaMemsetAsync(pr->d_tests, 0, 3 * sizeof(unsigned long long), s));
-            SPASM_CUDA(launch_lift(pr->sc, pr->sc.Q, pr->d_place, pr->n_place, 0u, pr->d_q, s));
-        }
-        SPASM_CUDA(cudaMemsetAsync(dj.next, 0, sizeof(int), s));
+    // one graph: stage 1 of the problems not yet placed, the first lift of every problem, one
+    // persistent trajectory launch over all particles, then each problem's selection, re-lift
+    // loop and FP64 check; problems whose stage 1 kept nothing skip stage 2 on the device
+    Branches br1, br;   // branch streams live until the capture has ended
+    SPASM_TRY(run_graph(s, [&](cudaStream_t c) -> spasm_status {
+        SPASM_TRY(enqueue_place_all(prs, todo, c, br1));
+        SPASM_TRY(br.init(c, std::min(n, kMaxBranches)));
+        SPASM_TRY(br.fork());
+        for (int i = 0; i < n; ++i) SPASM_TRY(enqueue_traj_lift(prs[i], br[i]));
+        SPASM_TRY(br.join());
+        SPASM_CUDA(cudaMemsetAsync(dj.next, 0, sizeof(int), c));
         SPASM_CUDA(launch_traj_batch(dj.jobs, (int)L.jobs.size(), L.n_items, cfg.per_fetch, kTrajModeDescend, dj.next,
-                                     L.smem, grid, s));
-        for (int i : live) {
-            spasm_problem* pr = prs[i];
-            SPASM_TRY(traj_select(pr, s));
-            SPASM_CUDA(cudaMemcpyAsync(&h.p[i], pr->d_tnsat, sizeof(int), cudaMemcpyDeviceToHost, s));
-            SPASM_TRY(finish_enqueue(pr, s));
+                                     L.smem, grid, c));
+        SPASM_TRY(br.fork());
+        for (int i = 0; i < n; ++i) {
+            SPASM_TRY(enqueue_traj_retry(prs[i], br[i]));
+            SPASM_TRY(enqueue_finish(prs[i], br[i]));
         }
-        return SPASM_OK;
+        return br.join();
     }));
-    for (int i : live) {
+    mark_placed(prs, todo);
+    for (int i = 0; i < n; ++i) {
         spasm_problem* pr = prs[i];
-        const Scalars& sc = pr->sc;
-        count_launches(pr, 2);   // its lift; the shared trajectory launch belongs to no single problem
-        pr->stats.traj_launches += 1;
-        pr->stats.particle_iters += (long long)sc.Q * sc.K_traj;
-        pr->stats.d2h_bytes += sizeof(int);
-        int found = 0;
-        spasm_status st;
-        if (h.p[i] > 0) {
-            found = h.p[i] < sc.P ? h.p[i] : sc.P;
-            pr->traj_attempts = 1;
-            pr->stats.traj_attempts += 1;
-            st = finish_record(pr, found, true);
-        } else {
-            pr->stats.traj_attempts -= 1;   // traj_continue counts the batched attempt again
-            SPASM_TRY(traj_continue(pr, 1, sc.K_traj, 0, &found));
-            st = finish_record(pr, found, false);
-        }
-        if (st != SPASM_OK && st != SPASM_ERR_NOSOLUTION) return st;
+        pr->traj_pending = true;
+        pr->traj_timed = false;
+        pr->traj_batched = true;
     }
     return SPASM_OK;
 }
@@ -247,12 +267,20 @@ extern "C" spasm_status spasm_batch_autotune(spasm_problem_t* prs, int n, void* 
     SPASM_TRY(check_batch(prs, n, cuda_stream));
     if (!best) return fail(SPASM_ERR_INVALID, "null config");
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
-    for (int i = 0; i < n; ++i) SPASM_CUDA(cudaStreamSynchronize(prs[i]->stream));
-    std::vector<spasm_status> status;
-    SPASM_TRY(place_all(prs, n, s, status));
+    std::vector<int> todo;
+    for (int i = 0; i < n; ++i) {
+        SPASM_TRY(finalize(prs[i]));
+        SPASM_CUDA(cudaStreamSynchronize(prs[i]->stream));
+        if (!prs[i]->placed) todo.push_back(i);
+    }
+    Branches br;
+    SPASM_TRY(run_graph(s, [&](cudaStream_t c) { return enqueue_place_all(prs, todo, c, br); }));
+    mark_placed(prs, todo);
     std::vector<int> live;
-    for (int i = 0; i < n; ++i)
-        if (status[i] == SPASM_OK && prs[i]->n_place > 0) live.push_back(i);
+    for (int i = 0; i < n; ++i) {
+        SPASM_TRY(finalize(prs[i]));   // reads the placement counts
+        if (prs[i]->n_place > 0) live.push_back(i);
+    }
     spasm_batch_default_config(best);
     if (best_ms) *best_ms = 0.0;
     if (live.empty()) return SPASM_OK;
@@ -294,6 +322,7 @@ extern "C" spasm_status spasm_batch_autotune(spasm_problem_t* prs, int n, void* 
         }
     }
     for (int i : live) SPASM_TRY(check_device_error(prs[i]));
+    // the candidates' evaluations wrote nothing the next solve reads; q is lifted again there
     if (best_ms) *best_ms = best_t;
     return SPASM_OK;
 }

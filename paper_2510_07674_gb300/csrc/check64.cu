@@ -78,7 +78,7 @@ __global__ void __launch_bounds__(kChkThreads) k_check64(const __grid_constant__
                                                         int* __restrict__ ok, CheckAcc* __restrict__ acc, int split) {
     const int r = blockIdx.x, slice = blockIdx.y;
     if (r >= P) return;
-    const int n = min(*n_sol, P);
+    const int n = n_sol ? min(*n_sol, P) : P;
     const int tid = threadIdx.x;
     if (r >= n) {
         if (tid == 0 && slice == 0) ok[r] = 0;

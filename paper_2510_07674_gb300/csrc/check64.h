@@ -28,6 +28,8 @@ struct CheckAcc {
 };
 
 // cub: n_cub x 4 x double4 (centre, then R columns with half extents); osph: n_osph x double4.
+// q: P x C x 8 floats; n_sol: device count of the rows that hold solutions (rows from
+// min(*n_sol, P) on get ok = 0 and keep their metrics), or nullptr when all P rows do.
 // metrics: P x 6 (max arm/held penetration, max grasp error, max tilt, placement max
 // penetration, max CoM distance, max height error); ok: P flags.
 cudaError_t launch_check64(const Scalars64& s, const void* cub, const void* osph, const float* q, const int* n_sol, int P,

@@ -72,10 +72,11 @@ __device__ void ik_dls(const Scalars& sc, const float Rs[9], const float ps[3], 
     }
 }
 
-__device__ __forceinline__ void perturbed_home(const Scalars& sc, uint32_t c0, int p, uint32_t tag, uint32_t attempt,
-                                               float amp, float q[7]) {
-    const U4 a = philox4x32_10(2u * c0, (uint32_t)p, tag, attempt, sc.seed);
-    const U4 b = philox4x32_10(2u * c0 + 1u, (uint32_t)p, tag, attempt, sc.seed);
+// key: the Philox key (the problem's seed)
+__device__ __forceinline__ void perturbed_home(const Scalars& sc, uint64_t key, uint32_t c0, int p, uint32_t tag,
+                                               uint32_t attempt, float amp, float q[7]) {
+    const U4 a = philox4x32_10(2u * c0, (uint32_t)p, tag, attempt, key);
+    const U4 b = philox4x32_10(2u * c0 + 1u, (uint32_t)p, tag, attempt, key);
     const float u[7] = {u01(a.x), u01(a.y), u01(a.z), u01(a.w), u01(b.x), u01(b.y), u01(b.z)};
     for (int j = 0; j < 7; ++j) q[j] = fminf(fmaxf(sc.q_home[j] + amp * (2.f * u[j] - 1.f), sc.qlo[j]), sc.qhi[j]);
 }
@@ -219,10 +220,10 @@ constexpr int kQ6Strips = 31;
 
 // Tool target of IK target r = 2b + which of particle p: Rz(yaw + k pi/2) Rx(pi) at the top
 // face of block b (+ grasp offset), at its initial pose (which = 0) or its placement (1).
-__device__ __forceinline__ void lift_target(const Scalars& sc, const float* __restrict__ place, int np, int p, int b,
-                                            int which, uint32_t attempt, float Rs[9], float ps[3]) {
+__device__ __forceinline__ void lift_target(const Scalars& sc, uint64_t key, const float* __restrict__ place, int np, int p,
+                                            int b, int which, uint32_t attempt, float Rs[9], float ps[3]) {
     const int B = sc.B;
-    const U4 kk = philox4x32_10((uint32_t)b, (uint32_t)p, kTagGrasp, attempt, sc.seed);
+    const U4 kk = philox4x32_10((uint32_t)b, (uint32_t)p, kTagGrasp, attempt, key);
     float pose[4];
     if (which == 0) {
         pose[0] = sc.init[b].x; pose[1] = sc.init[b].y; pose[2] = sc.init[b].z; pose[3] = sc.init[b].w;
@@ -245,7 +246,9 @@ __device__ __forceinline__ void lift_target(const Scalars& sc, const float* __re
 // sequential scan.  A target without an in-limit solution falls back to damped least
 // squares on lane 0.
 __global__ void k_lift_ik_analytic(const __grid_constant__ Scalars sc, int n, const float* __restrict__ place, int np,
-                                   uint32_t attempt, float* __restrict__ q) {
+                                   uint32_t attempt, float* __restrict__ q, const LoopCtl* __restrict__ ctl) {
+    uint64_t key = sc.seed;
+    if (ctl) { attempt = ctl->t_attempt; np = ctl->n_place; key = ctl->seed; }
     const int lane = threadIdx.x & 31;
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int B = sc.B;
@@ -253,15 +256,15 @@ __global__ void k_lift_ik_analytic(const __grid_constant__ Scalars sc, int n, co
     const int p = gw / (2 * B), r = gw % (2 * B), b = r >> 1, which = r & 1;
     if (which == 1 && sc.kind == kKindP2P) return;   // point to point: no placement
     float Rs[9], ps[3], seed[7], best[7];
-    lift_target(sc, place, np, p, b, which, attempt, Rs, ps);
+    lift_target(sc, key, place, np, p, b, which, attempt, Rs, ps);
     const uint32_t c0 = (uint32_t)(2 * b + which);
-    perturbed_home(sc, c0, p, kTagIkSeed, attempt, 0.3f, seed);
+    perturbed_home(sc, key, c0, p, kTagIkSeed, attempt, 0.3f, seed);
 #pragma unroll
     for (int j = 0; j < 7; ++j) best[j] = seed[j];
     float q6 = seed[6];
     if (lane >= 1 && lane <= kQ6Strips) {
         const int i = lane - 1;
-        const U4 u = philox4x32_10(8u * c0 + (uint32_t)(i >> 2), (uint32_t)p, kTagQ6, attempt, sc.seed);
+        const U4 u = philox4x32_10(8u * c0 + (uint32_t)(i >> 2), (uint32_t)p, kTagQ6, attempt, key);
         const uint32_t word = (i & 3) == 0 ? u.x : (i & 3) == 1 ? u.y : (i & 3) == 2 ? u.z : u.w;
         const float strip = ((float)i + u01(word)) / (float)kQ6Strips;
         q6 = sc.qlo[6] + strip * (sc.qhi[6] - sc.qlo[6]);
@@ -291,7 +294,9 @@ __global__ void k_lift_ik_analytic(const __grid_constant__ Scalars sc, int n, co
 
 // Damped-least-squares lift (ik_mode 0), one thread per (particle, block, grasp|place)
 __global__ void k_lift_ik(const __grid_constant__ Scalars sc, int n, const float* __restrict__ place, int np,
-                          uint32_t attempt, float* __restrict__ q) {
+                          uint32_t attempt, float* __restrict__ q, const LoopCtl* __restrict__ ctl) {
+    uint64_t key = sc.seed;
+    if (ctl) { attempt = ctl->t_attempt; np = ctl->n_place; key = ctl->seed; }
     const int gid = blockIdx.x * blockDim.x + threadIdx.x;
     const int B = sc.B;
     if (gid >= n * 2 * B) return;
@@ -299,9 +304,9 @@ __global__ void k_lift_ik(const __grid_constant__ Scalars sc, int n, const float
     const int p = gid / (2 * B), r = gid % (2 * B), b = r >> 1, which = r & 1;
     if (which == 1 && sc.kind == kKindP2P) return;   // point to point: no placement
     float Rs[9], ps[3];
-    lift_target(sc, place, np, p, b, which, attempt, Rs, ps);
+    lift_target(sc, key, place, np, p, b, which, attempt, Rs, ps);
     float qq[7];
-    perturbed_home(sc, (uint32_t)(2 * b + which), p, kTagIkSeed, attempt, 0.3f, qq);
+    perturbed_home(sc, key, (uint32_t)(2 * b + which), p, kTagIkSeed, attempt, 0.3f, qq);
     ik_dls(sc, Rs, ps, qq);
     const int t = which == 0 ? t_grasp(sc.S, b) : t_place(sc.S, b);
     float* dst = q + ((size_t)p * sc.C + t) * 8;
@@ -312,7 +317,9 @@ __global__ void k_lift_ik(const __grid_constant__ Scalars sc, int n, const float
 // one thread per (particle, configuration): home, or linear interpolation
 // start -> via -> goal within the configuration's segment
 __global__ void k_lift_interp(const __grid_constant__ Scalars sc, int n, int np, uint32_t attempt,
-                              float* __restrict__ q) {
+                              float* __restrict__ q, const LoopCtl* __restrict__ ctl) {
+    uint64_t key = sc.seed;
+    if (ctl) { attempt = ctl->t_attempt; np = ctl->n_place; key = ctl->seed; }
     const int gid = blockIdx.x * blockDim.x + threadIdx.x;
     if (gid >= n * sc.C) return;
     if (np <= 0) return;
@@ -327,7 +334,7 @@ __global__ void k_lift_interp(const __grid_constant__ Scalars sc, int n, int np,
     if (jj == 0) return;   // segment endpoint, written by the IK kernel
     const int s = t / S, m = S / 2;
     float via[7];
-    perturbed_home(sc, (uint32_t)s, p, kTagVia, attempt, 0.3f, via);
+    perturbed_home(sc, key, (uint32_t)s, p, kTagVia, attempt, 0.3f, via);
     // segment 0 starts at home; this launch writes that row itself (t == 0 above), so it is
     // taken from the constants rather than read back from q
     const float* qa = s == 0 ? sc.q_home : q + ((size_t)p * sc.C + s * S) * 8;
@@ -343,19 +350,19 @@ __global__ void k_lift_interp(const __grid_constant__ Scalars sc, int n, int np,
 
 // ================================================================================== launcher
 cudaError_t launch_lift(const Scalars& sc, int n, const float* place, int n_place, uint32_t attempt, float* q,
-                        cudaStream_t st) {
+                        cudaStream_t st, const LoopCtl* ctl) {
     if (n <= 0) return cudaSuccess;
     const int n_ik = n * 2 * sc.B;
     if (sc.ik_mode == 1) {
         const long long threads = 32LL * n_ik;   // a warp per target
-        k_lift_ik_analytic<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(sc, n, place, n_place, attempt, q);
+        k_lift_ik_analytic<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(sc, n, place, n_place, attempt, q, ctl);
     } else {
-        k_lift_ik<<<(n_ik + 127) / 128, 128, 0, st>>>(sc, n, place, n_place, attempt, q);
+        k_lift_ik<<<(n_ik + 127) / 128, 128, 0, st>>>(sc, n, place, n_place, attempt, q, ctl);
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int n_cfg = n * sc.C;
-    k_lift_interp<<<(n_cfg + 255) / 256, 256, 0, st>>>(sc, n, n_place, attempt, q);
+    k_lift_interp<<<(n_cfg + 255) / 256, 256, 0, st>>>(sc, n, n_place, attempt, q, ctl);
     return cudaGetLastError();
 }
 

@@ -46,7 +46,10 @@ __device__ __forceinline__ bool s1_setup(const Scalars& sc, DevTables t, S1Smem&
 
 __global__ void __launch_bounds__(kS1Threads) k_place_sample_cost(const __grid_constant__ Scalars sc, DevTables t, int n,
                                                                    uint32_t attempt, float* __restrict__ x_out,
-                                                                   float* __restrict__ cost_out, int* err) {
+                                                                   float* __restrict__ cost_out, int* err,
+                                                                   const LoopCtl* __restrict__ ctl) {
+    uint64_t key = sc.seed;   // the Philox key
+    if (ctl) { attempt = ctl->attempt; key = ctl->seed; }
     S1Smem s;
     if (!s1_setup(sc, t, s, err)) return;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -55,7 +58,7 @@ __global__ void __launch_bounds__(kS1Threads) k_place_sample_cost(const __grid_c
     S1Warp& W = s.warp[w];
     if (lane < sc.B) {
         const int i = lane;
-        const U4 u = philox4x32_10((uint32_t)i, (uint32_t)p, kTagSample, attempt, sc.seed);
+        const U4 u = philox4x32_10((uint32_t)i, (uint32_t)p, kTagSample, attempt, key);
         const float zlo = sc.zlo[i];
         W.x[4 * i + 0] = sc.box_lo[0] + u01(u.x) * (sc.box_hi[0] - sc.box_lo[0]);
         W.x[4 * i + 1] = sc.box_lo[1] + u01(u.y) * (sc.box_hi[1] - sc.box_lo[1]);
@@ -174,12 +177,12 @@ static cudaError_t s1_prepare(const Scalars& sc) {
 }
 
 cudaError_t launch_place_sample_cost(const Scalars& sc, DevTables t, int n, uint32_t attempt, float* x, float* cost,
-                                     int* err, cudaStream_t st) {
+                                     int* err, cudaStream_t st, const LoopCtl* ctl) {
     if (n <= 0) return cudaSuccess;
     cudaError_t e = s1_prepare(sc);
     if (e != cudaSuccess) return e;
     k_place_sample_cost<<<(n + kS1Warps - 1) / kS1Warps, kS1Threads, s1_smem_bytes(sc), st>>>(sc, t, n, attempt, x,
-                                                                                               cost, err);
+                                                                                               cost, err, ctl);
     return cudaGetLastError();
 }
 

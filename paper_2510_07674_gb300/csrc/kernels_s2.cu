@@ -1126,6 +1126,7 @@ template <bool kP2P>
 __global__ void __launch_bounds__(kTThreads, 2) k_traj(const __grid_constant__ Scalars sc, DevTables tab, int n, int mode,
                                                       TrajIO io, int* err) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    if (io.active && *io.active <= 0) return;   // stage 1 of this problem found no placement
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
     float4* cub = reinterpret_cast<float4*>(smem_raw + t_env_offset());
     float4* osph = cub + 4 * sc.n_cub;
@@ -1188,7 +1189,8 @@ __global__ void __launch_bounds__(kTThreads, 2) k_traj_batch(const TrajJob* __re
             cur = j;
         }
         const int p0 = (it - job.first) * per_fetch;
-        const int p1 = min(p0 + per_fetch, job.n);
+        // a problem whose stage 1 found no placement has nothing to optimise
+        const int p1 = (io_s.active && *io_s.active <= 0) ? p0 : min(p0 + per_fetch, job.n);
         for (int p = p0; p < p1; ++p) {
             if (sc_s.kind == kKindP2P) traj_particle<true>(sc_s, p, mode, io_s, smem_raw);
             else traj_particle<false>(sc_s, p, mode, io_s, smem_raw);

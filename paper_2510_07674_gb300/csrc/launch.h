@@ -11,10 +11,27 @@ struct DevTables {
     const float4* osph;   // n_osph float4 (environment spheres)
 };
 
+// Device-side state of the two stages' re-initialisation loops (Alg. 1 restarts until a
+// particle satisfies, Sec. III-A; at most max_steps gradient steps, Sec. IV-C).  The
+// attempt counters are the Philox counters of the next attempt's draws.
+struct LoopCtl {
+    uint32_t attempt;     // stage 1: attempts done
+    int steps;            // stage 1: gradient steps spent
+    int n_place;          // satisfying placements kept, min(count, P); 0 until stage 1 ends
+    int place_pad;
+    uint32_t t_attempt;   // stage 2: attempts done
+    int t_steps;          // stage 2: gradient steps spent
+    int found;            // stage 2: solutions kept, min(count, P); 0 until stage 2 ends
+    int traj_pad;
+    uint64_t seed;        // the Philox key of both stages' draws (the problem's seed)
+};
+
 // ---- stage 1 ----
 // SampleUniform + Cost (linear form) for n particles; x is SoA [4B][n].
+// ctl (optional): the attempt counter and the Philox key are read from ctl->attempt and
+// ctl->seed on the device in place of `attempt` and sc.seed (the attempt loop runs there).
 cudaError_t launch_place_sample_cost(const Scalars& sc, DevTables t, int n, uint32_t attempt, float* x, float* cost,
-                                     int* err, cudaStream_t st);
+                                     int* err, cudaStream_t st, const LoopCtl* ctl = nullptr);
 // Cost (linear or quadratic) and optional gradient / metrics / terms for n particles (SoA [4B][n]).
 cudaError_t launch_place_eval(const Scalars& sc, DevTables t, int n, const float* x, int quad, float* cost,
                               float* grad, float* metrics, float* terms, int* err, cudaStream_t st);

@@ -20,6 +20,8 @@ struct TrajIO {
                                  // ones with a candidate obstacle (sphere-level work); accumulated
     int k_steps;       // descent steps
     int init_multipliers;   // descent starts from lambda = 0, mu = mu0
+    const int* active;  // optional device word: when it holds 0 or less the launch does nothing (the
+                        // trajectory stage of a problem whose stage 1 found no placement)
 };
 enum TrajModeHost { kTrajModeEval = 0, kTrajModeDescend = 1, kTrajModeCheck = 2 };
 
@@ -34,9 +36,12 @@ struct TrajJob {
 };
 
 size_t traj_smem_bytes(const Scalars& sc);
-// IK at grasp/place poses + interpolation; particle p lifts placement p % n_place.
+// IK at grasp/place poses + interpolation; particle p lifts placement p % n_place.  With
+// ctl != nullptr the attempt counter, the placement count and the Philox key are read on the
+// device (ctl->t_attempt, ctl->n_place, ctl->seed) in place of `attempt`, `n_place` and
+// sc.seed, and the launch writes nothing when ctl->n_place is 0.
 cudaError_t launch_lift(const Scalars& sc, int n, const float* place, int n_place, uint32_t attempt, float* q,
-                        cudaStream_t st);
+                        cudaStream_t st, const LoopCtl* ctl = nullptr);
 cudaError_t launch_traj(const Scalars& sc, DevTables t, int n, int mode, const TrajIO& io, int* err, cudaStream_t st);
 // Persistent batched launch over jobs[0..n_jobs) (n_items work items of per_fetch particles;
 // *next must be 0); smem_bytes = the largest traj_smem_bytes of the jobs.

@@ -50,6 +50,16 @@ struct spasm_problem {
     unsigned long long* d_tests = nullptr;   // [tests run, configurations culled] by the trajectory kernel
     bool optimized = false;
     int n_found = 0, traj_attempts = 0;
+    // device-side attempt loops (driver.cu): counters and the Philox key on the device, each
+    // stage's graph (built at creation), streams the graphs are captured on
+    spasm::LoopCtl* d_ctl = nullptr;
+    cudaGraphExec_t g_place = nullptr, g_traj = nullptr;
+    cudaStream_t cap = nullptr, cap_body = nullptr;
+    bool place_pending = false;   // a stage-1 run whose outcome the host has not read yet
+    bool traj_pending = false;    // likewise stage 2
+    bool place_timed = false;     // the pending stage-1 run is bracketed by ev[0], ev[1]
+    bool traj_timed = false;      // the pending stage-2 run recorded ev[2..6]
+    bool traj_batched = false;    // its first trajectory launch was shared with other problems
     std::vector<double> host_cub, host_osph;
     // FP64 final check
     spasm::Scalars64 s64;
@@ -78,24 +88,33 @@ inline spasm_status rec(spasm_problem* pr, int i) {
     return SPASM_OK;
 }
 
+// Makes the host wait for the problem's stream (counted in stats.host_waits).
+spasm_status host_wait(spasm_problem* pr);
 // Reads the problem's device error word (synchronises its stream).
 spasm_status check_device_error(spasm_problem* pr);
 
-// ---- the two-stage driver, in pieces shared by spasm_optimize and the batched form
-// Enqueue one attempt of Alg. 1 on stream s (count of satisfying particles -> d_nsat,
-// best placements -> d_place).
-spasm_status place_attempt(spasm_problem* pr, uint32_t attempt, cudaStream_t s);
-// Continue stage 1 after `attempt` attempts and `steps` gradient steps, whose last attempt
-// left `nsat` satisfying particles (0: none, or no attempt yet), until an attempt
-// satisfies or the step budget is spent; then record the placements.
-spasm_status place_continue(spasm_problem* pr, int attempt, int steps, int nsat);
-// Enqueue the rank costs and the satisfying mask of the trajectory particles (count -> d_tnsat).
-spasm_status traj_select(spasm_problem* pr, cudaStream_t s);
-// Enqueue the final selection of the best P trajectories and their FP64 check.
-spasm_status finish_enqueue(spasm_problem* pr, cudaStream_t s);
-// Continue stage 2 like place_continue; returns the number of solutions in *found.
-spasm_status traj_continue(spasm_problem* pr, int attempt, int steps, int nsat, int* found);
-// Record the outcome of stage 2 (enqueueing the finish first unless `finish_done`).
-spasm_status finish_record(spasm_problem* pr, int found, bool finish_done);
+// ---- the two-stage driver (driver.cu), in pieces shared by spasm_optimize and the batched
+// form.  The enqueue_* functions append to a stream that is being captured into a graph
+// (they add conditional nodes to it); the attempt loops run on the device.
+// Stage 1: the first attempt of Alg. 1, then a while node that repeats attempts until one
+// satisfies or max_steps gradient steps are spent; d_ctl->n_place receives the count kept.
+spasm_status enqueue_place(spasm_problem* pr, cudaStream_t s);
+// Stage 2, first attempt: reset the stage-2 counters and lift (reads d_ctl on the device).
+spasm_status enqueue_traj_lift(spasm_problem* pr, cudaStream_t s);
+// Stage 2, first attempt: the fused trajectory descent of all Q particles.
+spasm_status enqueue_traj_descent(spasm_problem* pr, cudaStream_t s);
+// Stage 2 after the first descent: satisfying mask and count, then a while node that
+// re-lifts and descends with the next attempt counter while none satisfies within max_steps.
+spasm_status enqueue_traj_retry(spasm_problem* pr, cudaStream_t s);
+// The final selection of the best P trajectories and their FP64 check.
+spasm_status enqueue_finish(spasm_problem* pr, cudaStream_t s);
+// Reads what the device loops left (attempts, counts, counters, success flags, the error
+// word) after the pending stages, once; synchronises the problem's stream.
+spasm_status finalize(spasm_problem* pr);
+// Builds the stage graphs the problem's kind uses (stage 1 unless point to point, stage 2
+// unless packing), once.
+spasm_status prepare_graphs(spasm_problem* pr);
+// Destroys the stage graphs.
+void drop_graphs(spasm_problem* pr);
 
 }  // namespace spasm
