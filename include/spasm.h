@@ -160,17 +160,24 @@ spasm_status spasm_destroy_problem(spasm_problem_t problem);
 const char* spasm_last_error(void);
 
 /* Stage 1, Alg. 1 with re-initialisation until a satisfying particle exists or max_steps
- * gradient steps are spent.  Synchronises once per attempt (reads the satisfying count).
- * On success the best P placements stay on the device for stage 2. */
+ * gradient steps are spent (Sec. III-A, the cap of Sec. IV-C).  Enqueues and returns: the
+ * attempt loop runs on the device (a CUDA graph whose conditional while node repeats an
+ * attempt while no particle satisfies), and the host does not wait for it.  The best P
+ * placements stay on the device for stage 2; spasm_placements reads them.  The first call
+ * (and the first after spasm_set_seed) captures the graph; later calls launch it.
+ * SPASM_ERR_NOSOLUTION, when no attempt satisfies, is reported by spasm_placements /
+ * spasm_result. */
 spasm_status spasm_place(spasm_problem_t problem);
 
 /* Stage 2: lift the stage-1 placements to Q trajectory particles, optimise, keep the
- * satisfying ones (re-lifting with the next Philox attempt if none, within max_steps),
- * FP64-check the best P.  Runs stage 1 first if it has not run.  Synchronises once per
- * attempt. */
+ * satisfying ones (re-lifting with the next Philox attempt while none does, within
+ * max_steps), FP64-check the best P.  Enqueues stage 1 first if it has not run.  Like
+ * spasm_place it enqueues one graph with a device-side attempt loop and returns without
+ * waiting; the outcome (including SPASM_ERR_NOSOLUTION) is read by spasm_result. */
 spasm_status spasm_optimize(spasm_problem_t problem);
 
-/* Copy results to host memory (synchronises).  Any output pointer may be NULL.
+/* Copy results to host memory (synchronises: the one host wait of a solve).  Any output
+ * pointer may be NULL.
  * n_found: number of returned solutions (<= P); placements: P x B x 4;
  * traj: P x C x 7; cost: P (ranking cost, ascending); success: P (1 if the solution
  * passes the FP64 re-evaluation of every penetration, the grasp and tilt errors, the
@@ -227,6 +234,19 @@ spasm_status spasm_traj_eval(spasm_problem_t problem, int n, const float* q, con
 spasm_status spasm_traj_descend(spasm_problem_t problem, int n, float* q, float* lam, float* mu, int k_steps,
                                 int init_multipliers, float* metrics, int* sat);
 
+/* FP64 final check (GetSatisfyingParticles of Alg. 1 applied to returned solutions, Sec.
+ * III; the check spasm_optimize runs on the best P) of n caller-given trajectories.
+ * q: device n x C x 8 floats (joints 0..6 of each configuration; q[.][0] is taken as
+ * given).  metrics: device n x 6 doubles, written: largest arm / held-block penetration
+ * over all configurations, largest grasp alignment (squared position error + roll^2 +
+ * pitch^2 at the grasp configurations), largest placement tilt (roll^2 + pitch^2), and on
+ * the placed blocks (fk of the place configurations): largest penetration, largest CoM
+ * distance, largest height error.  ok: device n ints, 1 where every penetration, CoM
+ * distance and height error is <= eps, the alignment and tilt <= eps_start and every joint
+ * within its limits (the limits rounded to float32, as the FP32 optimiser holds them).
+ * Evaluated in double precision from the float32 joint values. */
+spasm_status spasm_traj_check(spasm_problem_t problem, int n, const float* q, double* metrics, int* ok);
+
 /* Stage-1 sampling and elite selection that allocates no device memory (the paper has no
  * counterpart: this serves callers that cannot allocate while they plan, such as a planner
  * in a real-time control loop that must not stall on cudaMalloc, or a plug-in in a
@@ -235,16 +255,19 @@ spasm_status spasm_traj_descend(spasm_problem_t problem, int n, float* q, float*
  * m lowest-cost particles in ascending (cost, index) order and cost_elite (device, m) their
  * linear-form costs.  Intermediates live in one fixed 4 MiB device array of the library:
  * 4B*n + n + m floats must fit (else SPASM_ERR_INVALID), n <= 32768, m <= 8192.  The first
- * call on a device looks the array up (make it before any stream capture); calls share the
- * array, so calls that overlap on the GPU race and must be serialised by the caller. */
+ * call on a device is its set-up: it looks the array up, which may load the library's device
+ * code and create the array (so that call may allocate and synchronise); make it before any
+ * stream capture.  Later calls allocate nothing.  Calls share the array, so calls that
+ * overlap on the GPU race and must be serialised by the caller. */
 spasm_status spasm_place_select_static(spasm_problem_t problem, int n, uint32_t attempt, int m, float* x_elite,
                                        float* cost_elite);
 
 /* ---- run control and statistics (not in the paper: bookkeeping of this library) ---- */
 
-/* Counters and device times of the last spasm_place / spasm_optimize calls since the
- * last reset.  Times are CUDA-event durations on the problem's stream and are filled only
- * while timing is enabled. */
+/* Counters and device times of the spasm_place / spasm_optimize calls since the last
+ * reset.  Times are CUDA-event durations on the problem's stream and are filled only
+ * while timing is enabled.  Reading them synchronises the problem's stream when a solve's
+ * outcome has not been read yet. */
 typedef struct {
     int place_attempts;        /* Alg. 1 attempts (re-initialisations + 1) */
     int traj_attempts;         /* stage-2 lift + descent attempts */
@@ -266,7 +289,21 @@ typedef struct {
                                   iteration, valid while they moved less than its clearance) */
     long long cand_configs;    /* of those, configurations with a candidate obstacle, whose sphere
                                   centres, tests and gradient chain ran */
+    double ms_retry;           /* stage-2 attempts after the first (re-lift and descent), and the
+                                  satisfying selection; ms_lift and ms_traj time the first */
+    long long host_waits;      /* times the library made the host wait for the problem's stream
+                                  (spasm_place and spasm_optimize never do; the first of
+                                  spasm_result, spasm_placements and spasm_get_stats after a solve
+                                  waits once to read its outcome) */
 } spasm_stats;
+
+/* Measured FP32 fused-multiply-add throughput of the current device (not in the paper: the
+ * roofline denominator of the trajectory kernels, which are FP32 ALU work).  Runs a kernel of
+ * independent FMA chains filling every SM (8 CTAs of 256 threads each) for about target_ms
+ * (0 < target_ms <= 10000) on the legacy default stream and returns *tflops = 2 x FMAs /
+ * CUDA-event time; *ms and *flop (may be NULL) receive the time and the flop count.  Allocates
+ * and frees a small device buffer; synchronises the device's default stream. */
+spasm_status spasm_fp32_fma_peak(double target_ms, double* tflops, double* ms, double* flop);
 
 /* Replace the Philox seed (the key of every random stream) and forget previous results;
  * the next spasm_optimize re-runs both stages. */

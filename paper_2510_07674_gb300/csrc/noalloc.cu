@@ -10,7 +10,9 @@
 //
 // Set-up: the device address of the array is looked up once per device, with that device
 // current, by the first call made on it (cudaGetSymbolAddress); make that first call before
-// any stream capture begins.  The array is shared by every call on a device and keeps the
+// any stream capture begins.  With lazy module loading (the CUDA default) that lookup may be
+// what loads the library's device code and creates the array, so the first call can allocate
+// and synchronise; the calls after it allocate nothing.  The array is shared by every call on a device and keeps the
 // contents of the last call; nothing in it needs to start at zero because every call
 // overwrites what it reads.  Calls whose work overlaps on the GPU (different streams, or
 // different host threads) race on the array and must be serialised by the caller.

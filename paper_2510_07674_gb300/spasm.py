@@ -28,7 +28,7 @@ EXPORTED = ["spasm_create_problem", "spasm_destroy_problem", "spasm_last_error",
             "spasm_server_create", "spasm_server_submit", "spasm_server_poll", "spasm_server_wait",
             "spasm_server_result", "spasm_server_release", "spasm_server_destroy", "spasm_batch_default_config",
             "spasm_optimize_batch", "spasm_batch_autotune", "spasm_create_packing", "spasm_placements",
-            "spasm_create_p2p"]
+            "spasm_create_p2p", "spasm_traj_check", "spasm_fp32_fma_peak"]
 
 
 class SpasmError(RuntimeError):
@@ -78,7 +78,8 @@ class _Stats(ctypes.Structure):
                 ("particle_iters", ctypes.c_longlong), ("ms_place", ctypes.c_double), ("ms_lift", ctypes.c_double),
                 ("ms_traj", ctypes.c_double), ("ms_finish", ctypes.c_double), ("h2d_bytes", ctypes.c_longlong),
                 ("d2h_bytes", ctypes.c_longlong), ("tests_executed", ctypes.c_longlong),
-                ("cull_configs", ctypes.c_longlong), ("cand_configs", ctypes.c_longlong)]
+                ("cull_configs", ctypes.c_longlong), ("cand_configs", ctypes.c_longlong), ("ms_retry", ctypes.c_double),
+                ("host_waits", ctypes.c_longlong)]
 
 
 class _BatchConfig(ctypes.Structure):
@@ -115,6 +116,8 @@ def lib():
         L.spasm_get_stats.argtypes = [_V, ctypes.POINTER(_Stats)]
         L.spasm_reset_stats.argtypes = [_V]
         L.spasm_place_select_static.argtypes = [_V, ctypes.c_int, ctypes.c_uint32, ctypes.c_int, _V, _V]
+        L.spasm_traj_check.argtypes = [_V, ctypes.c_int, _V, _V, _V]
+        L.spasm_fp32_fma_peak.argtypes = [ctypes.c_double, _D, _D, _D]
         LL = ctypes.c_longlong
         L.spasm_server_create.argtypes = [LL, ctypes.c_int, ctypes.POINTER(_V)]
         L.spasm_server_submit.argtypes = [_V, ctypes.POINTER(_Robot), ctypes.POINTER(_Obstacles), ctypes.POINTER(_Goal),
@@ -306,6 +309,17 @@ def spasm_traj_descend(problem: Problem, n: int, q, lam, mu, k_steps: int, init_
                        sat=None):
     _check(lib().spasm_traj_descend(problem.handle, n, _dev(q), _dev(lam), _dev(mu), int(k_steps),
                                     int(init_multipliers), _dev(metrics), _dev(sat)))
+
+
+def spasm_traj_check(problem: Problem, n: int, q, metrics, ok):
+    _check(lib().spasm_traj_check(problem.handle, n, _dev(q), _dev(metrics), _dev(ok)))
+
+
+def spasm_fp32_fma_peak(target_ms: float = 200.0) -> dict:
+    """Measured FP32 FMA throughput of the current device (TFLOP/s, time, flop)."""
+    tf, ms, fl = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(lib().spasm_fp32_fma_peak(float(target_ms), ctypes.byref(tf), ctypes.byref(ms), ctypes.byref(fl)))
+    return {"tflops": tf.value, "ms": ms.value, "flop": fl.value}
 
 
 def spasm_set_seed(problem: Problem, seed: int):

@@ -8,6 +8,8 @@ This test calls it twice in a row through the C ABI and compares each result wit
 spasm_place_sample + spasm_select_topk + a gather of the same particles.  It lives in a file
 of its own that pytest collects last.
 """
+import ctypes
+
 import numpy as np
 import pytest
 
@@ -15,6 +17,27 @@ from paper_2510_07674_gb300 import scenes
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
+
+
+def _device_memory():
+    """(used, reserved) bytes of the device's default memory pool -- where the library's
+    stream-ordered allocations come from -- and the free bytes cudaMemGetInfo reports."""
+    rt = None
+    for name in ("libcudart.so.13", "libcudart.so", "/usr/local/cuda/lib64/libcudart.so"):
+        try:
+            rt = ctypes.CDLL(name)
+            break
+        except OSError:
+            continue
+    if rt is None:
+        pytest.skip("no CUDA runtime library to query the memory pool")
+    pool = ctypes.c_void_p()
+    assert rt.cudaDeviceGetDefaultMemPool(ctypes.byref(pool), torch.cuda.current_device()) == 0
+    used, reserved = ctypes.c_uint64(), ctypes.c_uint64()
+    assert rt.cudaMemPoolGetAttribute(pool, 7, ctypes.byref(used)) == 0        # UsedMemCurrent
+    assert rt.cudaMemPoolGetAttribute(pool, 5, ctypes.byref(reserved)) == 0    # ReservedMemCurrent
+    free, _ = torch.cuda.mem_get_info()
+    return used.value, reserved.value, free
 
 
 def test_static_scratch_matches_allocating_path_twice():
@@ -38,6 +61,27 @@ def test_static_scratch_matches_allocating_path_twice():
         np.testing.assert_allclose(c_el.cpu().numpy(), ref_c.cpu().numpy(), rtol=1e-6, atol=0)
         np.testing.assert_allclose(x_el.cpu().numpy(), ref_x.cpu().numpy(), rtol=1e-6, atol=0)
         assert np.all(np.diff(c_el.cpu().numpy()) >= 0)
+
+
+def test_static_scratch_allocates_nothing_after_the_first_call():
+    """The first call on a device is the set-up (it looks up the array and may load the
+    library's device code); after it, a call changes neither the default pool's used or
+    reserved bytes nor the device's free memory."""
+    from paper_2510_07674_gb300 import spasm as S
+    wl = scenes.make_problem("tower10", seed=4)
+    pr = S.Problem(wl)
+    B, n, m = pr.B, 16384, 4096
+    x_el = torch.empty(4 * B, m, device="cuda")
+    c_el = torch.empty(m, device="cuda")
+    S.spasm_place_select_static(pr, n, 0, m, x_el, c_el)   # set-up call
+    torch.cuda.synchronize()
+    before = _device_memory()
+    for attempt in (1, 2):
+        S.spasm_place_select_static(pr, n, attempt, m, x_el, c_el)
+    torch.cuda.synchronize()
+    after = _device_memory()
+    assert after == before, (before, after)
+    assert np.all(np.isfinite(c_el.cpu().numpy()))
 
 
 def test_static_scratch_rejects_sizes_beyond_its_array():
