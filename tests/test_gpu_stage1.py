@@ -93,23 +93,32 @@ def test_topk_bit_exact_vs_stable_argsort():
         np.testing.assert_array_equal(idx.cpu().numpy(), ref)
 
 
-def test_descend_few_steps_matches_oracle():
+@pytest.mark.parametrize("name,k_lin,k_quad", [("tower4", 2, 0), ("tower4", 1, 1), ("tower10", 2, 0)])
+def test_descend_one_step_matches_oracle_on_every_particle(name, k_lin, k_quad):
+    """One step of Alg. 1 from identical states, element-wise on every particle: K_lin = 2
+    gives the linear-form steps eta_init (1 - 1/2) and 0; K_lin = 1, K_quad = 1 gives a zero
+    linear step (only the box projection) and one quadratic-form step with alpha.  The step
+    agrees with the oracle's to 1e-4 of its size (the gradient's FP32 rounding) plus the
+    float32 rounding of the pose values."""
     S = _S()
-    wl = scenes.make_problem("tower4", seed=5)
-    orc = O.Oracle(wl)
+    wl = scenes.make_problem(name, seed=5)
+    orc = O.Oracle(wl, n_threads=8)
     pr = S.Problem(wl)
-    n, B = 64, pr.B
+    n, B = 256, pr.B
     xo = orc.place_sample(n)
     x = torch.from_numpy(xo.reshape(n, 4 * B).T.copy()).float().cuda().contiguous()
     x0 = _soa_to_particles(x, B)
-    S.spasm_place_descend(pr, n, x, 3, 2)
+    S.spasm_place_descend(pr, n, x, k_lin, k_quad)
     torch.cuda.synchronize()
     xg = _soa_to_particles(x, B)
-    xr = orc.place_descend(x0, 3, 2)
-    # a few steps of GD from identical float32 states stay within FP32 rounding of the
-    # gradient times the step size, except where a contact switches on/off (rare)
-    err = np.abs(xg - xr).max(axis=(1, 2))
-    assert np.mean(err < 1e-4) >= 0.9, np.sort(err)[-10:]
+    xr = orc.place_descend(x0, k_lin, k_quad)
+    moved = 0
+    for p in range(n):
+        step_g, step_o = xg[p] - x0[p], xr[p] - x0[p]
+        err = np.abs(step_g - step_o).max()
+        assert err <= RTOL * np.abs(step_o).max() + 1e-6, (p, err, np.abs(step_o).max())
+        moved += np.abs(step_o).max() > 1e-4
+    assert moved > n // 2
 
 
 @pytest.mark.parametrize("name", ["tower1", "tower4"])
