@@ -137,6 +137,11 @@ typedef struct {
  * C <= 1024, N <= 32768, M <= 8192, P <= M, Q >= 1.  Synchronises once. */
 spasm_status spasm_create_problem(const spasm_robot* robot, const spasm_obstacles* obstacles, const spasm_goal* goal,
                                   const spasm_params* params, void* cuda_stream, spasm_problem_t* out);
+/* Device memory, in bytes, that spasm_create_problem would allocate for this problem (the
+ * same buffer list, each rounded up to the pool's 512-byte granule); robot arrays do not
+ * matter.  The solver service admits requests against its budget with this figure. */
+spasm_status spasm_problem_bytes(const spasm_obstacles* obstacles, const spasm_goal* goal, const spasm_params* params,
+                                 long long* bytes);
 /* A packing problem (the appendix's Tetris problem) for stage 1 (spasm_place, the
  * kernel-level stage-1 entry points); the robot is validated and kept as for
  * spasm_create_problem, and spasm_optimize reports SPASM_ERR_INVALID (stage 2 is built for
@@ -304,6 +309,24 @@ typedef struct {
  * CUDA-event time; *ms and *flop (may be NULL) receive the time and the flop count.  Allocates
  * and frees a small device buffer; synchronises the device's default stream. */
 spasm_status spasm_fp32_fma_peak(double target_ms, double* tflops, double* ms, double* flop);
+
+/* Wait for the problem's stream and report what its kernels recorded: SPASM_ERR_DEVICE when a
+ * bounded device wait gave up or a kernel rejected its sizes (the error word is sticky: every
+ * later synchronising call of this problem reports it again), else SPASM_OK. */
+spasm_status spasm_synchronize(spasm_problem_t problem);
+
+/* ---- fault injection for tests (not in the paper: exercises the failure paths without a GPU
+ * fault) ----
+ * spasm_inject_wait_timeout enqueues on the problem's stream one CTA that waits, with the
+ * bounded wait of the kernels' table staging, on an mbarrier whose expected bytes no copy
+ * delivers (no copy is issued: nothing is left in flight); after max_polls polls
+ * (1..2^22) it records the timeout in the problem's error word and returns, and the next
+ * synchronising call reports SPASM_ERR_DEVICE.  spasm_inject_alloc_failure makes the nth
+ * device allocation of the library from now on (0: the next one) fail as if
+ * cudaMallocAsync had failed (SPASM_ERR_NOMEM); -1 turns the injection off.  The injection
+ * is process-wide and one-shot. */
+spasm_status spasm_inject_wait_timeout(spasm_problem_t problem, int max_polls);
+spasm_status spasm_inject_alloc_failure(int nth);
 
 /* Replace the Philox seed (the key of every random stream) and forget previous results;
  * the next spasm_optimize re-runs both stages. */

@@ -1,9 +1,12 @@
 // C ABI of the SPaSM hot path (see include/spasm.h): problem set-up, the two-stage
 // driver, and kernel-level entry points.
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <mutex>
+#include <type_traits>
 #include <set>
 #include <string>
 #include <utility>
@@ -33,12 +36,20 @@ spasm_status spasm::fail(spasm_status st, const std::string& msg) {
     return st;
 }
 
+// Fault injection (spasm_inject_alloc_failure): the number of allocations still to succeed
+// before one fails, or -1.
+static std::atomic<long long> g_alloc_countdown{-1};
+
 // Stream-ordered allocation from the device's default memory pool: unlike cudaMalloc /
 // cudaFree it does not synchronise the device, so problems created and destroyed on
 // their own streams (the solver service) do not stall each other.
 template <typename T>
 static spasm_status dalloc(T** p, size_t count, cudaStream_t st) {
     if (count == 0) count = 1;
+    if (g_alloc_countdown.load() >= 0 && g_alloc_countdown.fetch_sub(1) == 0) {
+        g_alloc_countdown.store(-1);
+        return fail(SPASM_ERR_NOMEM, "cudaMallocAsync: injected allocation failure");
+    }
     cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(p), count * sizeof(T), st);
     if (e != cudaSuccess) return fail(SPASM_ERR_NOMEM, std::string("cudaMallocAsync: ") + cudaGetErrorString(e));
     return SPASM_OK;
@@ -89,6 +100,62 @@ static cudaError_t reset_loops(spasm_problem* pr) {
 }
 
 extern "C" const char* spasm_last_error(void) { return g_last_error.c_str(); }
+
+// Every device buffer of a problem with its element count, in allocation order: the one list
+// that spasm_create_problem allocates and spasm_problem_bytes adds up.
+template <typename F>
+static void for_each_buffer(spasm_problem* pr, int B, int C, int n_cub, int n_osph, const spasm_params* prm, F&& f) {
+    const size_t N = prm->N, M = prm->M, P = prm->P, Q = prm->Q, NR = 9 * (size_t)B + 3;
+    f(pr->d_cub, 4 * (size_t)n_cub);
+    f(pr->d_osph, (size_t)n_osph);
+    f(pr->d_err, 1);
+    f(pr->d_xs, 4 * (size_t)B * N);
+    f(pr->d_cost, N);
+    f(pr->d_idx, M);
+    f(pr->d_xm, 4 * (size_t)B * M);
+    f(pr->d_costm, M);
+    f(pr->d_masked, M);
+    f(pr->d_sat, M);
+    f(pr->d_nsat, 1);
+    f(pr->d_best, P);
+    f(pr->d_place, P * (size_t)B * 4);
+    f(pr->d_q, Q * (size_t)C * 8);
+    f(pr->d_lam, Q * NR);
+    f(pr->d_mu, Q);
+    f(pr->d_metrics, Q * 8);
+    f(pr->d_tmasked, Q);
+    f(pr->d_tsat, Q);
+    f(pr->d_tnsat, 1);
+    f(pr->d_tbest, P);
+    f(pr->d_rq, P * (size_t)C * 8);
+    f(pr->d_rcost, P);
+    f(pr->d_rsucc, P);
+    f(pr->d_cub64, 16 * (size_t)n_cub);
+    f(pr->d_osph64, 4 * (size_t)n_osph);
+    f(pr->d_rmet64, 6 * P);
+    f(pr->d_tests, 3);
+    f(pr->d_sc, 1);
+    f(pr->d_chkacc, P);
+    f(pr->d_ctl, 1);
+}
+
+extern "C" spasm_status spasm_problem_bytes(const spasm_obstacles* obs, const spasm_goal* goal, const spasm_params* prm,
+                                            long long* bytes) {
+    if (!obs || !goal || !prm || !bytes) return fail(SPASM_ERR_INVALID, "null argument");
+    const int B = goal->n_blocks;
+    if (B < 1 || B > kMaxB || prm->W < 3 || obs->n_cuboids < 0 || obs->n_spheres < 0)
+        return fail(SPASM_ERR_INVALID, "sizes outside the limits of spasm_create_problem");
+    const int C = 2 * B * (prm->W - 1) + 1;
+    spasm_problem probe;   // only its pointer members' types are used
+    size_t total = 0;
+    for_each_buffer(&probe, B, C, obs->n_cuboids, obs->n_spheres, prm, [&](auto*& ptr, size_t count) {
+        using T = std::remove_pointer_t<std::remove_reference_t<decltype(ptr)>>;
+        // the pool hands out whole allocation granules: at least one per buffer, rounded to 512 bytes
+        total += ((std::max<size_t>(count, 1) * sizeof(T) + 511) / 512) * 512;
+    });
+    *bytes = (long long)total;
+    return SPASM_OK;
+}
 
 // The joint layout the analytic lift IK solves (the Franka arm's): twists (0, -pi/2, pi/2,
 // pi/2, -pi/2, pi/2, pi/2), a_0 = a_1 = a_2 = a_5 = 0, d_1 = d_3 = d_5 = d_6 = 0, and an
@@ -290,42 +357,10 @@ static spasm_status create_problem_impl(const spasm_robot* robot, const spasm_ob
     }
     pr->host_osph.assign(obs->sphere, obs->sphere + 4 * (size_t)sc.n_osph);
 
-    const int N = prm->N, M = prm->M, P = prm->P, Q = prm->Q, NR = sc.NR;
     spasm_status st = SPASM_OK;
-#define ALLOC(ptr, count) \
-    if (st == SPASM_OK) st = dalloc(&(ptr), (count), pr->stream)
-    ALLOC(pr->d_cub, cub.size());
-    ALLOC(pr->d_osph, osph.size());
-    ALLOC(pr->d_err, 1);
-    ALLOC(pr->d_xs, (size_t)4 * B * N);
-    ALLOC(pr->d_cost, N);
-    ALLOC(pr->d_idx, M);
-    ALLOC(pr->d_xm, (size_t)4 * B * M);
-    ALLOC(pr->d_costm, M);
-    ALLOC(pr->d_masked, M);
-    ALLOC(pr->d_sat, M);
-    ALLOC(pr->d_nsat, 1);
-    ALLOC(pr->d_best, P);
-    ALLOC(pr->d_place, (size_t)P * B * 4);
-    ALLOC(pr->d_q, (size_t)Q * C * 8);
-    ALLOC(pr->d_lam, (size_t)Q * NR);
-    ALLOC(pr->d_mu, Q);
-    ALLOC(pr->d_metrics, (size_t)Q * 8);
-    ALLOC(pr->d_tmasked, Q);
-    ALLOC(pr->d_tsat, Q);
-    ALLOC(pr->d_tnsat, 1);
-    ALLOC(pr->d_tbest, P);
-    ALLOC(pr->d_rq, (size_t)P * C * 8);
-    ALLOC(pr->d_rcost, P);
-    ALLOC(pr->d_rsucc, P);
-    ALLOC(pr->d_cub64, (size_t)16 * sc.n_cub);
-    ALLOC(pr->d_osph64, (size_t)4 * sc.n_osph);
-    ALLOC(pr->d_rmet64, (size_t)6 * P);
-    ALLOC(pr->d_tests, 3);
-    ALLOC(pr->d_sc, 1);
-    ALLOC(pr->d_chkacc, P);
-    ALLOC(pr->d_ctl, 1);
-#undef ALLOC
+    for_each_buffer(pr, B, C, sc.n_cub, sc.n_osph, prm, [&](auto*& ptr, size_t count) {
+        if (st == SPASM_OK) st = dalloc(&ptr, count, pr->stream);
+    });
     for (auto& ev : pr->ev)
         if (st == SPASM_OK && cudaEventCreate(&ev) != cudaSuccess) st = fail(SPASM_ERR_CUDA, "cudaEventCreate failed");
     // streams the attempt-loop graphs are captured on (the problem's own stream may be the
@@ -346,7 +381,7 @@ static spasm_status create_problem_impl(const spasm_robot* robot, const spasm_ob
         e = cudaMemcpyAsync(pr->d_osph64, osph64.data(), osph64.size() * sizeof(double), cudaMemcpyHostToDevice, pr->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(pr->d_sc, &pr->sc, sizeof(Scalars), cudaMemcpyHostToDevice, pr->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(pr->d_err, 0, sizeof(int), pr->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(pr->d_chkacc, 0, sizeof(CheckAcc) * (size_t)P, pr->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(pr->d_chkacc, 0, sizeof(CheckAcc) * (size_t)prm->P, pr->stream);
     if (e == cudaSuccess) e = reset_loops(pr);
     if (e != cudaSuccess) {
         free_all(pr);
@@ -603,6 +638,18 @@ extern "C" spasm_status spasm_traj_check(spasm_problem_t pr, int n, const float*
         SPASM_CUDA(launch_check64(pr->s64, pr->d_cub64, pr->d_osph64, q + (size_t)off * C * 8, nullptr, k,
                                   metrics + (size_t)off * 6, ok + off, pr->d_chkacc, pr->stream));
     }
+    return SPASM_OK;
+}
+
+extern "C" spasm_status spasm_synchronize(spasm_problem_t pr) {
+    if (!pr) return fail(SPASM_ERR_INVALID, "null problem");
+    SPASM_TRY(finalize(pr));
+    return check_device_error(pr);
+}
+
+extern "C" spasm_status spasm_inject_alloc_failure(int nth) {
+    if (nth < -1) return fail(SPASM_ERR_INVALID, "nth must be >= -1");
+    g_alloc_countdown.store(nth);
     return SPASM_OK;
 }
 

@@ -349,6 +349,14 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t phase) {
     return ok != 0;
 }
 
+// Polls phase `phase` of an mbarrier at most max_polls times; true once it has completed.
+constexpr int kTablePolls = 1 << 22;   // about a second of polling
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t phase, int max_polls) {
+    for (int polls = 0; polls < max_polls; ++polls)
+        if (mbar_try_wait(bar, phase)) return true;
+    return false;
+}
+
 // Copies up to two tables; every thread of the CTA calls it; returns false on timeout.
 // `init`: initialise the barrier first (its first use in the CTA); `phase`: parity of the
 // barrier phase this copy completes (0 for the first use, then alternating).
@@ -365,11 +373,13 @@ __device__ __forceinline__ bool stage_tables(void* dst0, const void* src0, uint3
         if (bytes0) bulk_g2s(dst0, src0, bytes0, bar);
         if (bytes1) bulk_g2s(dst1, src1, bytes1, bar);
     }
-    bool done = false;
-    for (int polls = 0; polls < (1 << 22); ++polls) {
-        if (mbar_try_wait(bar, phase)) { done = true; break; }
+    const bool done = mbar_wait_bounded(bar, phase, kTablePolls);
+    if (!done) {
+        set_error(err, kDevTimeout);
+        // the copies this CTA issued may still be landing in its shared memory: give them a
+        // second bounded wait before the CTA exits
+        mbar_wait_bounded(bar, phase, kTablePolls);
     }
-    if (!done) set_error(err, kDevTimeout);
     int all = __syncthreads_and(done ? 1 : 0);
     return all != 0;
 }

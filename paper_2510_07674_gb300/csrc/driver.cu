@@ -71,6 +71,21 @@ __global__ void k_traj_loop(LoopCtl* __restrict__ c, const int* __restrict__ tns
     cudaGraphSetConditional(h, more ? 1u : 0u);
 }
 
+// Fault injection of the bounded device wait: one CTA waits, with the bounded wait the table
+// staging uses, on an mbarrier whose phase expects 16 bytes that no copy delivers (none is
+// issued, so nothing is in flight); after max_polls polls it records kDevTimeout and returns.
+__global__ void k_wait_timeout(int max_polls, int* __restrict__ err) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) mbar_expect_tx(&bar, 16);
+    if (!mbar_wait_bounded(&bar, 0, max_polls) && threadIdx.x == 0) set_error(err, kDevTimeout);
+    __syncthreads();
+}
+
 __global__ void k_gather_solutions(const float* __restrict__ q, const float* __restrict__ metrics,
                                    const int* __restrict__ best, const int* __restrict__ nsat, int P, int C,
                                    float* __restrict__ rq, float* __restrict__ rcost, int* __restrict__ rsucc) {
@@ -357,5 +372,12 @@ extern "C" spasm_status spasm_optimize(spasm_problem_t pr) {
     pr->traj_pending = true;
     pr->traj_timed = pr->timing;
     pr->traj_batched = false;
+    return SPASM_OK;
+}
+
+extern "C" spasm_status spasm_inject_wait_timeout(spasm_problem_t pr, int max_polls) {
+    if (!pr || max_polls < 1 || max_polls > kTablePolls) return fail(SPASM_ERR_INVALID, "need 1 <= max_polls <= 2^22");
+    k_wait_timeout<<<1, 32, 0, pr->stream>>>(max_polls, pr->d_err);
+    SPASM_CUDA(cudaGetLastError());
     return SPASM_OK;
 }

@@ -28,7 +28,8 @@ EXPORTED = ["spasm_create_problem", "spasm_destroy_problem", "spasm_last_error",
             "spasm_server_create", "spasm_server_submit", "spasm_server_poll", "spasm_server_wait",
             "spasm_server_result", "spasm_server_release", "spasm_server_destroy", "spasm_batch_default_config",
             "spasm_optimize_batch", "spasm_batch_autotune", "spasm_create_packing", "spasm_placements",
-            "spasm_create_p2p", "spasm_traj_check", "spasm_fp32_fma_peak"]
+            "spasm_create_p2p", "spasm_traj_check", "spasm_fp32_fma_peak", "spasm_synchronize",
+            "spasm_inject_wait_timeout", "spasm_inject_alloc_failure", "spasm_problem_bytes"]
 
 
 class SpasmError(RuntimeError):
@@ -118,6 +119,11 @@ def lib():
         L.spasm_place_select_static.argtypes = [_V, ctypes.c_int, ctypes.c_uint32, ctypes.c_int, _V, _V]
         L.spasm_traj_check.argtypes = [_V, ctypes.c_int, _V, _V, _V]
         L.spasm_fp32_fma_peak.argtypes = [ctypes.c_double, _D, _D, _D]
+        L.spasm_synchronize.argtypes = [_V]
+        L.spasm_problem_bytes.argtypes = [ctypes.POINTER(_Obstacles), ctypes.POINTER(_Goal), ctypes.POINTER(_Params),
+                                          ctypes.POINTER(ctypes.c_longlong)]
+        L.spasm_inject_wait_timeout.argtypes = [_V, ctypes.c_int]
+        L.spasm_inject_alloc_failure.argtypes = [ctypes.c_int]
         LL = ctypes.c_longlong
         L.spasm_server_create.argtypes = [LL, ctypes.c_int, ctypes.POINTER(_V)]
         L.spasm_server_submit.argtypes = [_V, ctypes.POINTER(_Robot), ctypes.POINTER(_Obstacles), ctypes.POINTER(_Goal),
@@ -320,6 +326,26 @@ def spasm_fp32_fma_peak(target_ms: float = 200.0) -> dict:
     tf, ms, fl = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
     _check(lib().spasm_fp32_fma_peak(float(target_ms), ctypes.byref(tf), ctypes.byref(ms), ctypes.byref(fl)))
     return {"tflops": tf.value, "ms": ms.value, "flop": fl.value}
+
+
+def spasm_problem_bytes(workload, **overrides) -> int:
+    """Device bytes spasm_create_problem would allocate for this workload."""
+    d = ProblemDesc(workload, **overrides)
+    b = ctypes.c_longlong()
+    _check(lib().spasm_problem_bytes(ctypes.byref(d._obs), ctypes.byref(d._goal), ctypes.byref(d._params), ctypes.byref(b)))
+    return b.value
+
+
+def spasm_synchronize(problem: Problem):
+    _check(lib().spasm_synchronize(problem.handle))
+
+
+def spasm_inject_wait_timeout(problem: Problem, max_polls: int):
+    _check(lib().spasm_inject_wait_timeout(problem.handle, int(max_polls)))
+
+
+def spasm_inject_alloc_failure(nth: int):
+    _check(lib().spasm_inject_alloc_failure(int(nth)))
 
 
 def spasm_set_seed(problem: Problem, seed: int):
