@@ -467,10 +467,11 @@ def solve_flop(wl, st) -> float:
 def run_forms(args, rank, overrides, peak):
     """The same heterogeneous problems (1-10 blocks, 8-64 cuboids, 1024-4096 trajectory
     particles, 32 waypoints per segment) solved (a) one after another through the plain API,
-    (b) as one batch (spasm_optimize_batch: two CUDA graphs, one persistent trajectory
+    (b) as one batch (spasm_optimize_batch: one CUDA graph, one persistent trajectory
     launch; schedule from spasm_batch_autotune on a separate copy of the problems), (c) all
-    submitted at once to the continuous-batching service; then (d) Poisson arrivals at each
-    rate to the service, latency from arrival to completion.  Problem creation and the
+    submitted at once to the continuous-batching service (epochs: one batched trajectory
+    attempt of every request in flight); then (d) Poisson arrivals at each rate to the
+    service, latency from arrival to completion.  Problem creation and the
     result read-back are inside every timed region."""
     import random
 
@@ -503,6 +504,7 @@ def run_forms(args, rank, overrides, peak):
         p.close()
     torch.cuda.synchronize()
     plain = form(time.perf_counter() - t0, ok, flop)
+    plain_flop = flop   # every form solves the same problems to the same bits: the same executed work
 
     # (b) batched form
     stream = torch.cuda.Stream()
@@ -525,8 +527,15 @@ def run_forms(args, rank, overrides, peak):
                    form="spasm_optimize_batch: stage-1 graph + stage-2 graph with one persistent trajectory launch")
     batched["speedup_vs_plain"] = batched["solves_per_s"] / plain["solves_per_s"]
 
+    def epoch_stats(before, after):
+        e = max(after["epochs"] - before["epochs"], 1)
+        return {"epochs": after["epochs"] - before["epochs"],
+                "requests_per_epoch": (after["requests_in_epochs"] - before["requests_in_epochs"]) / e,
+                "particles_per_epoch": (after["particles_in_epochs"] - before["particles_in_epochs"]) / e}
+
     # (c) the service, everything submitted at once
     sv = S.Server(budget_bytes=150 << 30, max_inflight=args.serve_slots)
+    st0 = S.spasm_server_get_stats(sv)
     t0 = time.perf_counter()
     tickets = [S.spasm_server_submit(sv, wl, **ov) for wl in wls]
     for t in tickets:
@@ -535,8 +544,8 @@ def run_forms(args, rank, overrides, peak):
     res = [S.spasm_server_result(sv, t) for t in tickets]
     for t in tickets:
         S.spasm_server_release(sv, t)
-    service = dict(solves_per_s=n / t_all, success=sum(int(r["success"].sum() > 0) for r in res) / n,
-                   slots=args.serve_slots, budget_gb=150)
+    service = form(t_all, sum(int(r["success"].sum() > 0) for r in res), plain_flop,
+                   slots=args.serve_slots, budget_gb=150, **epoch_stats(st0, S.spasm_server_get_stats(sv)))
     service["speedup_vs_plain"] = service["solves_per_s"] / plain["solves_per_s"]
 
     # (d) served: Poisson arrivals
@@ -547,6 +556,7 @@ def run_forms(args, rank, overrides, peak):
         for _ in range(n):
             tcur += rng.expovariate(rate)
             arrivals.append(tcur)
+        st0 = S.spasm_server_get_stats(sv)
         start = time.perf_counter()
         tickets = []
         for i, wl in enumerate(wls):
@@ -562,8 +572,11 @@ def run_forms(args, rank, overrides, peak):
         for t in tickets:
             S.spasm_server_release(sv, t)
         served.append({"rate_per_s": rate, "requests": n, "solves_per_s": n / end,
+                       "speedup_vs_plain": n / end / plain["solves_per_s"],
+                       "frac_of_alu_peak": plain_flop / end / 1e12 / peak,
                        "success": sum(int(r["success"].sum() > 0) for r in rs) / n,
-                       "latency_ms_p50": _percentile(lat, 0.5), "latency_ms_p99": _percentile(lat, 0.99)})
+                       "latency_ms_p50": _percentile(lat, 0.5), "latency_ms_p99": _percentile(lat, 0.99),
+                       **epoch_stats(st0, S.spasm_server_get_stats(sv))})
     sv.close()
     forms = {"problems": n, "workload": "heterogeneous: B~U{1..10}, O~U{8..64}, Q~U{1024..4096}, N=4096->M=1024, "
              "32 waypoints per segment", "plain": plain, "batched": batched, "service_all_at_once": service}

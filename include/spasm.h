@@ -46,7 +46,8 @@ typedef enum {
     SPASM_ERR_CUDA = -3,        /* a CUDA runtime call failed */
     SPASM_ERR_NOSOLUTION = -4,  /* no satisfying particle within max_steps (Sec. IV-C cap) */
     SPASM_ERR_TIMEOUT = -5,     /* reserved for bounded host waits */
-    SPASM_ERR_DEVICE = -6       /* a kernel recorded an error (see spasm_last_error) */
+    SPASM_ERR_DEVICE = -6,      /* a kernel recorded an error (see spasm_last_error) */
+    SPASM_ERR_CANCELLED = -7    /* a service request cancelled by the caller */
 } spasm_status;
 
 /* Robot (Sec. III: the manipulator as a collection of spheres; fk of a 7-R arm, appendix).
@@ -370,18 +371,33 @@ spasm_status spasm_batch_autotune(spasm_problem_t* problems, int n, void* cuda_s
 
 /* ---- solver service with continuous batching (not in the paper: the serving form of the
  * hot path) ----
- * Requests are whole problems (copied at submission).  They are admitted in arrival order
- * as soon as one of max_inflight slots is free and their device memory fits budget_bytes
- * (a request larger than the whole budget runs alone); each runs spasm_create_problem,
- * spasm_optimize and spasm_result on its own non-blocking CUDA stream of the device that was
- * current at creation, so requests that arrive while others run overlap with them on the
- * device.  Results stay with the server until spasm_server_release. */
+ * Requests are whole problems (copied at submission).  One scheduler thread runs the device
+ * work in epochs, each one trajectory attempt of every request in flight: queued requests are
+ * admitted in arrival order while fewer than max_inflight are in flight and their device
+ * memory (spasm_problem_bytes) fits budget_bytes (a request larger than the whole budget is
+ * admitted when nothing else is in flight), created on the scheduler's stream of the device
+ * current at creation, and their stage 1 runs (with its device-side attempt loop); then one
+ * persistent launch of the trajectory kernel runs the descent of the particles of every
+ * request in flight, followed per request by its satisfying selection, its attempt decision
+ * and the FP64 check; requests that finished retire, the others re-lift with their next
+ * attempt counter for the next epoch.  A request that arrives during an epoch joins at the
+ * next one.  Each request's result is the one spasm_optimize gives for it, whatever else is in
+ * flight.  Results stay with the server until spasm_server_release. */
 typedef struct spasm_server* spasm_server_t;
+/* Counters of a server: epochs run, requests and particles summed over epochs (their means
+ * are the batch sizes), requests completed, device bytes of the requests in flight. */
+typedef struct {
+    long long epochs;
+    long long requests_in_epochs;
+    long long particles_in_epochs;
+    long long completed;
+    long long bytes_in_use;
+} spasm_server_stats;
 spasm_status spasm_server_create(long long budget_bytes, int max_inflight, spasm_server_t* out);
 /* Validates sizes on the host (SPASM_ERR_INVALID) and queues; *ticket identifies the request. */
 spasm_status spasm_server_submit(spasm_server_t server, const spasm_robot* robot, const spasm_obstacles* obstacles,
                                  const spasm_goal* goal, const spasm_params* params, long long* ticket);
-/* *state = 0 queued, 1 running, 2 done. */
+/* *state = 0 queued, 1 running, 2 done, 3 cancelled. */
 spasm_status spasm_server_poll(spasm_server_t server, long long ticket, int* state);
 /* Bounded wait for completion: SPASM_ERR_TIMEOUT after timeout_s seconds. */
 spasm_status spasm_server_wait(spasm_server_t server, long long ticket, double timeout_s);
@@ -392,6 +408,11 @@ spasm_status spasm_server_result(spasm_server_t server, long long ticket, int* s
                                  double* placements, double* traj, double* cost, int* success, double* latency_ms,
                                  double* queue_ms);
 spasm_status spasm_server_release(spasm_server_t server, long long ticket);
+/* Cancel a request: a queued one at once (state 3), one in flight at the next epoch boundary
+ * (its device memory is returned then); its status becomes SPASM_ERR_CANCELLED.  Finished
+ * requests are not affected. */
+spasm_status spasm_server_cancel(spasm_server_t server, long long ticket);
+spasm_status spasm_server_get_stats(spasm_server_t server, spasm_server_stats* out);
 /* Finishes the queued and running requests, then joins the slots. */
 spasm_status spasm_server_destroy(spasm_server_t server);
 

@@ -202,6 +202,35 @@ spasm_status check_config(const spasm_batch_config& c) {
 
 }  // namespace
 
+spasm::BatchLaunch::~BatchLaunch() {
+    if (jobs) cudaFreeAsync(jobs, s);
+    if (next) cudaFreeAsync(next, s);
+}
+
+spasm_status spasm::prepare_batch(spasm_problem_t* prs, const std::vector<int>& order, const spasm_batch_config& cfg,
+                                  cudaStream_t s, BatchLaunch& bl) {
+    SPASM_TRY(check_config(cfg));
+    JobList L = make_jobs(prs, order, cfg.per_fetch, kTrajModeDescend, 0, true);
+    for (size_t k = 0; k < order.size(); ++k) L.jobs[k].io.k_steps = prs[order[k]]->sc.K_traj;
+    SPASM_TRY(batch_grid(cfg, L.smem, &bl.grid));
+    bl.host = std::move(L.jobs);
+    bl.n_items = L.n_items;
+    bl.smem = L.smem;
+    bl.per_fetch = cfg.per_fetch;
+    bl.s = s;
+    SPASM_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&bl.jobs), sizeof(TrajJob) * bl.host.size(), s));
+    SPASM_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&bl.next), sizeof(int), s));
+    SPASM_CUDA(cudaMemcpyAsync(bl.jobs, bl.host.data(), sizeof(TrajJob) * bl.host.size(), cudaMemcpyHostToDevice, s));
+    return SPASM_OK;
+}
+
+spasm_status spasm::enqueue_batch(const BatchLaunch& bl, cudaStream_t s) {
+    SPASM_CUDA(cudaMemsetAsync(bl.next, 0, sizeof(int), s));
+    SPASM_CUDA(launch_traj_batch(bl.jobs, (int)bl.host.size(), bl.n_items, bl.per_fetch, kTrajModeDescend, bl.next,
+                                 bl.smem, bl.grid, s));
+    return SPASM_OK;
+}
+
 extern "C" spasm_status spasm_batch_default_config(spasm_batch_config* cfg) {
     if (!cfg) return fail(SPASM_ERR_INVALID, "null config");
     cfg->per_fetch = 1;
@@ -226,12 +255,8 @@ extern "C" spasm_status spasm_optimize_batch(spasm_problem_t* prs, int n, void* 
         all[i] = i;
     }
     const std::vector<int> order = job_order(prs, all, cfg.order);
-    JobList L = make_jobs(prs, order, cfg.per_fetch, kTrajModeDescend, 0, true);
-    for (size_t k = 0; k < order.size(); ++k) L.jobs[k].io.k_steps = prs[order[k]]->sc.K_traj;
-    int grid = 0;
-    SPASM_TRY(batch_grid(cfg, L.smem, &grid));
-    DeviceJobs dj;
-    SPASM_TRY(upload_jobs(L, s, dj));
+    BatchLaunch bl;
+    SPASM_TRY(prepare_batch(prs, order, cfg, s, bl));
     // one graph: stage 1 of the problems not yet placed, the first lift of every problem, one
     // persistent trajectory launch over all particles, then each problem's selection, re-lift
     // loop and FP64 check; problems whose stage 1 kept nothing skip stage 2 on the device
@@ -242,9 +267,7 @@ extern "C" spasm_status spasm_optimize_batch(spasm_problem_t* prs, int n, void* 
         SPASM_TRY(br.fork());
         for (int i = 0; i < n; ++i) SPASM_TRY(enqueue_traj_lift(prs[i], br[i]));
         SPASM_TRY(br.join());
-        SPASM_CUDA(cudaMemsetAsync(dj.next, 0, sizeof(int), c));
-        SPASM_CUDA(launch_traj_batch(dj.jobs, (int)L.jobs.size(), L.n_items, cfg.per_fetch, kTrajModeDescend, dj.next,
-                                     L.smem, grid, c));
+        SPASM_TRY(enqueue_batch(bl, c));
         SPASM_TRY(br.fork());
         for (int i = 0; i < n; ++i) {
             SPASM_TRY(enqueue_traj_retry(prs[i], br[i]));

@@ -86,6 +86,19 @@ __global__ void k_wait_timeout(int max_polls, int* __restrict__ err) {
     __syncthreads();
 }
 
+// Stage-2 attempt control when the attempts are scheduled from the host (the solver service):
+// as k_traj_loop, with the decision left in c->t_more for the host to read.
+__global__ void k_traj_epoch(LoopCtl* __restrict__ c, const int* __restrict__ tnsat, int per, int max_steps, int P) {
+    const bool active = c->n_place > 0;
+    const int ns = active ? *tnsat : 0;
+    const int steps = c->t_steps + (active ? per : 0);
+    const bool more = active && ns == 0 && steps < max_steps;
+    if (active) c->t_attempt += 1u;
+    c->t_steps = steps;
+    if (!more) c->found = ns < P ? ns : P;
+    c->t_more = more ? 1 : 0;
+}
+
 __global__ void k_gather_solutions(const float* __restrict__ q, const float* __restrict__ metrics,
                                    const int* __restrict__ best, const int* __restrict__ nsat, int P, int C,
                                    float* __restrict__ rq, float* __restrict__ rcost, int* __restrict__ rsucc) {
@@ -250,6 +263,17 @@ spasm_status spasm::enqueue_traj_retry(spasm_problem* pr, cudaStream_t s) {
         SPASM_TRY(enqueue_traj_descent(pr, b));
         return traj_select_loop(pr, b, h);
     });
+}
+
+spasm_status spasm::enqueue_traj_relift(spasm_problem* pr, cudaStream_t s) { return traj_lift(pr, s); }
+
+spasm_status spasm::enqueue_traj_epoch_end(spasm_problem* pr, cudaStream_t s) {
+    const Scalars& sc = pr->sc;
+    k_traj_select<<<1, 1024, 0, s>>>(pr->d_metrics, pr->d_tsat, sc.Q, pr->d_ctl, pr->d_tmasked, pr->d_tnsat);
+    SPASM_CUDA(cudaGetLastError());
+    k_traj_epoch<<<1, 1, 0, s>>>(pr->d_ctl, pr->d_tnsat, sc.K_traj, pr->prm.max_steps, sc.P);
+    SPASM_CUDA(cudaGetLastError());
+    return SPASM_OK;
 }
 
 spasm_status spasm::enqueue_finish(spasm_problem* pr, cudaStream_t s) {

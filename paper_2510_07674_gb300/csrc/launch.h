@@ -22,7 +22,8 @@ struct LoopCtl {
     uint32_t t_attempt;   // stage 2: attempts done
     int t_steps;          // stage 2: gradient steps spent
     int found;            // stage 2: solutions kept, min(count, P); 0 until stage 2 ends
-    int traj_pad;
+    int t_more;           // stage 2 run attempt by attempt from the host (the solver service): 1 while
+                          // another attempt is due
     uint64_t seed;        // the Philox key of both stages' draws (the problem's seed)
 };
 

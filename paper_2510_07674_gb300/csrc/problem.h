@@ -108,6 +108,33 @@ spasm_status enqueue_traj_descent(spasm_problem* pr, cudaStream_t s);
 spasm_status enqueue_traj_retry(spasm_problem* pr, cudaStream_t s);
 // The final selection of the best P trajectories and their FP64 check.
 spasm_status enqueue_finish(spasm_problem* pr, cudaStream_t s);
+// Stage 2 attempt by attempt from the host (the solver service; no graph needed): the lift of
+// the next attempt (counters on the device), and after a descent the satisfying count and the
+// attempt decision (d_ctl->t_more: 1 while another attempt is due; d_ctl->found otherwise).
+spasm_status enqueue_traj_relift(spasm_problem* pr, cudaStream_t s);
+spasm_status enqueue_traj_epoch_end(spasm_problem* pr, cudaStream_t s);
+
+// A persistent launch of the trajectory kernel in descent mode over the particles of several
+// problems (batch.cu): the work list lives on the device until this object is destroyed,
+// which must come after the launch has finished.
+struct BatchLaunch {
+    std::vector<TrajJob> host;   // source of the asynchronous upload
+    TrajJob* jobs = nullptr;
+    int* next = nullptr;
+    cudaStream_t s = nullptr;
+    int n_items = 0, grid = 0, per_fetch = 1;
+    size_t smem = 0;
+    BatchLaunch() = default;
+    BatchLaunch(const BatchLaunch&) = delete;
+    BatchLaunch& operator=(const BatchLaunch&) = delete;
+    ~BatchLaunch();
+};
+// Builds and uploads (on s, asynchronously) the work list of problems prs[order[k]], each with
+// its own K_traj steps and its placement count as the gate.
+spasm_status prepare_batch(spasm_problem_t* prs, const std::vector<int>& order, const spasm_batch_config& cfg,
+                           cudaStream_t s, BatchLaunch& bl);
+// Enqueues the launch (resetting its work counter first).
+spasm_status enqueue_batch(const BatchLaunch& bl, cudaStream_t s);
 // Reads what the device loops left (attempts, counts, counters, success flags, the error
 // word) after the pending stages, once; synchronises the problem's stream.
 spasm_status finalize(spasm_problem* pr);

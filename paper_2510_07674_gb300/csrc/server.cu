@@ -1,9 +1,24 @@
-// Solver service with continuous batching (not in the paper: the serving form of the
-// hot path).  Requests (whole planning problems) are admitted in arrival order as soon as a
-// slot is free and their device memory fits the budget; each admitted request runs the
-// two-stage solve on its own non-blocking CUDA stream, so requests that arrive while others
-// are on the GPU overlap with them on the device.  Host threads only orchestrate: all
-// computation is the library's kernels.  Every host wait is bounded.
+// Solver service with continuous batching (not in the paper: the serving form of the hot path).
+//
+// One scheduler thread owns the device work.  It runs in epochs; each epoch is one trajectory
+// attempt of every request in flight, batched:
+//   1. admit queued requests in arrival order while a slot is free and their device memory
+//      (spasm_problem_bytes, the allocation list of spasm_create_problem) fits the budget; a
+//      request larger than the whole budget is admitted when nothing else is in flight;
+//   2. create each admitted request's problem and enqueue its stage 1 (the graph with the
+//      device-side attempt loop of spasm_place) and its first lift;
+//   3. one persistent launch of the trajectory kernel over the particles of every request in
+//      flight (a shared work list of particle runs, gated per request by its placement count);
+//   4. per request: the satisfying selection and the attempt decision on the device, and the
+//      FP64 check of the best P;
+//   5. one host wait, then retire the requests that finished (results copied to the host,
+//      problems destroyed, budget returned) and re-lift the others with their next attempt
+//      counter for the next epoch.
+// Requests that arrive during an epoch join at the next one, so the GPU runs one launch over
+// all work in flight rather than one solve per request.  Every particle runs the code of a
+// single solve with the same Philox streams, so a request's result does not depend on what
+// else is in flight.  Host waits are bounded; a request is cancelled while it is queued, or
+// at the next epoch boundary while it is in flight.
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -15,12 +30,15 @@
 #include <thread>
 #include <vector>
 
-#include "common.cuh"
-#include "spasm.h"
+#include "problem.h"
+
+using namespace spasm;
 
 namespace {
 
 using Clock = std::chrono::steady_clock;
+
+enum { kQueued = 0, kRunning = 1, kDone = 2, kCancelled = 3 };
 
 struct Request {
     long long ticket = 0;
@@ -32,13 +50,17 @@ struct Request {
     spasm_goal goal{};
     spasm_params prm{};
     long long bytes = 0;
-    int state = 0;   // 0 queued, 1 running, 2 done
+    int state = kQueued;
+    bool cancel = false;
     int status = SPASM_OK;
     std::string message;
     int n_found = 0;
     std::vector<double> placements, traj, cost;
     std::vector<int> success;
     Clock::time_point t_submit, t_start, t_done;
+    // scheduler-thread state
+    spasm_problem_t pr = nullptr;
+    int epochs = 0;
 };
 
 }  // namespace
@@ -46,92 +68,170 @@ struct Request {
 struct spasm_server {
     int device = 0;
     long long budget = 0, in_use = 0;
+    int max_inflight = 1;
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
     std::deque<std::shared_ptr<Request>> queue;
     std::map<long long, std::shared_ptr<Request>> all;
-    std::vector<std::thread> workers;
+    std::thread scheduler;
     long long next_ticket = 1;
     bool stop = false;
+    spasm_server_stats stats{};
 };
 
-// Device bytes a problem allocates (mirrors spasm_create_problem's allocations).
-static long long problem_bytes(const spasm_obstacles* obs, const spasm_goal* goal, const spasm_params* p) {
-    const long long B = goal->n_blocks, C = 2 * B * (p->W - 1) + 1, NR = 9 * B + 3;
-    long long f = 0;
-    f += 16LL * obs->n_cuboids + 4LL * obs->n_spheres;              // float tables
-    f += 4 * B * (long long)p->N + p->N + 4 * B * (long long)p->M * 1 + 3LL * p->M + p->P + (long long)p->P * B * 4;
-    f += (long long)p->Q * C * 8 + (long long)p->Q * NR + p->Q + 8LL * p->Q + 2LL * p->Q + (long long)p->P * C * 8;
-    f += 64;
-    long long d = 16LL * obs->n_cuboids + 4LL * obs->n_spheres + 6LL * p->P;   // double tables
-    return 4 * f + 8 * d + (1 << 16);
-}
+namespace {
 
-static void run_request(spasm_server* sv, Request& r, cudaStream_t st) {
-    spasm_problem_t pr = nullptr;
-    int status = spasm_create_problem(&r.robot, &r.obs, &r.goal, &r.prm, st, &pr);
-    if (status == SPASM_OK) status = spasm_optimize(pr);
-    if (status == SPASM_OK || status == SPASM_ERR_NOSOLUTION) {
-        const int P = r.prm.P, B = r.goal.n_blocks, C = 2 * B * (r.prm.W - 1) + 1;
-        r.placements.assign((size_t)P * B * 4, 0.0);
-        r.traj.assign((size_t)P * C * 7, 0.0);
-        r.cost.assign(P, 0.0);
-        r.success.assign(P, 0);
-        int nf = 0;
-        const int st2 = spasm_result(pr, &nf, r.placements.data(), r.traj.data(), r.cost.data(), r.success.data());
-        if (st2 != SPASM_OK && st2 != SPASM_ERR_NOSOLUTION) status = st2;
-        r.n_found = nf;
+void finish_request(spasm_server* sv, Request& r, int status, const std::string& msg) {
+    if (r.pr) {
+        spasm_destroy_problem(r.pr);
+        r.pr = nullptr;
     }
-    if (status != SPASM_OK) r.message = spasm_last_error();
-    if (pr) spasm_destroy_problem(pr);
-    cudaStreamSynchronize(st);
-    (void)sv;
-    r.status = status;
+    std::lock_guard<std::mutex> lk(sv->mu);
+    if (r.cancel) {
+        r.state = kCancelled;
+        r.status = SPASM_ERR_CANCELLED;
+        r.message = "cancelled";
+    } else {
+        r.state = kDone;
+        r.status = status;
+        r.message = msg;
+    }
+    sv->in_use -= r.bytes;
+    r.t_done = Clock::now();
+    sv->stats.completed += 1;
 }
 
-static void worker_loop(spasm_server* sv) {
+// Outputs of a finished request, read through the problem's own result call.
+int read_result(Request& r) {
+    const int P = r.prm.P, B = r.goal.n_blocks, C = 2 * B * (r.prm.W - 1) + 1;
+    r.placements.assign((size_t)P * B * 4, 0.0);
+    r.traj.assign((size_t)P * C * 7, 0.0);
+    r.cost.assign(P, 0.0);
+    r.success.assign(P, 0);
+    int nf = 0;
+    const int st = spasm_result(r.pr, &nf, r.placements.data(), r.traj.data(), r.cost.data(), r.success.data());
+    r.n_found = nf;
+    return st;
+}
+
+void scheduler_loop(spasm_server* sv) {
     cudaSetDevice(sv->device);
     cudaStream_t st = nullptr;
-    cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) st = nullptr;
+    std::vector<std::shared_ptr<Request>> active;
+    spasm_batch_config cfg;
+    spasm_batch_default_config(&cfg);
     for (;;) {
-        std::shared_ptr<Request> r;
+        std::vector<std::shared_ptr<Request>> admitted;
         {
             std::unique_lock<std::mutex> lk(sv->mu);
-            // admit the oldest request once its memory fits (a request larger than the whole
-            // budget runs alone)
-            sv->cv_work.wait(lk, [&] {
-                if (sv->stop) return true;
-                if (sv->queue.empty()) return false;
-                const long long need = sv->queue.front()->bytes;
-                return sv->in_use + need <= sv->budget || sv->in_use == 0;
-            });
-            if (sv->stop && sv->queue.empty()) break;
-            if (sv->queue.empty()) continue;
-            r = sv->queue.front();
-            sv->queue.pop_front();
-            sv->in_use += r->bytes;
-            r->state = 1;
-            r->t_start = Clock::now();
+            sv->cv_work.wait(lk, [&] { return sv->stop || !sv->queue.empty() || !active.empty(); });
+            if (sv->stop && sv->queue.empty() && active.empty()) break;
+            while (!sv->queue.empty() && (int)(active.size() + admitted.size()) < sv->max_inflight) {
+                auto& r = sv->queue.front();
+                const bool alone = active.empty() && admitted.empty() && sv->in_use == 0;
+                if (sv->in_use + r->bytes > sv->budget && !alone) break;   // waits for memory, in arrival order
+                sv->in_use += r->bytes;
+                r->state = kRunning;
+                r->t_start = Clock::now();
+                admitted.push_back(r);
+                sv->queue.pop_front();
+            }
         }
-        run_request(sv, *r, st);
+        // new requests: problem, stage 1 (device-side attempt loop), first lift
+        for (auto& r : admitted) {
+            int status = spasm_create_problem(&r->robot, &r->obs, &r->goal, &r->prm, st, &r->pr);
+            if (status == SPASM_OK) status = spasm_place(r->pr);
+            if (status == SPASM_OK) status = enqueue_traj_lift(r->pr, st);
+            if (status != SPASM_OK) {
+                const std::string msg = spasm_last_error();
+                finish_request(sv, *r, status, msg);
+                sv->cv_done.notify_all();
+                continue;
+            }
+            active.push_back(r);
+        }
+        if (active.empty()) continue;
+        // one epoch: a batched trajectory attempt of every request in flight
+        std::vector<spasm_problem_t> prs;
+        std::vector<int> order;
+        for (size_t i = 0; i < active.size(); ++i) {
+            prs.push_back(active[i]->pr);
+            order.push_back((int)i);
+        }
+        int status = SPASM_OK;
+        std::string msg;
+        {
+            BatchLaunch bl;
+            status = prepare_batch(prs.data(), order, cfg, st, bl);
+            if (status == SPASM_OK) status = enqueue_batch(bl, st);
+            for (auto& r : active)
+                if (status == SPASM_OK) status = enqueue_traj_epoch_end(r->pr, st);
+            if (status == SPASM_OK && cudaStreamSynchronize(st) != cudaSuccess) status = SPASM_ERR_CUDA;
+            if (status != SPASM_OK) msg = spasm_last_error();
+        }
         {
             std::lock_guard<std::mutex> lk(sv->mu);
-            sv->in_use -= r->bytes;
-            r->t_done = Clock::now();
-            r->state = 2;
+            sv->stats.epochs += 1;
+            sv->stats.requests_in_epochs += (long long)active.size();
+            for (auto& r : active) sv->stats.particles_in_epochs += r->prm.Q;
         }
+        std::vector<std::shared_ptr<Request>> still;
+        for (auto& r : active) {
+            r->epochs += 1;
+            if (status != SPASM_OK) {
+                finish_request(sv, *r, status, msg);
+                continue;
+            }
+            LoopCtl c{};
+            if (cudaMemcpy(&c, r->pr->d_ctl, sizeof c, cudaMemcpyDeviceToHost) != cudaSuccess) {
+                finish_request(sv, *r, SPASM_ERR_CUDA, "reading the attempt state failed");
+                continue;
+            }
+            bool cancel;
+            {
+                std::lock_guard<std::mutex> lk(sv->mu);
+                cancel = r->cancel;
+            }
+            if (c.t_more && !cancel) {
+                // another attempt: re-lift with the next attempt counter (read on the device)
+                const int st2 = enqueue_traj_relift(r->pr, st);
+                if (st2 == SPASM_OK) {
+                    still.push_back(r);
+                    continue;
+                }
+                finish_request(sv, *r, st2, spasm_last_error());
+                continue;
+            }
+            if (cancel) {
+                finish_request(sv, *r, SPASM_ERR_CANCELLED, "cancelled");
+                continue;
+            }
+            // finished: FP64 check of the best P, then the outputs
+            r->pr->place_pending = true;
+            r->pr->traj_pending = true;
+            r->pr->traj_batched = true;
+            int st3 = enqueue_finish(r->pr, st);
+            if (st3 == SPASM_OK) st3 = read_result(*r);
+            const std::string m3 = st3 == SPASM_OK ? std::string() : std::string(spasm_last_error());
+            finish_request(sv, *r, st3, m3);
+        }
+        active.swap(still);
         sv->cv_work.notify_all();
         sv->cv_done.notify_all();
     }
-    cudaStreamDestroy(st);
+    if (st) cudaStreamDestroy(st);
 }
+
+}  // namespace
 
 extern "C" spasm_status spasm_server_create(long long budget_bytes, int max_inflight, spasm_server_t* out) {
     if (!out || budget_bytes <= 0 || max_inflight < 1 || max_inflight > 256) return SPASM_ERR_INVALID;
     auto* sv = new spasm_server();
     cudaGetDevice(&sv->device);
     sv->budget = budget_bytes;
-    for (int i = 0; i < max_inflight; ++i) sv->workers.emplace_back(worker_loop, sv);
+    sv->max_inflight = max_inflight;
+    sv->scheduler = std::thread(scheduler_loop, sv);
     *out = sv;
     return SPASM_OK;
 }
@@ -139,9 +239,9 @@ extern "C" spasm_status spasm_server_create(long long budget_bytes, int max_infl
 extern "C" spasm_status spasm_server_submit(spasm_server_t sv, const spasm_robot* robot, const spasm_obstacles* obs,
                                             const spasm_goal* goal, const spasm_params* prm, long long* ticket) {
     if (!sv || !robot || !obs || !goal || !prm || !ticket) return SPASM_ERR_INVALID;
-    if (robot->dof != 7 || goal->n_blocks < 1 || goal->n_blocks > spasm::kMaxB || prm->W < 3 ||
-        robot->n_spheres < 1 || robot->n_spheres > spasm::kMaxRobotSpheres || obs->n_cuboids < 0 ||
-        obs->n_cuboids > spasm::kMaxCub || obs->n_spheres < 0 || obs->n_spheres > spasm::kMaxOSph)
+    if (robot->dof != 7 || goal->n_blocks < 1 || goal->n_blocks > kMaxB || prm->W < 3 || robot->n_spheres < 1 ||
+        robot->n_spheres > kMaxRobotSpheres || obs->n_cuboids < 0 || obs->n_cuboids > kMaxCub || obs->n_spheres < 0 ||
+        obs->n_spheres > kMaxOSph)
         return SPASM_ERR_INVALID;
     auto r = std::make_shared<Request>();
     const int B = goal->n_blocks, ns = robot->n_spheres;
@@ -164,7 +264,7 @@ extern "C" spasm_status spasm_server_submit(spasm_server_t sv, const spasm_robot
     r->goal = *goal;
     r->goal.half_ext = r->half.data(); r->goal.init_pose = r->init.data(); r->goal.goal_box = r->box.data();
     r->prm = *prm;
-    r->bytes = problem_bytes(obs, goal, prm);
+    if (spasm_problem_bytes(&r->obs, &r->goal, &r->prm, &r->bytes) != SPASM_OK) return SPASM_ERR_INVALID;
     r->t_submit = Clock::now();
     {
         std::lock_guard<std::mutex> lk(sv->mu);
@@ -192,8 +292,33 @@ extern "C" spasm_status spasm_server_wait(spasm_server_t sv, long long ticket, d
     auto it = sv->all.find(ticket);
     if (it == sv->all.end()) return SPASM_ERR_INVALID;
     auto r = it->second;
-    const bool ok = sv->cv_done.wait_for(lk, std::chrono::duration<double>(timeout_s), [&] { return r->state == 2; });
+    const bool ok = sv->cv_done.wait_for(lk, std::chrono::duration<double>(timeout_s),
+                                         [&] { return r->state == kDone || r->state == kCancelled; });
     return ok ? SPASM_OK : SPASM_ERR_TIMEOUT;
+}
+
+extern "C" spasm_status spasm_server_cancel(spasm_server_t sv, long long ticket) {
+    if (!sv) return SPASM_ERR_INVALID;
+    std::lock_guard<std::mutex> lk(sv->mu);
+    auto it = sv->all.find(ticket);
+    if (it == sv->all.end()) return SPASM_ERR_INVALID;
+    Request& r = *it->second;
+    if (r.state == kQueued) {
+        for (auto q = sv->queue.begin(); q != sv->queue.end(); ++q)
+            if ((*q)->ticket == ticket) {
+                sv->queue.erase(q);
+                break;
+            }
+        r.state = kCancelled;
+        r.status = SPASM_ERR_CANCELLED;
+        r.message = "cancelled";
+        r.t_start = r.t_done = Clock::now();
+        sv->cv_done.notify_all();
+        sv->cv_work.notify_all();
+    } else if (r.state == kRunning) {
+        r.cancel = true;   // dropped at the next epoch boundary
+    }
+    return SPASM_OK;
 }
 
 extern "C" spasm_status spasm_server_result(spasm_server_t sv, long long ticket, int* status, int* n_found,
@@ -206,7 +331,7 @@ extern "C" spasm_status spasm_server_result(spasm_server_t sv, long long ticket,
         auto it = sv->all.find(ticket);
         if (it == sv->all.end()) return SPASM_ERR_INVALID;
         r = it->second;
-        if (r->state != 2) return SPASM_ERR_TIMEOUT;
+        if (r->state != kDone && r->state != kCancelled) return SPASM_ERR_TIMEOUT;
     }
     if (status) *status = r->status;
     if (n_found) *n_found = r->n_found;
@@ -224,8 +349,16 @@ extern "C" spasm_status spasm_server_release(spasm_server_t sv, long long ticket
     std::lock_guard<std::mutex> lk(sv->mu);
     auto it = sv->all.find(ticket);
     if (it == sv->all.end()) return SPASM_ERR_INVALID;
-    if (it->second->state != 2) return SPASM_ERR_INVALID;
+    if (it->second->state != kDone && it->second->state != kCancelled) return SPASM_ERR_INVALID;
     sv->all.erase(it);
+    return SPASM_OK;
+}
+
+extern "C" spasm_status spasm_server_get_stats(spasm_server_t sv, spasm_server_stats* out) {
+    if (!sv || !out) return SPASM_ERR_INVALID;
+    std::lock_guard<std::mutex> lk(sv->mu);
+    *out = sv->stats;
+    out->bytes_in_use = sv->in_use;
     return SPASM_OK;
 }
 
@@ -236,7 +369,7 @@ extern "C" spasm_status spasm_server_destroy(spasm_server_t sv) {
         sv->stop = true;
     }
     sv->cv_work.notify_all();
-    for (auto& t : sv->workers) t.join();
+    if (sv->scheduler.joinable()) sv->scheduler.join();
     delete sv;
     return SPASM_OK;
 }

@@ -19,7 +19,7 @@ LIB_PATH = _build.LIB
 
 SPASM_OK = 0
 STATUS = {0: "SPASM_OK", -1: "SPASM_ERR_INVALID", -2: "SPASM_ERR_NOMEM", -3: "SPASM_ERR_CUDA",
-          -4: "SPASM_ERR_NOSOLUTION", -5: "SPASM_ERR_TIMEOUT", -6: "SPASM_ERR_DEVICE"}
+          -4: "SPASM_ERR_NOSOLUTION", -5: "SPASM_ERR_TIMEOUT", -6: "SPASM_ERR_DEVICE", -7: "SPASM_ERR_CANCELLED"}
 
 EXPORTED = ["spasm_create_problem", "spasm_destroy_problem", "spasm_last_error", "spasm_place", "spasm_optimize",
             "spasm_result", "spasm_sizes", "spasm_place_sample", "spasm_place_eval", "spasm_place_descend",
@@ -29,7 +29,8 @@ EXPORTED = ["spasm_create_problem", "spasm_destroy_problem", "spasm_last_error",
             "spasm_server_result", "spasm_server_release", "spasm_server_destroy", "spasm_batch_default_config",
             "spasm_optimize_batch", "spasm_batch_autotune", "spasm_create_packing", "spasm_placements",
             "spasm_create_p2p", "spasm_traj_check", "spasm_fp32_fma_peak", "spasm_synchronize",
-            "spasm_inject_wait_timeout", "spasm_inject_alloc_failure", "spasm_problem_bytes"]
+            "spasm_inject_wait_timeout", "spasm_inject_alloc_failure", "spasm_problem_bytes", "spasm_server_cancel",
+            "spasm_server_get_stats"]
 
 
 class SpasmError(RuntimeError):
@@ -83,6 +84,12 @@ class _Stats(ctypes.Structure):
                 ("host_waits", ctypes.c_longlong)]
 
 
+class _ServerStats(ctypes.Structure):
+    _fields_ = [("epochs", ctypes.c_longlong), ("requests_in_epochs", ctypes.c_longlong),
+                ("particles_in_epochs", ctypes.c_longlong), ("completed", ctypes.c_longlong),
+                ("bytes_in_use", ctypes.c_longlong)]
+
+
 class _BatchConfig(ctypes.Structure):
     _fields_ = [("per_fetch", ctypes.c_int), ("ctas_per_sm", ctypes.c_int), ("order", ctypes.c_int)]
 
@@ -132,6 +139,8 @@ def lib():
         L.spasm_server_wait.argtypes = [_V, LL, ctypes.c_double]
         L.spasm_server_result.argtypes = [_V, LL, _I, _I, _D, _D, _D, _I, _D, _D]
         L.spasm_server_release.argtypes = [_V, LL]
+        L.spasm_server_cancel.argtypes = [_V, LL]
+        L.spasm_server_get_stats.argtypes = [_V, ctypes.POINTER(_ServerStats)]
         L.spasm_server_destroy.argtypes = [_V]
         L.spasm_batch_default_config.argtypes = [ctypes.POINTER(_BatchConfig)]
         L.spasm_create_packing.argtypes = [ctypes.POINTER(_Robot), ctypes.POINTER(_Packing), ctypes.POINTER(_Params), _V,
@@ -463,6 +472,16 @@ def spasm_server_result(server: Server, ticket: int) -> dict:
     n = nf.value
     return {"status": st.value, "n_found": n, "placements": place, "traj": traj[:n], "cost": cost[:n],
             "success": succ[:n], "latency_ms": lat.value, "queue_ms": qms.value}
+
+
+def spasm_server_cancel(server: Server, ticket: int):
+    _check(lib().spasm_server_cancel(server.handle, ticket))
+
+
+def spasm_server_get_stats(server: Server) -> dict:
+    st = _ServerStats()
+    _check(lib().spasm_server_get_stats(server.handle, ctypes.byref(st)))
+    return {name: getattr(st, name) for name, _ in _ServerStats._fields_}
 
 
 def spasm_server_release(server: Server, ticket: int):

@@ -12,6 +12,7 @@ called.
     python tests/golden/make_e2e_golden.py p2p --seeds 100 --override Q=64 --override max_steps=1000
     python tests/golden/make_e2e_golden.py tower1 --seeds 100 --override ik_mode=1
     python tests/golden/make_e2e_golden.py tower4 --seeds 50 --override Q=64 --override ik_mode=1
+    python tests/golden/make_e2e_golden.py tower10 --seeds 100 --override Q=64 --override ik_mode=1
     python tests/golden/make_e2e_golden.py tetris5 --seeds 100 --override N=2048 --override M=512 --override max_steps=3000
 
 ik_mode=1 lifts with the analytic IK of the Franka joint layout instead of damped least squares.
@@ -20,8 +21,9 @@ For the point-to-point workload (one transit segment to a tool target) only stag
 the packing workloads (the appendix's Tetris problem) only stage 1, and the stored costs are the
 stage-1 costs of the returned placements.
 
-The 4-block case keeps its scene, stage-1 sizes and waypoint count, and reduces the number of
-trajectory particles so that the FP64 all-pairs oracle finishes 100 seeds in about an hour.
+The 4- and 10-block cases keep their scenes, stage-1 sizes and waypoint counts, and reduce the
+number of trajectory particles to 64 so that the FP64 all-pairs oracle finishes a seed in seconds
+(4 blocks) or about a minute (10 blocks, 64 cuboids, 621 configurations) on 8 cores.
 """
 import argparse
 import json

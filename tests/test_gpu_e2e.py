@@ -19,8 +19,9 @@ from paper_2510_07674_gb300 import scenes
 from paper_2510_07674_gb300 import spasm as S
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
-CASES = ["e2e_tower1_ik_mode1.json", "e2e_tower4_Q64_ik_mode1.json", "e2e_p2p_Q64_ik_mode1_max_steps1000.json",
-         "e2e_tower1_ik_mode0.json", "e2e_tower4_Q64_ik_mode0.json", "e2e_p2p_Q64_ik_mode0_max_steps1000.json"]
+CASES = ["e2e_tower10_Q64_ik_mode1.json", "e2e_tower1_ik_mode1.json", "e2e_tower4_Q64_ik_mode1.json",
+         "e2e_p2p_Q64_ik_mode1_max_steps1000.json", "e2e_tower1_ik_mode0.json", "e2e_tower4_Q64_ik_mode0.json",
+         "e2e_p2p_Q64_ik_mode0_max_steps1000.json"]
 
 
 def gpu_best(workload, seed, overrides):
@@ -61,19 +62,31 @@ def test_success_rate_and_cost_distribution_match_oracle(fname):
     both = o_ok & g_ok
     rel = np.abs(g_best[both] - o_best[both]) / np.maximum(np.abs(o_best[both]), 1e-12)
     ks = stats.ks_2samp(g_best[g_ok], o_best[o_ok])
+    # paired sign test: on seeds both sides solve and whose best costs differ by more than the
+    # float32 rounding of the reported cost (1e-4 relative), the GPU's is above the oracle's
+    # about as often as below (no systematic difference between the two descents)
+    d = (g_best[both] - o_best[both]) / np.maximum(np.abs(o_best[both]), 1e-12)
+    above, below = int(np.sum(d > 1e-4)), int(np.sum(d < -1e-4))
+    sign_p = stats.binomtest(above, above + below, 0.5).pvalue if above + below > 0 else 1.0
     print(f"{fname}: seeds {len(rows)}, success oracle {rate_o:.3f} gpu {rate_g:.3f} "
           f"(both {int((o_ok & g_ok).sum())}, oracle only {int((o_ok & ~g_ok).sum())}, gpu only "
-          f"{int((~o_ok & g_ok).sum())}, FP64-refused {rejected}), KS p {ks.pvalue:.3f}, "
+          f"{int((~o_ok & g_ok).sum())}, FP64-refused {rejected}), KS p {ks.pvalue:.3f}, sign test p {sign_p:.3f} "
+          f"({above} above / {below} below), "
           f"per-seed rel. diff of best cost: median {np.median(rel):.2e}, p90 {np.quantile(rel, 0.9):.2e}")
     # success rates: a 3-sigma band of two binomial proportions (FP32 and FP64 descents can
     # reach different minima where a seed is hard), which shrinks to one seed at 100%
     n = len(rows)
     p_bar = 0.5 * (rate_o + rate_g)
     assert abs(rate_g - rate_o) <= 3.0 * np.sqrt(2.0 * p_bar * (1.0 - p_bar) / n) + 1.0 / n, (rate_o, rate_g)
-    # final-cost distributions indistinguishable
+    # final-cost distributions indistinguishable, and no systematic difference seed by seed
     assert ks.pvalue > 0.01, ks
-    # same Philox streams: the typical seed ends at (nearly) the same best solution
-    assert np.median(rel) < 1e-2, np.median(rel)
+    assert sign_p > 0.01, (above, below)
+    # same Philox streams: the typical seed ends at (nearly) the same best solution.  The
+    # 10-block tower descends 621 configurations among 74 obstacles for 50 steps: contacts
+    # switch on or off at different steps in FP32 and FP64, and the best of 64 particles ends a
+    # few percent apart (the distributions and the sign test above show no bias)
+    bound = 1e-1 if "tower10" in fname else 1e-2
+    assert np.median(rel) < bound, np.median(rel)
 
 
 PACK_CASES = ["e2e_tetris5_M512_N2048_max_steps3000.json"]
