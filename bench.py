@@ -398,6 +398,7 @@ def run_native(args, ws, rank, local):
     if args.serve_problems > 0:
         batched, served = run_forms(args, rank, overrides, peak)
     packing = run_packing(args, rank) if args.pack_seeds > 0 else None
+    sweep = sweep_leg(args, rank) if args.sweep_seconds > 0 else None
     p2p = run_p2p(args, rank) if args.p2p_seeds > 0 else None
     ik_modes = run_ik_modes(args, rank) if args.ik_seeds > 0 else None
 
@@ -432,6 +433,7 @@ def run_native(args, ws, rank, local):
         "batched": batched,
         "served": served,
         "packing": packing,
+        "sweep": sweep,
         "p2p": p2p,
         "ik_modes": ik_modes,
         "gpu_launches": int(sum(s["kernel_launches"] for s in stats)),
@@ -691,6 +693,43 @@ def run_sweep(args):
                       "metric": "stage-1 time to first solution (ms), mean over seeds"}))
 
 
+SWEEP_LEG_GRID = {
+    # workload: (N values, M values, seeds per cell)
+    "tetris5": ([512, 2048, 8192, 32768], [256, 1024, 4096], 5),
+    "tetris8": ([8192, 16384], [512, 1024, 2048, 4096], 10),
+    "tower10": ([1024, 8192, 32768], [256, 1024, 4096], 5),
+}
+
+
+def sweep_leg(args, rank) -> dict:
+    """The N x M stage-1 sweep (Sec. IV, Fig. 5 analogue) on a reduced grid, inside the
+    benchmark's JSON line: time to first solution (CUDA events around spasm_place) per cell, the
+    success fraction within the 30 000-step cap and the attempts; cells are run in order until
+    the leg's time budget is spent (the rest are listed as skipped)."""
+    from paper_2510_07674_gb300 import scenes
+    t_start = time.perf_counter()
+    rows, skipped = [], []
+    for name, (Ns, Ms, seeds) in SWEEP_LEG_GRID.items():
+        for N in Ns:
+            for M in Ms:
+                if M > N:
+                    continue
+                if time.perf_counter() - t_start > args.sweep_seconds:
+                    skipped.append(f"{name} N={N} M={M}")
+                    continue
+                times, ok, att = [], 0, []
+                for t in range(seeds):
+                    kw = dict(seed=rank * 1000 + t, N=N, M=M, P=min(8, M), max_steps=30000)
+                    wl = scenes.make_packing(name, **kw) if name in scenes.PACKINGS else scenes.make_problem(name, **kw)
+                    solved, ms, a = stage1_first_solution(wl)
+                    ok += solved
+                    times.append(ms)
+                    att.append(a)
+                rows.append(dict(workload=name, N=N, M=M, **_summary(times, ok, att)))
+    return {"metric": "stage-1 time to first solution (ms), 30 000-step cap", "cells": rows, "skipped": skipped,
+            "seconds": time.perf_counter() - t_start}
+
+
 # ------------------------------------------------------------------------------- oracle
 def cpu_baseline(wl, budget_s: float) -> dict:
     """The FP64 oracle, as it stands, on a bounded sample of the same workload: a stage-1
@@ -837,6 +876,8 @@ def main():
     ap.add_argument("--sweep", action="store_true", help="run the N x M stage-1 sweep instead of the benchmark")
     ap.add_argument("--sweep-workloads", nargs="*", default=["tetris5", "tetris8", "tower10"])
     ap.add_argument("--sweep-trials", type=int, default=5)
+    ap.add_argument("--sweep-seconds", type=float, default=90.0,
+                    help="time budget of the reduced N x M sweep leg inside the benchmark line (0 = skip)")
     ap.add_argument("--serve-rates", type=float, nargs="*", default=[10.0, 30.0, 100.0, 300.0, 1000.0, 2000.0])
     ap.add_argument("--override", action="append", default=[], metavar="PARAM=VALUE",
                     help="change a solver parameter (profiling of a reduced case only; recorded in config)")

@@ -329,6 +329,22 @@ spasm_status spasm_synchronize(spasm_problem_t problem);
 spasm_status spasm_inject_wait_timeout(spasm_problem_t problem, int max_polls);
 spasm_status spasm_inject_alloc_failure(int nth);
 
+/* Launch shape of the trajectory kernels (not in the paper: the tiling choices the autotuner
+ * searches).  sphere_tiling: how a warp's lanes hold the (up to 64) sphere items of a
+ * configuration, 0 strided (lane L holds items L and L + 32), 1 blocked (items 2L and 2L + 1);
+ * particles_per_cta: particles one CTA optimises at once, 1 (8 warps) or 2 (16 warps, each
+ * particle on its own 8 warps and shared-memory region; needs twice the shared memory).  The
+ * tiling reorders sums of the same terms (results agree to float32 rounding); the particles
+ * per CTA change nothing in a particle's arithmetic. */
+typedef struct {
+    int sphere_tiling;
+    int particles_per_cta;
+} spasm_kernel_config;
+/* Sets the launch shape of the problem's trajectory kernels (spasm_optimize and the
+ * kernel-level trajectory calls) and rebuilds its stage graphs; SPASM_ERR_INVALID for values
+ * outside the above or two particles whose shared memory does not fit one CTA.  Synchronises. */
+spasm_status spasm_set_kernel_config(spasm_problem_t problem, const spasm_kernel_config* cfg);
+
 /* Replace the Philox seed (the key of every random stream) and forget previous results;
  * the next spasm_optimize re-runs both stages. */
 spasm_status spasm_set_seed(spasm_problem_t problem, uint64_t seed);
@@ -354,18 +370,23 @@ spasm_status spasm_reset_stats(spasm_problem_t problem);
  * first, and the problems must not be used by another thread during the call.
  * The schedule of the persistent launch: */
 typedef struct {
-    int per_fetch;     /* particles per work item a CTA takes from the shared counter (1..64) */
+    int per_fetch;     /* particles per work item a group takes from the shared counter (1..64) */
     int ctas_per_sm;   /* resident CTAs per SM (0: as many as fit) */
     int order;         /* 0: the largest problem (particles x configurations) first, 1: as given */
+    int sphere_tiling;       /* 0 strided, 1 blocked (see spasm_kernel_config) */
+    int particles_per_cta;   /* 1 or 2 (see spasm_kernel_config) */
 } spasm_batch_config;
-/* per_fetch 1, ctas_per_sm 0, order 0. */
+/* per_fetch 1, ctas_per_sm 0, order 0, sphere_tiling 0, particles_per_cta 1. */
 spasm_status spasm_batch_default_config(spasm_batch_config* cfg);
 /* cfg NULL: the default schedule. */
 spasm_status spasm_optimize_batch(spasm_problem_t* problems, int n, void* cuda_stream, const spasm_batch_config* cfg);
-/* Autotuner of the schedule: places the problems not yet placed (stage 1, as above), lifts
- * them, times one evaluation of every particle under each candidate schedule (per_fetch in
- * {1, 2, 4} x ctas_per_sm in {all, 1} x both orders; CUDA events) and returns the fastest in
- * *best (and its time in *best_ms when not NULL).  The schedule changes no result. */
+/* Autotuner of the batched launch: places the problems not yet placed (stage 1, as above),
+ * lifts them, times one evaluation of every particle under each candidate (sphere tiling in
+ * {strided, blocked} x particles per CTA in {1, 2} (where its shared memory fits) x per_fetch
+ * in {1, 2, 4} x ctas_per_sm in {all, 1} x both orders; CUDA events, the better of two runs)
+ * and returns the fastest in *best (and its time in *best_ms when not NULL).  The schedule and
+ * the particles per CTA change no result; the sphere tiling changes results at float32
+ * rounding. */
 spasm_status spasm_batch_autotune(spasm_problem_t* problems, int n, void* cuda_stream, spasm_batch_config* best,
                                   double* best_ms);
 

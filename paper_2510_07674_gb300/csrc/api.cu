@@ -641,6 +641,25 @@ extern "C" spasm_status spasm_traj_check(spasm_problem_t pr, int n, const float*
     return SPASM_OK;
 }
 
+extern "C" spasm_status spasm_set_kernel_config(spasm_problem_t pr, const spasm_kernel_config* cfg) {
+    if (!pr || !cfg) return fail(SPASM_ERR_INVALID, "null argument");
+    if (cfg->sphere_tiling < 0 || cfg->sphere_tiling > 1 || cfg->particles_per_cta < 1 || cfg->particles_per_cta > 2)
+        return fail(SPASM_ERR_INVALID, "sphere_tiling must be 0 or 1 and particles_per_cta 1 or 2");
+    int dev = 0, max_smem = 0;
+    SPASM_CUDA(cudaGetDevice(&dev));
+    SPASM_CUDA(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    if (traj_cta_smem_bytes(pr->sc, cfg->particles_per_cta) > (size_t)max_smem)
+        return fail(SPASM_ERR_INVALID, "the shared memory of that many particles per CTA does not fit this problem");
+    SPASM_TRY(finalize(pr));
+    SPASM_TRY(host_wait(pr));
+    pr->sc.sphere_tiling = cfg->sphere_tiling;
+    pr->sc.particles_per_cta = cfg->particles_per_cta;
+    SPASM_CUDA(cudaMemcpyAsync(pr->d_sc, &pr->sc, sizeof(Scalars), cudaMemcpyHostToDevice, pr->stream));
+    SPASM_TRY(host_wait(pr));
+    drop_graphs(pr);   // their launches hold the old shape
+    return prepare_graphs(pr);
+}
+
 extern "C" spasm_status spasm_synchronize(spasm_problem_t pr) {
     if (!pr) return fail(SPASM_ERR_INVALID, "null problem");
     SPASM_TRY(finalize(pr));

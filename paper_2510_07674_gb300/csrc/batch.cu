@@ -187,7 +187,7 @@ spasm_status batch_grid(const spasm_batch_config& cfg, size_t smem, int* grid) {
     int dev = 0, sms = 0;
     SPASM_CUDA(cudaGetDevice(&dev));
     SPASM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    const int resident = traj_batch_ctas_per_sm(smem);
+    const int resident = traj_batch_ctas_per_sm(smem, cfg.sphere_tiling, cfg.particles_per_cta);
     if (resident < 1) return fail(SPASM_ERR_INVALID, "batched trajectory kernel does not fit this shared-memory size");
     const int per_sm = cfg.ctas_per_sm > 0 ? std::min(cfg.ctas_per_sm, resident) : resident;
     *grid = per_sm * sms;
@@ -195,8 +195,10 @@ spasm_status batch_grid(const spasm_batch_config& cfg, size_t smem, int* grid) {
 }
 
 spasm_status check_config(const spasm_batch_config& c) {
-    if (c.per_fetch < 1 || c.per_fetch > 64 || c.ctas_per_sm < 0 || c.ctas_per_sm > 8 || c.order < 0 || c.order > 1)
-        return fail(SPASM_ERR_INVALID, "batch config outside per_fetch 1..64, ctas_per_sm 0..8, order 0..1");
+    if (c.per_fetch < 1 || c.per_fetch > 64 || c.ctas_per_sm < 0 || c.ctas_per_sm > 8 || c.order < 0 || c.order > 1 ||
+        c.sphere_tiling < 0 || c.sphere_tiling > 1 || c.particles_per_cta < 1 || c.particles_per_cta > 2)
+        return fail(SPASM_ERR_INVALID, "batch config outside per_fetch 1..64, ctas_per_sm 0..8, order 0..1, "
+                                       "sphere_tiling 0..1, particles_per_cta 1..2");
     return SPASM_OK;
 }
 
@@ -217,6 +219,8 @@ spasm_status spasm::prepare_batch(spasm_problem_t* prs, const std::vector<int>& 
     bl.n_items = L.n_items;
     bl.smem = L.smem;
     bl.per_fetch = cfg.per_fetch;
+    bl.tiling = cfg.sphere_tiling;
+    bl.ppc = cfg.particles_per_cta;
     bl.s = s;
     SPASM_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&bl.jobs), sizeof(TrajJob) * bl.host.size(), s));
     SPASM_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&bl.next), sizeof(int), s));
@@ -227,7 +231,7 @@ spasm_status spasm::prepare_batch(spasm_problem_t* prs, const std::vector<int>& 
 spasm_status spasm::enqueue_batch(const BatchLaunch& bl, cudaStream_t s) {
     SPASM_CUDA(cudaMemsetAsync(bl.next, 0, sizeof(int), s));
     SPASM_CUDA(launch_traj_batch(bl.jobs, (int)bl.host.size(), bl.n_items, bl.per_fetch, kTrajModeDescend, bl.next,
-                                 bl.smem, bl.grid, s));
+                                 bl.smem, bl.grid, s, bl.tiling, bl.ppc));
     return SPASM_OK;
 }
 
@@ -236,6 +240,8 @@ extern "C" spasm_status spasm_batch_default_config(spasm_batch_config* cfg) {
     cfg->per_fetch = 1;
     cfg->ctas_per_sm = 0;
     cfg->order = 0;
+    cfg->sphere_tiling = 0;
+    cfg->particles_per_cta = 1;
     return SPASM_OK;
 }
 
@@ -321,29 +327,30 @@ extern "C" spasm_status spasm_batch_autotune(spasm_problem_t* prs, int n, void* 
     } ev{e0, e1};
     double best_t = 1e300;
     const int fetches[] = {1, 2, 4};
-    for (int order = 0; order <= 1; ++order) {
-        for (int pf : fetches) {
-            for (int per_sm : {0, 1}) {
-                spasm_batch_config c{pf, per_sm, order};
-                JobList L = make_jobs(prs, job_order(prs, live, order), pf, kTrajModeEval, 0, true);
-                int grid = 0;
-                SPASM_TRY(batch_grid(c, L.smem, &grid));
-                DeviceJobs dj;
-                SPASM_TRY(upload_jobs(L, s, dj));
-                double t = 1e300;
-                for (int rep = 0; rep < 2; ++rep) {   // the first repetition warms caches
-                    SPASM_CUDA(cudaMemsetAsync(dj.next, 0, sizeof(int), s));
-                    SPASM_CUDA(cudaEventRecord(e0, s));
-                    SPASM_CUDA(launch_traj_batch(dj.jobs, (int)L.jobs.size(), L.n_items, pf, kTrajModeEval, dj.next,
-                                                 L.smem, grid, s));
-                    SPASM_CUDA(cudaEventRecord(e1, s));
-                    SPASM_CUDA(cudaEventSynchronize(e1));
-                    if (rep > 0) t = ev_ms(e0, e1);
-                }
-                if (t < best_t) { best_t = t; *best = c; }
-            }
-        }
-    }
+    for (int tiling = 0; tiling <= 1; ++tiling)
+        for (int ppc = 1; ppc <= 2; ++ppc)
+            for (int order = 0; order <= 1; ++order)
+                for (int pf : fetches)
+                    for (int per_sm : {0, 1}) {
+                        spasm_batch_config c{pf, per_sm, order, tiling, ppc};
+                        JobList L = make_jobs(prs, job_order(prs, live, order), pf, kTrajModeEval, 0, true);
+                        int grid = 0;
+                        if (traj_batch_ctas_per_sm(L.smem, tiling, ppc) < 1) continue;   // two particles do not fit
+                        SPASM_TRY(batch_grid(c, L.smem, &grid));
+                        DeviceJobs dj;
+                        SPASM_TRY(upload_jobs(L, s, dj));
+                        double t = 1e300;
+                        for (int rep = 0; rep < 2; ++rep) {   // the first repetition warms caches
+                            SPASM_CUDA(cudaMemsetAsync(dj.next, 0, sizeof(int), s));
+                            SPASM_CUDA(cudaEventRecord(e0, s));
+                            SPASM_CUDA(launch_traj_batch(dj.jobs, (int)L.jobs.size(), L.n_items, pf, kTrajModeEval,
+                                                         dj.next, L.smem, grid, s, tiling, ppc));
+                            SPASM_CUDA(cudaEventRecord(e1, s));
+                            SPASM_CUDA(cudaEventSynchronize(e1));
+                            if (rep > 0) t = ev_ms(e0, e1);
+                        }
+                        if (t < best_t) { best_t = t; *best = c; }
+                    }
     for (int i : live) SPASM_TRY(check_device_error(prs[i]));
     // the candidates' evaluations wrote nothing the next solve reads; q is lifted again there
     if (best_ms) *best_ms = best_t;

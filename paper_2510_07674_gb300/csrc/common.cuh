@@ -56,6 +56,9 @@ struct Scalars {
     float w_stable, w_height, w_coll, w_start, w_arm, w_block, w_path, w_jl;
     float mu0, mu_max, ik_damp;
     int ik_mode;                     // lift IK: 0 damped least squares, 1 analytic (Franka joint layout)
+    int sphere_tiling;               // trajectory kernels: sphere items per lane, 0 strided (lane + 32 k),
+                                     // 1 blocked (2 lane + k); the same terms, summed in another order
+    int particles_per_cta;           // trajectory kernels: particles a CTA runs at once, 1 or 2 (0 = 1)
     unsigned long long seed;
     // packing goal (the appendix's Tetris problem), kind = kKindPack: block i is a polyomino
     // of unit cubes of edge cell_size centred at cell[cell_start[i] .. cell_start[i+1]) in

@@ -15,6 +15,20 @@ constexpr int kSlots = 2;   // sphere items per lane: up to 56 robot + 8 held-bl
 
 constexpr int kChunk = 4;   // configurations whose kinematics one warp evaluates together
 
+// A trajectory CTA runs 1 or 2 particles at once (particles per CTA, a launch option): each on
+// its own group of kTThreads threads, with its own region of dynamic shared memory and its own
+// named barrier 1 + group.  With one particle the group is the whole CTA.
+template <int kPpc>
+__device__ __forceinline__ int grp_tid() { return kPpc == 1 ? (int)threadIdx.x : (int)(threadIdx.x & (kTThreads - 1)); }
+template <int kPpc>
+__device__ __forceinline__ int grp_index() { return kPpc == 1 ? 0 : (int)(threadIdx.x / kTThreads); }
+template <int kPpc>
+__device__ __forceinline__ void grp_sync() {
+    if (kPpc == 1) __syncthreads();
+    else if (threadIdx.x < kTThreads) asm volatile("bar.sync 1, %0;" ::"n"(kTThreads) : "memory");
+    else asm volatile("bar.sync 2, %0;" ::"n"(kTThreads) : "memory");
+}
+
 // Cached cull.  When a chunk's cull finds no candidate for any of its configurations, it
 // also returns the chunk's clearances: the smallest separation (largest per-axis gap) between
 // any of its link boxes and any static box that could touch it (the environment, blocks at
@@ -98,19 +112,29 @@ size_t traj_smem_bytes(const Scalars& sc) {
            (size_t)t_n_chunks(sc.C) * (2 * sizeof(float) + sizeof(int));
 }
 
-// The robot spheres a lane owns (item lane + 32 k), loaded once per kernel launch: link-
-// frame centre, radius, link index.  Items beyond the robot spheres are the held block's.
+// Sphere item held in slot k by a lane: strided tiling, item lane + 32 k (the spheres of a link
+// spread over neighbouring lanes), or blocked tiling, item kSlots lane + k (a lane's spheres are
+// neighbours, mostly on one link).  Either covers 64 items; the choice reorders the per-lane
+// sums only.
+template <int kTile>
+__device__ __forceinline__ int slot_item(int lane, int k) {
+    return kTile ? kSlots * lane + k : lane + 32 * k;
+}
+
+// The robot spheres a lane owns (slot_item), loaded once per kernel launch: link-frame centre,
+// radius, link index.  Items beyond the robot spheres are the held block's.
 struct LaneSpheres {
     float lx[kSlots], ly[kSlots], lz[kSlots], r[kSlots];
     int link[kSlots];
 };
 
+template <int kTile>
 __device__ __forceinline__ LaneSpheres lane_spheres(const Scalars& sc) {
     const int lane = threadIdx.x & 31;
     LaneSpheres ls;
 #pragma unroll
     for (int k = 0; k < kSlots; ++k) {
-        const int it = lane + 32 * k;
+        const int it = slot_item<kTile>(lane, k);
         if (it < sc.n_rsph) {
             const float4 v = sc.rsph[it];
             ls.lx[k] = v.x; ls.ly[k] = v.y; ls.lz[k] = v.z; ls.r[k] = v.w;
@@ -207,13 +231,14 @@ __device__ __forceinline__ void chunk_fk(const Scalars& sc, const TShared& sh, c
 
 // World centres of the lane's sphere items for one configuration (frames F, held-block
 // frame H); items beyond the robot spheres are the held block's (transfer interior only).
+template <int kTile>
 __device__ __forceinline__ void sphere_centres(const Scalars& sc, const LaneSpheres& ls, const float4 (*F)[3],
                                                const float4* H, int n_items, int b, float* cx, float* cy, float* cz,
                                                float* rr, bool* act, bool* isblk) {
     const int lane = threadIdx.x & 31;
 #pragma unroll
     for (int k = 0; k < kSlots; ++k) {
-        const int it = lane + 32 * k;
+        const int it = slot_item<kTile>(lane, k);
         act[k] = it < n_items;
         isblk[k] = act[k] && it >= sc.n_rsph;
         float x = ls.lx[k], y = ls.ly[k], z = ls.lz[k];
@@ -240,6 +265,7 @@ __device__ __forceinline__ void sphere_centres(const Scalars& sc, const LaneSphe
 // per configuration lanes own sphere items, screen both slots branch-free and evaluate the
 // penetration only where the separation test fails.  With `grad`, writes the unscaled group
 // gradients G_arm[t], G_blk[t] and accumulates placed-pose derivatives in the warp scratch.
+template <int kTile>
 __device__ __forceinline__ bool chunk_collisions(const Scalars& sc, const LaneSpheres& ls,
                                                  const float4* __restrict__ cub, const float4* __restrict__ osph,
                                                  const float4* __restrict__ aabb, TShared& sh, TWarp& tw, float* G_arm,
@@ -376,7 +402,7 @@ __device__ __forceinline__ bool chunk_collisions(const Scalars& sc, const LaneSp
         }
         none = false;
         ++n_cand;
-        sphere_centres(sc, ls, tw.F[ci], tw.H[ci], n_items, b, cx, cy, cz, rr, act, isblk);
+        sphere_centres<kTile>(sc, ls, tw.F[ci], tw.H[ci], n_items, b, cx, cy, cz, rr, act, isblk);
         float gx[kSlots], gy[kSlots], gz[kSlots], pen_sum[kSlots];
 #pragma unroll
         for (int sl = 0; sl < kSlots; ++sl) gx[sl] = gy[sl] = gz[sl] = pen_sum[sl] = 0.f;
@@ -608,10 +634,11 @@ __device__ __forceinline__ void start_terms(const Scalars& sc, int b, int which,
 // test screens each pair before the exact one.  Per warp: the sum and maximum of the
 // penetrations (tw.pc); with `grad`, the unscaled pose gradient dC_coll/dx, sphere side in
 // sh.pg[w][j] and cuboid side in sh.pgc[i] (written by the one warp that owns cuboid i).
+template <int kPpc>
 __device__ __forceinline__ void placed_collisions(const Scalars& sc, const float4* __restrict__ cub,
                                                   const float4* __restrict__ osph, const float4* __restrict__ aabb,
                                                   TShared& sh, bool grad) {
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31, w = grp_tid<kPpc>() >> 5;
     const int B = sc.B, n_items = 8 * B;
     float coll = 0.f, maxpen = 0.f;
     if (grad && lane < 4)
@@ -708,13 +735,13 @@ __device__ __forceinline__ void cuboid_aabb(const float4* c, float4* box) {
 // Evaluate the whole particle: kinematics of the grasp/place configurations and the placed
 // poses, the configuration loop, residuals and objective; with `grad`, the assembled dL/dq
 // ends up in G_blk (G_arm holds the unscaled arm-group gradient).
-template <bool kP2P>
+template <bool kP2P, int kTile, int kPpc>
 __device__ void traj_evaluate(const Scalars& sc, const LaneSpheres& ls, const float4* cub, const float4* osph,
                               const float4* aabb, TShared& sh, SpecialFrames* sp, float* q, float* G_arm,
                               float* G_blk, float* disp, float* cblk, __half2* cgap, int* ccand, bool grad,
                               unsigned long long& n_tests, unsigned long long& n_cull,
                               unsigned long long& n_cand) {
-    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int tid = grp_tid<kPpc>(), lane = tid & 31, w = tid >> 5;
     const int B = sc.B, S = sc.S, C = sc.C, NR = sc.NR;
     // point to point (kP2P): one segment ending at the target's grasp configuration; no placement
     constexpr bool p2p = kP2P;
@@ -727,7 +754,7 @@ __device__ void traj_evaluate(const Scalars& sc, const LaneSpheres& ls, const fl
         chunk_fk(sc, sh, q, ok ? (si + 1) * S : 1, ok, true, sp[ok ? si : 0].F, sp[ok ? si : 0].H, nullptr);
     }
     for (int i = lane; i < 2 * kMaxB * 4; i += 32) (&sh.warp[w].wr[0][0][0])[i] = 0.f;
-    __syncthreads();
+    grp_sync<kPpc>();
     // placed poses: the block frame at each place configuration, (x, y, z, yaw)
     if (w == 0) {
         float moved = 0.f;
@@ -761,7 +788,7 @@ __device__ void traj_evaluate(const Scalars& sc, const LaneSpheres& ls, const fl
         if (lane < B) sh.blk_cum[lane] += moved;
         if (lane == 0) sh.pose_prev_ok = 1;
     }
-    __syncthreads();
+    grp_sync<kPpc>();
 
     // (2) configuration loop: chunks of kChunk consecutive configurations per warp
     float acc_arm = 0.f, acc_blk = 0.f, acc_max = 0.f;
@@ -806,7 +833,7 @@ __device__ void traj_evaluate(const Scalars& sc, const LaneSpheres& ls, const fl
             if (lane < 7 * nk) G_blk[(tk + lane / 7) * 8 + lane % 7] = 0.f;
         }
     }
-    __syncthreads();
+    grp_sync<kPpc>();
     // warp w takes positions w, w + 8, ... of the concatenated lists, tier by tier, group by group
     int start = 0;
     for (int tg = 0; tg < (kChunk + 1) * kTWarps; ++tg) {
@@ -825,7 +852,7 @@ __device__ void traj_evaluate(const Scalars& sc, const LaneSpheres& ls, const fl
             __syncwarp();
             float clearance, clearance_moving;
             const unsigned long long cand0 = n_cand;
-            const bool none = chunk_collisions(sc, ls, cub, osph, aabb, sh, sh.warp[w], G_arm, G_blk, t0, nc, grad, box,
+            const bool none = chunk_collisions<kTile>(sc, ls, cub, osph, aabb, sh, sh.warp[w], G_arm, G_blk, t0, nc, grad, box,
                                                acc_arm, acc_blk, acc_max, n_tests, n_cand, clearance,
                                                clearance_moving);
             n_cull += (unsigned)nc;
@@ -846,9 +873,9 @@ __device__ void traj_evaluate(const Scalars& sc, const LaneSpheres& ls, const fl
     acc_max = warp_max(acc_max);
     if (lane == 0) { sh.warp[w].part[0] = acc_arm; sh.warp[w].part[1] = acc_blk; sh.warp[w].part[2] = acc_max; }
     // collisions of the placed tower, all warps (reads only the placed poses of step 1)
-    if (!p2p) placed_collisions(sc, cub, osph, aabb, sh, grad);
+    if (!p2p) placed_collisions<kPpc>(sc, cub, osph, aabb, sh, grad);
     else if (lane == 0) { sh.warp[w].pc[0] = 0.f; sh.warp[w].pc[1] = 0.f; }
-    __syncthreads();
+    grp_sync<kPpc>();
 
     // (3) epilogue.  (a) warp 0: group sums and the placement residuals; warp 1: start residuals
     if (w == 0) {
@@ -889,7 +916,7 @@ __device__ void traj_evaluate(const Scalars& sc, const LaneSpheres& ls, const fl
         if (!p2p) start_terms(sc, lane, 1, sp[2 * lane + 1], &sh.h[5 * B + 2 * lane], nullptr, nullptr, nullptr);
         else sh.h[5 * B + 2 * lane] = sh.h[5 * B + 2 * lane + 1] = 0.f;
     }
-    __syncthreads();
+    grp_sync<kPpc>();
     // (b) objective and dL/dh
     if (w == 0) {
         float v_start = 0.f, v_tilt = 0.f;
@@ -914,7 +941,7 @@ __device__ void traj_evaluate(const Scalars& sc, const LaneSpheres& ls, const fl
             sh.s_arm = sh.s[9 * B + 1]; sh.s_blk = sh.s[9 * B + 2];
         }
     }
-    __syncthreads();
+    grp_sync<kPpc>();
     if (grad) {
         // (c) warp 0: placement gradient w.r.t. the placed poses, then (d) the place configurations'
         // gradient rows; warp 1: grasp gradients
@@ -944,7 +971,7 @@ __device__ void traj_evaluate(const Scalars& sc, const LaneSpheres& ls, const fl
             float hbuf[5];
             start_terms(sc, lane, 0, sp[2 * lane], hbuf, &sh.s[5 * lane], sh.extra[lane], nullptr);
         }
-        __syncthreads();
+        grp_sync<kPpc>();
     }
 
     // (4) path length, joint limits; assemble the gradient into G_blk
@@ -982,7 +1009,7 @@ __device__ void traj_evaluate(const Scalars& sc, const LaneSpheres& ls, const fl
     path = warp_sum(path);
     jl = warp_sum(jl);
     if (lane == 0) { sh.warp[w].part[0] = path; sh.warp[w].part[1] = jl; }
-    __syncthreads();
+    grp_sync<kPpc>();
     if (tid == 0) {
         float p = 0.f, l = 0.f;
         for (int i = 0; i < kTWarps; ++i) { p += sh.warp[i].part[0]; l += sh.warp[i].part[1]; }
@@ -990,13 +1017,13 @@ __device__ void traj_evaluate(const Scalars& sc, const LaneSpheres& ls, const fl
         sh.jl = l;
         sh.L += sc.w_path * p + sc.w_jl * l;
     }
-    __syncthreads();
+    grp_sync<kPpc>();
 }
 
 // One particle of the trajectory stage by the whole CTA: load its state, run the descent (or
 // the single evaluation), write the outputs.  The environment tables are already in shared
 // memory (smem_raw, laid out by the t_*_offset functions of this problem).
-template <bool kP2P>
+template <bool kP2P, int kTile, int kPpc>
 __device__ __forceinline__ void traj_particle(const Scalars& sc, int p, int mode, const TrajIO& io,
                                               unsigned char* smem_raw) {
     float4* cub = reinterpret_cast<float4*>(smem_raw + t_env_offset());
@@ -1012,7 +1039,7 @@ __device__ __forceinline__ void traj_particle(const Scalars& sc, int p, int mode
     float* cblk = disp + sc.C;
     __half2* cgap = reinterpret_cast<__half2*>(cblk + n_chunks);   // (static, moving) clearances
     int* ccand = reinterpret_cast<int*>(cgap + n_chunks);
-    const int tid = threadIdx.x;
+    const int tid = grp_tid<kPpc>();
     const int C = sc.C, NR = sc.NR, B = sc.B;
     for (int i = tid; i < C; i += kTThreads) disp[i] = 0.f;
     for (int i = tid; i < n_chunks; i += kTThreads) { cblk[i] = 0.f; cgap[i] = __float2half2_rn(0.f); ccand[i] = kChunk; }
@@ -1040,16 +1067,16 @@ __device__ __forceinline__ void traj_particle(const Scalars& sc, int p, int mode
         aabb[2 * (sc.n_cub + o) + 1] = make_float4(sp.x + sp.w, sp.y + sp.w, sp.z + sp.w, 0.f);
     }
     unsigned long long n_tests = 0, n_cull = 0, n_cand = 0;
-    const LaneSpheres ls = lane_spheres(sc);
+    const LaneSpheres ls = lane_spheres<kTile>(sc);
     const bool fresh = mode == kTrajDescend && io.init_multipliers;
     for (int r = tid; r < NR; r += kTThreads) sh.lam[r] = (fresh || !io.lam) ? 0.f : io.lam[(size_t)p * NR + r];
     if (tid == 0) sh.mu = (fresh || !io.mu) ? sc.mu0 : io.mu[p];
-    __syncthreads();
+    grp_sync<kPpc>();
 
     if (mode == kTrajDescend) {
         const int K = io.k_steps;
         for (int k = 1; k <= K; ++k) {
-            traj_evaluate<kP2P>(sc, ls, cub, osph, aabb, sh, sp, q, G_arm, G_blk, disp, cblk, cgap, ccand, true,
+            traj_evaluate<kP2P, kTile, kPpc>(sc, ls, cub, osph, aabb, sh, sp, q, G_arm, G_blk, disp, cblk, cgap, ccand, true,
                                 n_tests,
                                 n_cull, n_cand);
             const float eta = sc.eta_traj * (1.f - (float)k / (float)K);
@@ -1073,14 +1100,14 @@ __device__ __forceinline__ void traj_particle(const Scalars& sc, int p, int mode
             }
             if (sc.K_al > 0 && k % sc.K_al == 0) {
                 for (int r = tid; r < NR; r += kTThreads) sh.lam[r] += sh.mu * residual_sqrt_weight(sc, r) * sh.h[r];
-                __syncthreads();
+                grp_sync<kPpc>();
                 if (tid == 0) sh.mu = fminf(sh.mu * 2.f, sc.mu_max);
             }
-            __syncthreads();
+            grp_sync<kPpc>();
         }
     }
     const bool want_grad = mode == kTrajEval && io.grad != nullptr;
-    traj_evaluate<kP2P>(sc, ls, cub, osph, aabb, sh, sp, q, G_arm, G_blk, disp, cblk, cgap, ccand, want_grad, n_tests,
+    traj_evaluate<kP2P, kTile, kPpc>(sc, ls, cub, osph, aabb, sh, sp, q, G_arm, G_blk, disp, cblk, cgap, ccand, want_grad, n_tests,
                         n_cull, n_cand);
     if (io.tests && (threadIdx.x & 31) == 0) {
         atomicAdd(io.tests, n_tests);
@@ -1121,41 +1148,85 @@ __device__ __forceinline__ void traj_particle(const Scalars& sc, int p, int mode
     }
 }
 
-// One CTA per particle of one problem (kP2P: the point-to-point instantiation).
-template <bool kP2P>
-__global__ void __launch_bounds__(kTThreads, 2) k_traj(const __grid_constant__ Scalars sc, DevTables tab, int n, int mode,
-                                                      TrajIO io, int* err) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+// Bulk-copy staging of the environment tables into one group's region, with the group's own
+// barrier: stage_tables for a group of kTThreads threads (the bounded wait, the error word, a
+// second bounded wait for copies in flight after a timeout).  `init`: first use of the
+// group's mbarrier; `phase`: the parity this copy completes.
+template <int kPpc>
+__device__ __forceinline__ bool stage_tables_grp(void* dst0, const void* src0, uint32_t bytes0, void* dst1,
+                                                 const void* src1, uint32_t bytes1, uint64_t* bar, int* err,
+                                                 bool init = true, uint32_t phase = 0) {
+    volatile uint32_t* okw = reinterpret_cast<volatile uint32_t*>(bar + 1);   // the region header's second word
+    if (grp_tid<kPpc>() == 0) {
+        if (init) {
+            mbar_init(bar, 1);
+            fence_mbar_init();
+        }
+        *okw = 1u;
+    }
+    grp_sync<kPpc>();
+    if (grp_tid<kPpc>() == 0) {
+        mbar_expect_tx(bar, bytes0 + bytes1);
+        if (bytes0) bulk_g2s(dst0, src0, bytes0, bar);
+        if (bytes1) bulk_g2s(dst1, src1, bytes1, bar);
+    }
+    const bool done = mbar_wait_bounded(bar, phase, kTablePolls);
+    if (!done) {
+        set_error(err, kDevTimeout);
+        mbar_wait_bounded(bar, phase, kTablePolls);
+        *okw = 0u;
+    }
+    grp_sync<kPpc>();
+    const bool all = *okw != 0u;
+    grp_sync<kPpc>();   // every thread has read the flag before a later call resets it
+    return all;
+}
+
+// kPpc particles per CTA (one CTA per particle, or two): group g of CTA i takes particle
+// kPpc i + g in its own shared-memory region of `region` bytes (kP2P: the point-to-point
+// instantiation; kTile: the sphere tiling).
+template <bool kP2P, int kTile, int kPpc>
+__global__ void __launch_bounds__(kTThreads * kPpc, 3 - kPpc) k_traj(const __grid_constant__ Scalars sc, DevTables tab,
+                                                                    int n, int mode, TrajIO io, int* err, int region) {
+    extern __shared__ __align__(16) unsigned char smem_all[];
     if (io.active && *io.active <= 0) return;   // stage 1 of this problem found no placement
+    unsigned char* smem_raw = smem_all + (size_t)grp_index<kPpc>() * region;
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
     float4* cub = reinterpret_cast<float4*>(smem_raw + t_env_offset());
     float4* osph = cub + 4 * sc.n_cub;
-    if (!stage_tables(cub, tab.cub, (uint32_t)sc.n_cub * 64u, osph, tab.osph, (uint32_t)sc.n_osph * 16u, bar, err))
+    if (!stage_tables_grp<kPpc>(cub, tab.cub, (uint32_t)sc.n_cub * 64u, osph, tab.osph, (uint32_t)sc.n_osph * 16u, bar, err))
         return;
-    const int p = blockIdx.x;
+    const int p = blockIdx.x * kPpc + grp_index<kPpc>();
     if (p >= n) return;
-    traj_particle<kP2P>(sc, p, mode, io, smem_raw);
+    traj_particle<kP2P, kTile, kPpc>(sc, p, mode, io, smem_raw);
 }
 
 static_assert(sizeof(Scalars) % 16 == 0, "the batched kernel copies Scalars in 16-byte words");
 
 // Batched form: a persistent grid over the particles of several problems.  Work items are
 // runs of `per_fetch` consecutive particles of one problem, numbered problem after problem
-// (jobs[j].first is the first item of problem j); each CTA takes the next item from *next
-// until none is left.  On a change of problem the CTA stages that problem's constants and
-// tables into shared memory.  Every particle runs exactly the code of k_traj, so results
-// equal the single-problem launches bit for bit, whatever the schedule.
-__global__ void __launch_bounds__(kTThreads, 2) k_traj_batch(const TrajJob* __restrict__ jobs, int n_jobs, int n_items,
-                                                            int per_fetch, int mode, int* next) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ __align__(16) Scalars sc_s;
-    __shared__ TrajIO io_s;
-    __shared__ int s_item, s_job;
+// (jobs[j].first is the first item of problem j); each group (kPpc per CTA) takes the next
+// item from *next until none is left.  On a change of problem the group stages that
+// problem's constants and tables into its shared memory.  Every particle runs exactly the
+// code of k_traj, so results equal the single-problem launches bit for bit, whatever the
+// schedule.
+template <int kTile, int kPpc>
+__global__ void __launch_bounds__(kTThreads * kPpc, 3 - kPpc) k_traj_batch(const TrajJob* __restrict__ jobs, int n_jobs,
+                                                                          int n_items, int per_fetch, int mode, int* next,
+                                                                          int region) {
+    extern __shared__ __align__(16) unsigned char smem_all[];
+    __shared__ __align__(16) Scalars sc_arr[kPpc];
+    __shared__ TrajIO io_arr[kPpc];
+    __shared__ int s_item[kPpc], s_job[kPpc];
+    const int g = grp_index<kPpc>(), tid = grp_tid<kPpc>();
+    unsigned char* smem_raw = smem_all + (size_t)g * region;
+    Scalars& sc_s = sc_arr[g];
+    TrajIO& io_s = io_arr[g];
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
     int cur = -1;
     uint32_t uses = 0;
     for (;;) {
-        if (threadIdx.x == 0) {
+        if (tid == 0) {
             const int it = atomicAdd(next, 1);
             int j = -1;
             if (it < n_items) {   // last job whose first item is <= it
@@ -1166,24 +1237,24 @@ __global__ void __launch_bounds__(kTThreads, 2) k_traj_batch(const TrajJob* __re
                 }
                 j = lo;
             }
-            s_item = it;
-            s_job = j;
+            s_item[g] = it;
+            s_job[g] = j;
         }
-        __syncthreads();
-        const int it = s_item, j = s_job;
+        grp_sync<kPpc>();
+        const int it = s_item[g], j = s_job[g];
         if (j < 0) break;
         const TrajJob& job = jobs[j];
         if (j != cur) {
             // stage the problem's constants (int4 words) and its tables
             const int4* src = reinterpret_cast<const int4*>(job.sc);
             int4* dst = reinterpret_cast<int4*>(&sc_s);
-            for (int i = threadIdx.x; i < (int)(sizeof(Scalars) / 16); i += blockDim.x) dst[i] = src[i];
-            if (threadIdx.x == 0) io_s = job.io;
-            __syncthreads();
+            for (int i = tid; i < (int)(sizeof(Scalars) / 16); i += kTThreads) dst[i] = src[i];
+            if (tid == 0) io_s = job.io;
+            grp_sync<kPpc>();
             float4* cub = reinterpret_cast<float4*>(smem_raw + t_env_offset());
             float4* osph = cub + 4 * sc_s.n_cub;
-            if (!stage_tables(cub, job.tab.cub, (uint32_t)sc_s.n_cub * 64u, osph, job.tab.osph,
-                              (uint32_t)sc_s.n_osph * 16u, bar, job.err, uses == 0, uses & 1u))
+            if (!stage_tables_grp<kPpc>(cub, job.tab.cub, (uint32_t)sc_s.n_cub * 64u, osph, job.tab.osph,
+                                  (uint32_t)sc_s.n_osph * 16u, bar, job.err, uses == 0, uses & 1u))
                 return;
             ++uses;
             cur = j;
@@ -1192,44 +1263,82 @@ __global__ void __launch_bounds__(kTThreads, 2) k_traj_batch(const TrajJob* __re
         // a problem whose stage 1 found no placement has nothing to optimise
         const int p1 = (io_s.active && *io_s.active <= 0) ? p0 : min(p0 + per_fetch, job.n);
         for (int p = p0; p < p1; ++p) {
-            if (sc_s.kind == kKindP2P) traj_particle<true>(sc_s, p, mode, io_s, smem_raw);
-            else traj_particle<false>(sc_s, p, mode, io_s, smem_raw);
-            __syncthreads();
+            if (sc_s.kind == kKindP2P) traj_particle<true, kTile, kPpc>(sc_s, p, mode, io_s, smem_raw);
+            else traj_particle<false, kTile, kPpc>(sc_s, p, mode, io_s, smem_raw);
+            grp_sync<kPpc>();
         }
     }
 }
 
 // ================================================================================== launchers
-cudaError_t launch_traj_batch(const TrajJob* jobs, int n_jobs, int n_items, int per_fetch, int mode, int* next,
-                              size_t smem_bytes, int grid, cudaStream_t st) {
-    if (n_items <= 0) return cudaSuccess;
-    cudaError_t e = allow_max_dynamic_smem(k_traj_batch, smem_bytes);
+// Shared memory of one group: the problem's layout, rounded to 128 bytes.
+static int t_region(size_t bytes) { return (int)((bytes + 127) & ~(size_t)127); }
+
+template <int kTile, int kPpc>
+static cudaError_t batch_kernel(const TrajJob* jobs, int n_jobs, int n_items, int per_fetch, int mode, int* next,
+                                size_t smem_bytes, int grid, cudaStream_t st) {
+    const int region = t_region(smem_bytes);
+    const size_t dyn = (size_t)region * kPpc;
+    cudaError_t e = allow_max_dynamic_smem(k_traj_batch<kTile, kPpc>, dyn);
     if (e != cudaSuccess) return e;
-    k_traj_batch<<<grid, kTThreads, smem_bytes, st>>>(jobs, n_jobs, n_items, per_fetch, mode, next);
+    k_traj_batch<kTile, kPpc><<<grid, kTThreads * kPpc, dyn, st>>>(jobs, n_jobs, n_items, per_fetch, mode, next, region);
     return cudaGetLastError();
 }
 
-int traj_batch_ctas_per_sm(size_t smem_bytes) {
+cudaError_t launch_traj_batch(const TrajJob* jobs, int n_jobs, int n_items, int per_fetch, int mode, int* next,
+                              size_t smem_bytes, int grid, cudaStream_t st, int tiling, int ppc) {
+    if (n_items <= 0) return cudaSuccess;
+    if (ppc == 2)
+        return tiling ? batch_kernel<1, 2>(jobs, n_jobs, n_items, per_fetch, mode, next, smem_bytes, grid, st)
+                      : batch_kernel<0, 2>(jobs, n_jobs, n_items, per_fetch, mode, next, smem_bytes, grid, st);
+    return tiling ? batch_kernel<1, 1>(jobs, n_jobs, n_items, per_fetch, mode, next, smem_bytes, grid, st)
+                  : batch_kernel<0, 1>(jobs, n_jobs, n_items, per_fetch, mode, next, smem_bytes, grid, st);
+}
+
+template <int kTile, int kPpc>
+static int batch_occupancy(size_t smem_bytes) {
     int n = 0;
-    if (allow_max_dynamic_smem(k_traj_batch, smem_bytes) != cudaSuccess) return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_traj_batch, kTThreads, smem_bytes) != cudaSuccess) return 0;
+    const size_t dyn = (size_t)t_region(smem_bytes) * kPpc;
+    if (allow_max_dynamic_smem(k_traj_batch<kTile, kPpc>, dyn) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_traj_batch<kTile, kPpc>, kTThreads * kPpc, dyn) !=
+        cudaSuccess)
+        return 0;
     return n;
+}
+
+int traj_batch_ctas_per_sm(size_t smem_bytes, int tiling, int ppc) {
+    if (ppc == 2) return tiling ? batch_occupancy<1, 2>(smem_bytes) : batch_occupancy<0, 2>(smem_bytes);
+    return tiling ? batch_occupancy<1, 1>(smem_bytes) : batch_occupancy<0, 1>(smem_bytes);
+}
+
+template <bool kP2P, int kTile, int kPpc>
+static cudaError_t traj_kernel(const Scalars& sc, DevTables t, int n, int mode, const TrajIO& io, int* err,
+                               cudaStream_t st) {
+    const int region = t_region(traj_smem_bytes(sc));
+    const size_t dyn = (size_t)region * kPpc;
+    cudaError_t e = allow_max_dynamic_smem(k_traj<kP2P, kTile, kPpc>, dyn);
+    if (e != cudaSuccess) return e;
+    k_traj<kP2P, kTile, kPpc><<<(n + kPpc - 1) / kPpc, kTThreads * kPpc, dyn, st>>>(sc, t, n, mode, io, err, region);
+    return cudaGetLastError();
+}
+
+template <bool kP2P>
+static cudaError_t traj_dispatch(const Scalars& sc, DevTables t, int n, int mode, const TrajIO& io, int* err,
+                                 cudaStream_t st) {
+    if (sc.particles_per_cta == 2)
+        return sc.sphere_tiling ? traj_kernel<kP2P, 1, 2>(sc, t, n, mode, io, err, st)
+                                : traj_kernel<kP2P, 0, 2>(sc, t, n, mode, io, err, st);
+    return sc.sphere_tiling ? traj_kernel<kP2P, 1, 1>(sc, t, n, mode, io, err, st)
+                            : traj_kernel<kP2P, 0, 1>(sc, t, n, mode, io, err, st);
 }
 
 cudaError_t launch_traj(const Scalars& sc, DevTables t, int n, int mode, const TrajIO& io, int* err,
                         cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
-    const size_t bytes = traj_smem_bytes(sc);
-    if (sc.kind == kKindP2P) {
-        cudaError_t e = allow_max_dynamic_smem(k_traj<true>, bytes);
-        if (e != cudaSuccess) return e;
-        k_traj<true><<<n, kTThreads, bytes, st>>>(sc, t, n, mode, io, err);
-    } else {
-        cudaError_t e = allow_max_dynamic_smem(k_traj<false>, bytes);
-        if (e != cudaSuccess) return e;
-        k_traj<false><<<n, kTThreads, bytes, st>>>(sc, t, n, mode, io, err);
-    }
-    return cudaGetLastError();
+    return sc.kind == kKindP2P ? traj_dispatch<true>(sc, t, n, mode, io, err, st)
+                               : traj_dispatch<false>(sc, t, n, mode, io, err, st);
 }
+
+size_t traj_cta_smem_bytes(const Scalars& sc, int ppc) { return (size_t)t_region(traj_smem_bytes(sc)) * ppc; }
 
 }  // namespace spasm

@@ -45,9 +45,14 @@ cudaError_t launch_lift(const Scalars& sc, int n, const float* place, int n_plac
 cudaError_t launch_traj(const Scalars& sc, DevTables t, int n, int mode, const TrajIO& io, int* err, cudaStream_t st);
 // Persistent batched launch over jobs[0..n_jobs) (n_items work items of per_fetch particles;
 // *next must be 0); smem_bytes = the largest traj_smem_bytes of the jobs.
+// tiling, ppc: the sphere tiling (Scalars::sphere_tiling) and the particles per CTA
+// (Scalars::particles_per_cta) of the launch, the same for every job.
 cudaError_t launch_traj_batch(const TrajJob* jobs, int n_jobs, int n_items, int per_fetch, int mode, int* next,
-                              size_t smem_bytes, int grid, cudaStream_t st);
-// Resident CTAs per SM of the batched kernel at that shared-memory size (0 on error).
-int traj_batch_ctas_per_sm(size_t smem_bytes);
+                              size_t smem_bytes, int grid, cudaStream_t st, int tiling = 0, int ppc = 1);
+// Resident CTAs per SM of the batched kernel at that per-particle shared-memory size (0 on error
+// or when it does not fit).
+int traj_batch_ctas_per_sm(size_t smem_bytes, int tiling = 0, int ppc = 1);
+// Dynamic shared memory of one trajectory CTA with ppc particles.
+size_t traj_cta_smem_bytes(const Scalars& sc, int ppc);
 
 }  // namespace spasm

@@ -122,7 +122,7 @@ struct BatchLaunch {
     TrajJob* jobs = nullptr;
     int* next = nullptr;
     cudaStream_t s = nullptr;
-    int n_items = 0, grid = 0, per_fetch = 1;
+    int n_items = 0, grid = 0, per_fetch = 1, tiling = 0, ppc = 1;
     size_t smem = 0;
     BatchLaunch() = default;
     BatchLaunch(const BatchLaunch&) = delete;

@@ -30,7 +30,7 @@ EXPORTED = ["spasm_create_problem", "spasm_destroy_problem", "spasm_last_error",
             "spasm_optimize_batch", "spasm_batch_autotune", "spasm_create_packing", "spasm_placements",
             "spasm_create_p2p", "spasm_traj_check", "spasm_fp32_fma_peak", "spasm_synchronize",
             "spasm_inject_wait_timeout", "spasm_inject_alloc_failure", "spasm_problem_bytes", "spasm_server_cancel",
-            "spasm_server_get_stats"]
+            "spasm_server_get_stats", "spasm_set_kernel_config"]
 
 
 class SpasmError(RuntimeError):
@@ -91,7 +91,12 @@ class _ServerStats(ctypes.Structure):
 
 
 class _BatchConfig(ctypes.Structure):
-    _fields_ = [("per_fetch", ctypes.c_int), ("ctas_per_sm", ctypes.c_int), ("order", ctypes.c_int)]
+    _fields_ = [("per_fetch", ctypes.c_int), ("ctas_per_sm", ctypes.c_int), ("order", ctypes.c_int),
+                ("sphere_tiling", ctypes.c_int), ("particles_per_cta", ctypes.c_int)]
+
+
+class _KernelConfig(ctypes.Structure):
+    _fields_ = [("sphere_tiling", ctypes.c_int), ("particles_per_cta", ctypes.c_int)]
 
 
 _lib = None
@@ -127,6 +132,7 @@ def lib():
         L.spasm_traj_check.argtypes = [_V, ctypes.c_int, _V, _V, _V]
         L.spasm_fp32_fma_peak.argtypes = [ctypes.c_double, _D, _D, _D]
         L.spasm_synchronize.argtypes = [_V]
+        L.spasm_set_kernel_config.argtypes = [_V, ctypes.POINTER(_KernelConfig)]
         L.spasm_problem_bytes.argtypes = [ctypes.POINTER(_Obstacles), ctypes.POINTER(_Goal), ctypes.POINTER(_Params),
                                           ctypes.POINTER(ctypes.c_longlong)]
         L.spasm_inject_wait_timeout.argtypes = [_V, ctypes.c_int]
@@ -396,17 +402,27 @@ def _batch_stream(stream):
     return _V(int(stream))
 
 
+_BATCH_KEYS = [name for name, _ in _BatchConfig._fields_]
+
+
 def spasm_batch_default_config() -> dict:
     c = _BatchConfig()
     _check(lib().spasm_batch_default_config(ctypes.byref(c)))
-    return {"per_fetch": c.per_fetch, "ctas_per_sm": c.ctas_per_sm, "order": c.order}
+    return {k: getattr(c, k) for k in _BATCH_KEYS}
+
+
+def spasm_set_kernel_config(problem: Problem, sphere_tiling: int = 0, particles_per_cta: int = 1):
+    c = _KernelConfig(int(sphere_tiling), int(particles_per_cta))
+    _check(lib().spasm_set_kernel_config(problem.handle, ctypes.byref(c)))
 
 
 def spasm_optimize_batch(problems, stream=None, config: Optional[dict] = None):
     """Solve the problems together (batched form); read each with spasm_result."""
     cfg = None
     if config is not None:
-        cfg = _BatchConfig(int(config["per_fetch"]), int(config["ctas_per_sm"]), int(config["order"]))
+        base = spasm_batch_default_config()
+        base.update({k: v for k, v in config.items() if k in _BATCH_KEYS})
+        cfg = _BatchConfig(*[int(base[k]) for k in _BATCH_KEYS])
     _check(lib().spasm_optimize_batch(_handles(problems), len(problems), _batch_stream(stream),
                                       ctypes.byref(cfg) if cfg is not None else None))
 
@@ -417,7 +433,9 @@ def spasm_batch_autotune(problems, stream=None) -> dict:
     ms = ctypes.c_double()
     _check(lib().spasm_batch_autotune(_handles(problems), len(problems), _batch_stream(stream), ctypes.byref(c),
                                       ctypes.byref(ms)))
-    return {"per_fetch": c.per_fetch, "ctas_per_sm": c.ctas_per_sm, "order": c.order, "ms": ms.value}
+    out = {k: getattr(c, k) for k in _BATCH_KEYS}
+    out["ms"] = ms.value
+    return out
 
 
 class Server:

@@ -17,9 +17,10 @@ def mixed_workloads():
     return out
 
 
-def solve_alone(wl):
+def solve_alone(wl, sphere_tiling=0, particles_per_cta=1):
     pr = S.Problem(wl)
     try:
+        S.spasm_set_kernel_config(pr, sphere_tiling, particles_per_cta)
         S.spasm_optimize(pr)
         return S.spasm_result(pr, allow_empty=True)
     finally:
@@ -61,15 +62,17 @@ def test_autotune_returns_a_candidate_and_keeps_results():
     try:
         best = S.spasm_batch_autotune(prs, stream=stream.cuda_stream)
         assert best["per_fetch"] in (1, 2, 4) and best["ctas_per_sm"] in (0, 1) and best["order"] in (0, 1)
+        assert best["sphere_tiling"] in (0, 1) and best["particles_per_cta"] in (1, 2)
         assert best["ms"] > 0
-        # the problems are placed by the tuner; the tuned batch still equals the plain solve
+        # the problems are placed by the tuner; the tuned batch equals the plain solve with the
+        # same launch shape (the sphere tiling reorders float sums)
         S.spasm_optimize_batch(prs, stream=stream.cuda_stream, config=best)
         batch = [S.spasm_result(p, allow_empty=True) for p in prs]
     finally:
         for p in prs:
             p.close()
     for wl, b in zip(wls, batch):
-        same(solve_alone(wl), b)
+        same(solve_alone(wl, best["sphere_tiling"], best["particles_per_cta"]), b)
 
 
 @pytest.mark.gpu
