@@ -119,6 +119,10 @@ def issue_from_profile() -> dict:
         pass
     if "top stalls per issued instruction" in vals:
         out["top_stalls_per_issue"] = vals["top stalls per issued instruction"]
+    try:   # FADD + FMUL + 2 FFMA thread instructions counted by the hardware, per launch
+        out["fp32_flop_counted_per_launch"] = float(vals["fp32_flop_counted"].split()[0])
+    except (KeyError, ValueError, IndexError):
+        pass
     return out
 
 
@@ -292,6 +296,8 @@ def run_native(args, ws, rank, local):
     probs = [S.Problem(w, **overrides) for w in wls]
     for p in probs:
         S.spasm_set_timing(p, True)
+        if args.launch_mode == "eager":   # kernel by kernel, for profilers that cannot enter the graphs
+            S.spasm_set_launch_mode(p, S.SPASM_LAUNCH_EAGER)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2
     fp32_peak = measured_fp32_peak(local)
 
@@ -408,7 +414,8 @@ def run_native(args, ws, rank, local):
         "vs_baseline": None, "dtype": "f32 (FP64 final check)", "data": "synthetic",
         "config": {"workload": WORKLOAD_DESC, "parallelism": f"replicas x{ws}", "l2": "flushed between steps "
                    "(256 MB write outside the per-step events)", "max_steps": args.max_steps,
-                   "overrides": {k: v for k, v in overrides.items() if k != "max_steps"}},
+                   "overrides": {k: v for k, v in overrides.items() if k != "max_steps"},
+                   "launch_mode": args.launch_mode},
         # p50 / p99 over the tail leg's seeds when it ran (the metric's distribution), else over the
         # timed steps
         "solve_ms_p50": tail["p50_ms"] if tail else float(statistics.median(times)),
@@ -862,6 +869,9 @@ def main():
     ap.add_argument("--max-steps", type=int, default=1000,
                     help="cap on gradient steps per stage (re-initialisation budget)")
     ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--launch-mode", choices=["graph", "eager"], default="graph",
+                    help="graph: each stage one CUDA graph with a device-side attempt loop; eager: the same kernels "
+                         "launched one at a time with the loop on the host (for kernel profilers)")
     ap.add_argument("--tail-seeds", type=int, default=100,
                     help="10-block solves (one per seed, 0..n-1) for the p50 / p99 of the metric (0 = skip)")
     ap.add_argument("--cpu-budget-s", type=float, default=20.0)

@@ -169,8 +169,9 @@ const char* spasm_last_error(void);
  * gradient steps are spent (Sec. III-A, the cap of Sec. IV-C).  Enqueues and returns: the
  * attempt loop runs on the device (a CUDA graph whose conditional while node repeats an
  * attempt while no particle satisfies), and the host does not wait for it.  The best P
- * placements stay on the device for stage 2; spasm_placements reads them.  The first call
- * (and the first after spasm_set_seed) captures the graph; later calls launch it.
+ * placements stay on the device for stage 2; spasm_placements reads them.  The graphs of
+ * both stages are built when the problem is created (they read the seed from device memory,
+ * so spasm_set_seed keeps them).
  * SPASM_ERR_NOSOLUTION, when no attempt satisfies, is reported by spasm_placements /
  * spasm_result. */
 spasm_status spasm_place(spasm_problem_t problem);
@@ -181,6 +182,18 @@ spasm_status spasm_place(spasm_problem_t problem);
  * spasm_place it enqueues one graph with a device-side attempt loop and returns without
  * waiting; the outcome (including SPASM_ERR_NOSOLUTION) is read by spasm_result. */
 spasm_status spasm_optimize(spasm_problem_t problem);
+
+/* Launch mode of spasm_place / spasm_optimize.  SPASM_LAUNCH_GRAPH (the default): each stage
+ * is one CUDA graph whose attempt loop is a conditional while node.  SPASM_LAUNCH_EAGER: the
+ * same kernels with the same arguments in the same order, launched one at a time on the
+ * problem's stream, the attempt loop on the host, which reads the loop decision after every
+ * attempt (one wait each: the calls return once the last attempt is enqueued); the results
+ * are the same bits.  It serves tools that cannot look inside graphs with conditional nodes
+ * (kernel profilers).  spasm_optimize_batch and the service always use graphs.  Completes the
+ * pending stages first.  SPASM_ERR_INVALID for another mode. */
+#define SPASM_LAUNCH_GRAPH 0
+#define SPASM_LAUNCH_EAGER 1
+spasm_status spasm_set_launch_mode(spasm_problem_t problem, int mode);
 
 /* Copy results to host memory (synchronises: the one host wait of a solve).  Any output
  * pointer may be NULL.

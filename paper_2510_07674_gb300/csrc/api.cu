@@ -175,6 +175,7 @@ static bool franka_layout(const double* dh) {
 
 static spasm_status create_problem_impl(const spasm_robot* robot, const spasm_obstacles* obs, const spasm_goal* goal,
                                         const spasm_params* prm, void* cuda_stream, spasm_problem_t* out) {
+    Range range("spasm create problem");
     if (!robot || !obs || !goal || !prm || !out) return fail(SPASM_ERR_INVALID, "null argument");
     *out = nullptr;
     if (robot->dof != 7) return fail(SPASM_ERR_INVALID, "dof must be 7");

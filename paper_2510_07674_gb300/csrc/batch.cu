@@ -247,6 +247,7 @@ extern "C" spasm_status spasm_batch_default_config(spasm_batch_config* cfg) {
 
 extern "C" spasm_status spasm_optimize_batch(spasm_problem_t* prs, int n, void* cuda_stream,
                                              const spasm_batch_config* cfg_in) {
+    Range r("spasm_optimize_batch");
     SPASM_TRY(check_batch(prs, n, cuda_stream));
     spasm_batch_config cfg;
     spasm_batch_default_config(&cfg);
@@ -293,6 +294,7 @@ extern "C" spasm_status spasm_optimize_batch(spasm_problem_t* prs, int n, void* 
 
 extern "C" spasm_status spasm_batch_autotune(spasm_problem_t* prs, int n, void* cuda_stream, spasm_batch_config* best,
                                              double* best_ms) {
+    Range r("spasm_batch_autotune");
     SPASM_TRY(check_batch(prs, n, cuda_stream));
     if (!best) return fail(SPASM_ERR_INVALID, "null config");
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);

@@ -20,6 +20,9 @@ using namespace spasm;
 
 namespace {
 
+// Stage-1 attempt control: the loop condition goes to the while node (kGraph) or to c->more
+// for the host to read (the eager mode).
+template <bool kGraph>
 __global__ void k_place_loop(LoopCtl* __restrict__ c, const int* __restrict__ nsat, int per, int max_steps, int P,
                              cudaGraphConditionalHandle h) {
     const int steps = c->steps + per;
@@ -28,7 +31,8 @@ __global__ void k_place_loop(LoopCtl* __restrict__ c, const int* __restrict__ ns
     c->attempt += 1u;
     c->steps = steps;
     if (!more) c->n_place = ns < P ? ns : P;
-    cudaGraphSetConditional(h, more ? 1u : 0u);
+    if constexpr (kGraph) cudaGraphSetConditional(h, more ? 1u : 0u);
+    else c->more = more ? 1 : 0;
 }
 
 __global__ void k_traj_begin(LoopCtl* __restrict__ c, int* __restrict__ tnsat) {
@@ -177,9 +181,13 @@ spasm_status place_attempt(spasm_problem* pr, cudaStream_t s) {
 }
 constexpr int kPlaceAttemptKernels = 7;   // the six above and the loop control
 
-spasm_status place_loop(spasm_problem* pr, cudaStream_t s, cudaGraphConditionalHandle h) {
+// The loop control after an attempt: into the while node on h, or (eager, h unused) into c->more.
+spasm_status place_loop(spasm_problem* pr, cudaStream_t s, cudaGraphConditionalHandle h, bool eager = false) {
     const Scalars& sc = pr->sc;
-    k_place_loop<<<1, 1, 0, s>>>(pr->d_ctl, pr->d_nsat, sc.K_lin + sc.K_quad, pr->prm.max_steps, sc.P, h);
+    if (eager)
+        k_place_loop<false><<<1, 1, 0, s>>>(pr->d_ctl, pr->d_nsat, sc.K_lin + sc.K_quad, pr->prm.max_steps, sc.P, h);
+    else
+        k_place_loop<true><<<1, 1, 0, s>>>(pr->d_ctl, pr->d_nsat, sc.K_lin + sc.K_quad, pr->prm.max_steps, sc.P, h);
     SPASM_CUDA(cudaGetLastError());
     return SPASM_OK;
 }
@@ -228,7 +236,53 @@ spasm_status build_graph(cudaStream_t cap, cudaGraphExec_t* out, F enqueue) {
     return SPASM_OK;
 }
 
+// The eager mode: the graphs' kernels in the graphs' order, launched one at a time, with the
+// loop decision read by the host after every attempt (one wait per attempt).
+spasm_status read_more(spasm_problem* pr, const int* d_more, int* more) {
+    SPASM_CUDA(cudaMemcpyAsync(more, d_more, sizeof(int), cudaMemcpyDeviceToHost, pr->stream));
+    SPASM_TRY(host_wait(pr));
+    pr->stats.d2h_bytes += sizeof(int);
+    return SPASM_OK;
+}
+
+spasm_status record(spasm_problem* pr, int i) {
+    SPASM_CUDA(cudaEventRecord(pr->ev[i], pr->stream));
+    return SPASM_OK;
+}
+
 }  // namespace
+
+spasm_status spasm::run_place_eager(spasm_problem* pr) {
+    Range r("spasm stage 1 (eager)");
+    cudaStream_t s = pr->stream;
+    SPASM_CUDA(cudaMemsetAsync(pr->d_ctl, 0, offsetof(LoopCtl, t_attempt), s));
+    for (int more = 1; more;) {
+        SPASM_TRY(place_attempt(pr, s));
+        SPASM_TRY(place_loop(pr, s, 0, true));
+        SPASM_TRY(read_more(pr, &pr->d_ctl->more, &more));
+    }
+    return SPASM_OK;
+}
+
+spasm_status spasm::run_traj_eager(spasm_problem* pr) {
+    Range r("spasm stage 2 (eager)");
+    cudaStream_t s = pr->stream;
+    SPASM_TRY(record(pr, 2));
+    SPASM_TRY(enqueue_traj_lift(pr, s));
+    SPASM_TRY(record(pr, 3));
+    SPASM_TRY(enqueue_traj_descent(pr, s));
+    SPASM_TRY(record(pr, 4));
+    for (int more = 1;;) {
+        SPASM_TRY(enqueue_traj_epoch_end(pr, s));   // the selection and the loop control
+        SPASM_TRY(read_more(pr, &pr->d_ctl->t_more, &more));
+        if (!more) break;
+        SPASM_TRY(enqueue_traj_relift(pr, s));
+        SPASM_TRY(enqueue_traj_descent(pr, s));
+    }
+    SPASM_TRY(record(pr, 5));
+    SPASM_TRY(enqueue_finish(pr, s));
+    return record(pr, 6);
+}
 
 spasm_status spasm::enqueue_place(spasm_problem* pr, cudaStream_t s) {
     cudaGraphConditionalHandle h;
@@ -297,6 +351,7 @@ void spasm::drop_graphs(spasm_problem* pr) {
 
 spasm_status spasm::finalize(spasm_problem* pr) {
     if (!pr->place_pending && !pr->traj_pending) return SPASM_OK;
+    Range r("spasm finalize (reads the stage outcome)");
     const bool place = pr->place_pending, traj = pr->traj_pending;
     const int P = pr->sc.P;
     LoopCtl c{};
@@ -374,10 +429,12 @@ spasm_status spasm::prepare_graphs(spasm_problem* pr) {
 extern "C" spasm_status spasm_place(spasm_problem_t pr) {
     if (!pr) return fail(SPASM_ERR_INVALID, "null problem");
     if (pr->sc.kind == kKindP2P) return fail(SPASM_ERR_INVALID, "a point-to-point problem has no stage 1");
+    Range r("spasm_place");
     SPASM_TRY(finalize(pr));   // fold a previous run's counters first
-    SPASM_TRY(prepare_graphs(pr));
+    if (!pr->eager) SPASM_TRY(prepare_graphs(pr));
     if (pr->timing) SPASM_CUDA(cudaEventRecord(pr->ev[0], pr->stream));
-    SPASM_CUDA(cudaGraphLaunch(pr->g_place, pr->stream));
+    if (pr->eager) SPASM_TRY(run_place_eager(pr));
+    else SPASM_CUDA(cudaGraphLaunch(pr->g_place, pr->stream));
     if (pr->timing) SPASM_CUDA(cudaEventRecord(pr->ev[1], pr->stream));
     pr->placed = true;
     pr->place_pending = true;
@@ -389,10 +446,15 @@ extern "C" spasm_status spasm_optimize(spasm_problem_t pr) {
     if (!pr) return fail(SPASM_ERR_INVALID, "null problem");
     if (pr->sc.kind == kKindPack)
         return fail(SPASM_ERR_INVALID, "stage 2 is implemented for the tower goal only; packing runs stage 1 (spasm_place)");
+    Range r("spasm_optimize");
     if (pr->traj_pending) SPASM_TRY(finalize(pr));
     if (!pr->placed) SPASM_TRY(spasm_place(pr));
-    SPASM_TRY(prepare_graphs(pr));
-    SPASM_CUDA(cudaGraphLaunch(pr->g_traj, pr->stream));
+    if (pr->eager) {
+        SPASM_TRY(run_traj_eager(pr));
+    } else {
+        SPASM_TRY(prepare_graphs(pr));
+        SPASM_CUDA(cudaGraphLaunch(pr->g_traj, pr->stream));
+    }
     pr->traj_pending = true;
     pr->traj_timed = pr->timing;
     pr->traj_batched = false;
@@ -403,5 +465,14 @@ extern "C" spasm_status spasm_inject_wait_timeout(spasm_problem_t pr, int max_po
     if (!pr || max_polls < 1 || max_polls > kTablePolls) return fail(SPASM_ERR_INVALID, "need 1 <= max_polls <= 2^22");
     k_wait_timeout<<<1, 32, 0, pr->stream>>>(max_polls, pr->d_err);
     SPASM_CUDA(cudaGetLastError());
+    return SPASM_OK;
+}
+
+extern "C" spasm_status spasm_set_launch_mode(spasm_problem_t pr, int mode) {
+    if (!pr) return fail(SPASM_ERR_INVALID, "null problem");
+    if (mode != SPASM_LAUNCH_GRAPH && mode != SPASM_LAUNCH_EAGER)
+        return fail(SPASM_ERR_INVALID, "mode must be SPASM_LAUNCH_GRAPH or SPASM_LAUNCH_EAGER");
+    SPASM_TRY(finalize(pr));
+    pr->eager = mode == SPASM_LAUNCH_EAGER;
     return SPASM_OK;
 }

@@ -18,11 +18,12 @@ struct LoopCtl {
     uint32_t attempt;     // stage 1: attempts done
     int steps;            // stage 1: gradient steps spent
     int n_place;          // satisfying placements kept, min(count, P); 0 until stage 1 ends
-    int place_pad;
+    int more;             // stage 1 run attempt by attempt from the host (the eager launch mode): 1 while
+                          // another attempt is due
     uint32_t t_attempt;   // stage 2: attempts done
     int t_steps;          // stage 2: gradient steps spent
     int found;            // stage 2: solutions kept, min(count, P); 0 until stage 2 ends
-    int t_more;           // stage 2 run attempt by attempt from the host (the solver service): 1 while
+    int t_more;           // stage 2 run attempt by attempt from the host (the service, the eager mode): 1 while
                           // another attempt is due
     uint64_t seed;        // the Philox key of both stages' draws (the problem's seed)
 };

@@ -4,6 +4,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "spasm.h"
 #include "check64.h"
 #include "launch_s2.h"
@@ -60,6 +62,8 @@ struct spasm_problem {
     bool place_timed = false;     // the pending stage-1 run is bracketed by ev[0], ev[1]
     bool traj_timed = false;      // the pending stage-2 run recorded ev[2..6]
     bool traj_batched = false;    // its first trajectory launch was shared with other problems
+    bool eager = false;           // spasm_place / spasm_optimize launch kernel by kernel, the attempt
+                                  // loops on the host (the same kernels and order as the graphs)
     std::vector<double> host_cub, host_osph;
     // FP64 final check
     spasm::Scalars64 s64;
@@ -76,6 +80,15 @@ struct spasm_problem {
 namespace spasm {
 
 inline void count_launches(spasm_problem* pr, int n) { pr->stats.kernel_launches += n; }
+
+// A named range on the host timeline of profilers (NVTX push/pop) for the life of the object;
+// free when no profiler is attached.
+struct Range {
+    explicit Range(const char* name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+    Range(const Range&) = delete;
+    Range& operator=(const Range&) = delete;
+};
 
 inline float ev_ms(cudaEvent_t a, cudaEvent_t b) {
     float ms = 0.f;
@@ -143,5 +156,9 @@ spasm_status finalize(spasm_problem* pr);
 spasm_status prepare_graphs(spasm_problem* pr);
 // Destroys the stage graphs.
 void drop_graphs(spasm_problem* pr);
+// The eager mode's stage runs on the problem's stream: the graphs' kernels in the same order,
+// the attempt loops on the host (one wait per attempt).
+spasm_status run_place_eager(spasm_problem* pr);
+spasm_status run_traj_eager(spasm_problem* pr);
 
 }  // namespace spasm

@@ -139,6 +139,7 @@ void scheduler_loop(spasm_server* sv) {
             }
         }
         // new requests: problem, stage 1 (device-side attempt loop), first lift
+        Range epoch_range("spasm service epoch");
         for (auto& r : admitted) {
             int status = spasm_create_problem(&r->robot, &r->obs, &r->goal, &r->prm, st, &r->pr);
             if (status == SPASM_OK) status = spasm_place(r->pr);

@@ -30,7 +30,8 @@ EXPORTED = ["spasm_create_problem", "spasm_destroy_problem", "spasm_last_error",
             "spasm_optimize_batch", "spasm_batch_autotune", "spasm_create_packing", "spasm_placements",
             "spasm_create_p2p", "spasm_traj_check", "spasm_fp32_fma_peak", "spasm_synchronize",
             "spasm_inject_wait_timeout", "spasm_inject_alloc_failure", "spasm_problem_bytes", "spasm_server_cancel",
-            "spasm_server_get_stats", "spasm_set_kernel_config"]
+            "spasm_server_get_stats", "spasm_set_kernel_config", "spasm_set_launch_mode"]
+SPASM_LAUNCH_GRAPH, SPASM_LAUNCH_EAGER = 0, 1
 
 
 class SpasmError(RuntimeError):
@@ -133,6 +134,7 @@ def lib():
         L.spasm_fp32_fma_peak.argtypes = [ctypes.c_double, _D, _D, _D]
         L.spasm_synchronize.argtypes = [_V]
         L.spasm_set_kernel_config.argtypes = [_V, ctypes.POINTER(_KernelConfig)]
+        L.spasm_set_launch_mode.argtypes = [_V, ctypes.c_int]
         L.spasm_problem_bytes.argtypes = [ctypes.POINTER(_Obstacles), ctypes.POINTER(_Goal), ctypes.POINTER(_Params),
                                           ctypes.POINTER(ctypes.c_longlong)]
         L.spasm_inject_wait_timeout.argtypes = [_V, ctypes.c_int]
@@ -414,6 +416,11 @@ def spasm_batch_default_config() -> dict:
 def spasm_set_kernel_config(problem: Problem, sphere_tiling: int = 0, particles_per_cta: int = 1):
     c = _KernelConfig(int(sphere_tiling), int(particles_per_cta))
     _check(lib().spasm_set_kernel_config(problem.handle, ctypes.byref(c)))
+
+
+def spasm_set_launch_mode(problem: Problem, mode: int):
+    """SPASM_LAUNCH_GRAPH (default) or SPASM_LAUNCH_EAGER (kernel by kernel, host attempt loop)."""
+    _check(lib().spasm_set_launch_mode(problem.handle, int(mode)))
 
 
 def spasm_optimize_batch(problems, stream=None, config: Optional[dict] = None):

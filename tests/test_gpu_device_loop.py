@@ -90,3 +90,43 @@ def test_stage2_retries_match_oracle():
         assert r["n_found"] == 0
     finally:
         pr.close()
+
+
+def _solve(S, wl, eager, place_only=False):
+    pr = S.Problem(wl)
+    try:
+        if eager:
+            S.spasm_set_launch_mode(pr, S.SPASM_LAUNCH_EAGER)
+        S.spasm_reset_stats(pr)
+        if place_only:
+            S.spasm_place(pr)
+            out = S.spasm_placements(pr, allow_empty=True)
+        else:
+            S.spasm_optimize(pr)
+            out = S.spasm_result(pr, allow_empty=True)
+        return out, S.spasm_get_stats(pr)
+    finally:
+        pr.close()
+
+
+@pytest.mark.parametrize("case", ["tower4", "cap", "retries", "p2p", "tetris5"])
+def test_eager_mode_gives_the_same_bits_as_the_graphs(case):
+    """The eager launch mode runs the graphs' kernels one at a time with the attempt loops on
+    the host: the same results and counters, one host wait per attempt and stage."""
+    S = _S()
+    wl = {"tower4": lambda: scenes.make_problem("tower4", seed=3, Q=256, N=1024, M=256),
+          "cap": lambda: scenes.make_problem("tower4", seed=1, B=2, O=6, W=6, N=512, M=128, eps=1e-9, max_steps=100),
+          "retries": lambda: scenes.make_problem("tower1", seed=2, Q=8, P=4, eps_start=1e-30, max_steps=150),
+          "p2p": lambda: scenes.make_p2p("p2p", seed=4, Q=64),
+          "tetris5": lambda: scenes.make_packing("tetris5", seed=5, N=2048, M=512)}[case]()
+    place_only = case == "tetris5"
+    g, sg = _solve(S, wl, False, place_only)
+    e, se = _solve(S, wl, True, place_only)
+    assert g.keys() == e.keys()
+    for key in g:
+        assert np.array_equal(np.asarray(g[key]), np.asarray(e[key])), key
+    for key in ("place_attempts", "traj_attempts", "particle_iters", "kernel_launches", "n_found", "n_success"):
+        assert sg[key] == se[key], (key, sg[key], se[key])
+    # the eager mode adds one wait per attempt of each stage to the result read's waits
+    stage2 = 0 if place_only else max(se["traj_attempts"], 1)
+    assert se["host_waits"] - sg["host_waits"] == se["place_attempts"] + stage2, (sg, se)
