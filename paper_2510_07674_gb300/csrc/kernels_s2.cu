@@ -1073,42 +1073,41 @@ __device__ __forceinline__ void traj_particle(const Scalars& sc, int p, int mode
     if (tid == 0) sh.mu = (fresh || !io.mu) ? sc.mu0 : io.mu[p];
     grp_sync<kPpc>();
 
-    if (mode == kTrajDescend) {
-        const int K = io.k_steps;
-        for (int k = 1; k <= K; ++k) {
-            traj_evaluate<kP2P, kTile, kPpc>(sc, ls, cub, osph, aabb, sh, sp, q, G_arm, G_blk, disp, cblk, cgap, ccand, true,
-                                n_tests,
-                                n_cull, n_cand);
-            const float eta = sc.eta_traj * (1.f - (float)k / (float)K);
-            // q <- clamp(q - eta g) per configuration, and the bound on how far its spheres moved
-            for (int t = 1 + tid; t < C; t += kTThreads) {
-                float4* qv = reinterpret_cast<float4*>(q + t * 8);
-                const float4* gv = reinterpret_cast<const float4*>(G_blk + t * 8);
-                const float4 qa = qv[0], qb = qv[1], ga = gv[0], gb = gv[1];
-                const float old[7] = {qa.x, qa.y, qa.z, qa.w, qb.x, qb.y, qb.z};
-                const float g[7] = {ga.x, ga.y, ga.z, ga.w, gb.x, gb.y, gb.z};
-                float nw[7], moved = 0.f;
-#pragma unroll
-                for (int j = 0; j < 7; ++j) {
-                    const float v = old[j] - eta * g[j];
-                    nw[j] = fminf(fmaxf(v, sc.qlo[j]), sc.qhi[j]);
-                    moved += fabsf(nw[j] - old[j]) * sc.sweep[j];
-                }
-                qv[0] = make_float4(nw[0], nw[1], nw[2], nw[3]);
-                qv[1] = make_float4(nw[4], nw[5], nw[6], qb.w);
-                disp[t] += moved * 1.0001f + 1e-7f;
-            }
-            if (sc.K_al > 0 && k % sc.K_al == 0) {
-                for (int r = tid; r < NR; r += kTThreads) sh.lam[r] += sh.mu * residual_sqrt_weight(sc, r) * sh.h[r];
-                grp_sync<kPpc>();
-                if (tid == 0) sh.mu = fminf(sh.mu * 2.f, sc.mu_max);
-            }
-            grp_sync<kPpc>();
-        }
-    }
+    // K descent iterations (evaluation with gradient, update), then the final evaluation: one
+    // call site of traj_evaluate, so that its code is inlined once
     const bool want_grad = mode == kTrajEval && io.grad != nullptr;
-    traj_evaluate<kP2P, kTile, kPpc>(sc, ls, cub, osph, aabb, sh, sp, q, G_arm, G_blk, disp, cblk, cgap, ccand, want_grad, n_tests,
-                        n_cull, n_cand);
+    const int K = mode == kTrajDescend ? io.k_steps : 0;
+    for (int k = 1;; ++k) {
+        const bool last = k > K;
+        traj_evaluate<kP2P, kTile, kPpc>(sc, ls, cub, osph, aabb, sh, sp, q, G_arm, G_blk, disp, cblk, cgap, ccand,
+                                         last ? want_grad : true, n_tests, n_cull, n_cand);
+        if (last) break;
+        const float eta = sc.eta_traj * (1.f - (float)k / (float)K);
+        // q <- clamp(q - eta g) per configuration, and the bound on how far its spheres moved
+        for (int t = 1 + tid; t < C; t += kTThreads) {
+            float4* qv = reinterpret_cast<float4*>(q + t * 8);
+            const float4* gv = reinterpret_cast<const float4*>(G_blk + t * 8);
+            const float4 qa = qv[0], qb = qv[1], ga = gv[0], gb = gv[1];
+            const float old[7] = {qa.x, qa.y, qa.z, qa.w, qb.x, qb.y, qb.z};
+            const float g[7] = {ga.x, ga.y, ga.z, ga.w, gb.x, gb.y, gb.z};
+            float nw[7], moved = 0.f;
+#pragma unroll
+            for (int j = 0; j < 7; ++j) {
+                const float v = old[j] - eta * g[j];
+                nw[j] = fminf(fmaxf(v, sc.qlo[j]), sc.qhi[j]);
+                moved += fabsf(nw[j] - old[j]) * sc.sweep[j];
+            }
+            qv[0] = make_float4(nw[0], nw[1], nw[2], nw[3]);
+            qv[1] = make_float4(nw[4], nw[5], nw[6], qb.w);
+            disp[t] += moved * 1.0001f + 1e-7f;
+        }
+        if (sc.K_al > 0 && k % sc.K_al == 0) {
+            for (int r = tid; r < NR; r += kTThreads) sh.lam[r] += sh.mu * residual_sqrt_weight(sc, r) * sh.h[r];
+            grp_sync<kPpc>();
+            if (tid == 0) sh.mu = fminf(sh.mu * 2.f, sc.mu_max);
+        }
+        grp_sync<kPpc>();
+    }
     if (io.tests && (threadIdx.x & 31) == 0) {
         atomicAdd(io.tests, n_tests);
         atomicAdd(io.tests + 1, n_cull);
