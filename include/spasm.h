@@ -31,6 +31,7 @@
  */
 #ifndef SPASM_H
 #define SPASM_H
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -280,6 +281,25 @@ spasm_status spasm_traj_check(spasm_problem_t problem, int n, const float* q, do
  * overlap on the GPU race and must be serialised by the caller. */
 spasm_status spasm_place_select_static(spasm_problem_t problem, int n, uint32_t attempt, int m, float* x_elite,
                                        float* cost_elite);
+
+/* ---- checkpoint / resume (not in the paper: bookkeeping of this library) ----
+ * A snapshot holds a problem's search state as its last completed stage left it: the Philox
+ * key, the attempt and step counters of both stages, the stage-1 outcome (count and the best
+ * P placements) and the returned solutions (count, P x C configurations, ranking costs, FP64
+ * success flags), behind a header with the problem's kind and sizes, a digest of its
+ * obstacle set and a digest of the payload.  The trajectory particles themselves are not
+ * kept.  spasm_snapshot_bytes gives the size for this problem.  spasm_snapshot writes one to
+ * caller memory (host, at least that many bytes; completes the pending stages first and
+ * synchronises).  spasm_restore loads one into a problem created from the same inputs (the
+ * library checks the kind, the sizes and the obstacle digest; SPASM_ERR_INVALID otherwise, and
+ * for a truncated or corrupted snapshot, leaving the problem as it was); afterwards
+ * spasm_placements / spasm_result return what the snapshotted problem returned, and after a
+ * snapshot taken between the stages spasm_optimize runs stage 2 only, from the restored
+ * placements with the restored key, and returns the solutions the uninterrupted solve
+ * returns.  Synchronises. */
+spasm_status spasm_snapshot_bytes(spasm_problem_t problem, size_t* bytes);
+spasm_status spasm_snapshot(spasm_problem_t problem, void* host, size_t bytes);
+spasm_status spasm_restore(spasm_problem_t problem, const void* host, size_t bytes);
 
 /* ---- run control and statistics (not in the paper: bookkeeping of this library) ---- */
 

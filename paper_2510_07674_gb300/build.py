@@ -16,7 +16,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(os.path.dirname(PKG), "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libspasm.so")
-SOURCES = ["api.cu", "driver.cu", "kernels_s1.cu", "kernels_s2.cu", "kernels_lift.cu", "check64.cu", "noalloc.cu", "server.cu", "batch.cu", "peak.cu"]
+SOURCES = ["api.cu", "driver.cu", "kernels_s1.cu", "kernels_s2.cu", "kernels_lift.cu", "check64.cu", "noalloc.cu", "server.cu", "batch.cu", "peak.cu", "snapshot.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE]
 

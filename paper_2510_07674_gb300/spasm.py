@@ -30,7 +30,8 @@ EXPORTED = ["spasm_create_problem", "spasm_destroy_problem", "spasm_last_error",
             "spasm_optimize_batch", "spasm_batch_autotune", "spasm_create_packing", "spasm_placements",
             "spasm_create_p2p", "spasm_traj_check", "spasm_fp32_fma_peak", "spasm_synchronize",
             "spasm_inject_wait_timeout", "spasm_inject_alloc_failure", "spasm_problem_bytes", "spasm_server_cancel",
-            "spasm_server_get_stats", "spasm_set_kernel_config", "spasm_set_launch_mode"]
+            "spasm_server_get_stats", "spasm_set_kernel_config", "spasm_set_launch_mode",
+            "spasm_snapshot_bytes", "spasm_snapshot", "spasm_restore"]
 SPASM_LAUNCH_GRAPH, SPASM_LAUNCH_EAGER = 0, 1
 
 
@@ -135,6 +136,9 @@ def lib():
         L.spasm_synchronize.argtypes = [_V]
         L.spasm_set_kernel_config.argtypes = [_V, ctypes.POINTER(_KernelConfig)]
         L.spasm_set_launch_mode.argtypes = [_V, ctypes.c_int]
+        L.spasm_snapshot_bytes.argtypes = [_V, ctypes.POINTER(ctypes.c_size_t)]
+        L.spasm_snapshot.argtypes = [_V, _V, ctypes.c_size_t]
+        L.spasm_restore.argtypes = [_V, _V, ctypes.c_size_t]
         L.spasm_problem_bytes.argtypes = [ctypes.POINTER(_Obstacles), ctypes.POINTER(_Goal), ctypes.POINTER(_Params),
                                           ctypes.POINTER(ctypes.c_longlong)]
         L.spasm_inject_wait_timeout.argtypes = [_V, ctypes.c_int]
@@ -421,6 +425,25 @@ def spasm_set_kernel_config(problem: Problem, sphere_tiling: int = 0, particles_
 def spasm_set_launch_mode(problem: Problem, mode: int):
     """SPASM_LAUNCH_GRAPH (default) or SPASM_LAUNCH_EAGER (kernel by kernel, host attempt loop)."""
     _check(lib().spasm_set_launch_mode(problem.handle, int(mode)))
+
+
+def spasm_snapshot_bytes(problem: Problem) -> int:
+    n = ctypes.c_size_t()
+    _check(lib().spasm_snapshot_bytes(problem.handle, ctypes.byref(n)))
+    return n.value
+
+
+def spasm_snapshot(problem: Problem) -> bytes:
+    """The problem's search state after its last stage (see spasm_restore)."""
+    n = spasm_snapshot_bytes(problem)
+    buf = ctypes.create_string_buffer(n)
+    _check(lib().spasm_snapshot(problem.handle, buf, n))
+    return buf.raw
+
+
+def spasm_restore(problem: Problem, snapshot: bytes):
+    buf = ctypes.create_string_buffer(bytes(snapshot), len(snapshot))
+    _check(lib().spasm_restore(problem.handle, buf, len(snapshot)))
 
 
 def spasm_optimize_batch(problems, stream=None, config: Optional[dict] = None):
