@@ -894,7 +894,7 @@ __device__ void traj_evaluate(const Scalars& sc, const LaneSpheres& ls, const fl
         for (int i = 0; i < kTWarps; ++i) c_coll += __shfl_sync(0xffffffffu, pcl, i);
         pm = warp_max(pm);
         float my_D = 0.f, my_e = 0.f;
-        if (!p2p) place_stack_warp(sc, sh.pose, kPlaceForward, nullptr, nullptr, nullptr, sh.ps, my_D, my_e);
+        if (!p2p) place_stack_warp(sc, sh.pose, kPlaceUnit, nullptr, nullptr, nullptr, sh.ps, my_D, my_e);
         const float c_stable = warp_sum(lane < B ? my_D : 0.f);
         const float c_height = warp_sum(lane < B ? my_e * my_e : 0.f);
         const float max_D = warp_max(lane < B ? my_D : 0.f);
@@ -946,8 +946,7 @@ __device__ void traj_evaluate(const Scalars& sc, const LaneSpheres& ls, const fl
         // (c) warp 0: placement gradient w.r.t. the placed poses, then (d) the place configurations'
         // gradient rows; warp 1: grasp gradients
         if (w == 0 && !p2p) {
-            float my_D, my_e;
-            place_stack_warp(sc, sh.pose, kPlaceExplicit, &sh.s[8 * B], &sh.s[7 * B], sh.g4, sh.ps, my_D, my_e);
+            place_stack_grad(sc, sh.ps, &sh.s[8 * B], &sh.s[7 * B], sh.g4);
             const float s_arm = sh.s_arm, s_blk = sh.s_blk, s_coll = sh.s[9 * B];
             for (int i = lane; i < 4 * B; i += 32) {
                 const int kb = i >> 2, c = i & 3;

@@ -25,12 +25,15 @@ struct PlaceScratch {
 };
 
 // Coefficient modes of the gradient: stage-1 cost (a = w_stable, b = 2 w_height e,
-// s_coll = w_coll), or explicit per-residual coefficients (stage 2).
-enum PlaceMode { kPlaceForward = 0, kPlaceStage1 = 1, kPlaceExplicit = 2 };
+// s_coll = w_coll), explicit per-residual coefficients (stage 2), or the residuals with the
+// unit-coefficient support factors (a = 1) left in ps.stab and no gradient written (stage 2
+// scales them by its multipliers once those are known).
+enum PlaceMode { kPlaceForward = 0, kPlaceStage1 = 1, kPlaceExplicit = 2, kPlaceUnit = 3 };
 
 // Per-block terms of the tower (lane i < B owns block i): height residual e_i, support
-// distance D_i and the block cuboids in ps.  With mode != kPlaceForward, sets
-//   g = sum_i a_i dD_i/dx + sum_i b_i de_i/dx   (the collision part is added by the caller).
+// distance D_i and the block cuboids in ps.  With mode kPlaceStage1 or kPlaceExplicit, sets
+//   g = sum_i a_i dD_i/dx + sum_i b_i de_i/dx   (the collision part is added by the caller);
+// with kPlaceUnit, leaves dD_i/d(centre of mass, yaw) in ps.stab for place_stack_grad.
 // x, g: per-warp shared arrays of 4B floats.  Must be called by all 32 lanes of the warp.
 __device__ __forceinline__ void place_stack_warp(const Scalars& sc, const float* x, int mode, const float* a_in,
                                                  const float* b_in, float* g, PlaceScratch& ps, float& my_D,
@@ -56,7 +59,7 @@ __device__ __forceinline__ void place_stack_warp(const Scalars& sc, const float*
             const float ex = fmaxf(fabsf(ux) - sc.half[i].x, 0.f), ey = fmaxf(fabsf(uy) - sc.half[i].y, 0.f);
             my_D = sqrtf(ex * ex + ey * ey);
             if (want_grad && my_D > 0.f) {
-                const float a = mode == kPlaceStage1 ? sc.w_stable : a_in[i];
+                const float a = mode == kPlaceStage1 ? sc.w_stable : mode == kPlaceUnit ? 1.f : a_in[i];
                 const float du_x = (ux >= 0.f ? ex : -ex) / my_D, du_y = (uy >= 0.f ? ey : -ey) / my_D;
                 dvx = a * (c * du_x - s * du_y);
                 dvy = a * (s * du_x + c * du_y);
@@ -67,7 +70,7 @@ __device__ __forceinline__ void place_stack_warp(const Scalars& sc, const float*
         ps.D[i] = my_D;
     }
     __syncwarp();
-    if (want_grad && lane < B) {
+    if (want_grad && mode != kPlaceUnit && lane < B) {
         const int i = lane;
         float gx = -ps.stab[i][0], gy = -ps.stab[i][1];
         for (int k = 0; k < i; ++k) {
@@ -77,6 +80,25 @@ __device__ __forceinline__ void place_stack_warp(const Scalars& sc, const float*
         }
         const float b = mode == kPlaceStage1 ? 2.f * sc.w_height * my_e : b_in[i];
         g[4 * i] = gx; g[4 * i + 1] = gy; g[4 * i + 2] = b; g[4 * i + 3] = ps.stab[i][2];
+    }
+    __syncwarp();
+}
+
+// The gradient place_stack_warp writes in mode kPlaceExplicit, from the factors its kPlaceUnit
+// pass left in ps (a_i dD_i/d... = a_i times the unit factor, in the same order of operations).
+__device__ __forceinline__ void place_stack_grad(const Scalars& sc, const PlaceScratch& ps, const float* a_in,
+                                                 const float* b_in, float* g) {
+    const int lane = threadIdx.x & 31;
+    const int B = sc.B;
+    if (lane < B) {
+        const int i = lane;
+        float gx = -(a_in[i] * ps.stab[i][0]), gy = -(a_in[i] * ps.stab[i][1]);
+        for (int k = 0; k < i; ++k) {
+            const float inv = 1.f / (float)(B - 1 - k);
+            gx += (a_in[k] * ps.stab[k][0]) * inv;
+            gy += (a_in[k] * ps.stab[k][1]) * inv;
+        }
+        g[4 * i] = gx; g[4 * i + 1] = gy; g[4 * i + 2] = b_in[i]; g[4 * i + 3] = a_in[i] * ps.stab[i][2];
     }
     __syncwarp();
 }
