@@ -65,8 +65,9 @@ struct TShared {
     float pose[4 * kMaxB];   // placed poses (x, y, z, yaw)
     float g4[4 * kMaxB];     // dL/d(placed pose)
     float h[kMaxNR], lam[kMaxNR], s[kMaxNR];
+    float sw[kMaxNR];          // sqrt of each residual's weight, set once per launch
     float extra[2 * kMaxB][8];   // gradient rows of grasp (b) and place (B + b) configurations
-    float coef_a[kMaxB], coef_b[kMaxB];
+    float rpt[2 * kMaxB][6];   // (w_roll, w_pitch) of the grasp (b) and place (B + b) block frames, from the residual pass
     float pg[kTWarps][kMaxB][4];   // dC_coll/d(placed pose j), sphere side, per warp
     float pgc[kMaxB][4];           // dC_coll/d(placed pose i), cuboid side of block pairs
     PlaceScratch ps;
@@ -575,28 +576,33 @@ __device__ __forceinline__ bool chunk_collisions(const Scalars& sc, const LaneSp
 }
 
 // Residuals of the start group at the grasp (which = 0) or place (which = 1) configuration
-// of block b from that configuration's frames, and, with s_r != nullptr, their weighted
-// joint gradient sum_r s_r dh_r/dq (plus the placed-pose gradient g4 at a place config).
+// of block b from that configuration's frames (s_r == nullptr; the roll and pitch torques go
+// to rpt), or, with s_r, their weighted joint gradient sum_r s_r dh_r/dq (plus the placed-pose
+// gradient g4 at a place config) from the torques the residual pass left in rpt.
 __device__ __forceinline__ void start_terms(const Scalars& sc, int b, int which, const SpecialFrames& sf, float* h_out,
-                                            const float* s_r, float grad_out[7], const float* g4 /*4 or null*/) {
+                                            const float* s_r, float grad_out[7], const float* g4 /*4 or null*/,
+                                            float rpt[6]) {
     float Rb[9], pb[3];
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
         Rb[3 * r] = sf.H[r].x; Rb[3 * r + 1] = sf.H[r].y; Rb[3 * r + 2] = sf.H[r].z; pb[r] = sf.H[r].w;
     }
-    float roll, pitch, wr[3], wp[3];
-    roll_pitch_torque<float>(Rb, roll, pitch, wr, wp);
-    if (which == 0) {
-        h_out[0] = pb[0] - sc.init[b].x;
-        h_out[1] = pb[1] - sc.init[b].y;
-        h_out[2] = pb[2] - sc.init[b].z;
-        h_out[3] = roll;
-        h_out[4] = pitch;
-    } else {
-        h_out[0] = roll;
-        h_out[1] = pitch;
+    if (!s_r) {
+        float roll, pitch;
+        roll_pitch_torque<float>(Rb, roll, pitch, rpt, rpt + 3);
+        if (which == 0) {
+            h_out[0] = pb[0] - sc.init[b].x;
+            h_out[1] = pb[1] - sc.init[b].y;
+            h_out[2] = pb[2] - sc.init[b].z;
+            h_out[3] = roll;
+            h_out[4] = pitch;
+        } else {
+            h_out[0] = roll;
+            h_out[1] = pitch;
+        }
+        return;
     }
-    if (!s_r) return;
+    const float wr[3] = {rpt[0], rpt[1], rpt[2]}, wp[3] = {rpt[3], rpt[4], rpt[5]};
     // wrench at the block frame: force F (on p_blk), torque M (about the world origin)
     float F[3] = {0, 0, 0}, M[3] = {0, 0, 0};
     if (which == 0) {
@@ -912,8 +918,9 @@ __device__ void traj_evaluate(const Scalars& sc, const LaneSpheres& ls, const fl
             sh.pm_pen = pm; sh.pm_D = max_D; sh.pm_dz = max_dz;
         }
     } else if (w == 1 && lane < B) {
-        start_terms(sc, lane, 0, sp[2 * lane], &sh.h[5 * lane], nullptr, nullptr, nullptr);
-        if (!p2p) start_terms(sc, lane, 1, sp[2 * lane + 1], &sh.h[5 * B + 2 * lane], nullptr, nullptr, nullptr);
+        start_terms(sc, lane, 0, sp[2 * lane], &sh.h[5 * lane], nullptr, nullptr, nullptr, sh.rpt[lane]);
+        if (!p2p)
+            start_terms(sc, lane, 1, sp[2 * lane + 1], &sh.h[5 * B + 2 * lane], nullptr, nullptr, nullptr, sh.rpt[B + lane]);
         else sh.h[5 * B + 2 * lane] = sh.h[5 * B + 2 * lane + 1] = 0.f;
     }
     grp_sync<kPpc>();
@@ -930,7 +937,7 @@ __device__ void traj_evaluate(const Scalars& sc, const LaneSpheres& ls, const fl
         const float m_start = warp_max(v_start), m_tilt = warp_max(v_tilt);
         float Lp = 0.f;
         for (int r = lane; r < NR; r += 32) {
-            const float sw = residual_sqrt_weight(sc, r), hw = sw * sh.h[r];
+            const float sw = sh.sw[r], hw = sw * sh.h[r];
             Lp += sh.lam[r] * hw + 0.5f * sh.mu * hw * hw;
             sh.s[r] = (sh.lam[r] + sh.mu * hw) * sw;
         }
@@ -962,13 +969,11 @@ __device__ void traj_evaluate(const Scalars& sc, const LaneSpheres& ls, const fl
             __syncwarp();
             // (d) place configurations: tilt residuals and the placed-pose gradient through fk
             if (lane < B) {
-                float hbuf[5];
-                start_terms(sc, lane, 1, sp[2 * lane + 1], hbuf, &sh.s[5 * B + 2 * lane], sh.extra[B + lane],
-                            &sh.g4[4 * lane]);
+                start_terms(sc, lane, 1, sp[2 * lane + 1], nullptr, &sh.s[5 * B + 2 * lane], sh.extra[B + lane],
+                            &sh.g4[4 * lane], sh.rpt[B + lane]);
             }
         } else if (w == 1 && lane < B) {
-            float hbuf[5];
-            start_terms(sc, lane, 0, sp[2 * lane], hbuf, &sh.s[5 * lane], sh.extra[lane], nullptr);
+            start_terms(sc, lane, 0, sp[2 * lane], nullptr, &sh.s[5 * lane], sh.extra[lane], nullptr, sh.rpt[lane]);
         }
         grp_sync<kPpc>();
     }
@@ -1068,7 +1073,10 @@ __device__ __forceinline__ void traj_particle(const Scalars& sc, int p, int mode
     unsigned long long n_tests = 0, n_cull = 0, n_cand = 0;
     const LaneSpheres ls = lane_spheres<kTile>(sc);
     const bool fresh = mode == kTrajDescend && io.init_multipliers;
-    for (int r = tid; r < NR; r += kTThreads) sh.lam[r] = (fresh || !io.lam) ? 0.f : io.lam[(size_t)p * NR + r];
+    for (int r = tid; r < NR; r += kTThreads) {
+        sh.lam[r] = (fresh || !io.lam) ? 0.f : io.lam[(size_t)p * NR + r];
+        sh.sw[r] = residual_sqrt_weight(sc, r);
+    }
     if (tid == 0) sh.mu = (fresh || !io.mu) ? sc.mu0 : io.mu[p];
     grp_sync<kPpc>();
 
@@ -1101,7 +1109,7 @@ __device__ __forceinline__ void traj_particle(const Scalars& sc, int p, int mode
             disp[t] += moved * 1.0001f + 1e-7f;
         }
         if (sc.K_al > 0 && k % sc.K_al == 0) {
-            for (int r = tid; r < NR; r += kTThreads) sh.lam[r] += sh.mu * residual_sqrt_weight(sc, r) * sh.h[r];
+            for (int r = tid; r < NR; r += kTThreads) sh.lam[r] += sh.mu * sh.sw[r] * sh.h[r];
             grp_sync<kPpc>();
             if (tid == 0) sh.mu = fminf(sh.mu * 2.f, sc.mu_max);
         }
