@@ -978,36 +978,63 @@ __device__ void traj_evaluate(const Scalars& sc, const LaneSpheres& ls, const fl
         grp_sync<kPpc>();
     }
 
-    // (4) path length, joint limits; assemble the gradient into G_blk
+    // (4) path length, joint limits; assemble the gradient into G_blk: a configuration per
+    // thread (its own, previous and next rows as float4 pairs)
     float path = 0.f, jl = 0.f;
-    for (int i = tid; i < C * 7; i += kTThreads) {
-        const int t = i / 7, j = i % 7;
-        const float v = q[t * 8 + j];
-        float gsum = 0.f;
+    for (int t = tid; t < C; t += kTThreads) {
+        const float4* qv = reinterpret_cast<const float4*>(q + t * 8);
+        const float4 a0 = qv[0], a1 = qv[1];
+        const float v[7] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z};
+        float nx[7] = {0, 0, 0, 0, 0, 0, 0}, pv[7] = {0, 0, 0, 0, 0, 0, 0};
         if (t + 1 < C) {
-            const float d = q[(t + 1) * 8 + j] - v;
-            path += d * d;
-            gsum -= 2.f * sc.w_path * d;
+            const float4 b0 = qv[2], b1 = qv[3];
+            nx[0] = b0.x; nx[1] = b0.y; nx[2] = b0.z; nx[3] = b0.w; nx[4] = b1.x; nx[5] = b1.y; nx[6] = b1.z;
         }
         if (t > 0) {
-            const float d = v - q[(t - 1) * 8 + j];
-            gsum += 2.f * sc.w_path * d;
-            const float over = fmaxf(v - sc.qhi[j], 0.f), under = fmaxf(sc.qlo[j] - v, 0.f);
-            jl += over * over + under * under;
-            gsum += sc.w_jl * (2.f * over - 2.f * under);
+            const float4 c0 = qv[-2], c1 = qv[-1];
+            pv[0] = c0.x; pv[1] = c0.y; pv[2] = c0.z; pv[3] = c0.w; pv[4] = c1.x; pv[5] = c1.y; pv[6] = c1.z;
+        }
+        float g[8];
+#pragma unroll
+        for (int j = 0; j < 7; ++j) {
+            float gsum = 0.f;
+            if (t + 1 < C) {
+                const float d = nx[j] - v[j];
+                path += d * d;
+                gsum -= 2.f * sc.w_path * d;
+            }
+            if (t > 0) {
+                const float d = v[j] - pv[j];
+                gsum += 2.f * sc.w_path * d;
+                const float over = fmaxf(v[j] - sc.qhi[j], 0.f), under = fmaxf(sc.qlo[j] - v[j], 0.f);
+                jl += over * over + under * under;
+                gsum += sc.w_jl * (2.f * over - 2.f * under);
+            }
+            g[j] = gsum;
         }
         if (grad) {
+            float4* gv = reinterpret_cast<float4*>(G_blk + t * 8);
             if (t == 0) {
-                gsum = 0.f;
+                gv[0] = make_float4(0.f, 0.f, 0.f, 0.f);
+                gv[1] = make_float4(0.f, 0.f, 0.f, 0.f);
             } else {
-                gsum += sh.s_arm * G_arm[t * 8 + j] + sh.s_blk * G_blk[t * 8 + j];
+                const float4* av = reinterpret_cast<const float4*>(G_arm + t * 8);
+                const float4 p0 = av[0], p1 = av[1], r0 = gv[0], r1 = gv[1];
+                const float ga[7] = {p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z};
+                const float gb[7] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z};
+                const float* ex = nullptr;
                 if (t % S == 0) {
                     const int e = t / S - 1;   // t = (e+1) S: grasp of block e/2 (e even) or place (e odd)
-                    const int bb = e >> 1;
-                    gsum += (e & 1) ? sh.extra[B + bb][j] : sh.extra[bb][j];
+                    ex = (e & 1) ? sh.extra[B + (e >> 1)] : sh.extra[e >> 1];
                 }
+#pragma unroll
+                for (int j = 0; j < 7; ++j) {
+                    g[j] += sh.s_arm * ga[j] + sh.s_blk * gb[j];
+                    if (ex) g[j] += ex[j];
+                }
+                gv[0] = make_float4(g[0], g[1], g[2], g[3]);   // G_blk becomes the assembled gradient
+                gv[1] = make_float4(g[4], g[5], g[6], 0.f);
             }
-            G_blk[t * 8 + j] = gsum;   // G_blk becomes the assembled gradient
         }
     }
     path = warp_sum(path);
