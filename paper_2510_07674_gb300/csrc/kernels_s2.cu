@@ -1048,7 +1048,8 @@ __device__ void traj_evaluate(const Scalars& sc, const LaneSpheres& ls, const fl
         sh.jl = l;
         sh.L += sc.w_path * p + sc.w_jl * l;
     }
-    grp_sync<kPpc>();
+    // no barrier: the assembled gradient was complete at the one above, and only thread 0
+    // reads sh.path, sh.jl and sh.L before the next one
 }
 
 // One particle of the trajectory stage by the whole CTA: load its state, run the descent (or
