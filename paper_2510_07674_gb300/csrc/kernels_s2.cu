@@ -80,6 +80,7 @@ struct TShared {
     // candidate-free ones to cull again): active[tier][32g + i] for group g
     short active[kChunk + 1][(kMaxC + kChunk - 1) / kChunk];
     short n_group[kChunk + 1][kTWarps];
+    unsigned skip[kTWarps];       // bit i of word g: chunk 32g + i kept its cached cull this evaluation
     float blk_cum[kMaxB];         // [k]: running bound on how far the placed blocks 0..k have moved, summed
     int pose_prev_ok;
     float c_arm, c_blk, maxpen, c_coll, c_stable, c_height, c_start;
@@ -803,8 +804,8 @@ __device__ void traj_evaluate(const Scalars& sc, const LaneSpheres& ls, const fl
     // motion since below its clearances).  Warp g lists those of chunks
     // 32g .. 32g+31 in chunk order, by tier: the chunks with 4, 3, 2, 1 configurations with
     // candidates at the last cull (tests and the gradient chain), then the candidate-free
-    // chunks to cull again; it zeroes the block-group gradient rows of the skipped ones (their
-    // arm-group rows are still zero from their last cull).  The tiers, in that order, are
+    // chunks to cull again; it marks the skipped ones in sh.skip, whose block-group gradient rows
+    // the assembly reads as zero (their arm-group rows are still zero from their last cull).  The tiers, in that order, are
     // dealt to the warps round-robin, which keeps the per-warp sums deterministic and the
     // warps' shares of the remaining work even.
     static_assert((kMaxC + kChunk - 1) / kChunk <= 32 * kTWarps && (kTWarps & (kTWarps - 1)) == 0,
@@ -831,13 +832,9 @@ __device__ void traj_evaluate(const Scalars& sc, const LaneSpheres& ls, const fl
             if (tier == tr) sh.active[tr][32 * w + __popc(bal & ((1u << lane) - 1u))] = (short)chk;
             if (lane == 0) sh.n_group[tr][w] = (short)__popc(bal);
         }
-        unsigned skipped = __ballot_sync(0xffffffffu, chk < n_chunks && !active);
-        while (grad && skipped) {
-            const int k = 32 * w + __ffs(skipped) - 1;
-            skipped &= skipped - 1;
-            const int tk = 1 + kChunk * k, nk = min(kChunk, C - tk);
-            if (lane < 7 * nk) G_blk[(tk + lane / 7) * 8 + lane % 7] = 0.f;
-        }
+        // skipped chunks: their block-group rows count as zero in the assembly (step 4)
+        const unsigned skipped = __ballot_sync(0xffffffffu, chk < n_chunks && !active);
+        if (lane == 0) sh.skip[w] = skipped;
     }
     grp_sync<kPpc>();
     // warp w takes positions w, w + 8, ... of the concatenated lists, tier by tier, group by group
@@ -1019,7 +1016,10 @@ __device__ void traj_evaluate(const Scalars& sc, const LaneSpheres& ls, const fl
                 gv[1] = make_float4(0.f, 0.f, 0.f, 0.f);
             } else {
                 const float4* av = reinterpret_cast<const float4*>(G_arm + t * 8);
-                const float4 p0 = av[0], p1 = av[1], r0 = gv[0], r1 = gv[1];
+                const int chk = (t - 1) / kChunk;
+                const bool kept = (sh.skip[chk >> 5] >> (chk & 31)) & 1u;   // cached cull: no block-group rows
+                const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+                const float4 p0 = av[0], p1 = av[1], r0 = kept ? z : gv[0], r1 = kept ? z : gv[1];
                 const float ga[7] = {p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z};
                 const float gb[7] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z};
                 const float* ex = nullptr;
