@@ -297,6 +297,10 @@ static spasm_status create_problem_impl(const spasm_robot* robot, const spasm_ob
     sc.w_stable = (float)prm->w_stable; sc.w_height = (float)prm->w_height; sc.w_coll = (float)prm->w_coll;
     sc.w_start = (float)prm->w_start; sc.w_arm = (float)prm->w_arm; sc.w_block = (float)prm->w_block;
     sc.w_path = (float)prm->w_path; sc.w_jl = (float)prm->w_jl;
+    {
+        const float w6[6] = {sc.w_start, sc.w_height, sc.w_stable, sc.w_coll, sc.w_arm, sc.w_block};
+        for (int k = 0; k < 6; ++k) sc.sqw[k] = std::sqrt(w6[k]);   // IEEE float sqrt, as sqrtf on the device
+    }
     sc.mu0 = (float)prm->mu0; sc.mu_max = (float)prm->mu_max; sc.ik_damp = (float)prm->ik_damp;
     sc.ik_mode = prm->ik_mode;
     sc.seed = prm->seed;

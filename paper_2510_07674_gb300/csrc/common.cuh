@@ -54,6 +54,7 @@ struct Scalars {
     // optimiser parameters
     float eta_init, alpha, eta_traj, eps, eps_start;
     float w_stable, w_height, w_coll, w_start, w_arm, w_block, w_path, w_jl;
+    float sqw[6];                    // sqrt of w_start, w_height, w_stable, w_coll, w_arm, w_block (float sqrt)
     float mu0, mu_max, ik_damp;
     int ik_mode;                     // lift IK: 0 damped least squares, 1 analytic (Franka joint layout)
     int sphere_tiling;               // trajectory kernels: sphere items per lane, 0 strided (lane + 32 k),

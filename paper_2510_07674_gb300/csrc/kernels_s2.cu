@@ -65,9 +65,9 @@ struct TShared {
     float pose[4 * kMaxB];   // placed poses (x, y, z, yaw)
     float g4[4 * kMaxB];     // dL/d(placed pose)
     float h[kMaxNR], lam[kMaxNR], s[kMaxNR];
-    float sw[kMaxNR];          // sqrt of each residual's weight, set once per launch
-    float extra[2 * kMaxB][8];   // gradient rows of grasp (b) and place (B + b) configurations
-    float rpt[2 * kMaxB][6];   // (w_roll, w_pitch) of the grasp (b) and place (B + b) block frames, from the residual pass
+    // gradient rows of the grasp (b) and place (B + b) configurations; until the gradient pass
+    // overwrites them, their first 6 floats hold the residual pass's (w_roll, w_pitch) of that block frame
+    float extra[2 * kMaxB][8];
     float pg[kTWarps][kMaxB][4];   // dC_coll/d(placed pose j), sphere side, per warp
     float pgc[kMaxB][4];           // dC_coll/d(placed pose i), cuboid side of block pairs
     PlaceScratch ps;
@@ -78,7 +78,7 @@ struct TShared {
     float pose_prev[4 * kMaxB];   // placed poses of the previous evaluation
     // chunks to evaluate by tier (kChunk .. 1 configurations with candidates at the last cull, then the
     // candidate-free ones to cull again): active[tier][32g + i] for group g
-    short active[kChunk + 1][(kMaxC + kChunk - 1) / kChunk];
+    unsigned char active[kChunk + 1][(kMaxC + kChunk - 1) / kChunk];
     short n_group[kChunk + 1][kTWarps];
     unsigned skip[kTWarps];       // bit i of word g: chunk 32g + i kept its cached cull this evaluation
     float blk_cum[kMaxB];         // [k]: running bound on how far the placed blocks 0..k have moved, summed
@@ -808,6 +808,7 @@ __device__ void traj_evaluate(const Scalars& sc, const LaneSpheres& ls, const fl
     // the assembly reads as zero (their arm-group rows are still zero from their last cull).  The tiers, in that order, are
     // dealt to the warps round-robin, which keeps the per-warp sums deterministic and the
     // warps' shares of the remaining work even.
+    static_assert((kMaxC + kChunk - 1) / kChunk <= 256, "chunk indices fit the byte lists");
     static_assert((kMaxC + kChunk - 1) / kChunk <= 32 * kTWarps && (kTWarps & (kTWarps - 1)) == 0,
                   "one 32-chunk group per warp");
     // motion of the blocks placed before block b: the only placed blocks the configurations of a
@@ -829,7 +830,7 @@ __device__ void traj_evaluate(const Scalars& sc, const LaneSpheres& ls, const fl
 #pragma unroll
         for (int tr = 0; tr <= kChunk; ++tr) {
             const unsigned bal = __ballot_sync(0xffffffffu, tier == tr);
-            if (tier == tr) sh.active[tr][32 * w + __popc(bal & ((1u << lane) - 1u))] = (short)chk;
+            if (tier == tr) sh.active[tr][32 * w + __popc(bal & ((1u << lane) - 1u))] = (unsigned char)chk;
             if (lane == 0) sh.n_group[tr][w] = (short)__popc(bal);
         }
         // skipped chunks: their block-group rows count as zero in the assembly (step 4)
@@ -880,8 +881,32 @@ __device__ void traj_evaluate(const Scalars& sc, const LaneSpheres& ls, const fl
     else if (lane == 0) { sh.warp[w].pc[0] = 0.f; sh.warp[w].pc[1] = 0.f; }
     grp_sync<kPpc>();
 
-    // (3) epilogue.  (a) warp 0: group sums and the placement residuals; warp 1: start residuals
+    // (3) epilogue.  (a) warp 0: the placement residuals; warp 1: the start residuals, grasp
+    // configurations on lanes 0..15 and place configurations on lanes 16..31; warp 2: the group
+    // sums over the warps
     if (w == 0) {
+        float my_D = 0.f, my_e = 0.f;
+        if (!p2p) place_stack_warp(sc, sh.pose, kPlaceUnit, nullptr, nullptr, nullptr, sh.ps, my_D, my_e);
+        const float c_stable = warp_sum(lane < B ? my_D : 0.f);
+        const float c_height = warp_sum(lane < B ? my_e * my_e : 0.f);
+        const float max_D = warp_max(lane < B ? my_D : 0.f);
+        const float max_dz = warp_max(lane < B ? fabsf(my_e) : 0.f);
+        if (lane < B) {
+            sh.h[7 * B + lane] = my_e;
+            sh.h[8 * B + lane] = my_D;
+        }
+        if (lane == 0) { sh.c_stable = c_stable; sh.c_height = c_height; sh.pm_D = max_D; sh.pm_dz = max_dz; }
+    } else if (w == 1) {
+        const int which = lane >> 4, b = lane & 15;
+        if (b < B) {
+            if (which == 0)
+                start_terms(sc, b, 0, sp[2 * b], &sh.h[5 * b], nullptr, nullptr, nullptr, sh.extra[b]);
+            else if (!p2p)
+                start_terms(sc, b, 1, sp[2 * b + 1], &sh.h[5 * B + 2 * b], nullptr, nullptr, nullptr, sh.extra[B + b]);
+            else
+                sh.h[5 * B + 2 * b] = sh.h[5 * B + 2 * b + 1] = 0.f;
+        }
+    } else if (w == 2) {
         const float ca = lane < kTWarps ? sh.warp[lane].part[0] : 0.f;
         const float cb = lane < kTWarps ? sh.warp[lane].part[1] : 0.f;
         float cm = lane < kTWarps ? sh.warp[lane].part[2] : 0.f;
@@ -896,29 +921,13 @@ __device__ void traj_evaluate(const Scalars& sc, const LaneSpheres& ls, const fl
         float c_coll = 0.f;
         for (int i = 0; i < kTWarps; ++i) c_coll += __shfl_sync(0xffffffffu, pcl, i);
         pm = warp_max(pm);
-        float my_D = 0.f, my_e = 0.f;
-        if (!p2p) place_stack_warp(sc, sh.pose, kPlaceUnit, nullptr, nullptr, nullptr, sh.ps, my_D, my_e);
-        const float c_stable = warp_sum(lane < B ? my_D : 0.f);
-        const float c_height = warp_sum(lane < B ? my_e * my_e : 0.f);
-        const float max_D = warp_max(lane < B ? my_D : 0.f);
-        const float max_dz = warp_max(lane < B ? fabsf(my_e) : 0.f);
-        if (lane < B) {
-            sh.h[7 * B + lane] = my_e;
-            sh.h[8 * B + lane] = my_D;
-        }
         if (lane == 0) {
             sh.h[9 * B] = c_coll;
             sh.h[9 * B + 1] = tot_a;
             sh.h[9 * B + 2] = tot_b;
             sh.c_arm = tot_a; sh.c_blk = tot_b; sh.maxpen = cm;
-            sh.c_coll = c_coll; sh.c_stable = c_stable; sh.c_height = c_height;
-            sh.pm_pen = pm; sh.pm_D = max_D; sh.pm_dz = max_dz;
+            sh.c_coll = c_coll; sh.pm_pen = pm;
         }
-    } else if (w == 1 && lane < B) {
-        start_terms(sc, lane, 0, sp[2 * lane], &sh.h[5 * lane], nullptr, nullptr, nullptr, sh.rpt[lane]);
-        if (!p2p)
-            start_terms(sc, lane, 1, sp[2 * lane + 1], &sh.h[5 * B + 2 * lane], nullptr, nullptr, nullptr, sh.rpt[B + lane]);
-        else sh.h[5 * B + 2 * lane] = sh.h[5 * B + 2 * lane + 1] = 0.f;
     }
     grp_sync<kPpc>();
     // (b) objective and dL/dh
@@ -934,7 +943,7 @@ __device__ void traj_evaluate(const Scalars& sc, const LaneSpheres& ls, const fl
         const float m_start = warp_max(v_start), m_tilt = warp_max(v_tilt);
         float Lp = 0.f;
         for (int r = lane; r < NR; r += 32) {
-            const float sw = sh.sw[r], hw = sw * sh.h[r];
+            const float sw = residual_sqrt_weight(sc, r), hw = sw * sh.h[r];
             Lp += sh.lam[r] * hw + 0.5f * sh.mu * hw * hw;
             sh.s[r] = (sh.lam[r] + sh.mu * hw) * sw;
         }
@@ -967,10 +976,10 @@ __device__ void traj_evaluate(const Scalars& sc, const LaneSpheres& ls, const fl
             // (d) place configurations: tilt residuals and the placed-pose gradient through fk
             if (lane < B) {
                 start_terms(sc, lane, 1, sp[2 * lane + 1], nullptr, &sh.s[5 * B + 2 * lane], sh.extra[B + lane],
-                            &sh.g4[4 * lane], sh.rpt[B + lane]);
+                            &sh.g4[4 * lane], sh.extra[B + lane]);
             }
         } else if (w == 1 && lane < B) {
-            start_terms(sc, lane, 0, sp[2 * lane], nullptr, &sh.s[5 * lane], sh.extra[lane], nullptr, sh.rpt[lane]);
+            start_terms(sc, lane, 0, sp[2 * lane], nullptr, &sh.s[5 * lane], sh.extra[lane], nullptr, sh.extra[lane]);
         }
         grp_sync<kPpc>();
     }
@@ -1103,7 +1112,6 @@ __device__ __forceinline__ void traj_particle(const Scalars& sc, int p, int mode
     const bool fresh = mode == kTrajDescend && io.init_multipliers;
     for (int r = tid; r < NR; r += kTThreads) {
         sh.lam[r] = (fresh || !io.lam) ? 0.f : io.lam[(size_t)p * NR + r];
-        sh.sw[r] = residual_sqrt_weight(sc, r);
     }
     if (tid == 0) sh.mu = (fresh || !io.mu) ? sc.mu0 : io.mu[p];
     grp_sync<kPpc>();
@@ -1137,7 +1145,7 @@ __device__ __forceinline__ void traj_particle(const Scalars& sc, int p, int mode
             disp[t] += moved * 1.0001f + 1e-7f;
         }
         if (sc.K_al > 0 && k % sc.K_al == 0) {
-            for (int r = tid; r < NR; r += kTThreads) sh.lam[r] += sh.mu * sh.sw[r] * sh.h[r];
+            for (int r = tid; r < NR; r += kTThreads) sh.lam[r] += sh.mu * residual_sqrt_weight(sc, r) * sh.h[r];
             grp_sync<kPpc>();
             if (tid == 0) sh.mu = fminf(sh.mu * 2.f, sc.mu_max);
         }

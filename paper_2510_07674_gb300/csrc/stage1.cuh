@@ -33,7 +33,8 @@ enum PlaceMode { kPlaceForward = 0, kPlaceStage1 = 1, kPlaceExplicit = 2, kPlace
 // Per-block terms of the tower (lane i < B owns block i): height residual e_i, support
 // distance D_i and the block cuboids in ps.  With mode kPlaceStage1 or kPlaceExplicit, sets
 //   g = sum_i a_i dD_i/dx + sum_i b_i de_i/dx   (the collision part is added by the caller);
-// with kPlaceUnit, leaves dD_i/d(centre of mass, yaw) in ps.stab for place_stack_grad.
+// with kPlaceUnit, leaves dD_i/d(centre of mass, yaw) in ps.stab for place_stack_grad and
+// writes no block cuboids.
 // x, g: per-warp shared arrays of 4B floats.  Must be called by all 32 lanes of the warp.
 __device__ __forceinline__ void place_stack_warp(const Scalars& sc, const float* x, int mode, const float* a_in,
                                                  const float* b_in, float* g, PlaceScratch& ps, float& my_D,
@@ -46,7 +47,8 @@ __device__ __forceinline__ void place_stack_warp(const Scalars& sc, const float*
         const int i = lane;
         my_e = x[4 * i + 2] - sc.zt[i];
         ps.e[i] = my_e;
-        block_cuboid(x[4 * i], x[4 * i + 1], x[4 * i + 2], x[4 * i + 3], sc.half[i], ps.bc[i]);
+        if (mode != kPlaceUnit)   // the stage-2 caller keeps its own placed cuboids
+            block_cuboid(x[4 * i], x[4 * i + 1], x[4 * i + 2], x[4 * i + 3], sc.half[i], ps.bc[i]);
         float sx = 0.f, sy = 0.f, dvx = 0.f, dvy = 0.f, dyaw = 0.f;
         if (i + 1 < B) {
             const int n_above = B - 1 - i;

@@ -19,14 +19,8 @@ __host__ __device__ __forceinline__ int t_place(int S, int b) { return (2 * b + 
 //   [9B] placement collisions, [9B+1] C_arm, [9B+2] C_block.         (w_coll, w_arm, w_block)
 __device__ __forceinline__ float residual_sqrt_weight(const Scalars& sc, int r) {
     const int B = sc.B;
-    float w;
-    if (r < 7 * B) w = sc.w_start;
-    else if (r < 8 * B) w = sc.w_height;
-    else if (r < 9 * B) w = sc.w_stable;
-    else if (r == 9 * B) w = sc.w_coll;
-    else if (r == 9 * B + 1) w = sc.w_arm;
-    else w = sc.w_block;
-    return sqrtf(w);
+    const int k = r < 7 * B ? 0 : r < 8 * B ? 1 : r < 9 * B ? 2 : r == 9 * B ? 3 : r == 9 * B + 1 ? 4 : 5;
+    return sc.sqw[k];
 }
 
 // roll = atan2(R21, R22), pitch = atan2(-R20, hypot(R21, R22)) (ZYX) of a rotation R, and
