@@ -378,6 +378,14 @@ typedef struct {
  * outside the above or two particles whose shared memory does not fit one CTA.  Synchronises. */
 spasm_status spasm_set_kernel_config(spasm_problem_t problem, const spasm_kernel_config* cfg);
 
+/* Resident CTAs per SM of this problem's trajectory kernels under its launch shape: *single for
+ * the per-problem kernel of spasm_optimize, *batched for the batched kernel of
+ * spasm_optimize_batch in a batch whose largest problem is this one (CUDA's occupancy
+ * calculator with the shared memory the launches request; 0 where they do not fit).  Not in
+ * the paper: what a caller sizing batches, and a test guarding the shared-memory budget,
+ * read. */
+spasm_status spasm_traj_residency(spasm_problem_t problem, int* single, int* batched);
+
 /* Replace the Philox seed (the key of every random stream) and forget previous results;
  * the next spasm_optimize re-runs both stages. */
 spasm_status spasm_set_seed(spasm_problem_t problem, uint64_t seed);

@@ -665,6 +665,14 @@ extern "C" spasm_status spasm_set_kernel_config(spasm_problem_t pr, const spasm_
     return prepare_graphs(pr);
 }
 
+extern "C" spasm_status spasm_traj_residency(spasm_problem_t pr, int* single, int* batched) {
+    if (!pr || !single || !batched) return fail(SPASM_ERR_INVALID, "null argument");
+    *single = traj_ctas_per_sm(pr->sc);
+    *batched = traj_batch_ctas_per_sm(traj_smem_bytes(pr->sc), pr->sc.sphere_tiling,
+                                      pr->sc.particles_per_cta == 2 ? 2 : 1);
+    return SPASM_OK;
+}
+
 extern "C" spasm_status spasm_synchronize(spasm_problem_t pr) {
     if (!pr) return fail(SPASM_ERR_INVALID, "null problem");
     SPASM_TRY(finalize(pr));

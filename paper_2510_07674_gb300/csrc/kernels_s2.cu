@@ -1354,6 +1354,30 @@ int traj_batch_ctas_per_sm(size_t smem_bytes, int tiling, int ppc) {
 }
 
 template <bool kP2P, int kTile, int kPpc>
+static int single_occupancy(size_t smem_bytes) {
+    int n = 0;
+    const size_t dyn = (size_t)t_region(smem_bytes) * kPpc;
+    if (allow_max_dynamic_smem(k_traj<kP2P, kTile, kPpc>, dyn) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_traj<kP2P, kTile, kPpc>, kTThreads * kPpc, dyn) !=
+        cudaSuccess)
+        return 0;
+    return n;
+}
+
+template <bool kP2P>
+static int single_ctas(size_t smem, int tiling, int ppc) {
+    if (ppc == 2) return tiling ? single_occupancy<kP2P, 1, 2>(smem) : single_occupancy<kP2P, 0, 2>(smem);
+    return tiling ? single_occupancy<kP2P, 1, 1>(smem) : single_occupancy<kP2P, 0, 1>(smem);
+}
+
+int traj_ctas_per_sm(const Scalars& sc) {
+    const size_t smem = traj_smem_bytes(sc);
+    const int ppc = sc.particles_per_cta == 2 ? 2 : 1;
+    return sc.kind == kKindP2P ? single_ctas<true>(smem, sc.sphere_tiling, ppc)
+                               : single_ctas<false>(smem, sc.sphere_tiling, ppc);
+}
+
+template <bool kP2P, int kTile, int kPpc>
 static cudaError_t traj_kernel(const Scalars& sc, DevTables t, int n, int mode, const TrajIO& io, int* err,
                                cudaStream_t st) {
     const int region = t_region(traj_smem_bytes(sc));

@@ -52,6 +52,9 @@ cudaError_t launch_traj_batch(const TrajJob* jobs, int n_jobs, int n_items, int 
 // Resident CTAs per SM of the batched kernel at that per-particle shared-memory size (0 on error
 // or when it does not fit).
 int traj_batch_ctas_per_sm(size_t smem_bytes, int tiling = 0, int ppc = 1);
+// Resident CTAs per SM of the per-problem trajectory kernel for this problem's sizes and launch
+// shape (0 if it does not fit).
+int traj_ctas_per_sm(const Scalars& sc);
 // Dynamic shared memory of one trajectory CTA with ppc particles.
 size_t traj_cta_smem_bytes(const Scalars& sc, int ppc);
 

@@ -31,7 +31,7 @@ EXPORTED = ["spasm_create_problem", "spasm_destroy_problem", "spasm_last_error",
             "spasm_create_p2p", "spasm_traj_check", "spasm_fp32_fma_peak", "spasm_synchronize",
             "spasm_inject_wait_timeout", "spasm_inject_alloc_failure", "spasm_problem_bytes", "spasm_server_cancel",
             "spasm_server_get_stats", "spasm_set_kernel_config", "spasm_set_launch_mode",
-            "spasm_snapshot_bytes", "spasm_snapshot", "spasm_restore"]
+            "spasm_snapshot_bytes", "spasm_snapshot", "spasm_restore", "spasm_traj_residency"]
 SPASM_LAUNCH_GRAPH, SPASM_LAUNCH_EAGER = 0, 1
 
 
@@ -137,6 +137,7 @@ def lib():
         L.spasm_set_kernel_config.argtypes = [_V, ctypes.POINTER(_KernelConfig)]
         L.spasm_set_launch_mode.argtypes = [_V, ctypes.c_int]
         L.spasm_snapshot_bytes.argtypes = [_V, ctypes.POINTER(ctypes.c_size_t)]
+        L.spasm_traj_residency.argtypes = [_V, _I, _I]
         L.spasm_snapshot.argtypes = [_V, _V, ctypes.c_size_t]
         L.spasm_restore.argtypes = [_V, _V, ctypes.c_size_t]
         L.spasm_problem_bytes.argtypes = [ctypes.POINTER(_Obstacles), ctypes.POINTER(_Goal), ctypes.POINTER(_Params),
@@ -425,6 +426,13 @@ def spasm_set_kernel_config(problem: Problem, sphere_tiling: int = 0, particles_
 def spasm_set_launch_mode(problem: Problem, mode: int):
     """SPASM_LAUNCH_GRAPH (default) or SPASM_LAUNCH_EAGER (kernel by kernel, host attempt loop)."""
     _check(lib().spasm_set_launch_mode(problem.handle, int(mode)))
+
+
+def spasm_traj_residency(problem: Problem) -> dict:
+    """Resident CTAs per SM of the problem's trajectory kernels (per problem and batched)."""
+    a, b = ctypes.c_int32(), ctypes.c_int32()
+    _check(lib().spasm_traj_residency(problem.handle, ctypes.byref(a), ctypes.byref(b)))
+    return {"single": a.value, "batched": b.value}
 
 
 def spasm_snapshot_bytes(problem: Problem) -> int:

@@ -148,3 +148,19 @@ def test_autotuner_returns_a_valid_shape_and_two_particles_fit_tower10():
         assert S.spasm_result(pr, allow_empty=True)["n_found"] > 0
     finally:
         pr.close()
+
+
+def test_the_largest_workload_keeps_two_ctas_per_sm():
+    """The shared-memory budget: the 10-block workload (the largest of the benchmark's mixes)
+    runs two CTAs per SM in the per-problem and in the batched kernel (one particle per CTA),
+    and two particles per CTA still fit one SM."""
+    S = _S()
+    wl = scenes.make_problem("tower10", seed=0, Q=64)
+    pr = S.Problem(wl)
+    try:
+        assert S.spasm_traj_residency(pr) == {"single": 2, "batched": 2}
+        S.spasm_set_kernel_config(pr, 0, 2)
+        r = S.spasm_traj_residency(pr)
+        assert r["single"] >= 1 and r["batched"] >= 1, r
+    finally:
+        pr.close()
