@@ -134,7 +134,7 @@ def dist_env():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+    """nvidia-smi clocks and throttle reasons sampled every 50 ms during a timed region."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -151,7 +151,7 @@ class ClockSampler:
             os.close(fd)
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh,
+                                          "--format=csv,noheader,nounits", "-lms", "50"], stdout=self.fh,
                                          stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
@@ -215,6 +215,8 @@ def tail_leg(args, rank, overrides, flush) -> dict:
     from paper_2510_07674_gb300 import scenes
     from paper_2510_07674_gb300 import spasm as S
     times, ok, att1, att2 = [], 0, [], []
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
     for i in range(args.tail_seeds):
         wl = scenes.make_problem(WORKLOAD, seed=rank * 100000 + i,
                                  **{k: v for k, v in overrides.items() if k != "max_steps"})
@@ -235,11 +237,13 @@ def tail_leg(args, rank, overrides, flush) -> dict:
             att2.append(st["traj_attempts"])
         finally:
             pr.close()
+    clocks = sampler.stop()
     return {"seeds": len(times), "p50_ms": _percentile(times, 0.5), "p99_ms": _percentile(times, 0.99),
             "max_ms": max(times), "mean_ms": statistics.mean(times), "success_rate": ok / len(times),
             "stage1_attempts_mean": statistics.mean(att1), "stage2_attempts_mean": statistics.mean(att2),
             "timed": "CUDA events around spasm_optimize (both stages, graphs with device-side attempt loops), "
-                     "L2 flushed before each solve"}
+                     "L2 flushed before each solve",
+            "clocks": clocks}
 
 
 def count_tests(wl) -> dict:
