@@ -34,9 +34,9 @@ __device__ __forceinline__ void grp_sync() {
 // any of its link boxes and any static box that could touch it (the environment, blocks at
 // their initial poses), and the same for the placed blocks, which move.  Later iterations
 // skip the chunk (kinematics, cull and tests: its terms are zero) while the bound on how far
-// its spheres moved since stays below the static clearance and, plus how far the blocks
-// placed before the chunk's own block moved, below the moving one, so the skipped work is
-// exactly the work whose result is zero.
+// its spheres moved since stays below the static clearance and, plus a bound on how far any
+// one of the blocks placed before the chunk's own block moved, below the moving one, so the
+// skipped work is exactly the work whose result is zero.
 constexpr float kClearSlack = 1e-5f;   // FP32 rounding of the boxes, metres
 
 struct TWarp {
@@ -81,7 +81,7 @@ struct TShared {
     unsigned char active[kChunk + 1][(kMaxC + kChunk - 1) / kChunk];
     short n_group[kChunk + 1][kTWarps];
     unsigned skip[kTWarps];       // bit i of word g: chunk 32g + i kept its cached cull this evaluation
-    float blk_cum[kMaxB];         // [k]: running bound on how far the placed blocks 0..k have moved, summed
+    float blk_cum[kMaxB];         // [k]: sum over the evaluations of the largest motion among the placed blocks 0..k
     int pose_prev_ok;
     float c_arm, c_blk, maxpen, c_coll, c_stable, c_height, c_start;
     float max_start, max_tilt, pm_pen, pm_D, pm_dz, path, jl;
@@ -786,11 +786,14 @@ __device__ void traj_evaluate(const Scalars& sc, const LaneSpheres& ls, const fl
             sh.baabb[lane][0] = make_float4(3.4e38f, 3.4e38f, 3.4e38f, 0.f);   // an empty box: never a candidate
             sh.baabb[lane][1] = make_float4(-3.4e38f, -3.4e38f, -3.4e38f, 0.f);
         }
-        // inclusive scan over the blocks: blk_cum[k] accumulates the motion of blocks 0..k
+        // inclusive max-scan over the blocks: blk_cum[k] accumulates, evaluation by evaluation, the
+        // largest motion among blocks 0..k.  Summed over the evaluations since a chunk's cull it
+        // bounds the motion of each of those blocks since then, which is all that a gap to any
+        // one of them needs (a sum over the blocks would bound their total motion instead)
 #pragma unroll
         for (int off = 1; off < 32; off <<= 1) {
             const float up = __shfl_up_sync(0xffffffffu, moved, off);
-            if (lane >= off) moved += up;
+            if (lane >= off) moved = fmaxf(moved, up);
         }
         if (lane < B) sh.blk_cum[lane] += moved;
         if (lane == 0) sh.pose_prev_ok = 1;
@@ -811,8 +814,9 @@ __device__ void traj_evaluate(const Scalars& sc, const LaneSpheres& ls, const fl
     static_assert((kMaxC + kChunk - 1) / kChunk <= 256, "chunk indices fit the byte lists");
     static_assert((kMaxC + kChunk - 1) / kChunk <= 32 * kTWarps && (kTWarps & (kTWarps - 1)) == 0,
                   "one 32-chunk group per warp");
-    // motion of the blocks placed before block b: the only placed blocks the configurations of a
-    // chunk whose last configuration belongs to block b's segments can touch
+    // bound on the motion of each block placed before block b (the only placed blocks the
+    // configurations of a chunk whose last configuration belongs to block b's segments can
+    // touch): its difference between two evaluations bounds any one block's motion between them
     auto blk_before = [&](int b) { return b > 0 ? sh.blk_cum[b - 1] : 0.f; };
     auto chunk_block = [&](int t0c) { return (min(t0c + kChunk - 1, C - 1) - 1) / S >> 1; };
     {
