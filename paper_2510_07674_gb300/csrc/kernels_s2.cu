@@ -36,7 +36,10 @@ __device__ __forceinline__ void grp_sync() {
 // skip the chunk (kinematics, cull and tests: its terms are zero) while the bound on how far
 // its spheres moved since stays below the static clearance and, plus a bound on how far any
 // one of the blocks placed before the chunk's own block moved, below the moving one, so the
-// skipped work is exactly the work whose result is zero.
+// skipped work is exactly the work whose result is zero.  A chunk whose configurations have
+// candidates but whose spheres all miss them (no penetration anywhere: its terms are zero as
+// well) is kept the same way; for the obstacles its spheres were tested against, its
+// clearance is the smallest sphere-level gap those tests found.
 constexpr float kClearSlack = 1e-5f;   // FP32 rounding of the boxes, metres
 
 struct TWarp {
@@ -267,6 +270,10 @@ __device__ __forceinline__ void sphere_centres(const Scalars& sc, const LaneSphe
 // per configuration lanes own sphere items, screen both slots branch-free and evaluate the
 // penetration only where the separation test fails.  With `grad`, writes the unscaled group
 // gradients G_arm[t], G_blk[t] and accumulates placed-pose derivatives in the warp scratch.
+// Returns whether the chunk's collision terms are zero (no candidate, or candidates that no
+// sphere penetrates); then `clearance` / `clearance_moving` bound from below how far any of
+// its spheres is from a static box / a placed block it could touch: the gaps between link
+// boxes and the boxes apart from them, and the sphere-level gaps of the tests that ran.
 template <int kTile>
 __device__ __forceinline__ bool chunk_collisions(const Scalars& sc, const LaneSpheres& ls,
                                                  const float4* __restrict__ cub, const float4* __restrict__ osph,
@@ -314,7 +321,8 @@ __device__ __forceinline__ bool chunk_collisions(const Scalars& sc, const LaneSp
             const float4 blo = boxes[stride * (base + bit)], bhi = boxes[stride * (base + bit) + 1];
             const float s2 = fmaxf(fmaxf(fmaxf(blo.x - lb[3], lb[0] - bhi.x), fmaxf(blo.y - lb[4], lb[1] - bhi.y)),
                                    fmaxf(blo.z - lb[5], lb[2] - bhi.z));
-            if (relevant(bit)) clear = fminf(clear, s2);
+            // a box that overlaps this link's box is tested against the spheres, which give the gap
+            if (relevant(bit) && s2 > 0.f) clear = fminf(clear, s2);
             const unsigned bal = __ballot_sync(0xffffffffu, s2 <= 0.f);
 #pragma unroll
             for (int c = 0; c < kChunk; ++c)
@@ -382,9 +390,12 @@ __device__ __forceinline__ bool chunk_collisions(const Scalars& sc, const LaneSp
     }
     __syncwarp();
 
-    // pass 2: every configuration against the candidates
+    // pass 2: every configuration against the candidates.  gap_s / gap_m: the lane's smallest
+    // sphere-level gap (lower bound) to a tested static box / placed block; the fixed base's
+    // spheres do not move relative to static boxes and are left out of gap_s.
     const int seg0 = (t0 - 1) / S, r0 = (t0 - 1) - seg0 * S;
-    bool none = true;
+    bool none = true, chunk_hit = false;
+    float gap_s = 3.4e38f, gap_m = 3.4e38f;
     for (int ci = 0; ci < nc; ++ci) {
         const int t = t0 + ci;
         int seg = seg0, r = r0 + ci;
@@ -405,6 +416,9 @@ __device__ __forceinline__ bool chunk_collisions(const Scalars& sc, const LaneSp
         none = false;
         ++n_cand;
         sphere_centres<kTile>(sc, ls, tw.F[ci], tw.H[ci], n_items, b, cx, cy, cz, rr, act, isblk);
+        bool fixed[kSlots];
+#pragma unroll
+        for (int sl = 0; sl < kSlots; ++sl) fixed[sl] = !isblk[sl] && ls.link[sl] == 0;
         float gx[kSlots], gy[kSlots], gz[kSlots], pen_sum[kSlots];
 #pragma unroll
         for (int sl = 0; sl < kSlots; ++sl) gx[sl] = gy[sl] = gz[sl] = pen_sum[sl] = 0.f;
@@ -425,6 +439,8 @@ __device__ __forceinline__ bool chunk_collisions(const Scalars& sc, const LaneSp
                                               q1[sl], q2[sl]);
 #pragma unroll
                 for (int sl = 0; sl < kSlots; ++sl) {
+                    // separated along a box axis by qm: the sphere is at least qm - r from the box
+                    if (act[sl] && !fixed[sl]) gap_s = fminf(gap_s, fmaxf(qm[sl] - rr[sl], 0.f));
                     if (!act[sl] || !(qm[sl] < rr[sl])) continue;
                     float ax, ay, az;
                     const float pen = pen_finish<float>(p0[sl], p1[sl], p2[sl], q0[sl], q1[sl], q2[sl], qm[sl], rr[sl],
@@ -448,6 +464,11 @@ __device__ __forceinline__ bool chunk_collisions(const Scalars& sc, const LaneSp
 #pragma unroll
                 for (int sl = 0; sl < kSlots; ++sl) {
                     if (!act[sl]) continue;
+                    if (!fixed[sl]) {
+                        // the largest per-axis offset bounds the centre distance from below
+                        const float dm = fmaxf(fmaxf(fabsf(cx[sl] - os.x), fabsf(cy[sl] - os.y)), fabsf(cz[sl] - os.z));
+                        gap_s = fminf(gap_s, fmaxf(dm - rr[sl] - os.w, 0.f));
+                    }
                     float ax, ay, az;
                     const float pen = pen_sphere<float>(cx[sl], cy[sl], cz[sl], rr[sl], os, ax, ay, az);
                     if (pen > 0.f) {
@@ -478,6 +499,11 @@ __device__ __forceinline__ bool chunk_collisions(const Scalars& sc, const LaneSp
                                               q1[sl], q2[sl]);
 #pragma unroll
                 for (int sl = 0; sl < kSlots; ++sl) {
+                    if (act[sl]) {
+                        const float g = fmaxf(qm[sl] - rr[sl], 0.f);
+                        if (placed) gap_m = fminf(gap_m, g);
+                        else if (!fixed[sl]) gap_s = fminf(gap_s, g);
+                    }
                     if (!act[sl] || !(qm[sl] < rr[sl])) continue;
                     float ax, ay, az;
                     const float pen = pen_finish<float>(p0[sl], p1[sl], p2[sl], q0[sl], q1[sl], q2[sl], qm[sl], rr[sl],
@@ -507,6 +533,7 @@ __device__ __forceinline__ bool chunk_collisions(const Scalars& sc, const LaneSp
             }
         }
         n_tests += (unsigned long long)visits * (unsigned)n_items;
+        chunk_hit |= any_hit;
 #pragma unroll
         for (int sl = 0; sl < kSlots; ++sl) {
             if (isblk[sl]) acc_blk += pen_sum[sl];
@@ -573,7 +600,13 @@ __device__ __forceinline__ bool chunk_collisions(const Scalars& sc, const LaneSp
             if ((lane & 1) == 0 && (j & 7) != 7) (j < 8 ? G_arm : G_blk)[t * 8 + (j & 7)] = v[0];
         }
     }
-    return none;
+    if (none) return true;
+    // candidates, but no sphere penetrates any of them: the chunk's terms are zero, and the
+    // tests' gaps join the clearances
+    if (__any_sync(0xffffffffu, chunk_hit)) return false;
+    clearance = fminf(clearance, warp_min(gap_s));
+    clearance_moving = fminf(clearance_moving, warp_min(gap_m));
+    return true;
 }
 
 // Residuals of the start group at the grasp (which = 0) or place (which = 1) configuration
@@ -860,12 +893,12 @@ __device__ void traj_evaluate(const Scalars& sc, const LaneSpheres& ls, const fl
             __syncwarp();
             float clearance, clearance_moving;
             const unsigned long long cand0 = n_cand;
-            const bool none = chunk_collisions<kTile>(sc, ls, cub, osph, aabb, sh, sh.warp[w], G_arm, G_blk, t0, nc, grad, box,
+            const bool zero = chunk_collisions<kTile>(sc, ls, cub, osph, aabb, sh, sh.warp[w], G_arm, G_blk, t0, nc, grad, box,
                                                acc_arm, acc_blk, acc_max, n_tests, n_cand, clearance,
                                                clearance_moving);
             n_cull += (unsigned)nc;
             if (lane == 0) {
-                ccand[chk] = none ? 0 : (int)(n_cand - cand0);   // 0: a candidate-free (cacheable) chunk
+                ccand[chk] = zero ? 0 : (int)(n_cand - cand0);   // 0: a chunk whose terms are zero (cacheable)
                 cblk[chk] = blk_before(chunk_block(t0));
                 // fp16, rounded down: still a lower bound on either clearance
                 cgap[chk] = __halves2half2(__float2half_rd(clearance - kClearSlack),
