@@ -42,12 +42,23 @@ __device__ __forceinline__ void grp_sync() {
 // clearance is the smallest sphere-level gap those tests found.
 constexpr float kClearSlack = 1e-5f;   // FP32 rounding of the boxes, metres
 
+// Work queue of an evaluation: its items (the residual jobs, the chunks, the slices of the
+// placed tower's collisions) go to the warps in list order from a shared counter, heaviest
+// first, so that the warps finish together.  What the items add up goes into fixed-point
+// accumulators (integer sums are exact, hence independent of which warp took which item and
+// when): a value v becomes round(v 2^40), |v| < 8e6.
+constexpr float kFix = 1099511627776.f;   // 2^40
+__device__ __forceinline__ void fx_add(long long* acc, float v) {
+    atomicAdd(reinterpret_cast<unsigned long long*>(acc), (unsigned long long)__float2ll_rn(v * kFix));
+}
+__device__ __forceinline__ float fx_value(long long a) { return __ll2float_rn(a) * (1.f / kFix); }
+constexpr int kPlaceUnits = (8 * kMaxB + 31) / 32;   // slices of 32 block spheres of the placed tower
+constexpr int kResidualJobs = 2;                      // placement residuals; start residuals
+
 struct TWarp {
     float4 F[kChunk][8][3];  // frames 0..7 of each configuration of the chunk: rows (R_i0, R_i1, R_i2, o_i)
     float4 H[kChunk][3];     // held-block frame of each configuration (same row layout)
-    float wr[2][kMaxB][4];   // d/d(placed pose k): group arm, group block
-    float part[4];           // C_arm, C_block, max penetration
-    float pc[2];             // placed tower: sum and maximum of its penetrations (this warp's share)
+    float part[4];           // this warp's path length and joint-limit sums [0, 1], maximum penetration [2]
     uint32_t cmask[kChunk][kMaxCub / 32];    // environment cuboids that may touch configuration c of the chunk
     uint32_t smask[kChunk][kMaxOSph / 32];   // environment spheres that may touch configuration c
     uint32_t bmask[2][kChunk];               // placed / not-yet-moved blocks that may touch configuration c
@@ -71,8 +82,12 @@ struct TShared {
     // gradient rows of the grasp (b) and place (B + b) configurations; until the gradient pass
     // overwrites them, their first 6 floats hold the residual pass's (w_roll, w_pitch) of that block frame
     float extra[2 * kMaxB][8];
-    float pg[kTWarps][kMaxB][4];   // dC_coll/d(placed pose j), sphere side, per warp
-    float pgc[kMaxB][4];           // dC_coll/d(placed pose i), cuboid side of block pairs
+    float pg[kMaxB][4];                // dC_coll/d(placed pose j), sphere side (from the slice holding block j)
+    float pgc[kPlaceUnits][kMaxB][4];  // dC_coll/d(placed pose i), cuboid side of block pairs, per slice
+    float pcu[kPlaceUnits][2];         // per slice: sum and maximum of the tower's penetrations
+    long long fx_wr[2][kMaxB][4];      // d/d(placed pose k) of the arm and block groups (fixed point)
+    long long fx_arm, fx_blk;          // C_arm, C_block (fixed point)
+    int next;                          // the work queue's counter
     PlaceScratch ps;
     float4 dh[8];            // joint j: cos alpha, sin alpha, a, d (per-lane reads in the kinematics)
     float th0[8];            // joint offsets
@@ -524,10 +539,10 @@ __device__ __forceinline__ bool chunk_collisions(const Scalars& sc, const LaneSp
                     dax = warp_sum(dax); day = warp_sum(day); daz = warp_sum(daz); dayaw = warp_sum(dayaw);
                     dbx = warp_sum(dbx); dby = warp_sum(dby); dbz = warp_sum(dbz); dbyaw = warp_sum(dbyaw);
                     if (lane == 0) {
-                        tw.wr[0][kb][0] += dax; tw.wr[0][kb][1] += day; tw.wr[0][kb][2] += daz;
-                        tw.wr[0][kb][3] += dayaw;
-                        tw.wr[1][kb][0] += dbx; tw.wr[1][kb][1] += dby; tw.wr[1][kb][2] += dbz;
-                        tw.wr[1][kb][3] += dbyaw;
+                        fx_add(&sh.fx_wr[0][kb][0], dax); fx_add(&sh.fx_wr[0][kb][1], day);
+                        fx_add(&sh.fx_wr[0][kb][2], daz); fx_add(&sh.fx_wr[0][kb][3], dayaw);
+                        fx_add(&sh.fx_wr[1][kb][0], dbx); fx_add(&sh.fx_wr[1][kb][1], dby);
+                        fx_add(&sh.fx_wr[1][kb][2], dbz); fx_add(&sh.fx_wr[1][kb][3], dbyaw);
                     }
                 }
             }
@@ -668,96 +683,115 @@ __device__ __forceinline__ void start_terms(const Scalars& sc, int b, int which,
     }
 }
 
-// Collisions of the placed tower (the C_coll residual of the placement terms), spread over
-// all warps of the CTA: lanes own (block j, sphere m) items, warp w takes the environment
-// obstacles o = w (mod kTWarps) and the lower-block cuboids i = w (mod kTWarps), and a box
-// test screens each pair before the exact one.  Per warp: the sum and maximum of the
-// penetrations (tw.pc); with `grad`, the unscaled pose gradient dC_coll/dx, sphere side in
-// sh.pg[w][j] and cuboid side in sh.pgc[i] (written by the one warp that owns cuboid i).
-template <int kPpc>
-__device__ __forceinline__ void placed_collisions(const Scalars& sc, const float4* __restrict__ cub,
-                                                  const float4* __restrict__ osph, const float4* __restrict__ aabb,
-                                                  TShared& sh, bool grad) {
-    const int lane = threadIdx.x & 31, w = grp_tid<kPpc>() >> 5;
+// Collisions of the placed tower (the C_coll residual of the placement terms), slice u of its
+// block spheres (items 32u .. 32u+31, item 8j + m: sphere m of block j) by one warp.  An exact
+// cull first keeps the environment obstacles whose boxes overlap the tower's box (every block
+// sphere lies inside its block's cuboid box); a box test screens each pair before the exact
+// one; each sphere of block j is also tested against the cuboids of the blocks i < j below it.
+// Writes the slice's sum and maximum of the penetrations (sh.pcu[u]); with `grad`, the
+// unscaled pose gradient dC_coll/dx, sphere side in sh.pg[j] for the slice's blocks and
+// cuboid side in sh.pgc[u][i] for every i < B - 1.
+__device__ __forceinline__ void placed_slice(const Scalars& sc, const float4* __restrict__ cub,
+                                             const float4* __restrict__ osph, const float4* __restrict__ aabb,
+                                             TShared& sh, bool grad, int u) {
+    const int lane = threadIdx.x & 31;
     const int B = sc.B, n_items = 8 * B;
-    float coll = 0.f, maxpen = 0.f;
-    if (grad && lane < 4)
-        for (int i = w; i + 1 < B; i += kTWarps) sh.pgc[i][lane] = 0.f;
-    __syncwarp();
-    for (int base = 0; base < n_items; base += 32) {
-        const int it = base + lane;
-        const bool valid = it < n_items;
-        const int j = valid ? it >> 3 : 0, m = it & 7;
-        const float4 h = sc.half[j];
-        float lx, ly, lz;
-        block_sphere_local(h, m, lx, ly, lz);
-        const float c = sh.bcub[j][1].x, s = sh.bcub[j][1].y;
-        const float cx = sh.pose[4 * j] + c * lx - s * ly;
-        const float cy = sh.pose[4 * j + 1] + s * lx + c * ly;
-        const float cz = sh.pose[4 * j + 2] + lz;
-        const float r = h.w;
-        auto apart = [&](const float4& lo, const float4& hi) {
-            return lo.x > cx + r || hi.x < cx - r || lo.y > cy + r || hi.y < cy - r || lo.z > cz + r || hi.z < cz - r;
-        };
-        float ax = 0.f, ay = 0.f, az = 0.f;   // dC/dc of this item
-        if (valid) {
-            for (int o = w; o < sc.n_cub; o += kTWarps) {
-                if (apart(aabb[2 * o], aabb[2 * o + 1])) continue;
-                float gx, gy, gz;
-                const float pen = pen_cuboid<float>(cx, cy, cz, r, cub[4 * o], cub[4 * o + 1], cub[4 * o + 2],
-                                                    cub[4 * o + 3], gx, gy, gz);
-                if (pen > 0.f) {
-                    coll += pen; maxpen = fmaxf(maxpen, pen);
-                    ax += gx; ay += gy; az += gz;
-                }
-            }
-            for (int o = w; o < sc.n_osph; o += kTWarps) {
-                float gx, gy, gz;
-                const float pen = pen_sphere<float>(cx, cy, cz, r, osph[o], gx, gy, gz);
-                if (pen > 0.f) {
-                    coll += pen; maxpen = fmaxf(maxpen, pen);
-                    ax += gx; ay += gy; az += gz;
-                }
-            }
-        }
-        // blocks below in the stack: sphere of j against the cuboid of i < j
-        for (int i = w; i + 1 < B; i += kTWarps) {
-            float bx = 0.f, by = 0.f, bz = 0.f, byaw = 0.f;   // dC/d(pose i) from this item
-            bool hit = false;
-            if (valid && i < j && !apart(sh.baabb[i][0], sh.baabb[i][1])) {
-                float gx, gy, gz;
-                const float pen = pen_cuboid<float>(cx, cy, cz, r, sh.bcub[i][0], sh.bcub[i][1], sh.bcub[i][2],
-                                                    sh.bcub[i][3], gx, gy, gz);
-                if (pen > 0.f) {
-                    hit = true;
-                    coll += pen; maxpen = fmaxf(maxpen, pen);
-                    ax += gx; ay += gy; az += gz;
-                    // the cuboid moves rigidly: d/dP_i = -g, d/dyaw_i = -((c - P_i) x g)_z
-                    bx = -gx; by = -gy; bz = -gz;
-                    byaw = -((cx - sh.pose[4 * i]) * gy - (cy - sh.pose[4 * i + 1]) * gx);
-                }
-            }
-            if (grad && __any_sync(0xffffffffu, hit)) {
-                bx = warp_sum(bx); by = warp_sum(by); bz = warp_sum(bz); byaw = warp_sum(byaw);
-                if (lane == 0) { sh.pgc[i][0] += bx; sh.pgc[i][1] += by; sh.pgc[i][2] += bz; sh.pgc[i][3] += byaw; }
-            }
-        }
-        if (grad) {
-            float gyaw = ax * (-s * lx - c * ly) + ay * (c * lx - s * ly);   // dc/dyaw_j
+    const int it = 32 * u + lane;
+    const bool valid = it < n_items;
+    const int j = valid ? it >> 3 : 0, m = it & 7;
+    const float4 h = sc.half[j];
+    float lx, ly, lz;
+    block_sphere_local(h, m, lx, ly, lz);
+    const float c = sh.bcub[j][1].x, s = sh.bcub[j][1].y;
+    const float cx = sh.pose[4 * j] + c * lx - s * ly;
+    const float cy = sh.pose[4 * j + 1] + s * lx + c * ly;
+    const float cz = sh.pose[4 * j + 2] + lz;
+    const float r = h.w;
+    auto apart = [&](const float4& lo, const float4& hi) {
+        return lo.x > cx + r || hi.x < cx - r || lo.y > cy + r || hi.y < cy - r || lo.z > cz + r || hi.z < cz - r;
+    };
+    // the tower's box
+    float tlx = lane < B ? sh.baabb[lane][0].x : 3.4e38f, tly = lane < B ? sh.baabb[lane][0].y : 3.4e38f;
+    float tlz = lane < B ? sh.baabb[lane][0].z : 3.4e38f, thx = lane < B ? sh.baabb[lane][1].x : -3.4e38f;
+    float thy = lane < B ? sh.baabb[lane][1].y : -3.4e38f, thz = lane < B ? sh.baabb[lane][1].z : -3.4e38f;
 #pragma unroll
-            for (int off = 4; off > 0; off >>= 1) {
-                ax += __shfl_xor_sync(0xffffffffu, ax, off);
-                ay += __shfl_xor_sync(0xffffffffu, ay, off);
-                az += __shfl_xor_sync(0xffffffffu, az, off);
-                gyaw += __shfl_xor_sync(0xffffffffu, gyaw, off);
-            }
-            // one writer per (warp, block j): the lane with m == 0
-            if (valid && m == 0) { sh.pg[w][j][0] = ax; sh.pg[w][j][1] = ay; sh.pg[w][j][2] = az; sh.pg[w][j][3] = gyaw; }
+    for (int off = 16; off > 0; off >>= 1) {
+        tlx = fminf(tlx, __shfl_xor_sync(0xffffffffu, tlx, off));
+        tly = fminf(tly, __shfl_xor_sync(0xffffffffu, tly, off));
+        tlz = fminf(tlz, __shfl_xor_sync(0xffffffffu, tlz, off));
+        thx = fmaxf(thx, __shfl_xor_sync(0xffffffffu, thx, off));
+        thy = fmaxf(thy, __shfl_xor_sync(0xffffffffu, thy, off));
+        thz = fmaxf(thz, __shfl_xor_sync(0xffffffffu, thz, off));
+    }
+    float coll = 0.f, maxpen = 0.f;
+    float ax = 0.f, ay = 0.f, az = 0.f;   // dC/dc of this item
+    const int n_env = sc.n_cub + sc.n_osph;
+    for (int wd = 0; 32 * wd < n_env; ++wd) {
+        const int a_l = 32 * wd + lane;
+        bool near = false;
+        if (a_l < n_env) {
+            const float4 lo = aabb[2 * a_l], hi = aabb[2 * a_l + 1];
+            near = !(lo.x > thx || hi.x < tlx || lo.y > thy || hi.y < tly || lo.z > thz || hi.z < tlz);
         }
+        unsigned mk = __ballot_sync(0xffffffffu, near);
+        if (!valid) continue;
+        while (mk) {
+            const int a = 32 * wd + __ffs(mk) - 1;
+            mk &= mk - 1;
+            float gx, gy, gz, pen;
+            if (a < sc.n_cub) {
+                if (apart(aabb[2 * a], aabb[2 * a + 1])) continue;
+                pen = pen_cuboid<float>(cx, cy, cz, r, cub[4 * a], cub[4 * a + 1], cub[4 * a + 2], cub[4 * a + 3], gx,
+                                        gy, gz);
+            } else {
+                pen = pen_sphere<float>(cx, cy, cz, r, osph[a - sc.n_cub], gx, gy, gz);
+            }
+            if (pen > 0.f) {
+                coll += pen; maxpen = fmaxf(maxpen, pen);
+                ax += gx; ay += gy; az += gz;
+            }
+        }
+    }
+    // blocks below in the stack: sphere of j against the cuboid of i < j (the slice's highest
+    // block bounds i)
+    const int i_end = min(B - 1, (min(32 * u + 31, n_items - 1) >> 3));
+    for (int i = 0; i < B - 1; ++i) {
+        float bx = 0.f, by = 0.f, bz = 0.f, byaw = 0.f;   // dC/d(pose i) from this item
+        bool hit = false;
+        if (i < i_end && valid && i < j && !apart(sh.baabb[i][0], sh.baabb[i][1])) {
+            float gx, gy, gz;
+            const float pen = pen_cuboid<float>(cx, cy, cz, r, sh.bcub[i][0], sh.bcub[i][1], sh.bcub[i][2],
+                                                sh.bcub[i][3], gx, gy, gz);
+            if (pen > 0.f) {
+                hit = true;
+                coll += pen; maxpen = fmaxf(maxpen, pen);
+                ax += gx; ay += gy; az += gz;
+                // the cuboid moves rigidly: d/dP_i = -g, d/dyaw_i = -((c - P_i) x g)_z
+                bx = -gx; by = -gy; bz = -gz;
+                byaw = -((cx - sh.pose[4 * i]) * gy - (cy - sh.pose[4 * i + 1]) * gx);
+            }
+        }
+        if (!grad) continue;
+        if (__any_sync(0xffffffffu, hit)) {
+            bx = warp_sum(bx); by = warp_sum(by); bz = warp_sum(bz); byaw = warp_sum(byaw);
+        }
+        if (lane == 0) { sh.pgc[u][i][0] = bx; sh.pgc[u][i][1] = by; sh.pgc[u][i][2] = bz; sh.pgc[u][i][3] = byaw; }
+    }
+    if (grad) {
+        float gyaw = ax * (-s * lx - c * ly) + ay * (c * lx - s * ly);   // dc/dyaw_j
+#pragma unroll
+        for (int off = 4; off > 0; off >>= 1) {
+            ax += __shfl_xor_sync(0xffffffffu, ax, off);
+            ay += __shfl_xor_sync(0xffffffffu, ay, off);
+            az += __shfl_xor_sync(0xffffffffu, az, off);
+            gyaw += __shfl_xor_sync(0xffffffffu, gyaw, off);
+        }
+        // one writer per block j: the lane with m == 0
+        if (valid && m == 0) { sh.pg[j][0] = ax; sh.pg[j][1] = ay; sh.pg[j][2] = az; sh.pg[j][3] = gyaw; }
     }
     coll = warp_sum(coll);
     maxpen = warp_max(maxpen);
-    if (lane == 0) { sh.warp[w].pc[0] = coll; sh.warp[w].pc[1] = maxpen; }
+    if (lane == 0) { sh.pcu[u][0] = coll; sh.pcu[u][1] = maxpen; }
 }
 
 // Modes of the trajectory kernel
@@ -793,7 +827,8 @@ __device__ void traj_evaluate(const Scalars& sc, const LaneSpheres& ls, const fl
         const bool ok = si < n_sp;
         chunk_fk(sc, sh, q, ok ? (si + 1) * S : 1, ok, true, sp[ok ? si : 0].F, sp[ok ? si : 0].H, nullptr);
     }
-    for (int i = lane; i < 2 * kMaxB * 4; i += 32) (&sh.warp[w].wr[0][0][0])[i] = 0.f;
+    for (int i = tid; i < 2 * kMaxB * 4; i += kTThreads) (&sh.fx_wr[0][0][0])[i] = 0;
+    if (tid == 0) { sh.fx_arm = 0; sh.fx_blk = 0; sh.next = 0; }
     grp_sync<kPpc>();
     // placed poses: the block frame at each place configuration, (x, y, z, yaw)
     if (w == 0) {
@@ -833,20 +868,20 @@ __device__ void traj_evaluate(const Scalars& sc, const LaneSpheres& ls, const fl
     }
     grp_sync<kPpc>();
 
-    // (2) configuration loop: chunks of kChunk consecutive configurations per warp
-    float acc_arm = 0.f, acc_blk = 0.f, acc_max = 0.f;
+    // (2) the evaluation's work queue: chunks of kChunk consecutive configurations, the slices of
+    // the placed tower's collisions and the residual jobs
+    float acc_max = 0.f;
     const int n_chunks = (C - 1 + kChunk - 1) / kChunk;
-    // Chunks to evaluate: those without a valid cached cull (none at its last cull, and the
-    // motion since below its clearances).  Warp g lists those of chunks
-    // 32g .. 32g+31 in chunk order, by tier: the chunks with 4, 3, 2, 1 configurations with
-    // candidates at the last cull (tests and the gradient chain), then the candidate-free
-    // chunks to cull again; it marks the skipped ones in sh.skip, whose block-group gradient rows
-    // the assembly reads as zero (their arm-group rows are still zero from their last cull).  The tiers, in that order, are
-    // dealt to the warps round-robin, which keeps the per-warp sums deterministic and the
-    // warps' shares of the remaining work even.
+    // Chunks to evaluate: those without a valid cached cull (terms zero at its last cull, and
+    // the motion since below its clearances).  Warp g lists those of chunks 32g .. 32g+31 in
+    // chunk order, by tier: the chunks with 4, 3, 2, 1 configurations with candidates at the
+    // last cull (tests and the gradient chain), then the chunks to cull again; it marks the
+    // skipped ones in sh.skip, whose block-group gradient rows the assembly reads as zero
+    // (their arm-group rows are still zero from their last cull).
     static_assert((kMaxC + kChunk - 1) / kChunk <= 256, "chunk indices fit the byte lists");
     static_assert((kMaxC + kChunk - 1) / kChunk <= 32 * kTWarps && (kTWarps & (kTWarps - 1)) == 0,
                   "one 32-chunk group per warp");
+    static_assert(kChunk * kTWarps == 32, "a lane per (tier, group) of the candidate tiers");
     // bound on the motion of each block placed before block b (the only placed blocks the
     // configurations of a chunk whose last configuration belongs to block b's segments can
     // touch): its difference between two evaluations bounds any one block's motion between them
@@ -875,13 +910,76 @@ __device__ void traj_evaluate(const Scalars& sc, const LaneSpheres& ls, const fl
         if (lane == 0) sh.skip[w] = skipped;
     }
     grp_sync<kPpc>();
-    // warp w takes positions w, w + 8, ... of the concatenated lists, tier by tier, group by group
-    int start = 0;
-    for (int tg = 0; tg < (kChunk + 1) * kTWarps; ++tg) {
-        const int tier = tg / kTWarps, g = tg % kTWarps;
-        const int n_g = sh.n_group[tier][g];
-        for (int i = (w - start) & (kTWarps - 1); i < n_g; i += kTWarps) {
-            const int chk = sh.active[tier][32 * g + i];
+    // The queue, in order: the residual jobs (they need only the placed poses and the special
+    // frames), the chunks of the candidate tiers (tier by tier, group by group), the slices of
+    // the placed tower, the chunks to cull again.  Lane l holds the list of (tier l / 8,
+    // group l % 8): its count and first position in the candidate part of the queue.
+    const int n_cnt = sh.n_group[lane >> 3][lane & (kTWarps - 1)];
+    int c_end = n_cnt;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const int up = __shfl_up_sync(0xffffffffu, c_end, off);
+        if (lane >= off) c_end += up;
+    }
+    const int c_first = c_end - n_cnt, n_heavy = __shfl_sync(0xffffffffu, c_end, 31);
+    const int n_rc = lane < kTWarps ? sh.n_group[kChunk][lane] : 0;
+    int r_end = n_rc;
+#pragma unroll
+    for (int off = 1; off < kTWarps; off <<= 1) {
+        const int up = __shfl_up_sync(0xffffffffu, r_end, off);
+        if (lane >= off) r_end += up;
+    }
+    const int r_first = r_end - n_rc, n_light = __shfl_sync(0xffffffffu, r_end, kTWarps - 1);
+    const int n_pu = p2p ? 0 : (8 * B + 31) / 32;
+    const int total = kResidualJobs + n_heavy + n_pu + n_light;
+    for (;;) {
+        int idx = 0;
+        if (lane == 0) idx = atomicAdd(&sh.next, 1);
+        idx = __shfl_sync(0xffffffffu, idx, 0);
+        if (idx >= total) break;
+        if (idx == 0) {
+            // placement residuals (tower terms) with their unit-coefficient support factors
+            float my_D = 0.f, my_e = 0.f;
+            if (!p2p) place_stack_warp(sc, sh.pose, kPlaceUnit, nullptr, nullptr, nullptr, sh.ps, my_D, my_e);
+            const float c_stable = warp_sum(lane < B ? my_D : 0.f);
+            const float c_height = warp_sum(lane < B ? my_e * my_e : 0.f);
+            const float max_D = warp_max(lane < B ? my_D : 0.f);
+            const float max_dz = warp_max(lane < B ? fabsf(my_e) : 0.f);
+            if (lane < B) {
+                sh.h[7 * B + lane] = my_e;
+                sh.h[8 * B + lane] = my_D;
+            }
+            if (lane == 0) { sh.c_stable = c_stable; sh.c_height = c_height; sh.pm_D = max_D; sh.pm_dz = max_dz; }
+            continue;
+        }
+        if (idx == 1) {
+            // start residuals: grasp configurations on lanes 0..15, place configurations on 16..31
+            const int which = lane >> 4, b = lane & 15;
+            if (b < B) {
+                if (which == 0)
+                    start_terms(sc, b, 0, sp[2 * b], &sh.h[5 * b], nullptr, nullptr, nullptr, sh.extra[b]);
+                else if (!p2p)
+                    start_terms(sc, b, 1, sp[2 * b + 1], &sh.h[5 * B + 2 * b], nullptr, nullptr, nullptr,
+                                sh.extra[B + b]);
+                else
+                    sh.h[5 * B + 2 * b] = sh.h[5 * B + 2 * b + 1] = 0.f;
+            }
+            continue;
+        }
+        idx -= kResidualJobs;
+        int chk;
+        if (idx < n_heavy) {
+            const int src = __ffs(__ballot_sync(0xffffffffu, c_first <= idx && idx < c_end)) - 1;
+            chk = sh.active[src >> 3][32 * (src & (kTWarps - 1)) + idx - __shfl_sync(0xffffffffu, c_first, src)];
+        } else if (idx - n_heavy < n_pu) {
+            placed_slice(sc, cub, osph, aabb, sh, grad, idx - n_heavy);
+            continue;
+        } else {
+            idx -= n_heavy + n_pu;
+            const int src = __ffs(__ballot_sync(0xffffffffu, r_first <= idx && idx < r_end)) - 1;
+            chk = sh.active[kChunk][32 * src + idx - __shfl_sync(0xffffffffu, r_first, src)];
+        }
+        {
             const int t0 = 1 + kChunk * chk;
             const int nc = min(kChunk, C - t0);
             const int c = lane >> 3;
@@ -891,13 +989,18 @@ __device__ void traj_evaluate(const Scalars& sc, const LaneSpheres& ls, const fl
             float box[6];
             chunk_fk(sc, sh, q, t0 + c, true, held_c, sh.warp[w].F[c], sh.warp[w].H[c], box);
             __syncwarp();
-            float clearance, clearance_moving;
+            float clearance, clearance_moving, c_arm = 0.f, c_blk = 0.f;
             const unsigned long long cand0 = n_cand;
-            const bool zero = chunk_collisions<kTile>(sc, ls, cub, osph, aabb, sh, sh.warp[w], G_arm, G_blk, t0, nc, grad, box,
-                                               acc_arm, acc_blk, acc_max, n_tests, n_cand, clearance,
-                                               clearance_moving);
+            const bool zero = chunk_collisions<kTile>(sc, ls, cub, osph, aabb, sh, sh.warp[w], G_arm, G_blk, t0, nc,
+                                                      grad, box, c_arm, c_blk, acc_max, n_tests, n_cand, clearance,
+                                                      clearance_moving);
             n_cull += (unsigned)nc;
+            if (!zero) {
+                c_arm = warp_sum(c_arm);
+                c_blk = warp_sum(c_blk);
+            }
             if (lane == 0) {
+                if (!zero) { fx_add(&sh.fx_arm, c_arm); fx_add(&sh.fx_blk, c_blk); }
                 ccand[chk] = zero ? 0 : (int)(n_cand - cand0);   // 0: a chunk whose terms are zero (cacheable)
                 cblk[chk] = blk_before(chunk_block(t0));
                 // fp16, rounded down: still a lower bound on either clearance
@@ -907,57 +1010,18 @@ __device__ void traj_evaluate(const Scalars& sc, const LaneSpheres& ls, const fl
             if (lane < nc) disp[t0 + lane] = 0.f;
             __syncwarp();
         }
-        start += n_g;
     }
-    acc_arm = warp_sum(acc_arm);
-    acc_blk = warp_sum(acc_blk);
     acc_max = warp_max(acc_max);
-    if (lane == 0) { sh.warp[w].part[0] = acc_arm; sh.warp[w].part[1] = acc_blk; sh.warp[w].part[2] = acc_max; }
-    // collisions of the placed tower, all warps (reads only the placed poses of step 1)
-    if (!p2p) placed_collisions<kPpc>(sc, cub, osph, aabb, sh, grad);
-    else if (lane == 0) { sh.warp[w].pc[0] = 0.f; sh.warp[w].pc[1] = 0.f; }
+    if (lane == 0) sh.warp[w].part[2] = acc_max;
     grp_sync<kPpc>();
 
-    // (3) epilogue.  (a) warp 0: the placement residuals; warp 1: the start residuals, grasp
-    // configurations on lanes 0..15 and place configurations on lanes 16..31; warp 2: the group
-    // sums over the warps
+    // (3) warp 0: the group sums, then the objective and dL/dh
     if (w == 0) {
-        float my_D = 0.f, my_e = 0.f;
-        if (!p2p) place_stack_warp(sc, sh.pose, kPlaceUnit, nullptr, nullptr, nullptr, sh.ps, my_D, my_e);
-        const float c_stable = warp_sum(lane < B ? my_D : 0.f);
-        const float c_height = warp_sum(lane < B ? my_e * my_e : 0.f);
-        const float max_D = warp_max(lane < B ? my_D : 0.f);
-        const float max_dz = warp_max(lane < B ? fabsf(my_e) : 0.f);
-        if (lane < B) {
-            sh.h[7 * B + lane] = my_e;
-            sh.h[8 * B + lane] = my_D;
-        }
-        if (lane == 0) { sh.c_stable = c_stable; sh.c_height = c_height; sh.pm_D = max_D; sh.pm_dz = max_dz; }
-    } else if (w == 1) {
-        const int which = lane >> 4, b = lane & 15;
-        if (b < B) {
-            if (which == 0)
-                start_terms(sc, b, 0, sp[2 * b], &sh.h[5 * b], nullptr, nullptr, nullptr, sh.extra[b]);
-            else if (!p2p)
-                start_terms(sc, b, 1, sp[2 * b + 1], &sh.h[5 * B + 2 * b], nullptr, nullptr, nullptr, sh.extra[B + b]);
-            else
-                sh.h[5 * B + 2 * b] = sh.h[5 * B + 2 * b + 1] = 0.f;
-        }
-    } else if (w == 2) {
-        const float ca = lane < kTWarps ? sh.warp[lane].part[0] : 0.f;
-        const float cb = lane < kTWarps ? sh.warp[lane].part[1] : 0.f;
-        float cm = lane < kTWarps ? sh.warp[lane].part[2] : 0.f;
-        float tot_a = 0.f, tot_b = 0.f;   // fixed-order sums over warps
-        for (int i = 0; i < kTWarps; ++i) {
-            tot_a += __shfl_sync(0xffffffffu, ca, i);
-            tot_b += __shfl_sync(0xffffffffu, cb, i);
-        }
-        cm = warp_max(cm);
-        const float pcl = lane < kTWarps ? sh.warp[lane].pc[0] : 0.f;
-        float pm = lane < kTWarps ? sh.warp[lane].pc[1] : 0.f;
-        float c_coll = 0.f;
-        for (int i = 0; i < kTWarps; ++i) c_coll += __shfl_sync(0xffffffffu, pcl, i);
-        pm = warp_max(pm);
+        const float tot_a = fx_value(sh.fx_arm), tot_b = fx_value(sh.fx_blk);
+        const float cm = warp_max(lane < kTWarps ? sh.warp[lane].part[2] : 0.f);
+        const float pm = warp_max(lane < n_pu ? sh.pcu[lane][1] : 0.f);
+        float c_coll = 0.f;   // fixed-order sum over the slices
+        for (int u = 0; u < n_pu; ++u) c_coll += sh.pcu[u][0];
         if (lane == 0) {
             sh.h[9 * B] = c_coll;
             sh.h[9 * B + 1] = tot_a;
@@ -965,10 +1029,7 @@ __device__ void traj_evaluate(const Scalars& sc, const LaneSpheres& ls, const fl
             sh.c_arm = tot_a; sh.c_blk = tot_b; sh.maxpen = cm;
             sh.c_coll = c_coll; sh.pm_pen = pm;
         }
-    }
-    grp_sync<kPpc>();
-    // (b) objective and dL/dh
-    if (w == 0) {
+        __syncwarp();   // the group residuals before every lane reads sh.h[]
         float v_start = 0.f, v_tilt = 0.f;
         if (lane < B) {
             const float* hg = &sh.h[5 * lane];
@@ -993,24 +1054,22 @@ __device__ void traj_evaluate(const Scalars& sc, const LaneSpheres& ls, const fl
     }
     grp_sync<kPpc>();
     if (grad) {
-        // (c) warp 0: placement gradient w.r.t. the placed poses, then (d) the place configurations'
+        // (4) warp 0: placement gradient w.r.t. the placed poses, then the place configurations'
         // gradient rows; warp 1: grasp gradients
         if (w == 0 && !p2p) {
             place_stack_grad(sc, sh.ps, &sh.s[8 * B], &sh.s[7 * B], sh.g4);
             const float s_arm = sh.s_arm, s_blk = sh.s_blk, s_coll = sh.s[9 * B];
+            const int n_pu = (8 * B + 31) / 32;
             for (int i = lane; i < 4 * B; i += 32) {
                 const int kb = i >> 2, c = i & 3;
-                float wa = 0.f, wb = 0.f, gc = 0.f;
-                for (int ww = 0; ww < kTWarps; ++ww) {
-                    wa += sh.warp[ww].wr[0][kb][c];
-                    wb += sh.warp[ww].wr[1][kb][c];
-                    gc += sh.pg[ww][kb][c];
-                }
-                if (kb + 1 < B) gc += sh.pgc[kb][c];
+                const float wa = fx_value(sh.fx_wr[0][kb][c]), wb = fx_value(sh.fx_wr[1][kb][c]);
+                float gc = sh.pg[kb][c];
+                if (kb + 1 < B)
+                    for (int u = 0; u < n_pu; ++u) gc += sh.pgc[u][kb][c];
                 sh.g4[i] += s_coll * gc + s_arm * wa + s_blk * wb;
             }
             __syncwarp();
-            // (d) place configurations: tilt residuals and the placed-pose gradient through fk
+            // place configurations: tilt residuals and the placed-pose gradient through fk
             if (lane < B) {
                 start_terms(sc, lane, 1, sp[2 * lane + 1], nullptr, &sh.s[5 * B + 2 * lane], sh.extra[B + lane],
                             &sh.g4[4 * lane], sh.extra[B + lane]);
@@ -1021,7 +1080,7 @@ __device__ void traj_evaluate(const Scalars& sc, const LaneSpheres& ls, const fl
         grp_sync<kPpc>();
     }
 
-    // (4) path length, joint limits; assemble the gradient into G_blk: a configuration per
+    // (5) path length, joint limits; assemble the gradient into G_blk: a configuration per
     // thread (its own, previous and next rows as float4 pairs)
     float path = 0.f, jl = 0.f;
     for (int t = tid; t < C; t += kTThreads) {
