@@ -905,15 +905,16 @@ __device__ void traj_evaluate(const Scalars& sc, const LaneSpheres& ls, const fl
             if (tier == tr) sh.active[tr][32 * w + __popc(bal & ((1u << lane) - 1u))] = (unsigned char)chk;
             if (lane == 0) sh.n_group[tr][w] = (short)__popc(bal);
         }
-        // skipped chunks: their block-group rows count as zero in the assembly (step 4)
+        // skipped chunks: their block-group rows count as zero in the assembly (step 5)
         const unsigned skipped = __ballot_sync(0xffffffffu, chk < n_chunks && !active);
         if (lane == 0) sh.skip[w] = skipped;
     }
     grp_sync<kPpc>();
-    // The queue, in order: the residual jobs (they need only the placed poses and the special
-    // frames), the chunks of the candidate tiers (tier by tier, group by group), the slices of
-    // the placed tower, the chunks to cull again.  Lane l holds the list of (tier l / 8,
-    // group l % 8): its count and first position in the candidate part of the queue.
+    // The queue, in order: the chunks of the candidate tiers (tier by tier, group by group), the
+    // chunks to cull again, the residual jobs (they need only the placed poses and the special
+    // frames), the slices of the placed tower: the smaller items come last, so that the warps
+    // finish together.  Lane l holds the list of (tier l / 8, group l % 8): its count and first
+    // position in the candidate part of the queue; lane l < 8 also that of (kChunk, group l).
     const int n_cnt = sh.n_group[lane >> 3][lane & (kTWarps - 1)];
     int c_end = n_cnt;
 #pragma unroll
@@ -931,13 +932,17 @@ __device__ void traj_evaluate(const Scalars& sc, const LaneSpheres& ls, const fl
     }
     const int r_first = r_end - n_rc, n_light = __shfl_sync(0xffffffffu, r_end, kTWarps - 1);
     const int n_pu = p2p ? 0 : (8 * B + 31) / 32;
-    const int total = kResidualJobs + n_heavy + n_pu + n_light;
+    const int n_chunk_items = n_heavy + n_light, total = n_chunk_items + kResidualJobs + n_pu;
     for (;;) {
         int idx = 0;
         if (lane == 0) idx = atomicAdd(&sh.next, 1);
         idx = __shfl_sync(0xffffffffu, idx, 0);
         if (idx >= total) break;
-        if (idx == 0) {
+        if (idx >= n_chunk_items + kResidualJobs) {
+            placed_slice(sc, cub, osph, aabb, sh, grad, idx - n_chunk_items - kResidualJobs);
+            continue;
+        }
+        if (idx == n_chunk_items) {
             // placement residuals (tower terms) with their unit-coefficient support factors
             float my_D = 0.f, my_e = 0.f;
             if (!p2p) place_stack_warp(sc, sh.pose, kPlaceUnit, nullptr, nullptr, nullptr, sh.ps, my_D, my_e);
@@ -952,7 +957,7 @@ __device__ void traj_evaluate(const Scalars& sc, const LaneSpheres& ls, const fl
             if (lane == 0) { sh.c_stable = c_stable; sh.c_height = c_height; sh.pm_D = max_D; sh.pm_dz = max_dz; }
             continue;
         }
-        if (idx == 1) {
+        if (idx == n_chunk_items + 1) {
             // start residuals: grasp configurations on lanes 0..15, place configurations on 16..31
             const int which = lane >> 4, b = lane & 15;
             if (b < B) {
@@ -966,16 +971,12 @@ __device__ void traj_evaluate(const Scalars& sc, const LaneSpheres& ls, const fl
             }
             continue;
         }
-        idx -= kResidualJobs;
         int chk;
         if (idx < n_heavy) {
             const int src = __ffs(__ballot_sync(0xffffffffu, c_first <= idx && idx < c_end)) - 1;
             chk = sh.active[src >> 3][32 * (src & (kTWarps - 1)) + idx - __shfl_sync(0xffffffffu, c_first, src)];
-        } else if (idx - n_heavy < n_pu) {
-            placed_slice(sc, cub, osph, aabb, sh, grad, idx - n_heavy);
-            continue;
         } else {
-            idx -= n_heavy + n_pu;
+            idx -= n_heavy;
             const int src = __ffs(__ballot_sync(0xffffffffu, r_first <= idx && idx < r_end)) - 1;
             chk = sh.active[kChunk][32 * src + idx - __shfl_sync(0xffffffffu, r_first, src)];
         }
