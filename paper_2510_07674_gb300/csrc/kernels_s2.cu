@@ -100,6 +100,7 @@ struct TShared {
     short n_group[kChunk + 1][kTWarps];
     unsigned skip[kTWarps];       // bit i of word g: chunk 32g + i kept its cached cull this evaluation
     float blk_cum[kMaxB];         // [k]: sum over the evaluations of the largest motion among the placed blocks 0..k
+    float bown[kMaxB];            // [k]: sum over the evaluations of placed block k's own motion
     int pose_prev_ok;
     float c_arm, c_blk, maxpen, c_coll, c_stable, c_height, c_start;
     float max_start, max_tilt, pm_pen, pm_D, pm_dz, path, jl;
@@ -121,15 +122,16 @@ __host__ __device__ inline size_t t_sp_offset(int n_cub, int n_osph, int C) {
 }
 __host__ __device__ inline int t_n_chunks(int C) { return (C - 1 + kChunk - 1) / kChunk; }
 // cached cull state: per configuration the motion bound since its chunk's last cull; per
-// chunk the motion of the blocks placed before its own at that cull, its (static, moving)
-// clearances as an fp16 pair and how many of its configurations had a candidate (0: none,
-// the chunk's cull is cacheable)
+// chunk, at that cull, the motion bound of the placed blocks below its top block and the top
+// block's own motion, its (static, moving) clearances as an fp16 pair, how many of its
+// configurations had a candidate (0: none, the chunk's cull is cacheable) and its fp16
+// clearance to the top block
 __host__ __device__ inline size_t t_cache_offset(int n_cub, int n_osph, int C, int B) {
     return (t_sp_offset(n_cub, n_osph, C) + (size_t)2 * B * sizeof(SpecialFrames) + 15) & ~(size_t)15;
 }
 size_t traj_smem_bytes(const Scalars& sc) {
     return t_cache_offset(sc.n_cub, sc.n_osph, sc.C, sc.B) + (size_t)sc.C * sizeof(float) +
-           (size_t)t_n_chunks(sc.C) * (2 * sizeof(float) + sizeof(int));
+           (size_t)t_n_chunks(sc.C) * (3 * sizeof(float) + sizeof(int) + sizeof(__half));
 }
 
 // Sphere item held in slot k by a lane: strided tiling, item lane + 32 k (the spheres of a link
@@ -286,9 +288,10 @@ __device__ __forceinline__ void sphere_centres(const Scalars& sc, const LaneSphe
 // penetration only where the separation test fails.  With `grad`, writes the unscaled group
 // gradients G_arm[t], G_blk[t] and accumulates placed-pose derivatives in the warp scratch.
 // Returns whether the chunk's collision terms are zero (no candidate, or candidates that no
-// sphere penetrates); then `clearance` / `clearance_moving` bound from below how far any of
-// its spheres is from a static box / a placed block it could touch: the gaps between link
-// boxes and the boxes apart from them, and the sphere-level gaps of the tests that ran.
+// sphere penetrates); then `clearance` / `clearance_top` / `clearance_moving` bound from below
+// how far any of its spheres is from a static box / the top placed block it could touch (the
+// block below the chunk's last block) / the other placed blocks: the gaps between link boxes
+// and the boxes apart from them, and the sphere-level gaps of the tests that ran.
 template <int kTile>
 __device__ __forceinline__ bool chunk_collisions(const Scalars& sc, const LaneSpheres& ls,
                                                  const float4* __restrict__ cub, const float4* __restrict__ osph,
@@ -296,7 +299,7 @@ __device__ __forceinline__ bool chunk_collisions(const Scalars& sc, const LaneSp
                                                  float* G_blk, int t0, int nc, bool grad, const float* lane_box,
                                                  float& acc_arm, float& acc_blk, float& acc_max,
                                                  unsigned long long& n_tests, unsigned long long& n_cand,
-                                                 float& clearance, float& clearance_moving) {
+                                                 float& clearance, float& clearance_moving, float& clearance_top) {
     const int lane = threadIdx.x & 31;
     const int S = sc.S, B = sc.B;
     float cx[kSlots], cy[kSlots], cz[kSlots], rr[kSlots];
@@ -378,6 +381,9 @@ __device__ __forceinline__ bool chunk_collisions(const Scalars& sc, const LaneSp
     if (lane == 0)
 #pragma unroll
         for (int c = 0; c < kChunk; ++c) tw.envany[c] = any[c];
+    // the highest placed block a configuration of the chunk can touch: it moves by its own motion,
+    // the blocks below it by at most the largest motion among them
+    const int top = ((min(t0 + nc - 1, sc.C - 1) - 1) / S >> 1) - 1;
     {
         // a configuration of block b's segments can touch the placed blocks k < b and the
         // blocks k > b still at their initial poses (the chunk: any of its configurations)
@@ -395,22 +401,32 @@ __device__ __forceinline__ bool chunk_collisions(const Scalars& sc, const LaneSp
         clearance = warp_min(clear);
         clear = 3.4e38f;
         const float sp = lane < B ? sep_chunk(sh.baabb[lane][0], sh.baabb[lane][1]) : 3.4e38f;
-        if (lane < b_last && sp > 0.f) clear = fminf(clear, sp);
+        if (lane < b_last && lane != top && sp > 0.f) clear = fminf(clear, sp);
         const unsigned bm_placed = __ballot_sync(0xffffffffu, sp <= 0.f);
-        refine(bm_placed, 0, &sh.baabb[0][0], 2, per, [&](int k) { return k < b_lane; });
+        refine(bm_placed, 0, &sh.baabb[0][0], 2, per, [&](int k) { return k < b_lane && k != top; });
         if (lane == 0)
 #pragma unroll
             for (int c = 0; c < kChunk; ++c) tw.bmask[0][c] = per[c];
         clearance_moving = warp_min(clear);
+        // the top block: the gap from each link box of the configurations it concerns
+        float ct = 3.4e38f;
+        if (top >= 0 && top < b_lane) {
+            const float4 blo = sh.baabb[top][0], bhi = sh.baabb[top][1];
+            const float g = fmaxf(fmaxf(fmaxf(blo.x - lb[3], lb[0] - bhi.x), fmaxf(blo.y - lb[4], lb[1] - bhi.y)),
+                                  fmaxf(blo.z - lb[5], lb[2] - bhi.z));
+            if (g > 0.f) ct = g;   // an overlapping box is tested against the spheres, which give the gap
+        }
+        clearance_top = warp_min(ct);
     }
     __syncwarp();
 
-    // pass 2: every configuration against the candidates.  gap_s / gap_m: the lane's smallest
-    // sphere-level gap (lower bound) to a tested static box / placed block; the fixed base's
+    // pass 2: every configuration against the candidates.  gap_s / gap_m / gap_t: the lane's smallest
+    // sphere-level gap (lower bound) to a tested static box / placed block below the top one / the
+    // top placed block; the fixed base's
     // spheres do not move relative to static boxes and are left out of gap_s.
     const int seg0 = (t0 - 1) / S, r0 = (t0 - 1) - seg0 * S;
     bool none = true, chunk_hit = false;
-    float gap_s = 3.4e38f, gap_m = 3.4e38f;
+    float gap_s = 3.4e38f, gap_m = 3.4e38f, gap_t = 3.4e38f;
     for (int ci = 0; ci < nc; ++ci) {
         const int t = t0 + ci;
         int seg = seg0, r = r0 + ci;
@@ -516,7 +532,10 @@ __device__ __forceinline__ bool chunk_collisions(const Scalars& sc, const LaneSp
                 for (int sl = 0; sl < kSlots; ++sl) {
                     if (act[sl]) {
                         const float g = fmaxf(qm[sl] - rr[sl], 0.f);
-                        if (placed) gap_m = fminf(gap_m, g);
+                        if (placed) {
+                            if (kb == top) gap_t = fminf(gap_t, g);
+                            else gap_m = fminf(gap_m, g);
+                        }
                         else if (!fixed[sl]) gap_s = fminf(gap_s, g);
                     }
                     if (!act[sl] || !(qm[sl] < rr[sl])) continue;
@@ -621,6 +640,7 @@ __device__ __forceinline__ bool chunk_collisions(const Scalars& sc, const LaneSp
     if (__any_sync(0xffffffffu, chunk_hit)) return false;
     clearance = fminf(clearance, warp_min(gap_s));
     clearance_moving = fminf(clearance_moving, warp_min(gap_m));
+    clearance_top = fminf(clearance_top, warp_min(gap_t));
     return true;
 }
 
@@ -812,7 +832,8 @@ __device__ __forceinline__ void cuboid_aabb(const float4* c, float4* box) {
 template <bool kP2P, int kTile, int kPpc>
 __device__ void traj_evaluate(const Scalars& sc, const LaneSpheres& ls, const float4* cub, const float4* osph,
                               const float4* aabb, TShared& sh, SpecialFrames* sp, float* q, float* G_arm,
-                              float* G_blk, float* disp, float* cblk, __half2* cgap, int* ccand, bool grad,
+                              float* G_blk, float* disp, float* cblk, __half2* cgap, int* ccand, float* ctopm,
+                              __half* ctop, bool grad,
                               unsigned long long& n_tests, unsigned long long& n_cull,
                               unsigned long long& n_cand) {
     const int tid = grp_tid<kPpc>(), lane = tid & 31, w = tid >> 5;
@@ -854,6 +875,7 @@ __device__ void traj_evaluate(const Scalars& sc, const LaneSpheres& ls, const fl
             sh.baabb[lane][0] = make_float4(3.4e38f, 3.4e38f, 3.4e38f, 0.f);   // an empty box: never a candidate
             sh.baabb[lane][1] = make_float4(-3.4e38f, -3.4e38f, -3.4e38f, 0.f);
         }
+        if (lane < B) sh.bown[lane] += moved;   // the block's own motion, before the scan
         // inclusive max-scan over the blocks: blk_cum[k] accumulates, evaluation by evaluation, the
         // largest motion among blocks 0..k.  Summed over the evaluations since a chunk's cull it
         // bounds the motion of each of those blocks since then, which is all that a gap to any
@@ -887,6 +909,8 @@ __device__ void traj_evaluate(const Scalars& sc, const LaneSpheres& ls, const fl
     // touch): its difference between two evaluations bounds any one block's motion between them
     auto blk_before = [&](int b) { return b > 0 ? sh.blk_cum[b - 1] : 0.f; };
     auto chunk_block = [&](int t0c) { return (min(t0c + kChunk - 1, C - 1) - 1) / S >> 1; };
+    // own motion of block k (the top block of a chunk of block k + 1's segments), 0 for none
+    auto own_motion = [&](int k) { return k >= 0 ? sh.bown[k] : 0.f; };
     {
         const int chk = 32 * w + lane;
         const int t0 = 1 + kChunk * chk, nc = min(kChunk, C - t0);
@@ -895,7 +919,9 @@ __device__ void traj_evaluate(const Scalars& sc, const LaneSpheres& ls, const fl
             float d = 0.f;
             for (int i = 0; i < nc; ++i) d = fmaxf(d, disp[t0 + i]);
             const __half2 cg = cgap[chk];
-            active = !(d < __low2float(cg) && d + (blk_before(chunk_block(t0)) - cblk[chk]) < __high2float(cg));
+            const int top = chunk_block(t0) - 1;
+            active = !(d < __low2float(cg) && d + (blk_before(top) - cblk[chk]) < __high2float(cg) &&
+                       d + (own_motion(top) - ctopm[chk]) < __half2float(ctop[chk]));
         }
         // tier: kChunk - (configurations with candidates), kChunk for a chunk to cull again
         const int tier = active ? (ccand[chk] == 0 ? kChunk : kChunk - ccand[chk]) : -1;
@@ -990,11 +1016,11 @@ __device__ void traj_evaluate(const Scalars& sc, const LaneSpheres& ls, const fl
             float box[6];
             chunk_fk(sc, sh, q, t0 + c, true, held_c, sh.warp[w].F[c], sh.warp[w].H[c], box);
             __syncwarp();
-            float clearance, clearance_moving, c_arm = 0.f, c_blk = 0.f;
+            float clearance, clearance_moving, clearance_top, c_arm = 0.f, c_blk = 0.f;
             const unsigned long long cand0 = n_cand;
             const bool zero = chunk_collisions<kTile>(sc, ls, cub, osph, aabb, sh, sh.warp[w], G_arm, G_blk, t0, nc,
                                                       grad, box, c_arm, c_blk, acc_max, n_tests, n_cand, clearance,
-                                                      clearance_moving);
+                                                      clearance_moving, clearance_top);
             n_cull += (unsigned)nc;
             if (!zero) {
                 c_arm = warp_sum(c_arm);
@@ -1003,10 +1029,13 @@ __device__ void traj_evaluate(const Scalars& sc, const LaneSpheres& ls, const fl
             if (lane == 0) {
                 if (!zero) { fx_add(&sh.fx_arm, c_arm); fx_add(&sh.fx_blk, c_blk); }
                 ccand[chk] = zero ? 0 : (int)(n_cand - cand0);   // 0: a chunk whose terms are zero (cacheable)
-                cblk[chk] = blk_before(chunk_block(t0));
-                // fp16, rounded down: still a lower bound on either clearance
+                const int top = chunk_block(t0) - 1;
+                cblk[chk] = blk_before(top);
+                ctopm[chk] = own_motion(top);
+                // fp16, rounded down: still lower bounds on the clearances
                 cgap[chk] = __halves2half2(__float2half_rd(clearance - kClearSlack),
                                            __float2half_rd(clearance_moving - kClearSlack));
+                ctop[chk] = __float2half_rd(clearance_top - kClearSlack);
             }
             if (lane < nc) disp[t0 + lane] = 0.f;
             __syncwarp();
@@ -1177,11 +1206,15 @@ __device__ __forceinline__ void traj_particle(const Scalars& sc, int p, int mode
     float* cblk = disp + sc.C;
     __half2* cgap = reinterpret_cast<__half2*>(cblk + n_chunks);   // (static, moving) clearances
     int* ccand = reinterpret_cast<int*>(cgap + n_chunks);
+    float* ctopm = reinterpret_cast<float*>(ccand + n_chunks);   // the top block's own motion at the cull
+    __half* ctop = reinterpret_cast<__half*>(ctopm + n_chunks);  // clearance to the top block
     const int tid = grp_tid<kPpc>();
     const int C = sc.C, NR = sc.NR, B = sc.B;
     for (int i = tid; i < C; i += kTThreads) disp[i] = 0.f;
-    for (int i = tid; i < n_chunks; i += kTThreads) { cblk[i] = 0.f; cgap[i] = __float2half2_rn(0.f); ccand[i] = kChunk; }
-    if (tid < kMaxB) sh.blk_cum[tid] = 0.f;
+    for (int i = tid; i < n_chunks; i += kTThreads) {
+        cblk[i] = 0.f; cgap[i] = __float2half2_rn(0.f); ccand[i] = kChunk; ctopm[i] = 0.f; ctop[i] = __float2half_rn(0.f);
+    }
+    if (tid < kMaxB) { sh.blk_cum[tid] = 0.f; sh.bown[tid] = 0.f; }
     if (tid == 0) sh.pose_prev_ok = 0;
 
     // particle state -> shared memory (coalesced float4)
@@ -1219,7 +1252,7 @@ __device__ __forceinline__ void traj_particle(const Scalars& sc, int p, int mode
     const int K = mode == kTrajDescend ? io.k_steps : 0;
     for (int k = 1;; ++k) {
         const bool last = k > K;
-        traj_evaluate<kP2P, kTile, kPpc>(sc, ls, cub, osph, aabb, sh, sp, q, G_arm, G_blk, disp, cblk, cgap, ccand,
+        traj_evaluate<kP2P, kTile, kPpc>(sc, ls, cub, osph, aabb, sh, sp, q, G_arm, G_blk, disp, cblk, cgap, ccand, ctopm, ctop,
                                          last ? want_grad : true, n_tests, n_cull, n_cand);
         if (last) break;
         const float eta = sc.eta_traj * (1.f - (float)k / (float)K);
