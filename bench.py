@@ -633,7 +633,7 @@ def run_packing(args, rank):
     first solution per seed, capped at 30 000 gradient steps as in the paper's runs."""
     from paper_2510_07674_gb300 import scenes
     out = {}
-    for name, n in (("tetris5", args.pack_seeds), ("tetris8", max(1, args.pack_seeds // 4))):
+    for name, n in (("tetris5", args.pack_seeds), ("tetris8", args.pack8_seeds)):
         times, ok, att = [], 0, []
         for i in range(n):
             solved, ms, a = stage1_first_solution(scenes.make_packing(name, seed=rank * 1000 + i, max_steps=30000))
@@ -884,6 +884,7 @@ def main():
                     help="heterogeneous problems for the batched / served measurements (0 = skip)")
     ap.add_argument("--serve-slots", type=int, default=8)
     ap.add_argument("--pack-seeds", type=int, default=12, help="seeds of the 5-block packing leg (0 = skip)")
+    ap.add_argument("--pack8-seeds", type=int, default=10, help="seeds of the 8-block packing leg (with --pack-seeds > 0)")
     ap.add_argument("--p2p-seeds", type=int, default=10, help="seeds of the point-to-point leg (0 = skip)")
     ap.add_argument("--ik-seeds", type=int, default=6,
                     help="10-block solves with the analytic lift IK, after timing both lift forms (0 = skip)")
