@@ -32,19 +32,21 @@ __device__ __forceinline__ void grp_sync() {
 // Cached cull.  When a chunk's cull finds no candidate for any of its configurations, it
 // also returns the chunk's clearances: the smallest separation (largest per-axis gap) between
 // any of its link boxes and any static box that could touch it (the environment, blocks at
-// their initial poses), and the same for the placed blocks, which move.  Later iterations
-// skip the chunk (kinematics, cull and tests: its terms are zero) while the bound on how far
-// its spheres moved since stays below the static clearance and, plus a bound on how far any
-// one of the blocks placed before the chunk's own block moved, below the moving one, so the
-// skipped work is exactly the work whose result is zero.  A chunk whose configurations have
+// their initial poses), and the same for the placed blocks, which move: the top one (the
+// highest block placed before the chunk's last block) on its own, the ones below it together.
+// Later iterations skip the chunk (kinematics, cull and tests: its terms are zero) while the
+// bound on how far its spheres moved since stays below the static clearance, plus the top
+// block's own motion since below the clearance to it, and plus a bound on how far any one of
+// the blocks below the top one moved below the clearance to those, so the skipped work is
+// exactly the work whose result is zero.  A chunk whose configurations have
 // candidates but whose spheres all miss them (no penetration anywhere: its terms are zero as
 // well) is kept the same way; for the obstacles its spheres were tested against, its
 // clearance is the smallest sphere-level gap those tests found.
 constexpr float kClearSlack = 1e-5f;   // FP32 rounding of the boxes, metres
 
-// Work queue of an evaluation: its items (the residual jobs, the chunks, the slices of the
-// placed tower's collisions) go to the warps in list order from a shared counter, heaviest
-// first, so that the warps finish together.  What the items add up goes into fixed-point
+// Work queue of an evaluation: its items (the chunks, the residual jobs, the slices of the
+// placed tower's collisions) go to the warps in list order from a shared counter, the larger
+// items first, so that the warps finish together.  What the items add up goes into fixed-point
 // accumulators (integer sums are exact, hence independent of which warp took which item and
 // when): a value v becomes round(v 2^40), |v| < 8e6.
 constexpr float kFix = 1099511627776.f;   // 2^40
