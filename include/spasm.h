@@ -422,12 +422,14 @@ spasm_status spasm_batch_default_config(spasm_batch_config* cfg);
 /* cfg NULL: the default schedule. */
 spasm_status spasm_optimize_batch(spasm_problem_t* problems, int n, void* cuda_stream, const spasm_batch_config* cfg);
 /* Autotuner of the batched launch: places the problems not yet placed (stage 1, as above),
- * lifts them, times one evaluation of every particle under each candidate (sphere tiling in
- * {strided, blocked} x particles per CTA in {1, 2} (where its shared memory fits) x per_fetch
- * in {1, 2, 4} x ctas_per_sm in {all, 1} x both orders; CUDA events, the better of two runs)
- * and returns the fastest in *best (and its time in *best_ms when not NULL).  The schedule and
- * the particles per CTA change no result; the sphere tiling changes results at float32
- * rounding. */
+ * lifts them, times each trajectory shape (sphere tiling in {strided, blocked} x particles per
+ * CTA in {1, 2}, where its shared memory fits) over one full descent of every particle, then,
+ * under the fastest shape, one evaluation of every particle per schedule (per_fetch in
+ * {1, 2, 4} x ctas_per_sm in {all, 1} x both orders; CUDA events, the better of two runs), and
+ * returns the fastest in *best (and that schedule's evaluation time in *best_ms when not
+ * NULL).  The tuning writes only buffers a solve sets again (the particles are lifted again
+ * and the multipliers start fresh).  The schedule and the particles per CTA change no result;
+ * the sphere tiling changes results at float32 rounding. */
 spasm_status spasm_batch_autotune(spasm_problem_t* problems, int n, void* cuda_stream, spasm_batch_config* best,
                                   double* best_ms);
 

@@ -315,11 +315,13 @@ extern "C" spasm_status spasm_batch_autotune(spasm_problem_t* prs, int n, void* 
     spasm_batch_default_config(best);
     if (best_ms) *best_ms = 0.0;
     if (live.empty()) return SPASM_OK;
-    // the candidates run one evaluation of every lifted particle (no writes besides q's reads)
-    for (int i : live) {
-        spasm_problem* pr = prs[i];
-        SPASM_CUDA(launch_lift(pr->sc, pr->sc.Q, pr->d_place, pr->n_place, 0u, pr->d_q, s));
-    }
+    auto lift_all = [&]() -> spasm_status {
+        for (int i : live) {
+            spasm_problem* pr = prs[i];
+            SPASM_CUDA(launch_lift(pr->sc, pr->sc.Q, pr->d_place, pr->n_place, 0u, pr->d_q, s));
+        }
+        return SPASM_OK;
+    };
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     SPASM_CUDA(cudaEventCreate(&e0));
     SPASM_CUDA(cudaEventCreate(&e1));
@@ -327,34 +329,63 @@ extern "C" spasm_status spasm_batch_autotune(spasm_problem_t* prs, int n, void* 
         cudaEvent_t a, b;
         ~Ev() { cudaEventDestroy(a); cudaEventDestroy(b); }
     } ev{e0, e1};
+    // (1) the trajectory shape (sphere tiling x particles per CTA), each over one full descent of
+    // every lifted particle: a descent mostly runs from the cached cull, which one evaluation
+    // (every chunk culled) does not show
+    double shape_t = 1e300;
+    for (int tiling = 0; tiling <= 1; ++tiling)
+        for (int ppc = 1; ppc <= 2; ++ppc) {
+            JobList L = make_jobs(prs, job_order(prs, live, 0), 1, kTrajModeDescend, 0, true);
+            for (size_t k = 0; k < L.jobs.size(); ++k) {
+                L.jobs[k].io.k_steps = prs[job_order(prs, live, 0)[k]]->sc.K_traj;
+                L.jobs[k].io.tests = nullptr;   // the problems' counters are the solves'
+            }
+            if (traj_batch_ctas_per_sm(L.smem, tiling, ppc) < 1) continue;   // two particles do not fit
+            spasm_batch_config c{1, 0, 0, tiling, ppc};
+            int grid = 0;
+            SPASM_TRY(batch_grid(c, L.smem, &grid));
+            DeviceJobs dj;
+            SPASM_TRY(upload_jobs(L, s, dj));
+            SPASM_TRY(lift_all());
+            SPASM_CUDA(cudaMemsetAsync(dj.next, 0, sizeof(int), s));
+            SPASM_CUDA(cudaEventRecord(e0, s));
+            SPASM_CUDA(launch_traj_batch(dj.jobs, (int)L.jobs.size(), L.n_items, 1, kTrajModeDescend, dj.next, L.smem,
+                                         grid, s, tiling, ppc));
+            SPASM_CUDA(cudaEventRecord(e1, s));
+            SPASM_CUDA(cudaEventSynchronize(e1));
+            const double t = ev_ms(e0, e1);
+            if (t < shape_t) { shape_t = t; best->sphere_tiling = tiling; best->particles_per_cta = ppc; }
+        }
+    // (2) the schedule of the persistent launch under that shape: one evaluation of every lifted
+    // particle per candidate (no writes besides q's reads)
+    SPASM_TRY(lift_all());
+    const int tiling = best->sphere_tiling, ppc = best->particles_per_cta;
     double best_t = 1e300;
     const int fetches[] = {1, 2, 4};
-    for (int tiling = 0; tiling <= 1; ++tiling)
-        for (int ppc = 1; ppc <= 2; ++ppc)
-            for (int order = 0; order <= 1; ++order)
-                for (int pf : fetches)
-                    for (int per_sm : {0, 1}) {
-                        spasm_batch_config c{pf, per_sm, order, tiling, ppc};
-                        JobList L = make_jobs(prs, job_order(prs, live, order), pf, kTrajModeEval, 0, true);
-                        int grid = 0;
-                        if (traj_batch_ctas_per_sm(L.smem, tiling, ppc) < 1) continue;   // two particles do not fit
-                        SPASM_TRY(batch_grid(c, L.smem, &grid));
-                        DeviceJobs dj;
-                        SPASM_TRY(upload_jobs(L, s, dj));
-                        double t = 1e300;
-                        for (int rep = 0; rep < 2; ++rep) {   // the first repetition warms caches
-                            SPASM_CUDA(cudaMemsetAsync(dj.next, 0, sizeof(int), s));
-                            SPASM_CUDA(cudaEventRecord(e0, s));
-                            SPASM_CUDA(launch_traj_batch(dj.jobs, (int)L.jobs.size(), L.n_items, pf, kTrajModeEval,
-                                                         dj.next, L.smem, grid, s, tiling, ppc));
-                            SPASM_CUDA(cudaEventRecord(e1, s));
-                            SPASM_CUDA(cudaEventSynchronize(e1));
-                            if (rep > 0) t = ev_ms(e0, e1);
-                        }
-                        if (t < best_t) { best_t = t; *best = c; }
-                    }
+    for (int order = 0; order <= 1; ++order)
+        for (int pf : fetches)
+            for (int per_sm : {0, 1}) {
+                spasm_batch_config c{pf, per_sm, order, tiling, ppc};
+                JobList L = make_jobs(prs, job_order(prs, live, order), pf, kTrajModeEval, 0, true);
+                int grid = 0;
+                SPASM_TRY(batch_grid(c, L.smem, &grid));
+                DeviceJobs dj;
+                SPASM_TRY(upload_jobs(L, s, dj));
+                double t = 1e300;
+                for (int rep = 0; rep < 2; ++rep) {   // the first repetition warms caches
+                    SPASM_CUDA(cudaMemsetAsync(dj.next, 0, sizeof(int), s));
+                    SPASM_CUDA(cudaEventRecord(e0, s));
+                    SPASM_CUDA(launch_traj_batch(dj.jobs, (int)L.jobs.size(), L.n_items, pf, kTrajModeEval, dj.next,
+                                                 L.smem, grid, s, tiling, ppc));
+                    SPASM_CUDA(cudaEventRecord(e1, s));
+                    SPASM_CUDA(cudaEventSynchronize(e1));
+                    if (rep > 0) t = ev_ms(e0, e1);
+                }
+                if (t < best_t) { best_t = t; *best = c; }
+            }
     for (int i : live) SPASM_TRY(check_device_error(prs[i]));
-    // the candidates' evaluations wrote nothing the next solve reads; q is lifted again there
+    // the candidates wrote nothing the next solve reads: it lifts q again and starts its descents
+    // from fresh multipliers
     if (best_ms) *best_ms = best_t;
     return SPASM_OK;
 }
